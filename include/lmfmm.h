@@ -1,0 +1,179 @@
+/*
+ * lmfmm.h -- C ABI of a GB300 (sm_103a) library that applies the 2-D
+ * three-layer Helmholtz Green's function to complex density vectors with the
+ * layered-media FMM of Cho & Huang, "Adapting free-space fast multipole method
+ * for layered media Green's function: algorithm and analysis"
+ * (arXiv:1902.08250).
+ *
+ * Medium (Sec. 3, Example 4): interfaces y = 0 and y = -d; wave numbers k1
+ * (y > 0), k2 (-d < y < 0), k3 (y < -d).  Sources and targets are the same N
+ * points, all in the middle layer.  The operator applied is
+ *
+ *   u_i = sum_{j != i} q_j (i/4) H0^(1)(k2 |x_i - x_j|) + sum_j q_j G_r(x_i, x_j)
+ *
+ * (Eq. (direct_sum) with the free-space part of Example 1 and the reflected
+ * part G_r written, like Eq. (Green), as four image terms tt, bb, tb, bt of the
+ * form Int e^{i lambda (x - x0)} e^{-s2 h_m} sigma_m(lambda) / (4 pi s2) d lambda,
+ * s2 = sqrt(lambda^2 - k2^2) with Re s2 >= 0).  The free-space self term j = i
+ * is excluded; the reflected self terms are included.
+ *
+ * Conventions shared by every entry point:
+ *  - Device pointers are CUDA global-memory pointers on the current device.
+ *    Complex arrays are interleaved (re, im) IEEE double, i.e. complex128,
+ *    laid out [nvec][n] (vector-major, contiguous, no padding).
+ *  - Host pointers are ordinary CPU memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work of a call is enqueued on it; calls return without
+ *    synchronising unless stated.
+ *  - The caller owns every buffer it passes; the library never frees or
+ *    retains caller buffers after a call returns.  Handles own their device
+ *    memory (tables, tree arrays, expansion scratch), which is allocated by
+ *    lm_build_tree and freed by lm_destroy_tree; lm_apply allocates nothing.
+ *  - Every call returns an lm_status; on failure lm_last_error() returns a
+ *    thread-local message.  Nothing aborts, traps or exits.
+ */
+#ifndef LMFMM_H
+#define LMFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LM_OK = 0,
+    LM_EINVAL = 1,   /* invalid argument: bad medium, point, size, alias */
+    LM_ENOMEM = 2,   /* device or host allocation failed */
+    LM_ECUDA = 3,    /* a CUDA runtime call failed */
+    LM_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    LM_ENOTSUP = 5   /* configuration outside what this build supports */
+} lm_status;
+
+typedef enum {
+    LM_FP64 = 0, /* every step in IEEE double */
+    LM_MIXED = 1 /* near field and expansions in FP32, tables built in FP64 */
+} lm_precision;
+
+typedef struct {
+    int p;           /* expansion order: coefficients -p..p (Sec. 4.1); 0 -> 20 */
+    int depth;       /* quadtree depth below the d x d roots; -1 -> automatic */
+    int leaf_target; /* automatic depth: least L >= 0 with n <= leaf_target * R * 4^L; 0 -> 48 */
+    int precision;   /* lm_precision */
+    int max_nvec;    /* largest nvec one apply processes at once (larger nvec is
+                        processed in chunks); 0 -> 16 */
+    int seg_order;   /* near-field contour: Gauss-Legendre points per segment panel; 0 -> 16 */
+    int tail_order;  /* near-field tail: Gauss-Legendre points per ray; 0 -> 64 (FP64), 24 (mixed) */
+    int tail_rays;   /* near-field tail: rays between the north and east directions; 0 -> 9 */
+} lm_options;
+
+typedef struct lm_medium_s *lm_medium; /* opaque, library-owned */
+typedef struct lm_tree_s *lm_tree;     /* opaque, library-owned */
+
+typedef struct {
+    int64_t n;        /* number of points */
+    int R;            /* number of d x d roots along x */
+    int depth;        /* L: leaves are at level L, width d 2^-L */
+    int p;            /* expansion order */
+    double x_origin;  /* left edge of the first root: floor(min x / d) d */
+    int64_t nleaf;    /* R 4^L */
+    int precision;    /* lm_precision */
+    int max_nvec;
+    int64_t device_bytes; /* device memory held by the tree handle */
+} lm_tree_info;
+
+/* Fill *opt with the defaults listed above. LM_EINVAL if opt is NULL. */
+lm_status lm_options_default(lm_options *opt);
+
+/*
+ * create_medium -- the three-layer medium of Sec. 3, Example 4.
+ *   k1, k2, k3: real wave numbers (> 0, finite); d: middle-layer thickness (> 0).
+ *   opt: NULL for defaults; copied, not retained.
+ *   out: receives a new handle (host object, no device work).
+ * Errors: LM_EINVAL for a non-positive or non-finite parameter or bad option.
+ */
+lm_status lm_create_medium(double k1, double k2, double k3, double d, const lm_options *opt,
+                           lm_medium *out);
+
+/*
+ * build_tree -- Algorithm 1, step 1: the adaptive hierarchical tree and the
+ * precomputed tables.  Here the tree is a forest of R roots, each a d x d
+ * square, tiling [x_origin, x_origin + R d) x (-d, 0), refined uniformly to
+ * depth L; box edges lie on both interfaces.  Builds, on the device and on
+ * `stream`: point keys and the tree order (sorted by leaf, ties by input
+ * index), interaction lists (free space and the four image lattices), the
+ * M2M / L2L / M2L translation tables (Lemmas M2M, M2L, L2L) and the
+ * near-field Sommerfeld quadrature tables (Sec. 4.2, Sec. 5 first contour).
+ *   x, y: device arrays of n doubles (point coordinates, input order); read
+ *         during the call only.
+ *   n >= 1.
+ * Synchronises `stream` (host needs the x extent and a validity flag).
+ * Errors: LM_EINVAL if a point is non-finite or not strictly inside
+ * -d < y < 0; LM_ENOMEM; LM_ENOTSUP if a leaf holds more than 8192 points;
+ * LM_ECUDA.
+ */
+lm_status lm_build_tree(lm_medium m, const double *x, const double *y, int64_t n, void *stream,
+                        lm_tree *out);
+
+/*
+ * apply -- u = G q by the FMM (Algorithm 1, steps 2-4).
+ *   q: device, complex128 [nvec][n] densities in input order.
+ *   u: device, complex128 [nvec][n] output (overwritten), input order; must
+ *      not overlap q.
+ *   nvec >= 1.
+ * Errors: LM_EINVAL (nvec < 1, NULL or overlapping buffers), LM_ECUDA.
+ */
+lm_status lm_apply(lm_tree t, const void *q, int nvec, void *u, void *stream);
+
+/*
+ * apply_adjoint -- w = G^H v.  The kernel is reciprocal, G(x, x0) = G(x0, x)
+ * (Sec. 3: every term depends on x - x0 through lambda^2-even integrands and
+ * on y, y0 symmetrically), so G^H v = conj(G conj(v)); the conjugations are
+ * fused into the permutation kernels.  Arguments and errors as lm_apply.
+ */
+lm_status lm_apply_adjoint(lm_tree t, const void *v, int nvec, void *w, void *stream);
+
+/* Geometry of a built tree (host struct). */
+lm_status lm_get_tree_info(lm_tree t, lm_tree_info *info);
+
+/*
+ * tree_export -- copy the tree order to host memory (synchronises `stream`).
+ *   perm: host int64[n], tree position -> input index (may be NULL).
+ *   leaf_start: host int64[nleaf + 1], first tree position of each leaf (may be NULL).
+ */
+lm_status lm_tree_export(lm_tree t, int64_t *perm, int64_t *leaf_start, void *stream);
+
+/*
+ * list_export -- copy one interaction list to host memory as rows of
+ * (target box, term, source box), box id = row * (R 2^l) + column, term
+ * 0 = free space, 1 = tt, 2 = bb, 3 = tb, 4 = bt; rows ordered by target,
+ * then term, then source (Algorithm 1: the interaction list of step 3 and
+ * the direct-interaction list of step 4).
+ *   which: 0 = V list of `level` (0..L), 1 = U list (leaf level; level ignored).
+ *   out: host int64[3 * cap]; *count receives the full length (rows written:
+ *   min(cap, *count)).  Synchronises `stream`.
+ */
+lm_status lm_list_export(lm_tree t, int which, int level, int64_t *out, int64_t cap,
+                         int64_t *count, void *stream);
+
+/*
+ * m2l_table_export -- copy one M2L translation matrix A_pq (Lemma M2L for
+ * term 1..4, the free-space translation for term 0), unscaled, p, q in
+ * -P..P, to host memory as complex128 [(2P+1)][(2P+1)] (row p, column q).
+ * The class is given by level, term, column offset dc = target col - source
+ * col and row offset dr = target row - image row (image rows as in
+ * lm_list_export's lists).  LM_EINVAL if that class is not in any list.
+ * Synchronises `stream`.
+ */
+lm_status lm_m2l_table_export(lm_tree t, int level, int term, int dc, int dr, double *out,
+                              void *stream);
+
+void lm_destroy_tree(lm_tree t);
+void lm_destroy_medium(lm_medium m);
+const char *lm_status_string(lm_status s);
+const char *lm_last_error(void); /* thread-local; never NULL */
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,208 @@
+"""Thin Python binding of liblmfmm (include/lmfmm.h): the layered-media FMM of
+Cho & Huang (arXiv:1902.08250) on a GB300 GPU.
+
+Argument marshalling only: every step of create/build/apply runs in the CUDA
+library.  PyTorch supplies device memory and the current stream.  If the
+library cannot be built or loaded, importing this package raises -- there is
+no CPU path.
+
+    import torch, paper_1902_08250_gb300 as lm
+    med = lm.create_medium(1.0, 1.5, 2.0, 1.0, p=20)
+    tree = lm.build_tree(med, x, y)          # x, y: float64 CUDA tensors
+    u = lm.apply(tree, q)                    # q: complex128 CUDA tensor [nvec, n] or [n]
+    w = lm.apply_adjoint(tree, v)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+__all__ = [
+    "LMError", "Medium", "Tree", "create_medium", "build_tree", "apply", "apply_adjoint", "library_path",
+    "FP64", "MIXED",
+]
+
+FP64, MIXED = 0, 1
+_STATUS = {0: "LM_OK", 1: "LM_EINVAL", 2: "LM_ENOMEM", 3: "LM_ECUDA", 4: "LM_ETIMEOUT", 5: "LM_ENOTSUP"}
+
+
+class LMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_target", ctypes.c_int),
+                ("precision", ctypes.c_int), ("max_nvec", ctypes.c_int), ("seg_order", ctypes.c_int),
+                ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int)]
+
+
+class _TreeInfo(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("R", ctypes.c_int), ("depth", ctypes.c_int), ("p", ctypes.c_int),
+                ("x_origin", ctypes.c_double), ("nleaf", ctypes.c_int64), ("precision", ctypes.c_int),
+                ("max_nvec", ctypes.c_int), ("device_bytes", ctypes.c_int64)]
+
+
+def _load():
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    V, P, I, I64, D = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "lm_options_default": (I, [P]),
+        "lm_create_medium": (I, [D, D, D, D, P, P]),
+        "lm_build_tree": (I, [V, P, P, I64, P, P]),
+        "lm_apply": (I, [V, P, I, P, P]),
+        "lm_apply_adjoint": (I, [V, P, I, P, P]),
+        "lm_get_tree_info": (I, [V, P]),
+        "lm_tree_export": (I, [V, P, P, P]),
+        "lm_list_export": (I, [V, I, I, P, I64, P, P]),
+        "lm_m2l_table_export": (I, [V, I, I, I, I, P, P]),
+        "lm_destroy_tree": (None, [V]),
+        "lm_destroy_medium": (None, [V]),
+        "lm_status_string": (ctypes.c_char_p, [I]),
+        "lm_last_error": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+_lib = _load()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status):
+    if status != 0:
+        raise LMError(status, _lib.lm_last_error().decode())
+
+
+def _stream(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Medium:
+    """Three-layer medium (Sec. 3, Example 4) plus FMM options."""
+
+    def __init__(self, handle, k1, k2, k3, d, opts):
+        self._h = ctypes.c_void_p(handle)
+        self.k1, self.k2, self.k3, self.d = k1, k2, k3, d
+        self.options = opts
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lm_destroy_medium(self._h)
+            self._h = None
+
+
+def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
+                  seg_order=16, tail_order=0, tail_rays=9) -> Medium:
+    if isinstance(precision, str):
+        precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays)
+    h = ctypes.c_void_p()
+    _check(_lib.lm_create_medium(k1, k2, k3, d, ctypes.byref(o), ctypes.byref(h)))
+    return Medium(h.value, k1, k2, k3, d, dict(p=p, depth=depth, leaf_target=leaf_target,
+                                              precision=precision, max_nvec=max_nvec))
+
+
+class Tree:
+    """A built tree: points, lists and translation tables on the device."""
+
+    def __init__(self, handle, medium):
+        self._h = ctypes.c_void_p(handle)
+        self.medium = medium
+        self.info = self._info()
+        self.n = self.info["n"]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lm_destroy_tree(self._h)
+            self._h = None
+
+    def _info(self):
+        i = _TreeInfo()
+        _check(_lib.lm_get_tree_info(self._h, ctypes.byref(i)))
+        return {f: getattr(i, f) for f, _ in _TreeInfo._fields_}
+
+    def export(self, stream=None):
+        """(perm, leaf_start) as numpy int64 arrays (tree order)."""
+        import numpy as np
+
+        perm = np.zeros(self.n, np.int64)
+        ls = np.zeros(self.info["nleaf"] + 1, np.int64)
+        _check(_lib.lm_tree_export(self._h, perm.ctypes.data_as(ctypes.c_void_p),
+                                   ls.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+        return perm, ls
+
+    def list_export(self, which, level=0, stream=None):
+        """Rows (target box, term, source box) of the V list of `level` (which=0) or the U list (1)."""
+        import numpy as np
+
+        cnt = ctypes.c_int64()
+        _check(_lib.lm_list_export(self._h, which, level, None, 0, ctypes.byref(cnt), _stream(stream)))
+        out = np.zeros((max(cnt.value, 1), 3), np.int64)
+        _check(_lib.lm_list_export(self._h, which, level, out.ctypes.data_as(ctypes.c_void_p), cnt.value,
+                                   ctypes.byref(cnt), _stream(stream)))
+        return out[:cnt.value]
+
+    def m2l_table(self, level, term, dc, dr, stream=None):
+        import numpy as np
+
+        P = self.info["p"]
+        out = np.zeros((2 * P + 1, 2 * P + 1), np.complex128)
+        _check(_lib.lm_m2l_table_export(self._h, level, term, dc, dr, out.ctypes.data_as(ctypes.c_void_p),
+                                        _stream(stream)))
+        return out
+
+
+def build_tree(medium: Medium, x, y, stream=None) -> Tree:
+    """x, y: contiguous float64 CUDA tensors of the point coordinates."""
+    import torch
+
+    for a in (x, y):
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+            raise ValueError("build_tree: x and y must be contiguous float64 CUDA tensors")
+    if x.numel() != y.numel():
+        raise ValueError("build_tree: x and y differ in length")
+    h = ctypes.c_void_p()
+    _check(_lib.lm_build_tree(medium._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                              x.numel(), _stream(stream), ctypes.byref(h)))
+    return Tree(h.value, medium)
+
+
+def _apply(fn, tree, q, u, stream):
+    import torch
+
+    if not (q.is_cuda and q.dtype == torch.complex128 and q.is_contiguous()):
+        raise ValueError("apply: q must be a contiguous complex128 CUDA tensor")
+    one = q.dim() == 1
+    q2 = q.reshape(1, -1) if one else q
+    if q2.shape[-1] != tree.n:
+        raise ValueError(f"apply: q has {q2.shape[-1]} points, tree has {tree.n}")
+    if u is None:
+        u = torch.empty_like(q2)
+    _check(fn(tree._h, ctypes.c_void_p(q2.data_ptr()), q2.shape[0], ctypes.c_void_p(u.data_ptr()),
+              _stream(stream)))
+    return u.reshape(-1) if one else u
+
+
+def apply(tree: Tree, q, u=None, stream=None):
+    """u = G q (Algorithm 1). q: complex128 CUDA tensor [nvec, n] or [n]."""
+    return _apply(_lib.lm_apply, tree, q, u, stream)
+
+
+def apply_adjoint(tree: Tree, v, w=None, stream=None):
+    """w = G^H v = conj(G conj(v)) (reciprocity)."""
+    return _apply(_lib.lm_apply_adjoint, tree, v, w, stream)

@@ -1,0 +1,96 @@
+// internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/lmfmm.h"
+#include "common.cuh"
+
+#define LM_MAXP 48      // largest supported expansion order p
+#define LM_MAXV 16      // vectors per kernel pass
+#define LM_MAXLEAF 8192 // largest leaf the tree builder sorts
+
+void lm_set_error(const char *fmt, ...);
+
+#define LM_CUDA(call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess) {                                                            \
+            lm_set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                         __LINE__);                                                         \
+            return LM_ECUDA;                                                                \
+        }                                                                                   \
+    } while (0)
+
+struct lm_medium_s {
+    double k1, k2, k3, d;
+    lm_options opt;
+};
+
+// Near-field quadrature (Sec. 4.2 alternative directions, Sec. 5 first
+// contour) for the two image terms that reach the direct interactions
+// (tt near y = 0, bb near y = -d).  All weights include 1/(4 pi).
+struct NearQuad {
+    int nseg;    // nodes on the deformed segment t in [0, c]
+    int nray;    // number of tail rays (angles 0 .. pi/2)
+    int ntail;   // nodes per ray
+    double c;    // segment end
+    // device arrays
+    zd *seg_lam, *seg_s2, *seg_w;    // [nseg], [nseg], [2][nseg]: w * lambda' * sigma_m / s2 / 4pi
+    zd *tail_lam, *tail_s2, *tail_w; // [nray][ntail], ..., [2][nray][ntail]: 2 w dlambda sigma_m/s2/4pi
+};
+
+struct Level {
+    int l;
+    int64_t ncol, nrow, nbox;
+    double w;
+    // V list (target-major CSR): sources and table slots
+    int64_t nv;
+    int64_t *vstart; // [nbox + 1]
+    int32_t *vsrc;   // [nv]
+    int32_t *vslot;  // [nv]
+    int32_t *vterm;  // [nv]
+    // translation classes of this level (host copies) and their tables (device)
+    std::vector<int> cls_term, cls_dc, cls_dr;
+    zd *tab;         // [nclass][np][np] scaled M2L tables
+    double *scale;   // [p + 1] S_l(n) = (k w_l / 2)^n / n!
+    zd *m2m;         // [4][np][np]: child (level l+1) -> this level's box (l < L)
+    zd *l2l;         // [4][np][np]: parent (level l-1) -> child at this level (l > 0)
+    zd *M, *Lc;      // [nbox][np][LM_MAXV]
+    // mixed-precision copies
+    float *tab32;    // [nclass][2np][2np] real-block form
+};
+
+struct lm_tree_s {
+    lm_medium_s med;
+    int64_t n;
+    int R, L, p, np;
+    double x0;
+    int64_t nleaf;
+    int precision;
+    int max_nvec;
+    double *xs, *ys;     // tree order coordinates [n]
+    int64_t *perm;       // [n] tree position -> input index
+    int64_t *leaf_start; // [nleaf + 1]
+    // U list (leaf level, target-major CSR)
+    int64_t nu;
+    int64_t *ustart;  // [nleaf + 1]
+    int32_t *usrc;    // [nu]
+    int32_t *uterm;   // [nu]
+    std::vector<Level> lev;
+    NearQuad nq;
+    zd *qs, *us; // [LM_MAXV][n] tree-order scratch
+    int *dflag;  // device error flag
+    int64_t bytes;
+};
+
+// setup (lmfmm_setup.cu)
+lm_status lm_setup_tree(lm_tree_s *t, const double *x, const double *y, cudaStream_t st);
+lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st);
+lm_status lm_list_to_host(lm_tree_s *t, int which, int level, std::vector<int64_t> &rows,
+                          cudaStream_t st);
+void lm_free_tree_device(lm_tree_s *t);
+// apply (lmfmm_apply.cu)
+lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);

@@ -1,0 +1,306 @@
+// lmfmm_apply.cu -- Algorithm 1, steps 2-4 (upward pass, downward pass,
+// evaluation) as device kernels, FP64 form.
+#include <algorithm>
+
+#include "internal.h"
+
+static int gridn(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+// q (input order, [nvec][n]) -> qs (tree order, [nvec][n]), optionally conjugated
+__global__ void k_permute_in(const zd *q, const int64_t *perm, int64_t n, int nvec, int conjugate,
+                             zd *qs)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    for (int v = 0; v < nvec; ++v) {
+        zd a = q[(int64_t)v * n + j];
+        qs[(int64_t)v * n + i] = conjugate ? conj(a) : a;
+    }
+}
+__global__ void k_permute_out(const zd *us, const int64_t *perm, int64_t n, int nvec, int conjugate,
+                              zd *u)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    for (int v = 0; v < nvec; ++v) {
+        zd a = us[(int64_t)v * n + i];
+        u[(int64_t)v * n + j] = conjugate ? conj(a) : a;
+    }
+}
+
+struct LeafGeom {
+    int64_t ncol;
+    double x0, w;
+};
+__device__ inline void leaf_centre(const LeafGeom &g, int64_t b, double *cx, double *cy)
+{
+    int64_t r = b / g.ncol, c = b % g.ncol;
+    *cx = g.x0 + (c + 0.5) * g.w;
+    *cy = -(r + 0.5) * g.w;
+}
+
+// ---------------------------------------------------------------------------
+// S2M (Eq. (multipole_coef)), scaled: Mhat_q = sum_j q_j Jhat_q(k r_j) e^{-i q theta_j}
+// One block per leaf; points staged 16 at a time.
+// ---------------------------------------------------------------------------
+#define P2M_CHUNK 16
+__global__ void k_p2m64(LeafGeom g, int P, double k, const double *xs, const double *ys,
+                        const int64_t *ls, const zd *qs, int64_t n, int nvec, zd *M)
+{
+    extern __shared__ unsigned char smem[];
+    const int np = 2 * P + 1;
+    zd *B = (zd *)smem;                      // [P2M_CHUNK][np]
+    zd *Q = B + P2M_CHUNK * np;              // [P2M_CHUNK][LM_MAXV]
+    const int64_t b = blockIdx.x;
+    const int64_t lo = ls[b], hi = ls[b + 1];
+    double cx, cy;
+    leaf_centre(g, b, &cx, &cy);
+    const double sc = k * g.w;
+    const int nent = np * nvec;
+    zd acc[12];
+    for (int e = 0; e < 12; ++e) acc[e] = zd{0.0, 0.0};
+    for (int64_t base = lo; base < hi; base += P2M_CHUNK) {
+        __syncthreads();
+        int j = threadIdx.x;
+        if (j < P2M_CHUNK) {
+            int64_t i = base + j;
+            zd *row = B + j * np + P;
+            if (i < hi) {
+                double rx = xs[i] - cx, ry = ys[i] - cy, r = hypot(rx, ry);
+                double J[LM_MAXP + 1];
+                bessel_j_scaled<double>(P, k * r, sc, J);
+                zd z = r > 0.0 ? zd{rx / r, -ry / r} : zd{1.0, 0.0}; // e^{-i theta}
+                zd zp = {1.0, 0.0};
+                row[0] = zd{J[0], 0.0};
+                for (int m = 1; m <= P; ++m) {
+                    zp = zp * z;
+                    row[m] = J[m] * zp;
+                    double s = (m & 1) ? -J[m] : J[m];
+                    row[-m] = s * conj(zp);
+                }
+                for (int v = 0; v < nvec; ++v) Q[j * LM_MAXV + v] = qs[(int64_t)v * n + i];
+            } else {
+                for (int m = -P; m <= P; ++m) row[m] = zd{0.0, 0.0};
+                for (int v = 0; v < nvec; ++v) Q[j * LM_MAXV + v] = zd{0.0, 0.0};
+            }
+        }
+        __syncthreads();
+        for (int e = 0; e < 12; ++e) {
+            int idx = threadIdx.x + e * blockDim.x;
+            if (idx >= nent) break;
+            int qi = idx / nvec, v = idx % nvec;
+            zd s = acc[e];
+            for (int jj = 0; jj < P2M_CHUNK; ++jj) cfma(s, B[jj * np + qi], Q[jj * LM_MAXV + v]);
+            acc[e] = s;
+        }
+    }
+    for (int e = 0; e < 12; ++e) {
+        int idx = threadIdx.x + e * blockDim.x;
+        if (idx >= nent) break;
+        int qi = idx / nvec, v = idx % nvec;
+        M[(b * np + qi) * LM_MAXV + v] = acc[e];
+    }
+}
+
+// M2M (Lemma M2M): parent (level l) from its four children (level l+1)
+__global__ void k_m2m64(int64_t ncol, int64_t nbox, int P, int nvec, const zd *tabs, const zd *Mc,
+                        zd *Mp)
+{
+    const int np = 2 * P + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * nvec) return;
+    int v = idx % nvec;
+    int p = (idx / nvec) % np;
+    int64_t b = idx / (nvec * np);
+    int64_t r = b / ncol, c = b % ncol, ncc = 2 * ncol;
+    zd acc = {0.0, 0.0};
+    for (int pos = 0; pos < 4; ++pos) {
+        int dy = pos >> 1, dx = pos & 1;
+        int64_t ch = (2 * r + dy) * ncc + 2 * c + dx;
+        const zd *T = tabs + ((int64_t)pos * np + p) * np;
+        const zd *m = Mc + ch * np * LM_MAXV + v;
+        for (int q = 0; q < np; ++q) cfma(acc, T[q], m[q * LM_MAXV]);
+    }
+    Mp[(b * np + p) * LM_MAXV + v] = acc;
+}
+
+// L2L (Lemma L2L): child (level l) from its parent (level l-1); initialises L
+__global__ void k_l2l64(int64_t ncol, int64_t nbox, int P, int nvec, const zd *tabs, const zd *Lp,
+                        zd *Lc)
+{
+    const int np = 2 * P + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * nvec) return;
+    int v = idx % nvec;
+    int p = (idx / nvec) % np;
+    int64_t b = idx / (nvec * np);
+    int64_t r = b / ncol, c = b % ncol;
+    int pos = (int)((r & 1) * 2 + (c & 1));
+    int64_t par = (r / 2) * (ncol / 2) + c / 2;
+    const zd *T = tabs + ((int64_t)pos * np + p) * np;
+    const zd *m = Lp + par * np * LM_MAXV + v;
+    zd acc = {0.0, 0.0};
+    for (int q = 0; q < np; ++q) cfma(acc, T[q], m[q * LM_MAXV]);
+    Lc[(b * np + p) * LM_MAXV + v] = acc;
+}
+
+// M2L over the V list (free space and image terms)
+__global__ void k_m2l64(int64_t nbox, int P, int nvec, const int64_t *vstart, const int32_t *vsrc,
+                        const int32_t *vslot, const zd *tab, const zd *M, zd *Lc)
+{
+    const int np = 2 * P + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * nvec) return;
+    int v = idx % nvec;
+    int p = (idx / nvec) % np;
+    int64_t b = idx / (nvec * np);
+    zd acc = {0.0, 0.0};
+    for (int64_t e = vstart[b]; e < vstart[b + 1]; ++e) {
+        const zd *T = tab + ((int64_t)vslot[e] * np + p) * np;
+        const zd *m = M + (int64_t)vsrc[e] * np * LM_MAXV + v;
+        for (int q = 0; q < np; ++q) cfma(acc, T[q], m[q * LM_MAXV]);
+    }
+    Lc[(b * np + p) * LM_MAXV + v] += acc;
+}
+
+// ---------------------------------------------------------------------------
+// Direct interaction of one reflected term (tt: term 1, bb: term 2) for a
+// pair at horizontal distance X and image height h, by the near-field
+// quadrature tables (segment + nearest steepest-descent ray).
+// ---------------------------------------------------------------------------
+struct NearQuadD {
+    int nseg, nray, ntail;
+    const zd *seg_lam, *seg_s2, *seg_w, *tail_lam, *tail_s2, *tail_w;
+};
+__device__ zd near_refl64(const NearQuadD &q, int m, double X, double h)
+{
+    zd acc = {0.0, 0.0};
+    const zd *W = q.seg_w + (int64_t)m * q.nseg;
+    for (int i = 0; i < q.nseg; ++i) {
+        zd lam = q.seg_lam[i], s2 = q.seg_s2[i];
+        // e^{+i lam X - s2 h} + e^{-i lam X - s2 h}
+        double er = -s2.re * h, ei = -s2.im * h;
+        zd e1 = cexpd(zd{er - lam.im * X, ei + lam.re * X});
+        zd e2 = cexpd(zd{er + lam.im * X, ei - lam.re * X});
+        cfma(acc, W[i], e1 + e2);
+    }
+    int k = q.nray > 1 ? (int)rint(atan2(X, h) * (q.nray - 1) / (0.5 * M_PI)) : 0;
+    const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
+    const zd *tw = q.tail_w + ((int64_t)m * q.nray + k) * q.ntail;
+    double tre = 0.0;
+    for (int i = 0; i < q.ntail; ++i) {
+        zd lam = tl[i], s2 = ts[i];
+        zd e = cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
+        zd w = tw[i];
+        tre += w.re * e.re - w.im * e.im;
+    }
+    acc.re += tre;
+    return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Step 4: L2T (Eq. (local)) and S2T for every target of a leaf.
+// ---------------------------------------------------------------------------
+__global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs, const double *ys,
+                         const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
+                         const int32_t *uterm, NearQuadD nq, const zd *Lc, const zd *qs, int64_t n,
+                         int nvec, zd *us)
+{
+    const int np = 2 * P + 1;
+    const int64_t b = blockIdx.x;
+    double cx, cy;
+    leaf_centre(g, b, &cx, &cy);
+    const double sc = k * g.w;
+    const zd *Lb = Lc + b * np * LM_MAXV;
+    for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
+        const double xi = xs[i], yi = ys[i];
+        zd acc[LM_MAXV];
+        for (int v = 0; v < nvec; ++v) acc[v] = zd{0.0, 0.0};
+        {
+            double rx = xi - cx, ry = yi - cy, r = hypot(rx, ry);
+            double J[LM_MAXP + 1];
+            bessel_j_scaled<double>(P, k * r, sc, J);
+            zd z = r > 0.0 ? zd{rx / r, ry / r} : zd{1.0, 0.0}; // e^{i theta}
+            zd zp = {1.0, 0.0};
+            for (int v = 0; v < nvec; ++v) cfma(acc[v], zd{J[0], 0.0}, Lb[P * LM_MAXV + v]);
+            for (int m = 1; m <= P; ++m) {
+                zp = zp * z;
+                zd bp = J[m] * zp;
+                zd bn = ((m & 1) ? -J[m] : J[m]) * conj(zp);
+                for (int v = 0; v < nvec; ++v) {
+                    cfma(acc[v], bp, Lb[(P + m) * LM_MAXV + v]);
+                    cfma(acc[v], bn, Lb[(P - m) * LM_MAXV + v]);
+                }
+            }
+        }
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
+            const int32_t s = usrc[e], term = uterm[e];
+            for (int64_t j = ls[s]; j < ls[s + 1]; ++j) {
+                zd gij;
+                if (term == 0) {
+                    if (j == i) continue;
+                    double r = hypot(xi - xs[j], yi - ys[j]);
+                    gij = zd{-0.25 * y0(k * r), 0.25 * j0(k * r)}; // (i/4) H0^(1)(k r)
+                } else {
+                    double X = fabs(xi - xs[j]);
+                    double h = term == 1 ? -(yi + ys[j]) : yi + ys[j] + 2.0 * d;
+                    gij = near_refl64(nq, term - 1, X, h);
+                }
+                for (int v = 0; v < nvec; ++v) cfma(acc[v], gij, qs[(int64_t)v * n + j]);
+            }
+        }
+        for (int v = 0; v < nvec; ++v) us[(int64_t)v * n + i] = acc[v];
+    }
+}
+
+lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st)
+{
+    const int L = t->L, P = t->p, np = 2 * P + 1;
+    const int64_t n = t->n;
+    const double k = t->med.k2;
+    NearQuadD nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq.seg_lam, t->nq.seg_s2,
+                 t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w};
+    for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
+        const int nv = std::min(LM_MAXV, nvec - v0);
+        k_permute_in<<<gridn(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->perm, n, nv, adjoint, t->qs);
+        // step 2: upward pass
+        {
+            Level &lv = t->lev[L];
+            LeafGeom g{lv.ncol, t->x0, lv.w};
+            size_t shm = (P2M_CHUNK * np + P2M_CHUNK * LM_MAXV) * sizeof(zd);
+            k_p2m64<<<(unsigned)lv.nbox, 256, shm, st>>>(g, P, k, t->xs, t->ys, t->leaf_start, t->qs, n,
+                                                        nv, lv.M);
+        }
+        for (int l = L - 1; l >= 0; --l) {
+            Level &lv = t->lev[l];
+            int64_t tot = lv.nbox * np * nv;
+            k_m2m64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.m2m, t->lev[l + 1].M, lv.M);
+        }
+        // step 3: downward pass
+        for (int l = 0; l <= L; ++l) {
+            Level &lv = t->lev[l];
+            int64_t tot = lv.nbox * np * nv;
+            if (l == 0)
+                LM_CUDA(cudaMemsetAsync(lv.Lc, 0, lv.nbox * np * LM_MAXV * sizeof(zd), st));
+            else
+                k_l2l64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.l2l, t->lev[l - 1].Lc,
+                                                         lv.Lc);
+            if (lv.nv > 0)
+                k_m2l64<<<gridn(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot, lv.tab,
+                                                         lv.M, lv.Lc);
+        }
+        // step 4: evaluation
+        {
+            Level &lv = t->lev[L];
+            LeafGeom g{lv.ncol, t->x0, lv.w};
+            k_leaf64<<<(unsigned)lv.nbox, 64, 0, st>>>(g, P, k, t->med.d, t->xs, t->ys, t->leaf_start,
+                                                       t->ustart, t->usrc, t->uterm, nq, lv.Lc, t->qs, n,
+                                                       nv, t->us);
+        }
+        k_permute_out<<<gridn(n, 256), 256, 0, st>>>(t->us, t->perm, n, nv, adjoint, u + (int64_t)v0 * n);
+        LM_CUDA(cudaGetLastError());
+    }
+    return LM_OK;
+}

@@ -1,0 +1,982 @@
+// lmfmm_setup.cu -- Algorithm 1, step 1 on the device: the strip-forest
+// quadtree, interaction lists, translation tables and near-field quadrature.
+#include <math.h>
+#include <stdio.h>
+#include <algorithm>
+#include <map>
+#include <tuple>
+
+#include "internal.h"
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre nodes on [-1, 1] by Newton's method on P_n (three-term
+// recurrence), initial guess cos(pi (i + 3/4) / (n + 1/2)).
+// ---------------------------------------------------------------------------
+__device__ void gl_node(int n, int i, double *x, double *w)
+{
+    double z = cos(M_PI * (i + 0.75) / (n + 0.5)), pp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+        double p1 = 1.0, p2 = 0.0;
+        for (int j = 1; j <= n; ++j) {
+            double p3 = p2;
+            p2 = p1;
+            p1 = ((2.0 * j - 1.0) * z * p2 - (j - 1.0) * p3) / j;
+        }
+        pp = n * (z * p1 - p2) / (z * z - 1.0);
+        double dz = p1 / pp;
+        z -= dz;
+        if (fabs(dz) < 1e-16) break;
+    }
+    *x = -z; // ascending order
+    *w = 2.0 / ((1.0 - z * z) * pp * pp);
+}
+
+// ---------------------------------------------------------------------------
+// Tree
+// ---------------------------------------------------------------------------
+__global__ void k_minmax(const double *x, const double *y, int64_t n, double d, double *bmin,
+                         double *bmax, int *flag)
+{
+    __shared__ double smin[256], smax[256];
+    double mn = 1e308, mx = -1e308;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double xi = x[i], yi = y[i];
+        if (!isfinite(xi) || !isfinite(yi) || !(yi < 0.0) || !(yi > -d)) atomicOr(flag, 1);
+        mn = fmin(mn, xi);
+        mx = fmax(mx, xi);
+    }
+    smin[threadIdx.x] = mn;
+    smax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        bmin[blockIdx.x] = smin[0];
+        bmax[blockIdx.x] = smax[0];
+    }
+}
+
+// leaf of each point: col = floor((x - x0)/w), row = floor(-y/w), clamped
+__global__ void k_keys(const double *x, const double *y, int64_t n, double x0, double w,
+                       int64_t ncol, int64_t nrow, int32_t *key, int32_t *cnt)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t c = (int64_t)floor((x[i] - x0) / w), r = (int64_t)floor(-y[i] / w);
+    c = c < 0 ? 0 : (c > ncol - 1 ? ncol - 1 : c);
+    r = r < 0 ? 0 : (r > nrow - 1 ? nrow - 1 : r);
+    int32_t k = (int32_t)(r * ncol + c);
+    key[i] = k;
+    atomicAdd(&cnt[k], 1);
+}
+
+// exclusive scan of cnt[0..m) into start[0..m] by one block
+__global__ void k_scan(const int32_t *cnt, int64_t m, int64_t *start)
+{
+    __shared__ int64_t part[1024];
+    int64_t chunk = (m + blockDim.x - 1) / blockDim.x;
+    int64_t lo = threadIdx.x * chunk, hi = min(m, lo + chunk);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += cnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            int64_t v = part[i];
+            part[i] = acc;
+            acc += v;
+        }
+        start[m] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int64_t i = lo; i < hi; ++i) {
+        start[i] = acc;
+        acc += cnt[i];
+    }
+}
+
+__global__ void k_scatter(const int32_t *key, int64_t n, const int64_t *start, int32_t *cursor,
+                          int64_t *tmp)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int32_t k = key[i];
+    int pos = atomicAdd(&cursor[k], 1);
+    tmp[start[k] + pos] = i;
+}
+
+// sort each leaf's input indices ascending (bitonic sort in shared memory)
+__global__ void k_leafsort(const int64_t *start, int64_t *idx, int *flag)
+{
+    __shared__ int32_t s[LM_MAXLEAF];
+    int64_t b = blockIdx.x;
+    int64_t lo = start[b], cnt = start[b + 1] - lo;
+    if (cnt <= 1) return;
+    if (cnt > LM_MAXLEAF) {
+        if (threadIdx.x == 0) atomicOr(flag, 2);
+        return;
+    }
+    int m = 1;
+    while (m < cnt) m <<= 1;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s[i] = i < cnt ? (int32_t)idx[lo + i] : INT32_MAX;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    bool up = (i & k) == 0;
+                    int32_t a = s[i], c = s[ixj];
+                    if ((a > c) == up) {
+                        s[i] = c;
+                        s[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) idx[lo + i] = s[i];
+}
+
+__global__ void k_gather_pts(const double *x, const double *y, const int64_t *perm, int64_t n,
+                             double *xs, double *ys)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    xs[i] = x[j];
+    ys[i] = y[j];
+}
+
+// ---------------------------------------------------------------------------
+// Interaction lists.  Image row of source row r for term m at a level with
+// nrow rows: free r; tt -1-r (mirror in y = 0); bb 2nrow-1-r (mirror in
+// y = -d); tb r-2nrow (shift +2d); bt r+2nrow (shift -2d).
+// ---------------------------------------------------------------------------
+__host__ __device__ inline int64_t img_row(int term, int64_t r, int64_t nrow)
+{
+    switch (term) {
+    case 0: return r;
+    case 1: return -1 - r;
+    case 2: return 2 * nrow - 1 - r;
+    case 3: return r - 2 * nrow;
+    default: return r + 2 * nrow;
+    }
+}
+// inverse: source row whose image row is ri
+__host__ __device__ inline int64_t src_row(int term, int64_t ri, int64_t nrow)
+{
+    switch (term) {
+    case 0: return ri;
+    case 1: return -1 - ri;
+    case 2: return 2 * nrow - 1 - ri;
+    case 3: return ri + 2 * nrow;
+    default: return ri - 2 * nrow;
+    }
+}
+__host__ __device__ inline int64_t floordiv2(int64_t a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); }
+__host__ __device__ inline bool adj(int64_t c1, int64_t r1, int64_t c2, int64_t r2)
+{
+    return (c1 - c2 <= 1 && c2 - c1 <= 1) && (r1 - r2 <= 1 && r2 - r1 <= 1);
+}
+__host__ __device__ inline bool v_rule(int l, int64_t ct, int64_t rt, int64_t cs, int64_t ri)
+{
+    if (adj(ct, rt, cs, ri)) return false;
+    if (l == 0) return true;
+    return adj(ct / 2, floordiv2(rt), cs / 2, floordiv2(ri));
+}
+
+struct SlotMap {
+    int DC;          // dc in [-DC, DC]
+    int32_t *map;    // [5][2DC+1][7] slot or -1 (dr in [-3, 3])
+};
+__host__ __device__ inline int slot_index(int DC, int term, int dc, int dr)
+{
+    return (term * (2 * DC + 1) + (dc + DC)) * 7 + (dr + 3);
+}
+
+// pass 0: count; pass 1: fill. One thread per target box.
+__global__ void k_vlist(int l, int64_t ncol, int64_t nrow, int DC, const int32_t *slotmap,
+                        int64_t *vstart, int32_t *vsrc, int32_t *vslot, int32_t *vterm, int pass,
+                        int *flag)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ncol * nrow) return;
+    int64_t rt = t / ncol, ct = t % ncol;
+    int64_t pos = pass ? vstart[t] : 0, cnt = 0;
+    for (int term = 0; term < 5; ++term) {
+        // source rows in ascending order
+        int64_t rlo = 0, rhi = nrow - 1;
+        if (l > 0) {
+            int64_t a = src_row(term, rt - 3, nrow), b = src_row(term, rt + 3, nrow);
+            rlo = max((int64_t)0, min(a, b));
+            rhi = min(nrow - 1, max(a, b));
+        }
+        int64_t clo = l > 0 ? max((int64_t)0, ct - 3) : 0;
+        int64_t chi = l > 0 ? min(ncol - 1, ct + 3) : ncol - 1;
+        for (int64_t rs = rlo; rs <= rhi; ++rs) {
+            int64_t ri = img_row(term, rs, nrow);
+            for (int64_t cs = clo; cs <= chi; ++cs) {
+                if (!v_rule(l, ct, rt, cs, ri)) continue;
+                if (pass) {
+                    int64_t dc = ct - cs, dr = rt - ri;
+                    int slot = -1;
+                    if (dc >= -DC && dc <= DC && dr >= -3 && dr <= 3)
+                        slot = slotmap[slot_index(DC, term, (int)dc, (int)dr)];
+                    if (slot < 0) atomicOr(flag, 4);
+                    vsrc[pos] = (int32_t)(rs * ncol + cs);
+                    vslot[pos] = slot < 0 ? 0 : slot;
+                    vterm[pos] = term;
+                    ++pos;
+                }
+                ++cnt;
+            }
+        }
+    }
+    if (!pass) vstart[t] = cnt; // counts, scanned on the host side afterwards
+}
+
+// U list at the leaf level: image adjacent to target (free term includes itself)
+__global__ void k_ulist(int64_t ncol, int64_t nrow, int64_t *ustart, int32_t *usrc, int32_t *uterm,
+                        int pass)
+{
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ncol * nrow) return;
+    int64_t rt = t / ncol, ct = t % ncol;
+    int64_t pos = pass ? ustart[t] : 0, cnt = 0;
+    for (int term = 0; term < 5; ++term) {
+        int64_t a = src_row(term, rt - 1, nrow), b = src_row(term, rt + 1, nrow);
+        int64_t rlo = max((int64_t)0, min(a, b)), rhi = min(nrow - 1, max(a, b));
+        for (int64_t rs = rlo; rs <= rhi; ++rs) {
+            int64_t ri = img_row(term, rs, nrow);
+            for (int64_t cs = max((int64_t)0, ct - 1); cs <= min(ncol - 1, ct + 1); ++cs) {
+                if (!adj(ct, rt, cs, ri)) continue;
+                if (pass) {
+                    usrc[pos] = (int32_t)(rs * ncol + cs);
+                    uterm[pos] = term;
+                    ++pos;
+                }
+                ++cnt;
+            }
+        }
+    }
+    if (!pass) ustart[t] = cnt;
+}
+
+// in-place exclusive scan of counts c[0..m) (stored as int64) -> start[0..m]
+__global__ void k_scan64(int64_t *c, int64_t m)
+{
+    __shared__ int64_t part[1024];
+    int64_t chunk = (m + blockDim.x - 1) / blockDim.x;
+    int64_t lo = threadIdx.x * chunk, hi = min(m, lo + chunk);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += c[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            int64_t v = part[i];
+            part[i] = acc;
+            acc += v;
+        }
+        c[m] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int64_t i = lo; i < hi; ++i) {
+        int64_t v = c[i];
+        c[i] = acc;
+        acc += v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Image densities (reading R1 of the paper's Example 4 for a middle-layer
+// source): R_t = (k1^2-k2^2)/(s2+s1)^2, R_b = (k3^2-k2^2)/(s2+s3)^2,
+// Sigma = 1/(1 - R_t R_b e^{-2 d s2}); sigma_tt = R_t Sigma, sigma_bb =
+// R_b Sigma, sigma_tb = R_t R_b Sigma.
+// ---------------------------------------------------------------------------
+struct MediumD {
+    double k1, k2, k3, d;
+};
+__device__ void densities(const MediumD &m, zd lam, zd *s2o, zd sig[3])
+{
+    zd s1 = sbranch(lam, m.k1), s2 = sbranch(lam, m.k2), s3 = sbranch(lam, m.k3);
+    zd a = s2 + s1, b = s2 + s3;
+    zd Rt = cdiv(zd{m.k1 * m.k1 - m.k2 * m.k2, 0.0}, a * a);
+    zd Rb = cdiv(zd{m.k3 * m.k3 - m.k2 * m.k2, 0.0}, b * b);
+    zd E = cexpd(-2.0 * m.d * s2);
+    zd S = cdiv(zd{1.0, 0.0}, zd{1.0, 0.0} - Rt * Rb * E);
+    sig[0] = Rt * S;
+    sig[1] = Rb * S;
+    sig[2] = Rt * Rb * S;
+    *s2o = s2;
+}
+
+// ---------------------------------------------------------------------------
+// Near-field quadrature tables.
+//  Segment (first contour, Sec. 5): a trapezoid from 0 down to delta - i a,
+//  along -i a to c - delta - i a, and up to c; the negative half is folded
+//  onto it (integrand 2 cos(lambda X) ...).  Gauss-Legendre panels.
+//  Tail: rays lambda = c + t e^{i phi_k}, phi_k = k (pi/2) / (nray - 1),
+//  t = c v/(1-v), Gauss-Legendre in v; since sigma(conj lambda) =
+//  conj(sigma(lambda)) for real wave numbers, the two half-line tails sum to
+//  2 Re Int_ray e^{i lambda X} F(lambda) d lambda.
+// ---------------------------------------------------------------------------
+__global__ void k_near_seg(MediumD m, double c, double a, double delta, int nflat, int order,
+                           zd *lam_o, zd *s2_o, zd *w_o, int nseg)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nseg) return;
+    int pan = i / order, j = i % order;
+    double x, w;
+    gl_node(order, j, &x, &w);
+    zd z0, z1;
+    double flat = (c - 2.0 * delta) / nflat;
+    if (pan == 0) {
+        z0 = {0.0, 0.0};
+        z1 = {delta, -a};
+    } else if (pan == nflat + 1) {
+        z0 = {c - delta, -a};
+        z1 = {c, 0.0};
+    } else {
+        z0 = {delta + (pan - 1) * flat, -a};
+        z1 = {delta + pan * flat, -a};
+    }
+    zd dz = z1 - z0;
+    zd lam = z0 + (0.5 * (x + 1.0)) * dz;
+    zd s2, sig[3];
+    densities(m, lam, &s2, sig);
+    zd base = cdiv((0.5 * w / (4.0 * M_PI)) * dz, s2);
+    lam_o[i] = lam;
+    s2_o[i] = s2;
+    w_o[i] = base * sig[0];
+    w_o[nseg + i] = base * sig[1];
+}
+
+__global__ void k_near_tail(MediumD m, double c, int nray, int order, zd *lam_o, zd *s2_o, zd *w_o)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int tot = nray * order;
+    if (i >= tot) return;
+    int k = i / order, j = i % order;
+    double x, w;
+    gl_node(order, j, &x, &w);
+    double v = 0.5 * (x + 1.0), wv = 0.5 * w;
+    double t = c * v / (1.0 - v), dt = c / ((1.0 - v) * (1.0 - v));
+    double phi = (nray > 1) ? k * (0.5 * M_PI) / (nray - 1) : 0.0;
+    zd e = {cos(phi), sin(phi)};
+    zd lam = zd{c, 0.0} + t * e;
+    zd s2, sig[3];
+    densities(m, lam, &s2, sig);
+    zd base = cdiv((2.0 * wv * dt / (4.0 * M_PI)) * e, s2);
+    lam_o[i] = lam;
+    s2_o[i] = s2;
+    w_o[i] = base * sig[0];
+    w_o[tot + i] = base * sig[1];
+}
+
+// ---------------------------------------------------------------------------
+// Translation tables (scaled; S_l(n) = (k w_l / 2)^|n| / |n|!):
+//  M2M (Lemma M2M, reading G3): M_p += sum_q M_q J_{p-q}(k r) e^{-i (p-q) theta},
+//     (r, theta) = child centre - parent centre; scaled by S_child(q)/S_parent(p).
+//  L2L (Lemma L2L, reading G3): L_p += sum_q L_q J_{p-q}(k r) e^{-i (p-q) theta},
+//     (r, theta) = parent centre - child centre; scaled by S_child(p)/S_parent(q).
+// ---------------------------------------------------------------------------
+__device__ double besj_int(int n, double x)
+{
+    int a = n < 0 ? -n : n;
+    double v = jn(a, x);
+    return (n < 0 && (a & 1)) ? -v : v;
+}
+
+__global__ void k_shift_tables(double k, int P, double wc, const double *sc_child,
+                               const double *sc_par, zd *m2m, zd *l2l)
+{
+    int np = 2 * P + 1;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 4 * np * np) return;
+    int pos = idx / (np * np), p = (idx / np) % np - P, q = idx % np - P;
+    int dy = pos >> 1, dx = pos & 1;
+    // child centre - parent centre
+    double sx = (dx - 0.5) * wc, sy = -(dy - 0.5) * wc;
+    double r = hypot(sx, sy), th = atan2(sy, sx);
+    int n = p - q;
+    if (m2m) {
+        double j = besj_int(n, k * r);
+        double s = sc_child[q < 0 ? -q : q] / sc_par[p < 0 ? -p : p];
+        m2m[idx] = zd{j * cos(n * th) * s, -j * sin(n * th) * s};
+    }
+    if (l2l) {
+        // parent centre - child centre = -(sx, sy)
+        double th2 = atan2(-sy, -sx);
+        double j = besj_int(n, k * r);
+        double s = sc_child[p < 0 ? -p : p] / sc_par[q < 0 ? -q : q];
+        l2l[idx] = zd{j * cos(n * th2) * s, -j * sin(n * th2) * s};
+    }
+}
+
+// Free-space M2L (Rokhlin's translation): A_pq = (i/4) H_{q-p}(k rho) e^{i (q-p) theta},
+// c = target centre - source centre = (dc w, -dr w); scaled by S(p) S(q).
+__global__ void k_free_m2l(double k, int P, double w, const int *cdc, const int *cdr,
+                           const int *cidx, int ncls, const double *sc, zd *tab)
+{
+    int np = 2 * P + 1;
+    int ci = blockIdx.y;
+    if (ci >= ncls) return;
+    double cx = cdc[ci] * w, cy = -cdr[ci] * w;
+    double rho = hypot(cx, cy), th = atan2(cy, cx);
+    zd *T = tab + (int64_t)cidx[ci] * np * np;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < np * np;
+         idx += gridDim.x * blockDim.x) {
+        int p = idx / np - P, q = idx % np - P;
+        int n = q - p, a = n < 0 ? -n : n;
+        double jv = jn(a, k * rho), yv = yn(a, k * rho);
+        if (n < 0 && (a & 1)) {
+            jv = -jv;
+            yv = -yv;
+        }
+        double s = sc[p < 0 ? -p : p] * sc[q < 0 ? -q : q];
+        // (i/4)(J + iY) = (-Y/4) + i (J/4)
+        zd h = {-0.25 * yv * s, 0.25 * jv * s};
+        zd e = {cos(n * th), sin(n * th)};
+        T[idx] = h * e;
+    }
+}
+
+// Layered M2L (Lemma M2L, reading G2 for the phase i^{p-q}):
+//   A_pq = (i^{p-q}/4pi) Int Z_t^p Z_s^q e^{i lambda dx - s2 h} sigma_m / s2 d lambda,
+//   Z_t = (lambda + tau s2)/k2, Z_s = (lambda + vs s2)/k2,
+// scaled by S(p) S(q): the powers are formed as (Z sc/2)^|p| / |p|!.
+// Contour: trapezoid segment over [-c, c] (down on the right, up on the
+// left) at depth a = min(0.5, 1/|dx|), then steepest-descent rays from +-c.
+// One block per class; nodes staged in chunks through shared memory.
+#define TB_CHUNK 16
+__global__ void __launch_bounds__(256) k_image_m2l(MediumD m, int P, double w, double sc, const int *cterm,
+                            const int *cdc, const int *cdr, const int *cidx, int ncls, zd *tab,
+                            int *flag)
+{
+    extern __shared__ unsigned char smem[];
+    int np = 2 * P + 1;
+    zd *ZT = (zd *)smem;                 // [TB_CHUNK][np]
+    zd *ZS = ZT + TB_CHUNK * np;         // [TB_CHUNK][np]
+    zd *BW = ZS + TB_CHUNK * np;         // [TB_CHUNK]
+    int ci = blockIdx.x;
+    if (ci >= ncls) return;
+    int term = cterm[ci];
+    const int tau = (term == 2 || term == 4) ? 1 : -1;
+    const int vs = (term == 2 || term == 3) ? 1 : -1;
+    double dx = cdc[ci] * w, h = fabs((double)cdr[ci]) * w;
+    double km = fmax(m.k1, fmax(m.k2, m.k3)), kmin = fmin(m.k1, fmin(m.k2, m.k3));
+    double c = 1.5 * km + 1.0;
+    double a = fmin(0.5, 1.0 / fmax(fabs(dx), 1e-3));
+    double delta = fmin(0.25, 0.5 * kmin);
+    double width = fmin(fmin(0.5, 2.0 * a), 1.5 / fmax(fabs(dx), 1e-3));
+    int nflat = (int)ceil((c - 2.0 * delta) / width);
+    const int ORD = 24;
+    int nseg_half = (nflat + 2) * ORD;
+    double rho = hypot(dx, h);
+    double tmax = 1.5 * (2.0 * P + 60.0) / rho;
+    const int TPAN = P + 8 > 24 ? P + 8 : 24; // panels of ORD nodes resolving t^{2P} e^{-t rho}
+    int ntail = TPAN * ORD;
+    int ntot = 2 * nseg_half + 2 * ntail;
+    double phi = atan2(dx, h);
+    zd er = {cos(phi), sin(phi)};       // right ray direction
+    zd el = {-cos(phi), sin(phi)};      // left ray direction: -e^{-i phi}
+    // accumulators: each thread owns entries idx = tid + k*blockDim
+    const int MAXE = (2 * LM_MAXP + 1) * (2 * LM_MAXP + 1);
+    (void)MAXE;
+    int nent = np * np;
+    int per = (nent + blockDim.x - 1) / blockDim.x;
+    zd acc[48];
+    for (int e = 0; e < per && e < 48; ++e) acc[e] = zd{0.0, 0.0};
+    if (per > 48) {
+        if (threadIdx.x == 0) atomicOr(flag, 8);
+        return;
+    }
+    for (int base = 0; base < ntot; base += TB_CHUNK) {
+        __syncthreads();
+        // thread j < TB_CHUNK builds node base + j
+        if (threadIdx.x < TB_CHUNK) {
+            int i = base + threadIdx.x;
+            zd lam = {0.0, 0.0}, dl = {0.0, 0.0};
+            bool valid = i < ntot;
+            if (valid) {
+                if (i < 2 * nseg_half) {
+                    int side = i < nseg_half ? 1 : -1;
+                    int ii = i % nseg_half, pan = ii / ORD, j = ii % ORD;
+                    double x, gw;
+                    gl_node(ORD, j, &x, &gw);
+                    zd z0, z1;
+                    double flat = (c - 2.0 * delta) / nflat;
+                    if (pan == 0) {
+                        z0 = {0.0, 0.0};
+                        z1 = {delta, -a};
+                    } else if (pan == nflat + 1) {
+                        z0 = {c - delta, -a};
+                        z1 = {c, 0.0};
+                    } else {
+                        z0 = {delta + (pan - 1) * flat, -a};
+                        z1 = {delta + pan * flat, -a};
+                    }
+                    zd dz = z1 - z0;
+                    lam = z0 + (0.5 * (x + 1.0)) * dz;
+                    dl = (0.5 * gw) * dz;
+                    if (side < 0) {
+                        // mirror through the origin; orientation -c -> 0 keeps dl
+                        lam = -lam;
+                    }
+                } else {
+                    int ii = i - 2 * nseg_half;
+                    int side = ii < ntail ? 1 : -1;
+                    ii %= ntail;
+                    int pan = ii / ORD, j = ii % ORD;
+                    double x, gw;
+                    gl_node(ORD, j, &x, &gw);
+                    double t0 = tmax * pan / TPAN, t1 = tmax * (pan + 1) / TPAN;
+                    double t = t0 + 0.5 * (x + 1.0) * (t1 - t0), wt = 0.5 * gw * (t1 - t0);
+                    if (side > 0) {
+                        lam = zd{c, 0.0} + t * er;
+                        dl = wt * er;
+                    } else {
+                        lam = zd{-c, 0.0} + t * el;
+                        dl = -wt * el; // runs from -inf to -c
+                    }
+                }
+                zd s2, sig[3];
+                densities(m, lam, &s2, sig);
+                zd sg = sig[term == 1 ? 0 : (term == 2 ? 1 : 2)];
+                zd ex = cexpd(zd{-lam.im * dx, lam.re * dx} - h * s2);
+                BW[threadIdx.x] = cdiv(dl * ex * sg, s2) * (1.0 / (4.0 * M_PI));
+                // Z = (lam + sgn s2)/k2, non-cancelling form; its inverse (lam - sgn s2)/k2
+                zd zt_p, zt_m, zs_p, zs_m;
+                {
+                    zd ap = lam + (double)tau * s2, am = lam - (double)tau * s2;
+                    if (abs2(ap) >= abs2(am)) {
+                        zt_p = (1.0 / m.k2) * ap;
+                        zt_m = cdiv(zd{m.k2, 0.0}, ap);
+                    } else {
+                        zt_p = cdiv(zd{m.k2, 0.0}, am);
+                        zt_m = (1.0 / m.k2) * am;
+                    }
+                    zd bp = lam + (double)vs * s2, bm = lam - (double)vs * s2;
+                    if (abs2(bp) >= abs2(bm)) {
+                        zs_p = (1.0 / m.k2) * bp;
+                        zs_m = cdiv(zd{m.k2, 0.0}, bp);
+                    } else {
+                        zs_p = cdiv(zd{m.k2, 0.0}, bm);
+                        zs_m = (1.0 / m.k2) * bm;
+                    }
+                }
+                zd *zt = ZT + threadIdx.x * np + P, *zs = ZS + threadIdx.x * np + P;
+                zt[0] = zd{1.0, 0.0};
+                zs[0] = zd{1.0, 0.0};
+                zd up = zd{1.0, 0.0}, dn = zd{1.0, 0.0}, su = zd{1.0, 0.0}, sd = zd{1.0, 0.0};
+                for (int n = 1; n <= P; ++n) {
+                    double f = 0.5 * sc / n;
+                    up = up * (f * zt_p);
+                    dn = dn * (f * zt_m);
+                    su = su * (f * zs_p);
+                    sd = sd * (f * zs_m);
+                    zt[n] = up;
+                    zt[-n] = dn;
+                    zs[n] = su;
+                    zs[-n] = sd;
+                }
+            } else {
+                BW[threadIdx.x] = zd{0.0, 0.0};
+                for (int n = 0; n < np; ++n) {
+                    ZT[threadIdx.x * np + n] = zd{0.0, 0.0};
+                    ZS[threadIdx.x * np + n] = zd{0.0, 0.0};
+                }
+            }
+        }
+        __syncthreads();
+        for (int e = 0; e < per; ++e) {
+            int idx = threadIdx.x + e * blockDim.x;
+            if (idx >= nent) break;
+            int pi = idx / np, qi = idx % np;
+            zd s = acc[e];
+            for (int j = 0; j < TB_CHUNK; ++j) cfma(s, BW[j] * ZT[j * np + pi], ZS[j * np + qi]);
+            acc[e] = s;
+        }
+    }
+    zd *T = tab + (int64_t)cidx[ci] * nent;
+    for (int e = 0; e < per; ++e) {
+        int idx = threadIdx.x + e * blockDim.x;
+        if (idx >= nent) break;
+        int p = idx / np - P, q = idx % np - P;
+        int ph = ((p - q) % 4 + 4) % 4; // i^{p-q}
+        zd v = acc[e];
+        zd r = ph == 0 ? v : ph == 1 ? zd{-v.im, v.re} : ph == 2 ? -v : zd{v.im, -v.re};
+        if (!isfinite(r.re) || !isfinite(r.im)) atomicOr(flag, 16);
+        T[idx] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+template <typename T>
+static lm_status dalloc(lm_tree_s *t, T **p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        lm_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return LM_ENOMEM;
+    }
+    t->bytes += count * sizeof(T);
+    return LM_OK;
+}
+#define TRY(x)                       \
+    do {                             \
+        lm_status s_ = (x);          \
+        if (s_ != LM_OK) return s_;  \
+    } while (0)
+
+static int grid_for(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+lm_status lm_setup_tree(lm_tree_s *t, const double *x, const double *y, cudaStream_t st)
+{
+    const int64_t n = t->n;
+    const double d = t->med.d;
+    TRY(dalloc(t, &t->dflag, 4));
+    LM_CUDA(cudaMemsetAsync(t->dflag, 0, 4 * sizeof(int), st));
+    int nb = (int)std::min<int64_t>(1024, (n + 255) / 256);
+    double *bmin, *bmax;
+    TRY(dalloc(t, &bmin, nb));
+    TRY(dalloc(t, &bmax, nb));
+    k_minmax<<<nb, 256, 0, st>>>(x, y, n, d, bmin, bmax, t->dflag);
+    std::vector<double> hmin(nb), hmax(nb);
+    int hflag = 0;
+    LM_CUDA(cudaMemcpyAsync(hmin.data(), bmin, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaMemcpyAsync(hmax.data(), bmax, nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaMemcpyAsync(&hflag, t->dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaStreamSynchronize(st));
+    cudaFree(bmin);
+    cudaFree(bmax);
+    t->bytes -= 2 * nb * sizeof(double);
+    if (hflag & 1) {
+        lm_set_error("build_tree: a point is non-finite or not strictly inside -d < y < 0");
+        return LM_EINVAL;
+    }
+    double mn = hmin[0], mx = hmax[0];
+    for (int i = 1; i < nb; ++i) {
+        mn = fmin(mn, hmin[i]);
+        mx = fmax(mx, hmax[i]);
+    }
+    double f0 = floor(mn / d), f1 = floor(mx / d);
+    t->x0 = f0 * d;
+    t->R = (int)(f1 - f0) + 1;
+    if (t->med.opt.depth >= 0) {
+        t->L = t->med.opt.depth;
+    } else {
+        int L = 0;
+        while ((double)n > (double)t->med.opt.leaf_target * t->R * pow(4.0, L)) ++L;
+        t->L = L;
+    }
+    const int L = t->L;
+    const int64_t ncol = (int64_t)t->R << L, nrow = (int64_t)1 << L;
+    t->nleaf = ncol * nrow;
+    if (t->nleaf > (int64_t)1 << 30) {
+        lm_set_error("build_tree: %lld leaves is beyond this build", (long long)t->nleaf);
+        return LM_ENOTSUP;
+    }
+    int32_t *key, *cnt, *cursor;
+    int64_t *tmp;
+    TRY(dalloc(t, &key, n));
+    TRY(dalloc(t, &cnt, t->nleaf));
+    TRY(dalloc(t, &cursor, t->nleaf));
+    TRY(dalloc(t, &t->leaf_start, t->nleaf + 1));
+    TRY(dalloc(t, &t->perm, n));
+    LM_CUDA(cudaMemsetAsync(cnt, 0, t->nleaf * sizeof(int32_t), st));
+    LM_CUDA(cudaMemsetAsync(cursor, 0, t->nleaf * sizeof(int32_t), st));
+    double w = ldexp(d, -L);
+    k_keys<<<grid_for(n, 256), 256, 0, st>>>(x, y, n, t->x0, w, ncol, nrow, key, cnt);
+    k_scan<<<1, 1024, 0, st>>>(cnt, t->nleaf, t->leaf_start);
+    tmp = t->perm;
+    k_scatter<<<grid_for(n, 256), 256, 0, st>>>(key, n, t->leaf_start, cursor, tmp);
+    k_leafsort<<<(unsigned)t->nleaf, 256, 0, st>>>(t->leaf_start, t->perm, t->dflag);
+    TRY(dalloc(t, &t->xs, n));
+    TRY(dalloc(t, &t->ys, n));
+    k_gather_pts<<<grid_for(n, 256), 256, 0, st>>>(x, y, t->perm, n, t->xs, t->ys);
+    LM_CUDA(cudaGetLastError());
+    LM_CUDA(cudaMemcpyAsync(&hflag, t->dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaStreamSynchronize(st));
+    cudaFree(key);
+    cudaFree(cnt);
+    cudaFree(cursor);
+    t->bytes -= (n + 2 * t->nleaf) * sizeof(int32_t);
+    if (hflag & 2) {
+        lm_set_error("build_tree: a leaf holds more than %d points; use a deeper tree", LM_MAXLEAF);
+        return LM_ENOTSUP;
+    }
+    return LM_OK;
+}
+
+// classes (term, dc, dr) reachable under the list rules at level l
+static void enumerate_classes(int l, int R, std::vector<std::tuple<int, int, int>> &out)
+{
+    const int64_t nrow = (int64_t)1 << l, ncol = (int64_t)R << l;
+    std::map<std::tuple<int, int, int>, int> seen;
+    for (int term = 0; term < 5; ++term)
+        for (int64_t rt = 0; rt < nrow; ++rt) {
+            int64_t rlo = 0, rhi = nrow - 1;
+            if (l > 0) {
+                int64_t a = src_row(term, rt - 3, nrow), b = src_row(term, rt + 3, nrow);
+                rlo = std::max((int64_t)0, std::min(a, b));
+                rhi = std::min(nrow - 1, std::max(a, b));
+            }
+            for (int64_t rs = rlo; rs <= rhi; ++rs) {
+                int64_t ri = img_row(term, rs, nrow);
+                if (l == 0) {
+                    for (int64_t cs = 0; cs < ncol; ++cs) {
+                        int64_t ct = 0; // all dc are reached by some pair at level 0
+                        for (ct = 0; ct < ncol; ++ct)
+                            if (v_rule(0, ct, rt, cs, ri)) seen[{term, (int)(ct - cs), (int)(rt - ri)}] = 1;
+                    }
+                } else {
+                    for (int64_t ct = 8; ct <= 9; ++ct)
+                        for (int64_t cs = ct - 3; cs <= ct + 3; ++cs)
+                            if (v_rule(l, ct, rt, cs, ri)) seen[{term, (int)(ct - cs), (int)(rt - ri)}] = 1;
+                }
+            }
+        }
+    for (auto &kv : seen) out.push_back(kv.first);
+}
+
+lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
+{
+    const int L = t->L, P = t->p, np = 2 * P + 1;
+    const double k = t->med.k2, d = t->med.d;
+    MediumD md{t->med.k1, t->med.k2, t->med.k3, t->med.d};
+    t->lev.resize(L + 1);
+    // scale vectors
+    for (int l = 0; l <= L; ++l) {
+        Level &lv = t->lev[l];
+        lv.l = l;
+        lv.ncol = (int64_t)t->R << l;
+        lv.nrow = (int64_t)1 << l;
+        lv.nbox = lv.ncol * lv.nrow;
+        lv.w = ldexp(d, -l);
+        std::vector<double> sc(P + 1);
+        double f = 0.5 * k * lv.w, v = 1.0;
+        for (int n = 0; n <= P; ++n) {
+            sc[n] = v;
+            v *= f / (n + 1);
+        }
+        TRY(dalloc(t, &lv.scale, P + 1));
+        LM_CUDA(cudaMemcpyAsync(lv.scale, sc.data(), (P + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+        TRY(dalloc(t, &lv.M, lv.nbox * np * LM_MAXV));
+        TRY(dalloc(t, &lv.Lc, lv.nbox * np * LM_MAXV));
+    }
+    // shift tables
+    for (int l = 0; l <= L; ++l) {
+        Level &lv = t->lev[l];
+        lv.m2m = nullptr;
+        lv.l2l = nullptr;
+        if (l < L) TRY(dalloc(t, &lv.m2m, 4 * np * np));
+        if (l > 0) TRY(dalloc(t, &lv.l2l, 4 * np * np));
+    }
+    for (int l = 0; l < L; ++l) {
+        // child level l+1 -> parent level l
+        Level &par = t->lev[l], &ch = t->lev[l + 1];
+        k_shift_tables<<<grid_for(4 * np * np, 128), 128, 0, st>>>(k, P, ch.w, ch.scale, par.scale,
+                                                                   par.m2m, ch.l2l);
+    }
+    // lists and M2L classes
+    for (int l = 0; l <= L; ++l) {
+        Level &lv = t->lev[l];
+        std::vector<std::tuple<int, int, int>> cls;
+        enumerate_classes(l, t->R, cls);
+        int DC = l == 0 ? (int)std::max<int64_t>(3, lv.ncol - 1) : 3;
+        std::vector<int32_t> smap((size_t)5 * (2 * DC + 1) * 7, -1);
+        for (size_t i = 0; i < cls.size(); ++i) {
+            int term = std::get<0>(cls[i]), dc = std::get<1>(cls[i]), dr = std::get<2>(cls[i]);
+            lv.cls_term.push_back(term);
+            lv.cls_dc.push_back(dc);
+            lv.cls_dr.push_back(dr);
+            smap[slot_index(DC, term, dc, dr)] = (int32_t)i;
+        }
+        int32_t *dmap;
+        TRY(dalloc(t, &dmap, smap.size()));
+        LM_CUDA(cudaMemcpyAsync(dmap, smap.data(), smap.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRY(dalloc(t, &lv.vstart, lv.nbox + 1));
+        k_vlist<<<grid_for(lv.nbox, 128), 128, 0, st>>>(l, lv.ncol, lv.nrow, DC, dmap, lv.vstart,
+                                                        nullptr, nullptr, nullptr, 0, t->dflag);
+        k_scan64<<<1, 1024, 0, st>>>(lv.vstart, lv.nbox);
+        LM_CUDA(cudaMemcpyAsync(&lv.nv, lv.vstart + lv.nbox, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        LM_CUDA(cudaStreamSynchronize(st));
+        TRY(dalloc(t, &lv.vsrc, lv.nv));
+        TRY(dalloc(t, &lv.vslot, lv.nv));
+        TRY(dalloc(t, &lv.vterm, lv.nv));
+        k_vlist<<<grid_for(lv.nbox, 128), 128, 0, st>>>(l, lv.ncol, lv.nrow, DC, dmap, lv.vstart,
+                                                        lv.vsrc, lv.vslot, lv.vterm, 1, t->dflag);
+        // tables
+        int ncls = (int)cls.size();
+        TRY(dalloc(t, &lv.tab, (size_t)std::max(1, ncls) * np * np));
+        std::vector<int> fdc, fdr, fidx, idc, idr, iterm, iidx;
+        for (int i = 0; i < ncls; ++i) {
+            if (lv.cls_term[i] == 0) {
+                fdc.push_back(lv.cls_dc[i]);
+                fdr.push_back(lv.cls_dr[i]);
+                fidx.push_back(i);
+            } else {
+                iterm.push_back(lv.cls_term[i]);
+                idc.push_back(lv.cls_dc[i]);
+                idr.push_back(lv.cls_dr[i]);
+                iidx.push_back(i);
+            }
+        }
+        int *dbuf;
+        int nf = (int)fdc.size(), ni = (int)idc.size();
+        TRY(dalloc(t, &dbuf, 3 * nf + 4 * ni + 1));
+        std::vector<int> hb;
+        hb.insert(hb.end(), fdc.begin(), fdc.end());
+        hb.insert(hb.end(), fdr.begin(), fdr.end());
+        hb.insert(hb.end(), fidx.begin(), fidx.end());
+        hb.insert(hb.end(), iterm.begin(), iterm.end());
+        hb.insert(hb.end(), idc.begin(), idc.end());
+        hb.insert(hb.end(), idr.begin(), idr.end());
+        hb.insert(hb.end(), iidx.begin(), iidx.end());
+        if (!hb.empty())
+            LM_CUDA(cudaMemcpyAsync(dbuf, hb.data(), hb.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+        if (nf > 0) {
+            dim3 g(grid_for(np * np, 256), nf);
+            k_free_m2l<<<g, 256, 0, st>>>(k, P, lv.w, dbuf, dbuf + nf, dbuf + 2 * nf, nf, lv.scale, lv.tab);
+        }
+        if (ni > 0) {
+            size_t shm = (2 * TB_CHUNK * np + TB_CHUNK) * sizeof(zd);
+            LM_CUDA(cudaFuncSetAttribute(k_image_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            k_image_m2l<<<ni, 256, shm, st>>>(md, P, lv.w, k * lv.w, dbuf + 3 * nf, dbuf + 3 * nf + ni,
+                                              dbuf + 3 * nf + 2 * ni, dbuf + 3 * nf + 3 * ni, ni, lv.tab,
+                                              t->dflag);
+        }
+        LM_CUDA(cudaGetLastError());
+        LM_CUDA(cudaStreamSynchronize(st));
+        cudaFree(dbuf);
+        cudaFree(dmap);
+        t->bytes -= (3 * nf + 4 * ni + 1) * sizeof(int) + smap.size() * sizeof(int32_t);
+    }
+    // U list
+    {
+        const int64_t ncol = (int64_t)t->R << L, nrow = (int64_t)1 << L;
+        TRY(dalloc(t, &t->ustart, t->nleaf + 1));
+        k_ulist<<<grid_for(t->nleaf, 128), 128, 0, st>>>(ncol, nrow, t->ustart, nullptr, nullptr, 0);
+        k_scan64<<<1, 1024, 0, st>>>(t->ustart, t->nleaf);
+        LM_CUDA(cudaMemcpyAsync(&t->nu, t->ustart + t->nleaf, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        LM_CUDA(cudaStreamSynchronize(st));
+        TRY(dalloc(t, &t->usrc, t->nu));
+        TRY(dalloc(t, &t->uterm, t->nu));
+        k_ulist<<<grid_for(t->nleaf, 128), 128, 0, st>>>(ncol, nrow, t->ustart, t->usrc, t->uterm, 1);
+    }
+    // near-field quadrature
+    {
+        NearQuad &q = t->nq;
+        double km = fmax(md.k1, fmax(md.k2, md.k3)), kmin = fmin(md.k1, fmin(md.k2, md.k3));
+        q.c = 1.5 * km + 1.0;
+        double a = 0.5, delta = fmin(0.25, 0.5 * kmin);
+        int nflat = (int)ceil((q.c - 2.0 * delta) / 1.0);
+        int order = t->med.opt.seg_order;
+        q.nseg = (nflat + 2) * order;
+        q.nray = t->med.opt.tail_rays;
+        q.ntail = t->med.opt.tail_order;
+        TRY(dalloc(t, &q.seg_lam, q.nseg));
+        TRY(dalloc(t, &q.seg_s2, q.nseg));
+        TRY(dalloc(t, &q.seg_w, 2 * q.nseg));
+        int nt = q.nray * q.ntail;
+        TRY(dalloc(t, &q.tail_lam, nt));
+        TRY(dalloc(t, &q.tail_s2, nt));
+        TRY(dalloc(t, &q.tail_w, 2 * nt));
+        k_near_seg<<<grid_for(q.nseg, 64), 64, 0, st>>>(md, q.c, a, delta, nflat, order, q.seg_lam,
+                                                         q.seg_s2, q.seg_w, q.nseg);
+        k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2,
+                                                      q.tail_w);
+    }
+    // tree-order scratch for densities and potentials
+    TRY(dalloc(t, &t->qs, (size_t)LM_MAXV * t->n));
+    TRY(dalloc(t, &t->us, (size_t)LM_MAXV * t->n));
+    int hflag = 0;
+    LM_CUDA(cudaGetLastError());
+    LM_CUDA(cudaMemcpyAsync(&hflag, t->dflag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaStreamSynchronize(st));
+    if (hflag & 4) {
+        lm_set_error("build_tree: internal error, an interaction has no translation class");
+        return LM_ECUDA;
+    }
+    if (hflag & 8) {
+        lm_set_error("build_tree: expansion order too large for the table builder");
+        return LM_ENOTSUP;
+    }
+    if (hflag & 16) {
+        lm_set_error("build_tree: a layered M2L table overflowed; lower p");
+        return LM_ENOTSUP;
+    }
+    return LM_OK;
+}
+
+lm_status lm_list_to_host(lm_tree_s *t, int which, int level, std::vector<int64_t> &rows,
+                          cudaStream_t st)
+{
+    int64_t nb, ne;
+    const int64_t *start;
+    const int32_t *src, *term;
+    if (which == 0) {
+        if (level < 0 || level > t->L) {
+            lm_set_error("list_export: level %d out of range", level);
+            return LM_EINVAL;
+        }
+        Level &lv = t->lev[level];
+        nb = lv.nbox;
+        ne = lv.nv;
+        start = lv.vstart;
+        src = lv.vsrc;
+        term = lv.vterm;
+    } else {
+        nb = t->nleaf;
+        ne = t->nu;
+        start = t->ustart;
+        src = t->usrc;
+        term = t->uterm;
+    }
+    std::vector<int64_t> hs(nb + 1);
+    std::vector<int32_t> hsrc(ne), hterm(ne);
+    LM_CUDA(cudaMemcpyAsync(hs.data(), start, (nb + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (ne > 0) {
+        LM_CUDA(cudaMemcpyAsync(hsrc.data(), src, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        LM_CUDA(cudaMemcpyAsync(hterm.data(), term, ne * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    }
+    LM_CUDA(cudaStreamSynchronize(st));
+    rows.resize(3 * ne);
+    for (int64_t b = 0; b < nb; ++b)
+        for (int64_t e = hs[b]; e < hs[b + 1]; ++e) {
+            rows[3 * e] = b;
+            rows[3 * e + 1] = hterm[e];
+            rows[3 * e + 2] = hsrc[e];
+        }
+    return LM_OK;
+}
+
+void lm_free_tree_device(lm_tree_s *t)
+{
+    void *ptrs[] = {t->xs, t->ys, t->perm, t->leaf_start, t->ustart, t->usrc, t->uterm, t->qs, t->us,
+                    t->dflag, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
+                    t->nq.tail_w};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (Level &lv : t->lev) {
+        void *lp[] = {lv.vstart, lv.vsrc, lv.vslot, lv.vterm, lv.tab, lv.scale, lv.m2m, lv.l2l, lv.M, lv.Lc, lv.tab32};
+        for (void *p : lp)
+            if (p) cudaFree(p);
+    }
+}

@@ -1,0 +1,140 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle."""
+import os
+from math import factorial
+
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+HERE = os.path.dirname(os.path.abspath(__file__))
+MED_A = workloads.MEDIUM_A
+
+
+@pytest.fixture(scope="module")
+def lm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests")
+    import paper_1902_08250_gb300 as lm
+
+    return lm
+
+
+def _dev(*arrs):
+    import torch
+
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def _run(lm, med, x, y, q, **opt):
+    import torch
+
+    m = lm.create_medium(*med, **opt)
+    xd, yd = _dev(x, y)
+    t = lm.build_tree(m, xd, yd)
+    u = lm.apply(t, torch.from_numpy(np.ascontiguousarray(q)).cuda())
+    torch.cuda.synchronize()
+    return t, u.cpu().numpy()
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_tree_and_lists_bit_exact(lm, oracle):
+    for (x, y, _), L in ((workloads.small_uniform(), 3), (workloads.clustered(6000), 4)):
+        m = lm.create_medium(*MED_A, p=4, depth=L)
+        xd, yd = _dev(x, y)
+        t = lm.build_tree(m, xd, yd)
+        perm, ls = t.export()
+        x0, R, operm, ols = oracle.tree_build(x, y, MED_A[3], L)
+        assert t.info["x_origin"] == x0 and t.info["R"] == R and t.info["depth"] == L
+        assert np.array_equal(perm, operm) and np.array_equal(ls, ols)
+        for l in range(L + 1):
+            assert np.array_equal(t.list_export(0, l), oracle.vlist(R, l)), l
+        assert np.array_equal(t.list_export(1), oracle.ulist(R, L))
+
+
+def test_m2l_tables_match_oracle(lm, oracle):
+    x, y, _ = workloads.small_uniform()
+    P, L = 8, 3
+    m = lm.create_medium(*MED_A, p=P, depth=L)
+    xd, yd = _dev(x, y)
+    t = lm.build_tree(m, xd, yd)
+    k, d = MED_A[1], MED_A[3]
+    for l in range(L + 1):
+        V = t.list_export(0, l)
+        ncol, nrow = t.info["R"] << l, 1 << l
+        w = d / 2 ** l
+        sc = np.array([(0.5 * k * w) ** abs(n) / factorial(abs(n)) for n in range(-P, P + 1)])
+        S = np.outer(sc, sc)
+        seen = set()
+        for tb, term, sb in V:
+            rt, ct = divmod(int(tb), ncol)
+            rs, cs = divmod(int(sb), ncol)
+            ri = [rs, -1 - rs, 2 * nrow - 1 - rs, rs - 2 * nrow, rs + 2 * nrow][term]
+            key = (int(term), ct - cs, rt - ri)
+            if key in seen or (len(seen) > 12 and term == 0):
+                continue
+            seen.add(key)
+            A = t.m2l_table(l, *key)
+            if term == 0:
+                ref = oracle.m2l_free_table(k, (ct - cs) * w, -(rt - ri) * w, P)
+            else:
+                ref = oracle.m2l_image_table(MED_A, int(term), (ct - cs) * w, abs(rt - ri) * w, P)
+            err = np.max(np.abs((A - ref) * S)) / np.max(np.abs(ref * S))
+            assert err < 1e-11, (l, key, err)
+
+
+def test_fmm_matches_oracle_fmm_at_same_order(lm, oracle):
+    x, y, q = workloads.uniform_strip(300, 0.0, 2.0, -0.9, -0.1, nvec=2, seed=3)
+    P, L = 10, 2
+    _, u = _run(lm, MED_A, x, y, q, p=P, depth=L)
+    ref = oracle.fmm_apply(MED_A, x, y, q, L, P)
+    assert rel(u, ref) < 1e-11
+
+
+def test_fmm_fp64_matches_direct_sum(lm):
+    g = np.load(os.path.join(HERE, "golden", "small_direct.npz"))
+    x, y, q = workloads.small_uniform()
+    _, u = _run(lm, MED_A, x, y, q, p=22, depth=3)
+    assert rel(u[0], g["u"][0]) < 1e-10
+
+
+def test_adjoint_and_multivector(lm):
+    import torch
+
+    x, y, q = workloads.uniform_strip(2000, 0.0, 3.0, -0.9, -0.1, nvec=20, seed=5)
+    m = lm.create_medium(*MED_A, p=14, depth=3)
+    xd, yd = _dev(x, y)
+    t = lm.build_tree(m, xd, yd)
+    qd = torch.from_numpy(q).cuda()
+    u = lm.apply(t, qd).cpu().numpy()
+    u1 = lm.apply(t, qd[7].contiguous()).cpu().numpy()
+    assert np.array_equal(u[7], u1)               # chunking over 16 vectors is exact
+    w = lm.apply_adjoint(t, qd).cpu().numpy()
+    # <G a, b> = <a, G^H b>
+    lhs = np.vdot(q[1], u[0])
+    rhs = np.vdot(w[1], q[0])
+    assert abs(lhs - rhs) < 1e-9 * abs(lhs)
+
+
+def test_single_point_and_invalid_points(lm, oracle):
+    import torch
+
+    x, y = np.array([0.3]), np.array([-0.4])
+    q = np.array([[1.0 + 0.5j]])
+    _, u = _run(lm, MED_A, x, y, q, p=8)
+    ref = oracle.direct_apply(MED_A, x, y, q)
+    assert rel(u, ref) < 1e-11
+    m = lm.create_medium(*MED_A, p=8)
+    xd, yd = _dev(np.array([0.1, 0.2]), np.array([-0.5, 0.0]))  # a point on y = 0
+    with pytest.raises(lm.LMError) as e:
+        lm.build_tree(m, xd, yd)
+    assert e.value.status == 1
+    xd, yd = _dev(np.array([0.1, np.nan]), np.array([-0.5, -0.2]))
+    with pytest.raises(lm.LMError):
+        lm.build_tree(m, xd, yd)
