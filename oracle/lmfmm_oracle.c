@@ -526,6 +526,9 @@ static int green_refl(const orc_medium *m, double x, double y, double x0, double
     int st = 0;
     cx seg = 0.0;
     r.mask = mask;
+    /* the four terms can cancel in the sum: measure the error against the
+     * integrand's L1 size, not against the (possibly much smaller) integral */
+    g_l1 = 1;
     st |= sommerfeld(F_refl, &r, km, X, 0, 0.0, 1, 0, &seg);
     cx tails = 0.0;
     for (int dir = 0; dir < 2; ++dir) {
@@ -545,6 +548,7 @@ static int green_refl(const orc_medium *m, double x, double y, double x0, double
         st |= sommerfeld(F_refl, &r, km, X, dir, dir == 0 ? hmin : X, 0, 1, &tl);
         tails += tl;
     }
+    g_l1 = 0;
     *out = seg + tails;
     return st;
 }
