@@ -168,6 +168,30 @@ lm_status lm_list_export(lm_tree t, int which, int level, int64_t *out, int64_t 
 lm_status lm_m2l_table_export(lm_tree t, int level, int term, int dc, int dr, double *out,
                               void *stream);
 
+/*
+ * Phase profiling (instrumentation, no counterpart in the paper).  While
+ * enabled, lm_apply records a pair of CUDA events around each phase on the
+ * launching stream: 0 permute, 1 S2M, 2 M2M, 3 M2L, 4 L2L, 5 L2T + S2T,
+ * 6 mixed-precision refinement.
+ *   profile_begin: enable for at most max_applies applies (allocates host
+ *     event handles only; LM_EINVAL if max_applies < 1).
+ *   profile_end: synchronise on the recorded events, write per-phase total
+ *     milliseconds and kernel-launch counts into host arrays of nphase
+ *     entries (either may be NULL), and disable.  Applies beyond max_applies
+ *     are not recorded.
+ */
+lm_status lm_profile_begin(lm_tree t, int max_applies);
+lm_status lm_profile_end(lm_tree t, double *ms, int64_t *launches, int nphase, int *applies);
+
+/*
+ * Peak probe (instrumentation): time `iters` dependent-chain iterations of
+ * one arithmetic unit on every SM and return the achieved operation rate.
+ *   kind: 0 = FP64 FMA, 1 = FP32 FMA, 2 = FP32 sin/cos (SFU path), 3 = FP64 exp.
+ *   *rate receives operations per second (an FMA counts 2 flops for kinds
+ *   0 and 1, i.e. the value is FLOP/s).  Synchronises `stream`.
+ */
+lm_status lm_peak_probe(int kind, int64_t iters, void *stream, double *rate);
+
 void lm_destroy_tree(lm_tree t);
 void lm_destroy_medium(lm_medium m);
 const char *lm_status_string(lm_status s);

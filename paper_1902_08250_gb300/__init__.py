@@ -60,6 +60,9 @@ def _load():
         "lm_tree_export": (I, [V, P, P, P]),
         "lm_list_export": (I, [V, I, I, P, I64, P, P]),
         "lm_m2l_table_export": (I, [V, I, I, I, I, P, P]),
+        "lm_profile_begin": (I, [V, I]),
+        "lm_profile_end": (I, [V, P, P, I, P]),
+        "lm_peak_probe": (I, [I, I64, P, P]),
         "lm_destroy_tree": (None, [V]),
         "lm_destroy_medium": (None, [V]),
         "lm_status_string": (ctypes.c_char_p, [I]),

@@ -84,7 +84,19 @@ struct lm_tree_s {
     zd *qs, *us; // [LM_MAXV][n] tree-order scratch
     int *dflag;  // device error flag
     int64_t bytes;
+    // phase profiling
+    int prof_max, prof_used;
+    std::vector<cudaEvent_t> prof_ev; // [prof_max][LM_NPHASE][2]
+    int64_t prof_launch[8];
+    int prof_occ[8];             // occurrences of each phase in the apply being recorded
+    std::vector<int> prof_nocc;  // [prof_max][LM_NPHASE]
 };
+
+#define LM_NPHASE 7
+enum { PH_PERMUTE = 0, PH_S2M, PH_M2M, PH_M2L, PH_L2L, PH_LEAF, PH_REFINE };
+// record phase boundaries of the apply in progress (no-ops unless profiling)
+void lm_phase_begin(lm_tree_s *t, int ph, cudaStream_t st);
+void lm_phase_end(lm_tree_s *t, int ph, cudaStream_t st, int launches);
 
 // setup (lmfmm_setup.cu)
 lm_status lm_setup_tree(lm_tree_s *t, const double *x, const double *y, cudaStream_t st);

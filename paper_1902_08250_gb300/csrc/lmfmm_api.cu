@@ -11,6 +11,8 @@
 #include "internal.h"
 
 static thread_local char g_err[512] = "";
+void lm_profile_apply_start(lm_tree_s *t);
+void lm_profile_apply_stop(lm_tree_s *t);
 
 void lm_set_error(const char *fmt, ...)
 {
@@ -110,6 +112,7 @@ extern "C" void lm_destroy_medium(lm_medium m) { delete m; }
 extern "C" void lm_destroy_tree(lm_tree t)
 {
     if (!t) return;
+    for (cudaEvent_t e : t->prof_ev) cudaEventDestroy(e);
     lm_free_tree_device(t);
     delete t;
 }
@@ -172,14 +175,20 @@ extern "C" lm_status lm_apply(lm_tree t, const void *q, int nvec, void *u, void 
 {
     lm_status s = check_apply(t, q, nvec, u);
     if (s != LM_OK) return s;
-    return lm_run_apply(t, (const zd *)q, nvec, (zd *)u, false, (cudaStream_t)stream);
+    lm_profile_apply_start(t);
+    s = lm_run_apply(t, (const zd *)q, nvec, (zd *)u, false, (cudaStream_t)stream);
+    lm_profile_apply_stop(t);
+    return s;
 }
 
 extern "C" lm_status lm_apply_adjoint(lm_tree t, const void *v, int nvec, void *w, void *stream)
 {
     lm_status s = check_apply(t, v, nvec, w);
     if (s != LM_OK) return s;
-    return lm_run_apply(t, (const zd *)v, nvec, (zd *)w, true, (cudaStream_t)stream);
+    lm_profile_apply_start(t);
+    s = lm_run_apply(t, (const zd *)v, nvec, (zd *)w, true, (cudaStream_t)stream);
+    lm_profile_apply_stop(t);
+    return s;
 }
 
 extern "C" lm_status lm_get_tree_info(lm_tree t, lm_tree_info *info)
@@ -263,5 +272,172 @@ extern "C" lm_status lm_m2l_table_export(lm_tree t, int level, int term, int dc,
             out[2 * ((p + P) * np + (q + P))] = v.re / s;
             out[2 * ((p + P) * np + (q + P)) + 1] = v.im / s;
         }
+    return LM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// phase profiling: each phase of one apply may be entered several times (per
+// level); its events bracket the first begin and the last end of that apply.
+// ---------------------------------------------------------------------------
+static thread_local int tl_apply_slot = -1;
+#define LM_PROF_OCC 24 // event pairs per phase per apply (one per level at most)
+
+// each begin/end pair of a phase gets its own events; the phase total is the
+// sum of its pairs, so phases that interleave level by level are not double counted
+void lm_phase_begin(lm_tree_s *t, int ph, cudaStream_t st)
+{
+    if (t->prof_max == 0 || tl_apply_slot < 0) return;
+    int occ = t->prof_occ[ph];
+    if (occ >= LM_PROF_OCC) return;
+    cudaEventRecord(t->prof_ev[(((size_t)tl_apply_slot * LM_NPHASE + ph) * LM_PROF_OCC + occ) * 2], st);
+}
+void lm_phase_end(lm_tree_s *t, int ph, cudaStream_t st, int launches)
+{
+    if (t->prof_max == 0 || tl_apply_slot < 0) return;
+    int occ = t->prof_occ[ph];
+    if (occ >= LM_PROF_OCC) return;
+    cudaEventRecord(t->prof_ev[(((size_t)tl_apply_slot * LM_NPHASE + ph) * LM_PROF_OCC + occ) * 2 + 1], st);
+    t->prof_occ[ph] = occ + 1;
+    t->prof_launch[ph] += launches;
+}
+
+void lm_profile_apply_start(lm_tree_s *t)
+{
+    tl_apply_slot = -1;
+    if (t->prof_max > 0 && t->prof_used < t->prof_max) {
+        tl_apply_slot = t->prof_used++;
+        for (int i = 0; i < 8; ++i) t->prof_occ[i] = 0;
+    }
+}
+void lm_profile_apply_stop(lm_tree_s *t)
+{
+    if (tl_apply_slot >= 0)
+        for (int i = 0; i < LM_NPHASE; ++i) t->prof_nocc[(size_t)tl_apply_slot * LM_NPHASE + i] = t->prof_occ[i];
+    tl_apply_slot = -1;
+}
+
+extern "C" lm_status lm_profile_begin(lm_tree t, int max_applies)
+{
+    if (!t || max_applies < 1) {
+        lm_set_error("profile_begin: bad argument");
+        return LM_EINVAL;
+    }
+    for (cudaEvent_t e : t->prof_ev) cudaEventDestroy(e);
+    t->prof_ev.assign((size_t)max_applies * LM_NPHASE * LM_PROF_OCC * 2, nullptr);
+    for (auto &e : t->prof_ev) LM_CUDA(cudaEventCreate(&e));
+    t->prof_nocc.assign((size_t)max_applies * LM_NPHASE, 0);
+    t->prof_max = max_applies;
+    t->prof_used = 0;
+    for (int i = 0; i < 8; ++i) t->prof_launch[i] = 0;
+    return LM_OK;
+}
+
+extern "C" lm_status lm_profile_end(lm_tree t, double *ms, int64_t *launches, int nphase, int *applies)
+{
+    if (!t || t->prof_max == 0) {
+        lm_set_error("profile_end: profiling is not enabled");
+        return LM_EINVAL;
+    }
+    std::vector<double> acc(LM_NPHASE, 0.0);
+    for (int a = 0; a < t->prof_used; ++a)
+        for (int ph = 0; ph < LM_NPHASE; ++ph)
+            for (int o = 0; o < t->prof_nocc[(size_t)a * LM_NPHASE + ph]; ++o) {
+                cudaEvent_t *ev = &t->prof_ev[(((size_t)a * LM_NPHASE + ph) * LM_PROF_OCC + o) * 2];
+                LM_CUDA(cudaEventSynchronize(ev[1]));
+                float f = 0.f;
+                LM_CUDA(cudaEventElapsedTime(&f, ev[0], ev[1]));
+                acc[ph] += f;
+            }
+    for (int ph = 0; ph < nphase && ph < LM_NPHASE; ++ph) {
+        if (ms) ms[ph] = acc[ph];
+        if (launches) launches[ph] = t->prof_launch[ph];
+    }
+    if (applies) *applies = t->prof_used;
+    for (cudaEvent_t e : t->prof_ev) cudaEventDestroy(e);
+    t->prof_ev.clear();
+    t->prof_max = 0;
+    t->prof_used = 0;
+    return LM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// peak probe: independent FMA / transcendental chains on every SM
+// ---------------------------------------------------------------------------
+__global__ void k_probe_f64(int64_t iters, double *sink)
+{
+    double a0 = threadIdx.x * 1e-3, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, b = 0.999999, c = 1e-7;
+    for (int64_t i = 0; i < iters; ++i) {
+        a0 = fma(a0, b, c);
+        a1 = fma(a1, b, c);
+        a2 = fma(a2, b, c);
+        a3 = fma(a3, b, c);
+    }
+    if (a0 + a1 + a2 + a3 == 12345.0) sink[0] = a0;
+}
+__global__ void k_probe_f32(int64_t iters, float *sink)
+{
+    float a[8];
+    for (int j = 0; j < 8; ++j) a[j] = threadIdx.x * 1e-3f + j;
+    const float b = 0.999999f, c = 1e-7f;
+    for (int64_t i = 0; i < iters; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) a[j] = fmaf(a[j], b, c);
+    float s = 0.f;
+    for (int j = 0; j < 8; ++j) s += a[j];
+    if (s == 12345.f) sink[0] = s;
+}
+__global__ void k_probe_sfu(int64_t iters, float *sink)
+{
+    float a0 = threadIdx.x * 1e-3f, a1 = a0 + 0.5f;
+    for (int64_t i = 0; i < iters; ++i) {
+        a0 = __sinf(a0) + 0.5f;
+        a1 = __cosf(a1) + 0.25f;
+    }
+    if (a0 + a1 == 12345.f) sink[0] = a0;
+}
+__global__ void k_probe_exp64(int64_t iters, double *sink)
+{
+    double a0 = threadIdx.x * 1e-6, a1 = a0 + 0.1;
+    for (int64_t i = 0; i < iters; ++i) {
+        a0 = exp(-a0) * 0.5;
+        a1 = exp(-a1) * 0.5;
+    }
+    if (a0 + a1 == 12345.0) sink[0] = a0;
+}
+
+extern "C" lm_status lm_peak_probe(int kind, int64_t iters, void *stream, double *rate)
+{
+    if (!rate || iters < 1 || kind < 0 || kind > 3) {
+        lm_set_error("peak_probe: bad argument");
+        return LM_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    LM_CUDA(cudaGetDevice(&dev));
+    LM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    double *sink;
+    LM_CUDA(cudaMalloc(&sink, 64));
+    const int threads = 512, blocks = nsm * 4;
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0));
+    LM_CUDA(cudaEventCreate(&e1));
+    double ops = 0.0;
+    for (int rep = 0; rep < 2; ++rep) { // first run warms up
+        LM_CUDA(cudaEventRecord(e0, st));
+        switch (kind) {
+        case 0: k_probe_f64<<<blocks, threads, 0, st>>>(iters, sink); ops = 4.0 * 2; break;
+        case 1: k_probe_f32<<<blocks, threads, 0, st>>>(iters, (float *)sink); ops = 8.0 * 2; break;
+        case 2: k_probe_sfu<<<blocks, threads, 0, st>>>(iters, (float *)sink); ops = 2.0; break;
+        default: k_probe_exp64<<<blocks, threads, 0, st>>>(iters, sink); ops = 2.0; break;
+        }
+        LM_CUDA(cudaEventRecord(e1, st));
+    }
+    LM_CUDA(cudaEventSynchronize(e1));
+    float msf = 0.f;
+    LM_CUDA(cudaEventElapsedTime(&msf, e0, e1));
+    *rate = ops * (double)iters * blocks * threads / (msf * 1e-3);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
     return LM_OK;
 }

@@ -264,8 +264,11 @@ lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint,
                  t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w};
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
+        lm_phase_begin(t, PH_PERMUTE, st);
         k_permute_in<<<gridn(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->perm, n, nv, adjoint, t->qs);
+        lm_phase_end(t, PH_PERMUTE, st, 1);
         // step 2: upward pass
+        lm_phase_begin(t, PH_S2M, st);
         {
             Level &lv = t->lev[L];
             LeafGeom g{lv.ncol, t->x0, lv.w};
@@ -273,25 +276,34 @@ lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint,
             k_p2m64<<<(unsigned)lv.nbox, 256, shm, st>>>(g, P, k, t->xs, t->ys, t->leaf_start, t->qs, n,
                                                         nv, lv.M);
         }
+        lm_phase_end(t, PH_S2M, st, 1);
+        if (L > 0) lm_phase_begin(t, PH_M2M, st);
         for (int l = L - 1; l >= 0; --l) {
             Level &lv = t->lev[l];
             int64_t tot = lv.nbox * np * nv;
             k_m2m64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.m2m, t->lev[l + 1].M, lv.M);
         }
+        if (L > 0) lm_phase_end(t, PH_M2M, st, L);
+
         // step 3: downward pass
         for (int l = 0; l <= L; ++l) {
             Level &lv = t->lev[l];
             int64_t tot = lv.nbox * np * nv;
+            lm_phase_begin(t, PH_L2L, st);
             if (l == 0)
                 LM_CUDA(cudaMemsetAsync(lv.Lc, 0, lv.nbox * np * LM_MAXV * sizeof(zd), st));
             else
                 k_l2l64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.l2l, t->lev[l - 1].Lc,
                                                          lv.Lc);
+            lm_phase_end(t, PH_L2L, st, l > 0);
+            lm_phase_begin(t, PH_M2L, st);
             if (lv.nv > 0)
                 k_m2l64<<<gridn(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot, lv.tab,
                                                          lv.M, lv.Lc);
+            lm_phase_end(t, PH_M2L, st, lv.nv > 0);
         }
         // step 4: evaluation
+        lm_phase_begin(t, PH_LEAF, st);
         {
             Level &lv = t->lev[L];
             LeafGeom g{lv.ncol, t->x0, lv.w};
@@ -299,7 +311,10 @@ lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint,
                                                        t->ustart, t->usrc, t->uterm, nq, lv.Lc, t->qs, n,
                                                        nv, t->us);
         }
+        lm_phase_end(t, PH_LEAF, st, 1);
+        lm_phase_begin(t, PH_PERMUTE, st);
         k_permute_out<<<gridn(n, 256), 256, 0, st>>>(t->us, t->perm, n, nv, adjoint, u + (int64_t)v0 * n);
+        lm_phase_end(t, PH_PERMUTE, st, 1);
         LM_CUDA(cudaGetLastError());
     }
     return LM_OK;

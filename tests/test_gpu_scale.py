@@ -1,0 +1,48 @@
+"""GPU parity at full size: the 1M-point wide strip (k2 = 8) with the tree,
+lists and tables of the benchmark, checked on sampled outputs the oracle can
+compute one by one.  The density is nonzero on a random subset of sources, so
+each sampled target's exact value is a short oracle sum."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _sparse_case(n, nsrc, ntgt, seed):
+    x, y, _ = workloads.wide_uniform(n, 1, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    perm = rng.permutation(n)
+    src = np.sort(perm[:nsrc])
+    tg = np.sort(perm[nsrc:nsrc + ntgt])          # targets that carry no density
+    q = np.zeros((2, n), np.complex128)
+    q[:, src] = rng.standard_normal((2, nsrc)) + 1j * rng.standard_normal((2, nsrc))
+    return x, y, q, src, tg
+
+
+@pytest.fixture(scope="module")
+def case(oracle):
+    import torch
+
+    x, y, q, src, tg = _sparse_case(1_000_000, 1500, 48, seed=7)
+    # exact values at the sampled targets: the oracle sum over the nonzero sources
+    xs = np.concatenate([x[src], x[tg]])
+    ys = np.concatenate([y[src], y[tg]])
+    qq = np.concatenate([q[:, src], np.zeros((2, tg.size))], axis=1)
+    ref = oracle.direct_apply(workloads.MEDIUM_B, xs, ys, qq, targets=np.arange(src.size, src.size + tg.size))
+    return x, y, q, tg, ref, torch
+
+
+@pytest.mark.parametrize("p,tol", [(20, 1e-8), (26, 1e-10)])
+def test_wide_strip_fp64_sampled(case, p, tol):
+    import paper_1902_08250_gb300 as lm
+
+    x, y, q, tg, ref, torch = case
+    m = lm.create_medium(*workloads.MEDIUM_B, p=p)
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    assert t.info["R"] == 20
+    u = lm.apply(t, torch.from_numpy(q).cuda()).cpu().numpy()[:, tg]
+    err = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+    print(f"wide strip fp64 p={p} depth={t.info['depth']}: rel-l2 {err:.3e} on {tg.size} sampled targets")
+    assert err < tol
