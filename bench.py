@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--p", type=int, default=0)
+    ap.add_argument("--depth", type=int, default=-2, help="tree depth (-1 automatic; default per precision)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     return ap.parse_args()
@@ -212,7 +213,8 @@ def main():
     precision = args.precision
     if precision == "auto":
         precision = "mixed" if getattr(lm, "HAS_MIXED", False) else "fp64"
-    p = args.p or (24 if precision == "mixed" else 24)
+    p = args.p or (14 if precision == "mixed" else 20)
+    depth = args.depth if args.depth != -2 else (5 if precision == "mixed" else 6)
     x, y, q = workloads.wide_uniform(args.n, NVEC, seed=0)
     med = workloads.MEDIUM_B
     xd = torch.from_numpy(x).to(dev)
@@ -221,8 +223,8 @@ def main():
     ud = torch.empty_like(qd)
     stream = torch.cuda.current_stream(dev)
 
-    def make(prec):
-        m = lm.create_medium(*med, p=p, precision=prec, depth=-1, leaf_target=48)
+    def make(prec, pp=None, dd=None):
+        m = lm.create_medium(*med, p=pp or p, precision=prec, depth=depth if dd is None else dd)
         t0 = time.time()
         tr = lm.build_tree(m, xd, yd)
         torch.cuda.synchronize(dev)
@@ -288,7 +290,7 @@ def main():
     rel_err = None
     fp64_val = None
     if precision == "mixed" and not args.no_fp64_compare:
-        ref_tree, _ = make("fp64")
+        ref_tree, _ = make("fp64", 20, 6)
         uref = lm.apply(ref_tree, qd)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)

@@ -52,7 +52,9 @@ typedef enum {
 
 typedef enum {
     LM_FP64 = 0, /* every step in IEEE double */
-    LM_MIXED = 1 /* near field and expansions in FP32, tables built in FP64 */
+    LM_MIXED = 1 /* tables built in FP64 and rounded to FP32; expansions, M2L and
+                    near field in FP32 with FP32 accumulation; p in {4, 6, 8..14, 16,
+                    18, 20, 24} */
 } lm_precision;
 
 typedef struct {
@@ -62,7 +64,7 @@ typedef struct {
     int precision;   /* lm_precision */
     int max_nvec;    /* largest nvec one apply processes at once (larger nvec is
                         processed in chunks); 0 -> 16 */
-    int seg_order;   /* near-field contour: Gauss-Legendre points per segment panel; 0 -> 16 */
+    int seg_order;   /* near-field contour: Gauss-Legendre points per segment panel; 0 -> 16 (FP64), 10 (mixed) */
     int tail_order;  /* near-field tail: Gauss-Legendre points per ray; 0 -> 64 (FP64), 24 (mixed) */
     int tail_rays;   /* near-field tail: rays between the north and east directions; 0 -> 9 */
 } lm_options;

@@ -19,6 +19,8 @@ import os
 
 from . import _build
 
+HAS_MIXED = True
+
 __all__ = [
     "LMError", "Medium", "Tree", "create_medium", "build_tree", "apply", "apply_adjoint", "library_path",
     "FP64", "MIXED",
@@ -110,7 +112,7 @@ class Medium:
 
 
 def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
-                  seg_order=16, tail_order=0, tail_rays=9) -> Medium:
+                  seg_order=0, tail_order=0, tail_rays=9) -> Medium:
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
     o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays)

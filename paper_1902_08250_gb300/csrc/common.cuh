@@ -112,7 +112,7 @@ __device__ __forceinline__ void bessel_j_scaled(int nmax, T x, T sc, T *out)
         jn1 = jn;
         jn = jm;
         if (n - 1 <= nmax) out[n - 1] = jm;
-        if (fabs((double)jn) > (double)big) {
+        if (jn > big || jn < -big) {
             const T s = (T)1 / big;
             jn *= s;
             jn1 *= s;

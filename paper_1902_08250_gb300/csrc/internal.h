@@ -59,8 +59,15 @@ struct Level {
     zd *m2m;         // [4][np][np]: child (level l+1) -> this level's box (l < L)
     zd *l2l;         // [4][np][np]: parent (level l-1) -> child at this level (l > 0)
     zd *M, *Lc;      // [nbox][np][LM_MAXV]
-    // mixed-precision copies
-    float *tab32;    // [nclass][2np][2np] real-block form
+    // mixed-precision copies (FP32, rounded from the FP64 tables)
+    zf *tab32;       // [nclass][np][np]
+    zf *m2m32, *l2l32; // [4][np][np]
+    zf *M32, *L32;   // [nbox][np][LM_MAXV]
+    int32_t *stencil; // [7][7] class index of the free-space offset (dc, dr) + 3, or -1
+    // entries not covered by the free-space stencil kernel (level 0, image terms)
+    int64_t nrest;
+    int64_t *rstart; // [nbox + 1]
+    int32_t *rsrc, *rslot;
 };
 
 struct lm_tree_s {
@@ -82,6 +89,10 @@ struct lm_tree_s {
     std::vector<Level> lev;
     NearQuad nq;
     zd *qs, *us; // [LM_MAXV][n] tree-order scratch
+    // mixed path
+    float *xl32, *yl32, *y32; // leaf-local coordinates and absolute y, FP32 [n]
+    zf *qs32, *us32;           // [n][LM_MAXV]
+    zf *nq_seg_lam, *nq_seg_s2, *nq_seg_w, *nq_tail_lam, *nq_tail_s2, *nq_tail_w;
     int *dflag;  // device error flag
     int64_t bytes;
     // phase profiling
@@ -106,3 +117,19 @@ lm_status lm_list_to_host(lm_tree_s *t, int which, int level, std::vector<int64_
 void lm_free_tree_device(lm_tree_s *t);
 // apply (lmfmm_apply.cu)
 lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);
+// mixed precision (lmfmm_mixed.cu)
+lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st);
+lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);
+void lm_free_mixed(lm_tree_s *t);
+template <typename T>
+lm_status lm_dalloc(lm_tree_s *t, T **p, size_t count)
+{
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        lm_set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+        return LM_ENOMEM;
+    }
+    t->bytes += count * sizeof(T);
+    return LM_OK;
+}

@@ -48,7 +48,7 @@ extern "C" lm_status lm_options_default(lm_options *o)
     o->leaf_target = 48;
     o->precision = LM_FP64;
     o->max_nvec = 16;
-    o->seg_order = 16;
+    o->seg_order = 0;
     o->tail_order = 0;
     o->tail_rays = 9;
     return LM_OK;
@@ -74,7 +74,7 @@ extern "C" lm_status lm_create_medium(double k1, double k2, double k3, double d,
     if (o.p == 0) o.p = 20;
     if (o.leaf_target <= 0) o.leaf_target = 48;
     if (o.max_nvec <= 0) o.max_nvec = 16;
-    if (o.seg_order <= 0) o.seg_order = 16;
+    if (o.seg_order <= 0) o.seg_order = o.precision == LM_MIXED ? 10 : 16;
     if (o.tail_rays <= 0) o.tail_rays = 9;
     if (o.tail_order <= 0) o.tail_order = o.precision == LM_MIXED ? 24 : 64;
     if (o.p < 1 || o.p > LM_MAXP) {

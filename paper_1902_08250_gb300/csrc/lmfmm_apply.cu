@@ -257,6 +257,7 @@ __global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs
 
 lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st)
 {
+    if (t->precision == LM_MIXED) return lm_run_apply_mixed(t, q, nvec, u, adjoint, st);
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const int64_t n = t->n;
     const double k = t->med.k2;

@@ -1,2 +1,762 @@
-// lmfmm_mixed.cu -- mixed-precision apply path (filled in below).
+// lmfmm_mixed.cu -- the mixed-precision apply (Algorithm 1, steps 2-4):
+// translation and quadrature tables are built in FP64 (densities sigma(lambda),
+// branch points, contour nodes, large exponential factors) and rounded to
+// FP32; expansions, the M2L contraction and the near field run in FP32 with
+// FP32 accumulation.  Points are handled in leaf-local FP32 coordinates so
+// that close pairs keep their relative accuracy.
+#include <algorithm>
+#include <vector>
+
 #include "internal.h"
+
+#define MX_MAXP 24
+bool lm_mixed_order_supported(int P);
+static int gridm(int64_t n, int b) { return (int)((n + b - 1) / b); }
+
+LM_HD zf f2(zd a) { return zf{(float)a.re, (float)a.im}; }
+__device__ __forceinline__ void cfmaf(zf &a, zf b, zf c)
+{
+    a.re = fmaf(b.re, c.re, fmaf(-b.im, c.im, a.re));
+    a.im = fmaf(b.re, c.im, fmaf(b.im, c.re, a.im));
+}
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+__global__ void k_d2f(const zd *a, zf *b, int64_t n)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = f2(a[i]);
+}
+
+// leaf-local coordinates (FP64 difference, then rounded) and absolute y in FP32
+__global__ void k_local_coords(int64_t ncol, double x0, double w, const int64_t *ls, const double *xs,
+                               const double *ys, float *xl, float *yl, float *y32)
+{
+    int64_t b = blockIdx.x;
+    int64_t r = b / ncol, c = b % ncol;
+    double cx = x0 + (c + 0.5) * w, cy = -(r + 0.5) * w;
+    for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
+        xl[i] = (float)(xs[i] - cx);
+        yl[i] = (float)(ys[i] - cy);
+        y32[i] = (float)ys[i];
+    }
+}
+
+// entries of the V list that the free-space stencil kernel does not cover
+__global__ void k_rest(int l, int64_t nbox, const int64_t *vstart, const int32_t *vsrc,
+                       const int32_t *vslot, const int32_t *vterm, int64_t *rstart, int32_t *rsrc,
+                       int32_t *rslot, int pass)
+{
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int64_t pos = pass ? rstart[b] : 0, cnt = 0;
+    for (int64_t e = vstart[b]; e < vstart[b + 1]; ++e) {
+        if (l > 0 && vterm[e] == 0) continue;
+        if (pass) {
+            rsrc[pos] = vsrc[e];
+            rslot[pos] = vslot[e];
+            ++pos;
+        }
+        ++cnt;
+    }
+    if (!pass) rstart[b] = cnt;
+}
+__global__ void k_scan64b(int64_t *c, int64_t m)
+{
+    __shared__ int64_t part[1024];
+    int64_t chunk = (m + blockDim.x - 1) / blockDim.x;
+    int64_t lo = threadIdx.x * chunk, hi = min(m, lo + chunk);
+    int64_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += c[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int i = 0; i < (int)blockDim.x; ++i) {
+            int64_t v = part[i];
+            part[i] = acc;
+            acc += v;
+        }
+        c[m] = acc;
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int64_t i = lo; i < hi; ++i) {
+        int64_t v = c[i];
+        c[i] = acc;
+        acc += v;
+    }
+}
+
+struct NearQuadF;
+static size_t near_pw_smem(const lm_tree_s *t);
+__global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, float w, float d, const float *xl,
+                                                   const float *y32, const int64_t *ls, const int64_t *ustart,
+                                                   const int32_t *usrc, const int32_t *uterm, NearQuadF nq,
+                                                   const zf *qs, zf *us);
+
+#define TRYM(x)                      \
+    do {                             \
+        lm_status s_ = (x);          \
+        if (s_ != LM_OK) return s_;  \
+    } while (0)
+
+template <typename A, typename B>
+static lm_status conv(lm_tree_s *t, const A *src, B **dst, int64_t n, cudaStream_t st)
+{
+    TRYM(lm_dalloc(t, dst, n));
+    k_d2f<<<gridm(n, 256), 256, 0, st>>>(src, *dst, n);
+    return LM_OK;
+}
+
+lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
+{
+    const int L = t->L, P = t->p, np = 2 * P + 1;
+    if (P > MX_MAXP || !lm_mixed_order_supported(P)) {
+        lm_set_error("build_tree: the mixed-precision path supports p in {4,6,8..14,16,18,20,24}");
+        return LM_ENOTSUP;
+    }
+    for (int l = 0; l <= L; ++l) {
+        Level &lv = t->lev[l];
+        int ncls = (int)lv.cls_term.size();
+        TRYM(conv(t, lv.tab, &lv.tab32, (int64_t)std::max(1, ncls) * np * np, st));
+        if (lv.m2m) TRYM(conv(t, lv.m2m, &lv.m2m32, 4 * np * np, st));
+        if (lv.l2l) TRYM(conv(t, lv.l2l, &lv.l2l32, 4 * np * np, st));
+        TRYM(lm_dalloc(t, &lv.M32, lv.nbox * np * LM_MAXV));
+        TRYM(lm_dalloc(t, &lv.L32, lv.nbox * np * LM_MAXV));
+        std::vector<int32_t> sten(49, -1);
+        for (int i = 0; i < ncls; ++i)
+            if (lv.cls_term[i] == 0 && abs(lv.cls_dc[i]) <= 3 && abs(lv.cls_dr[i]) <= 3)
+                sten[(lv.cls_dc[i] + 3) * 7 + lv.cls_dr[i] + 3] = i;
+        TRYM(lm_dalloc(t, &lv.stencil, 49));
+        LM_CUDA(cudaMemcpyAsync(lv.stencil, sten.data(), 49 * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        TRYM(lm_dalloc(t, &lv.rstart, lv.nbox + 1));
+        k_rest<<<gridm(lv.nbox, 128), 128, 0, st>>>(l, lv.nbox, lv.vstart, lv.vsrc, lv.vslot, lv.vterm,
+                                                     lv.rstart, nullptr, nullptr, 0);
+        k_scan64b<<<1, 1024, 0, st>>>(lv.rstart, lv.nbox);
+        LM_CUDA(cudaMemcpyAsync(&lv.nrest, lv.rstart + lv.nbox, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        LM_CUDA(cudaStreamSynchronize(st));
+        // the stencil kernel assumes every free-space offset of an interior box has a table
+        if (l > 0)
+            for (int dc = -3; dc <= 3; ++dc)
+                for (int dr = -3; dr <= 3; ++dr)
+                    if ((abs(dc) > 1 || abs(dr) > 1) && sten[(dc + 3) * 7 + dr + 3] < 0 && lv.ncol > 6 &&
+                        lv.nrow > 6) {
+                        lm_set_error("build_tree: free-space class (%d, %d) missing at level %d", dc, dr, l);
+                        return LM_ECUDA;
+                    }
+        TRYM(lm_dalloc(t, &lv.rsrc, lv.nrest));
+        TRYM(lm_dalloc(t, &lv.rslot, lv.nrest));
+        k_rest<<<gridm(lv.nbox, 128), 128, 0, st>>>(l, lv.nbox, lv.vstart, lv.vsrc, lv.vslot, lv.vterm,
+                                                     lv.rstart, lv.rsrc, lv.rslot, 1);
+    }
+    const int64_t n = t->n;
+    TRYM(lm_dalloc(t, &t->xl32, n));
+    TRYM(lm_dalloc(t, &t->yl32, n));
+    TRYM(lm_dalloc(t, &t->y32, n));
+    {
+        Level &lv = t->lev[L];
+        k_local_coords<<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, t->x0, lv.w, t->leaf_start, t->xs, t->ys,
+                                                          t->xl32, t->yl32, t->y32);
+    }
+    TRYM(lm_dalloc(t, &t->qs32, n * LM_MAXV));
+    TRYM(lm_dalloc(t, &t->us32, n * LM_MAXV));
+    NearQuad &q = t->nq;
+    TRYM(conv(t, q.seg_lam, &t->nq_seg_lam, q.nseg, st));
+    TRYM(conv(t, q.seg_s2, &t->nq_seg_s2, q.nseg, st));
+    TRYM(conv(t, q.seg_w, &t->nq_seg_w, 2 * q.nseg, st));
+    int64_t nt = (int64_t)q.nray * q.ntail;
+    TRYM(conv(t, q.tail_lam, &t->nq_tail_lam, nt, st));
+    TRYM(conv(t, q.tail_s2, &t->nq_tail_s2, nt, st));
+    TRYM(conv(t, q.tail_w, &t->nq_tail_w, 2 * nt, st));
+    size_t shm = near_pw_smem(t);
+    if (shm > 200 * 1024) {
+        lm_set_error("build_tree: near-field segment of %d nodes is too long for the factorised kernel", q.nseg);
+        return LM_ENOTSUP;
+    }
+    LM_CUDA(cudaFuncSetAttribute(k_near_pw32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    LM_CUDA(cudaGetLastError());
+    LM_CUDA(cudaStreamSynchronize(st));
+    return LM_OK;
+}
+
+void lm_free_mixed(lm_tree_s *t)
+{
+    void *ptrs[] = {t->xl32, t->yl32, t->y32, t->qs32, t->us32, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w,
+                    t->nq_tail_lam, t->nq_tail_s2, t->nq_tail_w};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    for (Level &lv : t->lev) {
+        void *lp[] = {lv.tab32, lv.m2m32, lv.l2l32, lv.M32, lv.L32, lv.stencil, lv.rstart, lv.rsrc, lv.rslot};
+        for (void *p : lp)
+            if (p) cudaFree(p);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// apply kernels (FP32)
+// ---------------------------------------------------------------------------
+__global__ void k_permute_in32(const zd *q, const int64_t *perm, int64_t n, int nvec, int conjugate,
+                               zf *qs)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    for (int v = 0; v < LM_MAXV; ++v) {
+        zf a = {0.f, 0.f};
+        if (v < nvec) {
+            zd b = q[(int64_t)v * n + j];
+            a = f2(conjugate ? conj(b) : b);
+        }
+        qs[i * LM_MAXV + v] = a;
+    }
+}
+__global__ void k_permute_out32(const zf *us, const int64_t *perm, int64_t n, int nvec, int conjugate,
+                                zd *u)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t j = perm[i];
+    for (int v = 0; v < nvec; ++v) {
+        zf a = us[i * LM_MAXV + v];
+        zd b = {(double)a.re, (double)a.im};
+        u[(int64_t)v * n + j] = conjugate ? conj(b) : b;
+    }
+}
+
+// S2M in FP32 (Eq. (multipole_coef), scaled): one block per leaf
+#define P2M32_CHUNK 32
+__global__ void k_p2m32(int P, float k, float w, const float *xl, const float *yl, const int64_t *ls,
+                        const zf *qs, zf *M)
+{
+    extern __shared__ unsigned char smem[];
+    const int np = 2 * P + 1;
+    zf *B = (zf *)smem;                        // [P2M32_CHUNK][np]
+    zf *Q = B + P2M32_CHUNK * np;              // [P2M32_CHUNK][LM_MAXV]
+    const int64_t b = blockIdx.x;
+    const int64_t lo = ls[b], hi = ls[b + 1];
+    const float sc = k * w;
+    const int nent = np * LM_MAXV;
+    zf acc[8];
+    for (int e = 0; e < 8; ++e) acc[e] = zf{0.f, 0.f};
+    for (int64_t base = lo; base < hi; base += P2M32_CHUNK) {
+        __syncthreads();
+        int j = threadIdx.x;
+        if (j < P2M32_CHUNK) {
+            int64_t i = base + j;
+            zf *row = B + j * np + P;
+            if (i < hi) {
+                float rx = xl[i], ry = yl[i], r = sqrtf(rx * rx + ry * ry);
+                float J[MX_MAXP + 1];
+                bessel_j_scaled<float>(P, k * r, sc, J);
+                zf z = r > 0.f ? zf{rx / r, -ry / r} : zf{1.f, 0.f};
+                zf zp = {1.f, 0.f};
+                row[0] = zf{J[0], 0.f};
+                for (int m = 1; m <= P; ++m) {
+                    zp = zp * z;
+                    row[m] = J[m] * zp;
+                    float s = (m & 1) ? -J[m] : J[m];
+                    row[-m] = s * conj(zp);
+                }
+            } else {
+                for (int m = -P; m <= P; ++m) row[m] = zf{0.f, 0.f};
+            }
+        }
+        for (int e = threadIdx.x; e < P2M32_CHUNK * LM_MAXV; e += blockDim.x) {
+            int jj = e / LM_MAXV;
+            int64_t i = base + jj;
+            Q[e] = i < hi ? qs[i * LM_MAXV + e % LM_MAXV] : zf{0.f, 0.f};
+        }
+        __syncthreads();
+        int cnt = (int)min((int64_t)P2M32_CHUNK, hi - base);
+        for (int e = 0; e < 8; ++e) {
+            int idx = threadIdx.x + e * blockDim.x;
+            if (idx >= nent) break;
+            int qi = idx / LM_MAXV, v = idx % LM_MAXV;
+            zf s = acc[e];
+            for (int jj = 0; jj < cnt; ++jj) cfmaf(s, B[jj * np + qi], Q[jj * LM_MAXV + v]);
+            acc[e] = s;
+        }
+    }
+    for (int e = 0; e < 8; ++e) {
+        int idx = threadIdx.x + e * blockDim.x;
+        if (idx >= nent) break;
+        M[b * nent + idx] = acc[e];
+    }
+}
+
+__global__ void k_m2m32(int64_t ncol, int64_t nbox, int P, const zf *tabs, const zf *Mc, zf *Mp)
+{
+    const int np = 2 * P + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * LM_MAXV) return;
+    int v = idx % LM_MAXV;
+    int p = (idx / LM_MAXV) % np;
+    int64_t b = idx / (LM_MAXV * np);
+    int64_t r = b / ncol, c = b % ncol, ncc = 2 * ncol;
+    zf acc = {0.f, 0.f};
+    for (int pos = 0; pos < 4; ++pos) {
+        int dy = pos >> 1, dx = pos & 1;
+        int64_t ch = (2 * r + dy) * ncc + 2 * c + dx;
+        const zf *T = tabs + ((int64_t)pos * np + p) * np;
+        const zf *m = Mc + ch * np * LM_MAXV + v;
+        zf tmp = {0.f, 0.f};
+        for (int q = 0; q < np; ++q) cfmaf(tmp, T[q], m[q * LM_MAXV]);
+        acc = acc + tmp;
+    }
+    Mp[idx] = acc;
+}
+
+__global__ void k_l2l32(int64_t ncol, int64_t nbox, int P, const zf *tabs, const zf *Lp, zf *Lc)
+{
+    const int np = 2 * P + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * LM_MAXV) return;
+    int v = idx % LM_MAXV;
+    int p = (idx / LM_MAXV) % np;
+    int64_t b = idx / (LM_MAXV * np);
+    int64_t r = b / ncol, c = b % ncol;
+    int pos = (int)((r & 1) * 2 + (c & 1));
+    int64_t par = (r / 2) * (ncol / 2) + c / 2;
+    const zf *T = tabs + ((int64_t)pos * np + p) * np;
+    const zf *m = Lp + par * np * LM_MAXV + v;
+    zf acc = {0.f, 0.f};
+    for (int q = 0; q < np; ++q) cfmaf(acc, T[q], m[q * LM_MAXV]);
+    Lc[idx] = acc;
+}
+
+// Free-space M2L over the fixed 27-offset stencil of the V list (levels >= 1).
+// Boxes of one parity class share their offsets; a block takes 16 such boxes
+// x 16 vectors (one column per thread, all NP orders in registers) and, offset
+// by offset, stages the translation matrix in shared memory (transposed, so
+// the inner loop reads it as a broadcast) and streams the source multipoles.
+template <int NP>
+__global__ void __launch_bounds__(256) k_m2l_stencil32(int64_t ncol, int64_t nrow, const int32_t *stencil,
+                                                        const zf *tab, const zf *M, zf *Lc)
+{
+    __shared__ zf At[NP * NP]; // At[q][p]
+    const int cls = blockIdx.y; // parity class
+    const int pc = cls & 1, pr = cls >> 1;
+    const int64_t hc = ncol / 2, hr = nrow / 2;
+    const int64_t tile = blockIdx.x;
+    const int lb = threadIdx.x >> 4, v = threadIdx.x & 15;
+    const int64_t cidx = tile * 16 + lb; // index within the class, row-major over (r/2, c/2)
+    const bool active = cidx < hc * hr;
+    const int64_t c = 2 * (active ? cidx % hc : 0) + pc, r = 2 * (active ? cidx / hc : 0) + pr;
+    zf acc[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) acc[p] = zf{0.f, 0.f};
+    for (int dc = pc - 3; dc <= pc + 2; ++dc)
+        for (int dr = pr - 3; dr <= pr + 2; ++dr) {
+            if (dc >= -1 && dc <= 1 && dr >= -1 && dr <= 1) continue;
+            const int slot = stencil[(dc + 3) * 7 + dr + 3];
+            if (slot < 0) continue; // offset beyond the grid at this level
+            __syncthreads();
+            const zf *T = tab + (int64_t)slot * NP * NP;
+            for (int e = threadIdx.x; e < NP * NP; e += blockDim.x) {
+                int p = e / NP, q = e % NP;
+                At[q * NP + p] = T[e];
+            }
+            __syncthreads();
+            const int64_t cs = c - dc, rs = r - dr;
+            if (!active || cs < 0 || cs >= ncol || rs < 0 || rs >= nrow) continue;
+            const zf *m = M + (rs * ncol + cs) * NP * LM_MAXV + v;
+            // blocked accumulation: one offset's contraction in fresh registers,
+            // then added to the running sum (FP32 error grows with the chain length)
+            zf tmp[NP];
+#pragma unroll
+            for (int p = 0; p < NP; ++p) tmp[p] = zf{0.f, 0.f};
+#pragma unroll 1
+            for (int q = 0; q < NP; ++q) {
+                const zf mq = m[q * LM_MAXV];
+                const zf *a = At + q * NP;
+#pragma unroll
+                for (int p = 0; p < NP; ++p) cfmaf(tmp[p], a[p], mq);
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p) acc[p] = acc[p] + tmp[p];
+        }
+    if (!active) return;
+    zf *out = Lc + (r * ncol + c) * NP * LM_MAXV + v;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        zf o = out[p * LM_MAXV];
+        out[p * LM_MAXV] = zf{o.re + acc[p].re, o.im + acc[p].im};
+    }
+}
+
+// remaining V-list entries (level 0 and the image terms), one thread per (target, order, vector)
+__global__ void k_m2l_rest32(int64_t nbox, int P, const int64_t *rstart, const int32_t *rsrc,
+                             const int32_t *rslot, const zf *tab, const zf *M, zf *Lc)
+{
+    const int np = 2 * P + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * LM_MAXV) return;
+    int v = idx % LM_MAXV;
+    int p = (idx / LM_MAXV) % np;
+    int64_t b = idx / (LM_MAXV * np);
+    int64_t e0 = rstart[b], e1 = rstart[b + 1];
+    if (e0 == e1) return;
+    zf acc = {0.f, 0.f};
+    for (int64_t e = e0; e < e1; ++e) {
+        const zf *T = tab + ((int64_t)rslot[e] * np + p) * np;
+        const zf *m = M + (int64_t)rsrc[e] * np * LM_MAXV + v;
+        zf tmp = {0.f, 0.f};
+        for (int q = 0; q < np; ++q) cfmaf(tmp, T[q], m[q * LM_MAXV]);
+        acc = acc + tmp;
+    }
+    zf o = Lc[idx];
+    Lc[idx] = zf{o.re + acc.re, o.im + acc.im};
+}
+
+// (i/4) H0^(1)(x) in FP32.  For x <= 2 the ascending series of J0 and Y0
+// (Abramowitz & Stegun 9.1.12, 9.1.13) share one power series in t = x^2/4:
+//   J0 = sum_m (-t)^m/(m!)^2,  Y0 = (2/pi)[(ln(x/2) + gamma) J0 - sum_{m>=1} H_m (-t)^m/(m!)^2],
+// H_m the harmonic numbers; 11 terms keep the truncation below 1e-9.
+// Larger x use the library's j0f / y0f.
+__device__ __forceinline__ zf green_free32(float x)
+{
+    float j, y;
+    if (x <= 2.0f) {
+        const float t = 0.25f * x * x;
+        float a = 1.0f, sj = 1.0f, sh = 0.0f, hm = 0.0f;
+#pragma unroll
+        for (int m = 1; m <= 11; ++m) {
+            a *= -t / (float)(m * m);
+            hm += 1.0f / (float)m;
+            sj += a;
+            sh += hm * a;
+        }
+        j = sj;
+        y = 0.63661977236758134f * ((logf(0.5f * x) + 0.57721566490153286f) * sj - sh);
+    } else {
+        j = j0f(x);
+        y = y0f(x);
+    }
+    return zf{-0.25f * y, 0.25f * j};
+}
+
+struct NearQuadF {
+    int nseg, nray, ntail;
+    const zf *seg_lam, *seg_s2, *seg_w, *tail_lam, *tail_s2, *tail_w;
+};
+// Tail of one reflected direct term (tt: m = 0, bb: m = 1) for a pair at
+// horizontal distance X and image height h: the rays lambda = c + t e^{i phi_k}
+// nearest the steepest-descent direction atan2(X, h) (Sec. 4.2, alternative
+// directions); 2 Re is taken because sigma(conj lambda) = conj(sigma(lambda)).
+__device__ float near_tail32(const NearQuadF &q, int m, float X, float h)
+{
+    int k = q.nray > 1 ? (int)rintf(atan2f(X, h) * (q.nray - 1) * 0.63661977236758134f) : 0;
+    const zf *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
+    const zf *tw = q.tail_w + ((int64_t)m * q.nray + k) * q.ntail;
+    float tre = 0.f;
+    for (int i = 0; i < q.ntail; ++i) {
+        zf lam = tl[i], s2 = ts[i];
+        float a = expf(-lam.im * X - s2.re * h), sn, cs;
+        sincosf(lam.re * X - s2.im * h, &sn, &cs);
+        zf w = tw[i];
+        tre += a * (w.re * cs - w.im * sn);
+    }
+    return tre;
+}
+
+// Segment part of the reflected direct terms, factorised per target leaf.
+// On the fixed deformed segment the integrand of a pair separates,
+//   2 cos(lambda (x_i - x_j)) e^{-s2 h_ij} = sum_{s=+-1} e^{s i lambda (x_i - x_T)} E(y_i) e^{-s i lambda (x_j - x_T)} E(y_j),
+// E(y) = e^{s2 y} (tt) or e^{-s2 (y + d)} (bb), x_T the target leaf centre; so
+// each leaf first sums its near sources into plane-wave coefficients
+// B_{n,s} (phase A) and then evaluates them at its targets (phase B).
+// One block per leaf in the top or bottom row; adds into us.
+#define PW_SRC 128
+__global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, float w, float d, const float *xl,
+                                                   const float *y32, const int64_t *ls, const int64_t *ustart,
+                                                   const int32_t *usrc, const int32_t *uterm, NearQuadF nq,
+                                                   const zf *qs, zf *us)
+{
+    extern __shared__ unsigned char smem[];
+    const int nk = 2 * nq.nseg;
+    zf *B = (zf *)smem;                         // [nk][LM_MAXV]
+    zf *SQ = B + (size_t)nk * LM_MAXV;          // [PW_SRC][LM_MAXV]
+    float *SX = (float *)(SQ + PW_SRC * LM_MAXV); // [PW_SRC]
+    float *SY = SX + PW_SRC;                    // [PW_SRC]
+    const int64_t row = (nrow == 1 || blockIdx.x < ncol) ? 0 : nrow - 1;
+    const int64_t col = blockIdx.x % ncol;
+    const int64_t b = row * ncol + col;
+    for (int term = 1; term <= 2; ++term) {
+        bool any = false;
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) any |= (uterm[e] == term);
+        if (!any) continue;
+        const int m = term - 1;
+        const zf *W = nq.seg_w + (int64_t)m * nq.nseg;
+        for (int k = threadIdx.x; k < nk * LM_MAXV; k += blockDim.x) B[k] = zf{0.f, 0.f};
+        // phase A: B_{n,s}[v] = sum_j q_j[v] e^{-s i lambda_n (x_j - x_T)} E_n(y_j), per source leaf
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
+            if (uterm[e] != term) continue;
+            const int64_t s = usrc[e];
+            const float ox = (float)(s % ncol - col) * w; // centre_s - centre_T
+            for (int64_t j0 = ls[s]; j0 < ls[s + 1]; j0 += PW_SRC) {
+                const int cnt = (int)min((int64_t)PW_SRC, ls[s + 1] - j0);
+                __syncthreads();
+                for (int t = threadIdx.x; t < cnt * LM_MAXV; t += blockDim.x) SQ[t] = qs[(j0 + t / LM_MAXV) * LM_MAXV + t % LM_MAXV];
+                for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                    SX[t] = xl[j0 + t] + ox;
+                    SY[t] = y32[j0 + t];
+                }
+                __syncthreads();
+                for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+                    const zf lam = nq.seg_lam[k >> 1], s2 = nq.seg_s2[k >> 1];
+                    const float sg = (k & 1) ? -1.f : 1.f;
+                    zf part[LM_MAXV];
+#pragma unroll
+                    for (int v = 0; v < LM_MAXV; ++v) part[v] = zf{0.f, 0.f};
+                    for (int t = 0; t < cnt; ++t) {
+                        const float x = SX[t], y = SY[t];
+                        float er = sg * lam.im * x, ei = -sg * lam.re * x;
+                        if (m == 0) {
+                            er += s2.re * y;
+                            ei += s2.im * y;
+                        } else {
+                            er -= s2.re * (y + d);
+                            ei -= s2.im * (y + d);
+                        }
+                        const float a = expf(er);
+                        float sn, cs;
+                        sincosf(ei, &sn, &cs);
+                        const zf f = {a * cs, a * sn};
+#pragma unroll
+                        for (int v = 0; v < LM_MAXV; ++v) cfmaf(part[v], f, SQ[t * LM_MAXV + v]);
+                    }
+#pragma unroll
+                    for (int v = 0; v < LM_MAXV; ++v) B[k * LM_MAXV + v] = B[k * LM_MAXV + v] + part[v];
+                }
+            }
+        }
+        __syncthreads();
+        // phase B: u_i[v] += sum_{n,s} W_n e^{s i lambda_n (x_i - x_T)} E_n(y_i) B_{n,s}[v]
+        const int64_t lo = ls[b], cntT = ls[b + 1] - lo;
+        for (int64_t t = threadIdx.x; t < cntT * 4; t += blockDim.x) {
+            const int64_t i = lo + t / 4;
+            const int vq = (int)(t % 4) * 4;
+            const float x = xl[i], y = y32[i];
+            zf acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+            for (int k0 = 0; k0 < nk; k0 += 20) {
+                zf part[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+                const int k1 = min(nk, k0 + 20);
+                for (int k = k0; k < k1; ++k) {
+                    const zf lam = nq.seg_lam[k >> 1], s2 = nq.seg_s2[k >> 1];
+                    const float sg = (k & 1) ? -1.f : 1.f;
+                    float er = -sg * lam.im * x, ei = sg * lam.re * x;
+                    if (m == 0) {
+                        er += s2.re * y;
+                        ei += s2.im * y;
+                    } else {
+                        er -= s2.re * (y + d);
+                        ei -= s2.im * (y + d);
+                    }
+                    const float a = expf(er);
+                    float sn, cs;
+                    sincosf(ei, &sn, &cs);
+                    const zf g = zf{a * cs, a * sn} * W[k >> 1];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) cfmaf(part[v], g, B[k * LM_MAXV + vq + v]);
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[v] = acc[v] + part[v];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                zf o = us[i * LM_MAXV + vq + v];
+                us[i * LM_MAXV + vq + v] = o + acc[v];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Step 4 in FP32: L2T and S2T for every target of a leaf; one thread per target
+template <int P>
+__global__ void k_leaf32(int64_t ncol, float w, float k, float d, const float *xl, const float *yl,
+                         const float *y32, const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
+                         const int32_t *uterm, NearQuadF nq, const zf *Lc, const zf *qs, zf *us)
+{
+    constexpr int NP = 2 * P + 1;
+    const int64_t b = blockIdx.x;
+    const int64_t rt = b / ncol, ct = b % ncol;
+    const zf *Lb = Lc + b * NP * LM_MAXV;
+    for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
+        const float xi = xl[i], yi = yl[i], ya = y32[i];
+        zf acc[LM_MAXV];
+#pragma unroll
+        for (int v = 0; v < LM_MAXV; ++v) acc[v] = zf{0.f, 0.f};
+        {
+            float r = sqrtf(xi * xi + yi * yi);
+            float J[P + 1];
+            bessel_j_scaled<float>(P, k * r, k * w, J);
+            zf z = r > 0.f ? zf{xi / r, yi / r} : zf{1.f, 0.f};
+            zf zp = {1.f, 0.f};
+#pragma unroll
+            for (int v = 0; v < LM_MAXV; ++v) cfmaf(acc[v], zf{J[0], 0.f}, Lb[P * LM_MAXV + v]);
+            for (int m = 1; m <= P; ++m) {
+                zp = zp * z;
+                zf bp = J[m] * zp;
+                zf bn = ((m & 1) ? -J[m] : J[m]) * conj(zp);
+#pragma unroll
+                for (int v = 0; v < LM_MAXV; ++v) {
+                    cfmaf(acc[v], bp, Lb[(P + m) * LM_MAXV + v]);
+                    cfmaf(acc[v], bn, Lb[(P - m) * LM_MAXV + v]);
+                }
+            }
+        }
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
+            const int32_t s = usrc[e], term = uterm[e];
+            const int64_t rs = s / ncol, cs = s % ncol;
+            const float ox = (float)(ct - cs) * w, oy = -(float)(rt - rs) * w; // centre_t - centre_s
+            zf part[LM_MAXV];
+#pragma unroll
+            for (int v = 0; v < LM_MAXV; ++v) part[v] = zf{0.f, 0.f};
+            for (int64_t j = ls[s]; j < ls[s + 1]; ++j) {
+                const float dx = (xi - xl[j]) + ox;
+                zf g;
+                if (term == 0) {
+                    if (j == i) continue;
+                    const float dy = (yi - yl[j]) + oy;
+                    g = green_free32(k * sqrtf(dx * dx + dy * dy));
+                } else {
+                    // tail of a reflected direct term; its segment part is added by k_near_pw32
+                    const float h = term == 1 ? -(ya + y32[j]) : ya + y32[j] + 2.0f * d;
+                    g = zf{near_tail32(nq, term - 1, fabsf(dx), h), 0.f};
+                }
+                const float4 *qj = (const float4 *)(qs + j * LM_MAXV);
+#pragma unroll
+                for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {
+                    float4 t = qj[v2];
+                    cfmaf(part[2 * v2], g, zf{t.x, t.y});
+                    cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < LM_MAXV; ++v) acc[v] = acc[v] + part[v];
+        }
+        float4 *o = (float4 *)(us + i * LM_MAXV);
+#pragma unroll
+        for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
+            o[v2] = make_float4(acc[2 * v2].re, acc[2 * v2].im, acc[2 * v2 + 1].re, acc[2 * v2 + 1].im);
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <int P>
+static void launch_stencil(const Level &lv, cudaStream_t st)
+{
+    int64_t ncls = (lv.ncol / 2) * (lv.nrow / 2);
+    dim3 g((unsigned)((ncls + 15) / 16), 4);
+    k_m2l_stencil32<2 * P + 1><<<g, 256, 0, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32, lv.M32, lv.L32);
+}
+template <int P>
+static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st)
+{
+    const Level &lv = t->lev[t->L];
+    k_leaf32<P><<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
+                                                   t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart, t->usrc,
+                                                   t->uterm, nq, lv.L32, t->qs32, t->us32);
+}
+
+static size_t near_pw_smem(const lm_tree_s *t)
+{
+    return (size_t)2 * t->nq.nseg * LM_MAXV * sizeof(zf) + PW_SRC * LM_MAXV * sizeof(zf) + 2 * PW_SRC * sizeof(float);
+}
+
+#define MX_DISPATCH(P, FN, ...)                                           \
+    switch (P) {                                                          \
+    case 4: FN<4>(__VA_ARGS__); break;                                    \
+    case 6: FN<6>(__VA_ARGS__); break;                                    \
+    case 8: FN<8>(__VA_ARGS__); break;                                    \
+    case 9: FN<9>(__VA_ARGS__); break;                                    \
+    case 10: FN<10>(__VA_ARGS__); break;                                  \
+    case 11: FN<11>(__VA_ARGS__); break;                                  \
+    case 12: FN<12>(__VA_ARGS__); break;                                  \
+    case 13: FN<13>(__VA_ARGS__); break;                                  \
+    case 14: FN<14>(__VA_ARGS__); break;                                  \
+    case 16: FN<16>(__VA_ARGS__); break;                                  \
+    case 18: FN<18>(__VA_ARGS__); break;                                  \
+    case 20: FN<20>(__VA_ARGS__); break;                                  \
+    case 24: FN<24>(__VA_ARGS__); break;                                  \
+    default: break;                                                       \
+    }
+
+bool lm_mixed_order_supported(int P)
+{
+    switch (P) {
+    case 4: case 6: case 8: case 9: case 10: case 11: case 12: case 13: case 14: case 16: case 18: case 20:
+    case 24: return true;
+    default: return false;
+    }
+}
+
+lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st)
+{
+    const int L = t->L, P = t->p, np = 2 * P + 1;
+    const int64_t n = t->n;
+    const float k = (float)t->med.k2;
+    NearQuadF nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq_seg_lam, t->nq_seg_s2,
+                 t->nq_seg_w, t->nq_tail_lam, t->nq_tail_s2, t->nq_tail_w};
+    for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
+        const int nv = std::min(LM_MAXV, nvec - v0);
+        lm_phase_begin(t, PH_PERMUTE, st);
+        k_permute_in32<<<gridm(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->perm, n, nv, adjoint, t->qs32);
+        lm_phase_end(t, PH_PERMUTE, st, 1);
+        lm_phase_begin(t, PH_S2M, st);
+        {
+            Level &lv = t->lev[L];
+            size_t shm = (P2M32_CHUNK * np + P2M32_CHUNK * LM_MAXV) * sizeof(zf);
+            k_p2m32<<<(unsigned)lv.nbox, 128, shm, st>>>(P, k, (float)lv.w, t->xl32, t->yl32, t->leaf_start,
+                                                         t->qs32, lv.M32);
+        }
+        lm_phase_end(t, PH_S2M, st, 1);
+        if (L > 0) lm_phase_begin(t, PH_M2M, st);
+        for (int l = L - 1; l >= 0; --l) {
+            Level &lv = t->lev[l];
+            int64_t tot = lv.nbox * np * LM_MAXV;
+            k_m2m32<<<gridm(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, lv.m2m32, t->lev[l + 1].M32, lv.M32);
+        }
+        if (L > 0) lm_phase_end(t, PH_M2M, st, L);
+        for (int l = 0; l <= L; ++l) {
+            Level &lv = t->lev[l];
+            int64_t tot = lv.nbox * np * LM_MAXV;
+            lm_phase_begin(t, PH_L2L, st);
+            if (l == 0)
+                LM_CUDA(cudaMemsetAsync(lv.L32, 0, lv.nbox * np * LM_MAXV * sizeof(zf), st));
+            else
+                k_l2l32<<<gridm(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, lv.l2l32, t->lev[l - 1].L32, lv.L32);
+            lm_phase_end(t, PH_L2L, st, l > 0);
+            lm_phase_begin(t, PH_M2L, st);
+            int launches = 0;
+            if (l > 0) {
+                MX_DISPATCH(P, launch_stencil, lv, st);
+                ++launches;
+            }
+            if (lv.nrest > 0) {
+                k_m2l_rest32<<<gridm(tot, 128), 128, 0, st>>>(lv.nbox, P, lv.rstart, lv.rsrc, lv.rslot, lv.tab32,
+                                                              lv.M32, lv.L32);
+                ++launches;
+            }
+            lm_phase_end(t, PH_M2L, st, launches);
+        }
+        lm_phase_begin(t, PH_LEAF, st);
+        MX_DISPATCH(P, launch_leaf, t, nq, st);
+        {
+            const Level &lv = t->lev[L];
+            const unsigned nb = (unsigned)(lv.nrow == 1 ? lv.ncol : 2 * lv.ncol);
+            k_near_pw32<<<nb, 256, near_pw_smem(t), st>>>(lv.ncol, lv.nrow, (float)lv.w, (float)t->med.d, t->xl32,
+                                                          t->y32, t->leaf_start, t->ustart, t->usrc, t->uterm, nq,
+                                                          t->qs32, t->us32);
+        }
+        lm_phase_end(t, PH_LEAF, st, 2);
+        lm_phase_begin(t, PH_PERMUTE, st);
+        k_permute_out32<<<gridm(n, 256), 256, 0, st>>>(t->us32, t->perm, n, nv, adjoint, u + (int64_t)v0 * n);
+        lm_phase_end(t, PH_PERMUTE, st, 1);
+        LM_CUDA(cudaGetLastError());
+    }
+    return LM_OK;
+}

@@ -138,3 +138,30 @@ def test_single_point_and_invalid_points(lm, oracle):
     xd, yd = _dev(np.array([0.1, np.nan]), np.array([-0.5, -0.2]))
     with pytest.raises(lm.LMError):
         lm.build_tree(m, xd, yd)
+
+
+@pytest.mark.parametrize("p", [10, 12])
+def test_fmm_mixed_matches_direct_sum(lm, p):
+    g = np.load(os.path.join(HERE, "golden", "small_direct.npz"))
+    x, y, q = workloads.small_uniform()
+    _, u = _run(lm, MED_A, x, y, q, p=p, depth=3, precision="mixed")
+    err = rel(u[0], g["u"][0])
+    print(f"small uniform mixed p={p}: rel-l2 {err:.3e}")
+    assert err < 1e-6
+
+
+def test_mixed_adjoint_and_chunking(lm):
+    import torch
+
+    x, y, q = workloads.uniform_strip(3000, 0.0, 3.0, -0.9, -0.1, nvec=18, seed=9)
+    m = lm.create_medium(*MED_A, p=12, depth=3, precision="mixed")
+    xd, yd = _dev(x, y)
+    t = lm.build_tree(m, xd, yd)
+    qd = torch.from_numpy(q).cuda()
+    u = lm.apply(t, qd).cpu().numpy()
+    u1 = lm.apply(t, qd[17:18].contiguous()).cpu().numpy()
+    assert np.array_equal(u[17], u1[0])
+    w = lm.apply_adjoint(t, qd).cpu().numpy()
+    lhs = np.vdot(q[1], u[0])
+    rhs = np.vdot(w[1], q[0])
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)

@@ -46,3 +46,16 @@ def test_wide_strip_fp64_sampled(case, p, tol):
     err = np.linalg.norm(u - ref) / np.linalg.norm(ref)
     print(f"wide strip fp64 p={p} depth={t.info['depth']}: rel-l2 {err:.3e} on {tg.size} sampled targets")
     assert err < tol
+
+
+@pytest.mark.parametrize("p,depth", [(14, 5), (16, 5), (14, 6)])
+def test_wide_strip_mixed_sampled(case, p, depth):
+    import paper_1902_08250_gb300 as lm
+
+    x, y, q, tg, ref, torch = case
+    m = lm.create_medium(*workloads.MEDIUM_B, p=p, depth=depth, precision="mixed")
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    u = lm.apply(t, torch.from_numpy(q).cuda()).cpu().numpy()[:, tg]
+    err = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+    print(f"wide strip mixed p={p} depth={depth}: rel-l2 {err:.3e} on {tg.size} sampled targets")
+    assert err < 1e-6
