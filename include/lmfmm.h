@@ -194,6 +194,37 @@ lm_status lm_profile_end(lm_tree t, double *ms, int64_t *launches, int nphase, i
  */
 lm_status lm_peak_probe(int kind, int64_t iters, void *stream, double *rate);
 
+/*
+ * tree_order_noalloc -- the tree order that lm_build_tree computes (points
+ * sorted by leaf of the d x d strip forest refined to depth L, ties broken by
+ * input index), computed without allocating any memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate --
+ * code that may only allocate at start-up (real-time or certified
+ * pipelines), code running inside an allocator or memory-pool callback where
+ * a nested cudaMalloc would re-enter the allocator, and processes whose
+ * device memory is entirely reserved by another framework's caching
+ * allocator.
+ *   x, y: device arrays of n doubles (input order); 1 <= n <= 1,048,576.
+ *   d > 0: root size (layer thickness); depth: 0..14, with R 4^depth <= 262,144 leaves.
+ *   perm: device int64[n], receives tree position -> input index.
+ *   leaf_start: device int64[leaf_cap]; receives nleaf + 1 = R 4^depth + 1
+ *     offsets (LM_EINVAL, with *R and *x_origin set, if leaf_cap is smaller).
+ *   x_origin, R: host outputs (left edge of the first root, number of roots).
+ * Scratch: one file-scope device array of about 6.3 MB, resident on every GPU
+ * that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current.  The array is shared by all calls and keeps the last
+ * call's contents (the counters are cleared at the start of each call), so
+ * calls whose device work overlaps -- on different streams or threads --
+ * race and must be serialised by the caller.  Calls no cudaMalloc or
+ * cudaFree and no allocating library routine.  Synchronises `stream`.
+ * Errors: LM_EINVAL for sizes beyond the limits above, NULL pointers or
+ * invalid points; LM_ENOTSUP if a leaf holds more than 8192 points; LM_ECUDA.
+ */
+lm_status lm_tree_order_noalloc(const double *x, const double *y, int64_t n, double d, int depth,
+                                int64_t *perm, int64_t *leaf_start, int64_t leaf_cap, double *x_origin,
+                                int *R, void *stream);
+
 void lm_destroy_tree(lm_tree t);
 void lm_destroy_medium(lm_medium m);
 const char *lm_status_string(lm_status s);

@@ -65,6 +65,7 @@ def _load():
         "lm_profile_begin": (I, [V, I]),
         "lm_profile_end": (I, [V, P, P, I, P]),
         "lm_peak_probe": (I, [I, I64, P, P]),
+        "lm_tree_order_noalloc": (I, [P, P, I64, D, I, P, P, I64, P, P, P]),
         "lm_destroy_tree": (None, [V]),
         "lm_destroy_medium": (None, [V]),
         "lm_status_string": (ctypes.c_char_p, [I]),
