@@ -202,26 +202,38 @@ __global__ void k_permute_in32(const zd *q, const int64_t *perm, int64_t n, int 
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int64_t j = perm[i];
+    const int64_t j = perm[i];
+    zf a[LM_MAXV];
+#pragma unroll
     for (int v = 0; v < LM_MAXV; ++v) {
-        zf a = {0.f, 0.f};
+        a[v] = zf{0.f, 0.f};
         if (v < nvec) {
             zd b = q[(int64_t)v * n + j];
-            a = f2(conjugate ? conj(b) : b);
+            a[v] = f2(conjugate ? conj(b) : b);
         }
-        qs[i * LM_MAXV + v] = a;
     }
+    float4 *o = (float4 *)(qs + i * LM_MAXV);
+#pragma unroll
+    for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
+        o[v2] = make_float4(a[2 * v2].re, a[2 * v2].im, a[2 * v2 + 1].re, a[2 * v2 + 1].im);
 }
 __global__ void k_permute_out32(const zf *us, const int64_t *perm, int64_t n, int nvec, int conjugate,
                                 zd *u)
 {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int64_t j = perm[i];
-    for (int v = 0; v < nvec; ++v) {
-        zf a = us[i * LM_MAXV + v];
-        zd b = {(double)a.re, (double)a.im};
-        u[(int64_t)v * n + j] = conjugate ? conj(b) : b;
+    const int64_t j = perm[i];
+    const float4 *src = (const float4 *)(us + i * LM_MAXV);
+    float4 a[LM_MAXV / 2];
+#pragma unroll
+    for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) a[v2] = src[v2];
+#pragma unroll
+    for (int v = 0; v < LM_MAXV; ++v) {
+        if (v < nvec) {
+            const float4 t = a[v / 2];
+            zd b = (v & 1) ? zd{(double)t.z, (double)t.w} : zd{(double)t.x, (double)t.y};
+            u[(int64_t)v * n + j] = conjugate ? conj(b) : b;
+        }
     }
 }
 
@@ -327,26 +339,33 @@ __global__ void k_l2l32(int64_t ncol, int64_t nbox, int P, const zf *tabs, const
 }
 
 // Free-space M2L over the fixed 27-offset stencil of the V list (levels >= 1).
-// Boxes of one parity class share their offsets; a block takes 16 such boxes
-// x 16 vectors (one column per thread, all NP orders in registers) and, offset
-// by offset, stages the translation matrix in shared memory (transposed, so
-// the inner loop reads it as a broadcast) and streams the source multipoles.
+// Boxes of one parity class share their offsets.  A block takes 16 boxes of
+// one class; its threads form (row group of 4 orders) x (box, 4 vectors)
+// tiles, so each staged translation entry feeds 4 columns and each source
+// multipole quad feeds 4 orders.  Offset by offset the matrix is staged in
+// shared memory (transposed: warp-uniform broadcast reads) and the gathered
+// source multipoles stream from L2 as 32-byte vector loads.  Each offset's
+// contraction accumulates in fresh registers before joining the sum.
+#define ST_RG 4
 template <int NP>
-__global__ void __launch_bounds__(256) k_m2l_stencil32(int64_t ncol, int64_t nrow, const int32_t *stencil,
-                                                        const zf *tab, const zf *M, zf *Lc)
+__global__ void __launch_bounds__(64 * ((NP + ST_RG - 1) / ST_RG))
+    k_m2l_stencil32(int64_t ncol, int64_t nrow, const int32_t *stencil, const zf *tab, const zf *M, zf *Lc)
 {
     __shared__ zf At[NP * NP]; // At[q][p]
-    const int cls = blockIdx.y; // parity class
+    const int cls = blockIdx.y;
     const int pc = cls & 1, pr = cls >> 1;
     const int64_t hc = ncol / 2, hr = nrow / 2;
-    const int64_t tile = blockIdx.x;
-    const int lb = threadIdx.x >> 4, v = threadIdx.x & 15;
-    const int64_t cidx = tile * 16 + lb; // index within the class, row-major over (r/2, c/2)
+    const int rg = threadIdx.x >> 6, cg = threadIdx.x & 63;
+    const int lb = cg >> 2, vq = (cg & 3) * 4;
+    const int64_t cidx = (int64_t)blockIdx.x * 16 + lb;
     const bool active = cidx < hc * hr;
     const int64_t c = 2 * (active ? cidx % hc : 0) + pc, r = 2 * (active ? cidx / hc : 0) + pr;
-    zf acc[NP];
+    const int p0 = rg * ST_RG;
+    zf acc[ST_RG][4];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) acc[p] = zf{0.f, 0.f};
+    for (int i = 0; i < ST_RG; ++i)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[i][u] = zf{0.f, 0.f};
     for (int dc = pc - 3; dc <= pc + 2; ++dc)
         for (int dr = pr - 3; dr <= pr + 2; ++dr) {
             if (dc >= -1 && dc <= 1 && dr >= -1 && dr <= 1) continue;
@@ -361,28 +380,41 @@ __global__ void __launch_bounds__(256) k_m2l_stencil32(int64_t ncol, int64_t nro
             __syncthreads();
             const int64_t cs = c - dc, rs = r - dr;
             if (!active || cs < 0 || cs >= ncol || rs < 0 || rs >= nrow) continue;
-            const zf *m = M + (rs * ncol + cs) * NP * LM_MAXV + v;
-            // blocked accumulation: one offset's contraction in fresh registers,
-            // then added to the running sum (FP32 error grows with the chain length)
-            zf tmp[NP];
+            const zf *m = M + (rs * ncol + cs) * NP * LM_MAXV + vq;
+            zf tmp[ST_RG][4];
 #pragma unroll
-            for (int p = 0; p < NP; ++p) tmp[p] = zf{0.f, 0.f};
-#pragma unroll 1
+            for (int i = 0; i < ST_RG; ++i)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) tmp[i][u] = zf{0.f, 0.f};
+#pragma unroll 2
             for (int q = 0; q < NP; ++q) {
-                const zf mq = m[q * LM_MAXV];
-                const zf *a = At + q * NP;
+                const float4 m01 = *(const float4 *)(m + q * LM_MAXV);
+                const float4 m23 = *(const float4 *)(m + q * LM_MAXV + 2);
+                const zf mv[4] = {{m01.x, m01.y}, {m01.z, m01.w}, {m23.x, m23.y}, {m23.z, m23.w}};
+                const zf *a = At + q * NP + p0;
 #pragma unroll
-                for (int p = 0; p < NP; ++p) cfmaf(tmp[p], a[p], mq);
+                for (int i = 0; i < ST_RG; ++i) {
+                    if (p0 + i < NP) {
+                        const zf ai = a[i];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) cfmaf(tmp[i][u], ai, mv[u]);
+                    }
+                }
             }
 #pragma unroll
-            for (int p = 0; p < NP; ++p) acc[p] = acc[p] + tmp[p];
+            for (int i = 0; i < ST_RG; ++i)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[i][u] = acc[i][u] + tmp[i][u];
         }
     if (!active) return;
-    zf *out = Lc + (r * ncol + c) * NP * LM_MAXV + v;
+    zf *out = Lc + (r * ncol + c) * NP * LM_MAXV + vq;
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        zf o = out[p * LM_MAXV];
-        out[p * LM_MAXV] = zf{o.re + acc[p].re, o.im + acc[p].im};
+    for (int i = 0; i < ST_RG; ++i) {
+        if (p0 + i >= NP) break;
+        float4 *o = (float4 *)(out + (p0 + i) * LM_MAXV);
+        float4 x0 = o[0], x1 = o[1];
+        o[0] = make_float4(x0.x + acc[i][0].re, x0.y + acc[i][0].im, x0.z + acc[i][1].re, x0.w + acc[i][1].im);
+        o[1] = make_float4(x1.x + acc[i][2].re, x1.y + acc[i][2].im, x1.z + acc[i][3].re, x1.w + acc[i][3].im);
     }
 }
 
@@ -417,16 +449,20 @@ __global__ void k_m2l_rest32(int64_t nbox, int P, const int64_t *rstart, const i
 // Larger x use the library's j0f / y0f.
 __device__ __forceinline__ zf green_free32(float x)
 {
+    // 1/m^2 and the harmonic numbers H_m, m = 1..11
+    constexpr float kInvM2[11] = {1.0f, 0.25f, 0.11111111f, 0.0625f, 0.04f, 0.027777778f,
+                                  0.020408163f, 0.015625f, 0.012345679f, 0.01f, 0.0082644628f};
+    constexpr float kHarm[11] = {1.0f, 1.5f, 1.8333333f, 2.0833333f, 2.2833333f, 2.45f,
+                                 2.5928571f, 2.7178571f, 2.8289683f, 2.9289683f, 3.0198773f};
     float j, y;
     if (x <= 2.0f) {
-        const float t = 0.25f * x * x;
-        float a = 1.0f, sj = 1.0f, sh = 0.0f, hm = 0.0f;
+        const float mt = -0.25f * x * x;
+        float a = 1.0f, sj = 1.0f, sh = 0.0f;
 #pragma unroll
-        for (int m = 1; m <= 11; ++m) {
-            a *= -t / (float)(m * m);
-            hm += 1.0f / (float)m;
+        for (int m = 0; m < 11; ++m) {
+            a *= mt * kInvM2[m];
             sj += a;
-            sh += hm * a;
+            sh = fmaf(kHarm[m], a, sh);
         }
         j = sj;
         y = 0.63661977236758134f * ((logf(0.5f * x) + 0.57721566490153286f) * sj - sh);
@@ -649,9 +685,11 @@ __global__ void k_leaf32(int64_t ncol, float w, float k, float d, const float *x
 template <int P>
 static void launch_stencil(const Level &lv, cudaStream_t st)
 {
+    constexpr int NP = 2 * P + 1;
     int64_t ncls = (lv.ncol / 2) * (lv.nrow / 2);
     dim3 g((unsigned)((ncls + 15) / 16), 4);
-    k_m2l_stencil32<2 * P + 1><<<g, 256, 0, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32, lv.M32, lv.L32);
+    k_m2l_stencil32<NP><<<g, 64 * ((NP + ST_RG - 1) / ST_RG), 0, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32,
+                                                                         lv.M32, lv.L32);
 }
 template <int P>
 static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st)
