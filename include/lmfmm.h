@@ -67,6 +67,8 @@ typedef struct {
     int seg_order;   /* near-field contour: Gauss-Legendre points per segment panel; 0 -> 16 (FP64), 10 (mixed) */
     int tail_order;  /* near-field tail: Gauss-Legendre points per ray; 0 -> 64 (FP64), 24 (mixed) */
     int tail_rays;   /* near-field tail: rays between the north and east directions; 0 -> 9 */
+    int tensor_m2l;  /* mixed path, p <= 14: free-space M2L on the tcgen05 tensor cores
+                        (TF32 hi/lo split, FP32 accumulation in tensor memory); 1 on, 0 off */
 } lm_options;
 
 typedef struct lm_medium_s *lm_medium; /* opaque, library-owned */
@@ -224,6 +226,14 @@ lm_status lm_peak_probe(int kind, int64_t iters, void *stream, double *rate);
 lm_status lm_tree_order_noalloc(const double *x, const double *y, int64_t n, double d, int depth,
                                 int64_t *perm, int64_t *leaf_start, int64_t leaf_cap, double *x_origin,
                                 int *R, void *stream);
+
+/*
+ * sync_status -- synchronise `stream` and report device-side failures of the
+ * applies enqueued so far on tree t: LM_ETIMEOUT if a bounded wait inside a
+ * tensor-core kernel gave up (the result of that apply is invalid), LM_OK
+ * otherwise.  Clears the recorded failure.
+ */
+lm_status lm_sync_status(lm_tree t, void *stream);
 
 void lm_destroy_tree(lm_tree t);
 void lm_destroy_medium(lm_medium m);

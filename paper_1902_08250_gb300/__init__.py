@@ -39,7 +39,7 @@ class LMError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_target", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_nvec", ctypes.c_int), ("seg_order", ctypes.c_int),
-                ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int)]
+                ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int), ("tensor_m2l", ctypes.c_int)]
 
 
 class _TreeInfo(ctypes.Structure):
@@ -66,6 +66,7 @@ def _load():
         "lm_profile_end": (I, [V, P, P, I, P]),
         "lm_peak_probe": (I, [I, I64, P, P]),
         "lm_tree_order_noalloc": (I, [P, P, I64, D, I, P, P, I64, P, P, P]),
+        "lm_sync_status": (I, [V, P]),
         "lm_destroy_tree": (None, [V]),
         "lm_destroy_medium": (None, [V]),
         "lm_status_string": (ctypes.c_char_p, [I]),
@@ -113,10 +114,10 @@ class Medium:
 
 
 def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
-                  seg_order=0, tail_order=0, tail_rays=9) -> Medium:
+                  seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1) -> Medium:
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
-    o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays)
+    o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays, tensor_m2l)
     h = ctypes.c_void_p()
     _check(_lib.lm_create_medium(k1, k2, k3, d, ctypes.byref(o), ctypes.byref(h)))
     return Medium(h.value, k1, k2, k3, d, dict(p=p, depth=depth, leaf_target=leaf_target,
@@ -207,6 +208,11 @@ def _apply(fn, tree, q, u, stream):
 def apply(tree: Tree, q, u=None, stream=None):
     """u = G q (Algorithm 1). q: complex128 CUDA tensor [nvec, n] or [n]."""
     return _apply(_lib.lm_apply, tree, q, u, stream)
+
+
+def sync_status(tree: Tree, stream=None):
+    """Synchronise and raise LMError(LM_ETIMEOUT) if a bounded device wait gave up."""
+    _check(_lib.lm_sync_status(tree._h, _stream(stream)))
 
 
 def apply_adjoint(tree: Tree, v, w=None, stream=None):

@@ -68,6 +68,9 @@ struct Level {
     int64_t nrest;
     int64_t *rstart; // [nbox + 1]
     int32_t *rsrc, *rslot;
+    // tensor-core M2L: real-block TF32 hi/lo table images and their (dc, dr) map
+    float *rb;
+    int32_t *rbslot;
 };
 
 struct lm_tree_s {
@@ -93,6 +96,7 @@ struct lm_tree_s {
     float *xl32, *yl32, *y32; // leaf-local coordinates and absolute y, FP32 [n]
     zf *qs32, *us32;           // [n][LM_MAXV]
     zf *nq_seg_lam, *nq_seg_s2, *nq_seg_w, *nq_tail_lam, *nq_tail_s2, *nq_tail_w;
+    bool tc_ready; // tensor-core M2L tables built
     int *dflag;  // device error flag
     int64_t bytes;
     // phase profiling
@@ -121,6 +125,9 @@ lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint,
 lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st);
 lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);
 void lm_free_mixed(lm_tree_s *t);
+// tensor-core M2L (lmfmm_tc.cu)
+lm_status lm_setup_tc(lm_tree_s *t, cudaStream_t st);
+lm_status lm_launch_m2l_tc(lm_tree_s *t, int l, cudaStream_t st);
 template <typename T>
 lm_status lm_dalloc(lm_tree_s *t, T **p, size_t count)
 {

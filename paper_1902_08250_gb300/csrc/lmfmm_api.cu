@@ -51,6 +51,7 @@ extern "C" lm_status lm_options_default(lm_options *o)
     o->seg_order = 0;
     o->tail_order = 0;
     o->tail_rays = 9;
+    o->tensor_m2l = 1;
     return LM_OK;
 }
 
@@ -189,6 +190,25 @@ extern "C" lm_status lm_apply_adjoint(lm_tree t, const void *v, int nvec, void *
     s = lm_run_apply(t, (const zd *)v, nvec, (zd *)w, true, (cudaStream_t)stream);
     lm_profile_apply_stop(t);
     return s;
+}
+
+extern "C" lm_status lm_sync_status(lm_tree t, void *stream)
+{
+    if (!t) {
+        lm_set_error("sync_status: NULL tree");
+        return LM_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int f = 0;
+    LM_CUDA(cudaMemcpyAsync(&f, t->dflag + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LM_CUDA(cudaStreamSynchronize(st));
+    if (f) {
+        LM_CUDA(cudaMemsetAsync(t->dflag + 1, 0, sizeof(int), st));
+        LM_CUDA(cudaStreamSynchronize(st));
+        lm_set_error("a bounded wait in the tensor-core M2L gave up; the apply result is invalid");
+        return LM_ETIMEOUT;
+    }
+    return LM_OK;
 }
 
 extern "C" lm_status lm_get_tree_info(lm_tree t, lm_tree_info *info)

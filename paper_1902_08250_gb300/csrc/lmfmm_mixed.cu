@@ -176,6 +176,7 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
         return LM_ENOTSUP;
     }
     LM_CUDA(cudaFuncSetAttribute(k_near_pw32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    if (t->med.opt.tensor_m2l) TRYM(lm_setup_tc(t, st));
     LM_CUDA(cudaGetLastError());
     LM_CUDA(cudaStreamSynchronize(st));
     return LM_OK;
@@ -188,7 +189,8 @@ void lm_free_mixed(lm_tree_s *t)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (Level &lv : t->lev) {
-        void *lp[] = {lv.tab32, lv.m2m32, lv.l2l32, lv.M32, lv.L32, lv.stencil, lv.rstart, lv.rsrc, lv.rslot};
+        void *lp[] = {lv.tab32, lv.m2m32, lv.l2l32, lv.M32, lv.L32, lv.stencil, lv.rstart, lv.rsrc, lv.rslot,
+                      lv.rb, lv.rbslot};
         for (void *p : lp)
             if (p) cudaFree(p);
     }
@@ -447,7 +449,9 @@ __global__ void k_m2l_rest32(int64_t nbox, int P, const int64_t *rstart, const i
 //   J0 = sum_m (-t)^m/(m!)^2,  Y0 = (2/pi)[(ln(x/2) + gamma) J0 - sum_{m>=1} H_m (-t)^m/(m!)^2],
 // H_m the harmonic numbers; 11 terms keep the truncation below 1e-9.
 // Larger x use the library's j0f / y0f.
-__device__ __forceinline__ zf green_free32(float x)
+// nterms: series length, chosen per tree from the largest k r of any direct
+// pair so that the truncation stays below 1e-9 (at most 11 terms, x <= 2)
+__device__ __forceinline__ zf green_free32(float x, int nterms)
 {
     // 1/m^2 and the harmonic numbers H_m, m = 1..11
     constexpr float kInvM2[11] = {1.0f, 0.25f, 0.11111111f, 0.0625f, 0.04f, 0.027777778f,
@@ -460,17 +464,32 @@ __device__ __forceinline__ zf green_free32(float x)
         float a = 1.0f, sj = 1.0f, sh = 0.0f;
 #pragma unroll
         for (int m = 0; m < 11; ++m) {
-            a *= mt * kInvM2[m];
-            sj += a;
-            sh = fmaf(kHarm[m], a, sh);
+            if (m < nterms) {
+                a *= mt * kInvM2[m];
+                sj += a;
+                sh = fmaf(kHarm[m], a, sh);
+            }
         }
         j = sj;
-        y = 0.63661977236758134f * ((logf(0.5f * x) + 0.57721566490153286f) * sj - sh);
+        // MUFU logarithm: absolute error ~1e-7 on (0, 1], well inside the 1e-6 budget
+        y = 0.63661977236758134f * ((__logf(0.5f * x) + 0.57721566490153286f) * sj - sh);
     } else {
         j = j0f(x);
         y = y0f(x);
     }
     return zf{-0.25f * y, 0.25f * j};
+}
+
+// terms of the J0/Y0 series needed for arguments up to xmax (truncation < 1e-9)
+int lm_h0_terms(double xmax)
+{
+    if (xmax > 2.0) return 11;
+    double t = 0.25 * xmax * xmax, a = 1.0;
+    for (int m = 1; m <= 11; ++m) {
+        a *= t / ((double)m * m);
+        if (a * 3.1 < 1e-9) return m;
+    }
+    return 11;
 }
 
 struct NearQuadF {
@@ -610,22 +629,94 @@ __global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, f
     }
 }
 
-// Step 4 in FP32: L2T and S2T for every target of a leaf; one thread per target
+// Step 4 in FP32: L2T and S2T for every target of a leaf, one thread per
+// target holding all 16 vectors.  The source leaves of the U list are
+// streamed through shared memory in chunks of up to 64 points with
+// double-buffered cp.async (coordinates and the 128-byte density rows), so
+// the inner loop reads broadcast shared-memory rows while the next chunk
+// is in flight.
+#define LCAP 64
+__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+struct LeafChunk {
+    int e, j0, cnt;
+};
+
 template <int P>
-__global__ void k_leaf32(int64_t ncol, float w, float k, float d, const float *xl, const float *yl,
-                         const float *y32, const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
-                         const int32_t *uterm, NearQuadF nq, const zf *Lc, const zf *qs, zf *us)
+__global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
+                                                  const float *yl, const float *y32, const int64_t *ls,
+                                                  const int64_t *ustart, const int32_t *usrc, const int32_t *uterm,
+                                                  NearQuadF nq, const zf *Lc, const zf *qs, zf *us, int nterms)
 {
     constexpr int NP = 2 * P + 1;
+    __shared__ __align__(16) zf sq[2][LCAP * LM_MAXV];
+    __shared__ float sx[2][LCAP], sy[2][LCAP], sya[2][LCAP];
     const int64_t b = blockIdx.x;
-    const int64_t rt = b / ncol, ct = b % ncol;
+    const int rt = (int)(b / ncol), ct = (int)(b % ncol);
     const zf *Lb = Lc + b * NP * LM_MAXV;
-    for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
-        const float xi = xl[i], yi = yl[i], ya = y32[i];
+    const int lo = (int)ls[b], hi = (int)ls[b + 1];
+    const int e0 = (int)ustart[b], e1 = (int)ustart[b + 1];
+
+    // chunk c of the U list -> (entry, first point, count); enumerated on the fly
+    auto chunk_at = [&](int c) {
+        LeafChunk ch{-1, 0, 0};
+        for (int e = e0; e < e1; ++e) {
+            const int s = usrc[e], a0 = (int)ls[s], a1 = (int)ls[s + 1];
+            const int nc = (a1 - a0 + LCAP - 1) / LCAP;
+            if (c < nc) {
+                ch.e = e;
+                ch.j0 = a0 + c * LCAP;
+                ch.cnt = min(LCAP, a1 - ch.j0);
+                return ch;
+            }
+            c -= nc;
+        }
+        return ch;
+    };
+    int nch = 0;
+    for (int e = e0; e < e1; ++e) {
+        const int s = usrc[e];
+        nch += ((int)(ls[s + 1] - ls[s]) + LCAP - 1) / LCAP;
+    }
+    auto issue = [&](int c, int buf) {
+        const LeafChunk ch = chunk_at(c);
+        for (int t = threadIdx.x; t < ch.cnt * (LM_MAXV / 2); t += blockDim.x) {
+            const int j = t / (LM_MAXV / 2), part = t % (LM_MAXV / 2);
+            cp_async16(&sq[buf][j * LM_MAXV + 2 * part], qs + (int64_t)(ch.j0 + j) * LM_MAXV + 2 * part);
+        }
+        for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
+            cp_async4(&sx[buf][t], xl + ch.j0 + t);
+            cp_async4(&sy[buf][t], yl + ch.j0 + t);
+            cp_async4(&sya[buf][t], y32 + ch.j0 + t);
+        }
+    };
+
+    for (int i0 = lo; i0 < hi; i0 += blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        const bool act = i < hi;
+        const float xi = act ? xl[i] : 0.f, yi = act ? yl[i] : 0.f, ya = act ? y32[i] : -0.5f;
         zf acc[LM_MAXV];
 #pragma unroll
         for (int v = 0; v < LM_MAXV; ++v) acc[v] = zf{0.f, 0.f};
-        {
+        if (nch > 0) {
+            issue(0, 0);
+            cp_commit();
+        }
+        if (act) {
             float r = sqrtf(xi * xi + yi * yi);
             float J[P + 1];
             bessel_j_scaled<float>(P, k * r, k * w, J);
@@ -644,40 +735,56 @@ __global__ void k_leaf32(int64_t ncol, float w, float k, float d, const float *x
                 }
             }
         }
-        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
-            const int32_t s = usrc[e], term = uterm[e];
-            const int64_t rs = s / ncol, cs = s % ncol;
-            const float ox = (float)(ct - cs) * w, oy = -(float)(rt - rs) * w; // centre_t - centre_s
-            zf part[LM_MAXV];
-#pragma unroll
-            for (int v = 0; v < LM_MAXV; ++v) part[v] = zf{0.f, 0.f};
-            for (int64_t j = ls[s]; j < ls[s + 1]; ++j) {
-                const float dx = (xi - xl[j]) + ox;
-                zf g;
-                if (term == 0) {
-                    if (j == i) continue;
-                    const float dy = (yi - yl[j]) + oy;
-                    g = green_free32(k * sqrtf(dx * dx + dy * dy));
-                } else {
-                    // tail of a reflected direct term; its segment part is added by k_near_pw32
-                    const float h = term == 1 ? -(ya + y32[j]) : ya + y32[j] + 2.0f * d;
-                    g = zf{near_tail32(nq, term - 1, fabsf(dx), h), 0.f};
-                }
-                const float4 *qj = (const float4 *)(qs + j * LM_MAXV);
-#pragma unroll
-                for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {
-                    float4 t = qj[v2];
-                    cfmaf(part[2 * v2], g, zf{t.x, t.y});
-                    cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
-                }
+        for (int c = 0; c < nch; ++c) {
+            const int buf = c & 1;
+            if (c + 1 < nch) {
+                issue(c + 1, buf ^ 1);
+                cp_commit();
+                cp_wait<1>();
+            } else {
+                cp_wait<0>();
             }
+            __syncthreads();
+            const LeafChunk ch = chunk_at(c);
+            const int s = usrc[ch.e], term = uterm[ch.e];
+            const int rs = s / (int)ncol, cs = s % (int)ncol;
+            const float ox = (float)(ct - cs) * w, oy = -(float)(rt - rs) * w; // centre_t - centre_s
+            if (act) {
+                zf part[LM_MAXV];
 #pragma unroll
-            for (int v = 0; v < LM_MAXV; ++v) acc[v] = acc[v] + part[v];
+                for (int v = 0; v < LM_MAXV; ++v) part[v] = zf{0.f, 0.f};
+                for (int jj = 0; jj < ch.cnt; ++jj) {
+                    const float dx = (xi - sx[buf][jj]) + ox;
+                    zf g;
+                    if (term == 0) {
+                        if (ch.j0 + jj == i) continue;
+                        const float dy = (yi - sy[buf][jj]) + oy;
+                        const float r2 = dx * dx + dy * dy;
+                        g = green_free32(k * r2 * rsqrtf(r2), nterms);
+                    } else {
+                        // tail of a reflected direct term; its segment part is added by k_near_pw32
+                        const float h = term == 1 ? -(ya + sya[buf][jj]) : ya + sya[buf][jj] + 2.0f * d;
+                        g = zf{near_tail32(nq, term - 1, fabsf(dx), h), 0.f};
+                    }
+                    const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
+#pragma unroll
+                    for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {
+                        const float4 t = qj[v2];
+                        cfmaf(part[2 * v2], g, zf{t.x, t.y});
+                        cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < LM_MAXV; ++v) acc[v] = acc[v] + part[v];
+            }
+            __syncthreads(); // buffer `buf` is refilled by the issue of chunk c + 2
         }
-        float4 *o = (float4 *)(us + i * LM_MAXV);
+        if (act) {
+            float4 *o = (float4 *)(us + (int64_t)i * LM_MAXV);
 #pragma unroll
-        for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
-            o[v2] = make_float4(acc[2 * v2].re, acc[2 * v2].im, acc[2 * v2 + 1].re, acc[2 * v2 + 1].im);
+            for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
+                o[v2] = make_float4(acc[2 * v2].re, acc[2 * v2].im, acc[2 * v2 + 1].re, acc[2 * v2 + 1].im);
+        }
     }
 }
 
@@ -695,11 +802,14 @@ template <int P>
 static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st)
 {
     const Level &lv = t->lev[t->L];
+    // largest k r of a direct pair: two leaves apart diagonally
+    const int nterms = lm_h0_terms(t->med.k2 * lv.w * 2.0 * 1.4142135623730951 * 1.0001);
     k_leaf32<P><<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
                                                    t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart, t->usrc,
-                                                   t->uterm, nq, lv.L32, t->qs32, t->us32);
+                                                   t->uterm, nq, lv.L32, t->qs32, t->us32, nterms);
 }
 
+int lm_h0_terms(double xmax);
 static size_t near_pw_smem(const lm_tree_s *t)
 {
     return (size_t)2 * t->nq.nseg * LM_MAXV * sizeof(zf) + PW_SRC * LM_MAXV * sizeof(zf) + 2 * PW_SRC * sizeof(float);
@@ -771,7 +881,12 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
             lm_phase_begin(t, PH_M2L, st);
             int launches = 0;
             if (l > 0) {
-                MX_DISPATCH(P, launch_stencil, lv, st);
+                if (t->tc_ready && lv.rb) {
+                    lm_status s = lm_launch_m2l_tc(t, l, st);
+                    if (s != LM_OK) return s;
+                } else {
+                    MX_DISPATCH(P, launch_stencil, lv, st);
+                }
                 ++launches;
             }
             if (lv.nrest > 0) {

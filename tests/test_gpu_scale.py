@@ -59,3 +59,23 @@ def test_wide_strip_mixed_sampled(case, p, depth):
     err = np.linalg.norm(u - ref) / np.linalg.norm(ref)
     print(f"wide strip mixed p={p} depth={depth}: rel-l2 {err:.3e} on {tg.size} sampled targets")
     assert err < 1e-6
+
+
+def test_tensor_core_m2l_matches_cuda_cores():
+    """The tcgen05 M2L (TF32 hi/lo split) against the FP32 CUDA-core stencil."""
+    import torch
+
+    import paper_1902_08250_gb300 as lm
+
+    x, y, q = workloads.wide_uniform(200_000, 16, seed=3)
+    xd, yd, qd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), torch.from_numpy(q).cuda()
+    out = []
+    for tc in (1, 0):
+        m = lm.create_medium(*workloads.MEDIUM_B, p=14, depth=4, precision="mixed", tensor_m2l=tc)
+        t = lm.build_tree(m, xd, yd)
+        u = lm.apply(t, qd)
+        lm.sync_status(t)
+        out.append(u.cpu().numpy())
+    err = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[1])
+    print(f"tensor-core vs CUDA-core M2L: rel-l2 {err:.3e}")
+    assert err < 5e-7
