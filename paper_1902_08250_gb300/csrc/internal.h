@@ -94,6 +94,7 @@ struct lm_tree_s {
     zd *qs, *us; // [LM_MAXV][n] tree-order scratch
     // mixed path
     float *xl32, *yl32, *y32; // leaf-local coordinates and absolute y, FP32 [n]
+    int64_t *iperm;            // [n] input index -> tree position
     zf *qs32, *us32;           // [n][LM_MAXV]
     zf *nq_seg_lam, *nq_seg_s2, *nq_seg_w, *nq_tail_lam, *nq_tail_s2, *nq_tail_w;
     bool tc_ready; // tensor-core M2L tables built

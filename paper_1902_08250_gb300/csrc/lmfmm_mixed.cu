@@ -91,6 +91,7 @@ __global__ void k_scan64b(int64_t *c, int64_t m)
 
 struct NearQuadF;
 static size_t near_pw_smem(const lm_tree_s *t);
+__global__ void k_inverse_perm(const int64_t *perm, int64_t n, int64_t *iperm);
 __global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, float w, float d, const float *xl,
                                                    const float *y32, const int64_t *ls, const int64_t *ustart,
                                                    const int32_t *usrc, const int32_t *uterm, NearQuadF nq,
@@ -160,6 +161,8 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
         k_local_coords<<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, t->x0, lv.w, t->leaf_start, t->xs, t->ys,
                                                           t->xl32, t->yl32, t->y32);
     }
+    TRYM(lm_dalloc(t, &t->iperm, n));
+    k_inverse_perm<<<gridm(n, 256), 256, 0, st>>>(t->perm, n, t->iperm);
     TRYM(lm_dalloc(t, &t->qs32, n * LM_MAXV));
     TRYM(lm_dalloc(t, &t->us32, n * LM_MAXV));
     NearQuad &q = t->nq;
@@ -184,7 +187,7 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
 
 void lm_free_mixed(lm_tree_s *t)
 {
-    void *ptrs[] = {t->xl32, t->yl32, t->y32, t->qs32, t->us32, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w,
+    void *ptrs[] = {t->xl32, t->yl32, t->y32, t->qs32, t->us32, t->iperm, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w,
                     t->nq_tail_lam, t->nq_tail_s2, t->nq_tail_w};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -199,12 +202,13 @@ void lm_free_mixed(lm_tree_s *t)
 // ---------------------------------------------------------------------------
 // apply kernels (FP32)
 // ---------------------------------------------------------------------------
-__global__ void k_permute_in32(const zd *q, const int64_t *perm, int64_t n, int nvec, int conjugate,
-                               zf *qs)
+// input order -> tree order: one thread per input point, coalesced reads of
+// q[v][j], one 128-byte row written at the point's tree position
+__global__ void k_permute_in32(const zd *q, const int64_t *iperm, int64_t n, int nvec, int conjugate, zf *qs)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t j = perm[i];
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t i = iperm[j];
     zf a[LM_MAXV];
 #pragma unroll
     for (int v = 0; v < LM_MAXV; ++v) {
@@ -219,12 +223,13 @@ __global__ void k_permute_in32(const zd *q, const int64_t *perm, int64_t n, int 
     for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
         o[v2] = make_float4(a[2 * v2].re, a[2 * v2].im, a[2 * v2 + 1].re, a[2 * v2 + 1].im);
 }
-__global__ void k_permute_out32(const zf *us, const int64_t *perm, int64_t n, int nvec, int conjugate,
-                                zd *u)
+// tree order -> input order: one thread per input point, one 128-byte row
+// read at its tree position, coalesced writes of u[v][j]
+__global__ void k_permute_out32(const zf *us, const int64_t *iperm, int64_t n, int nvec, int conjugate, zd *u)
 {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int64_t j = perm[i];
+    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int64_t i = iperm[j];
     const float4 *src = (const float4 *)(us + i * LM_MAXV);
     float4 a[LM_MAXV / 2];
 #pragma unroll
@@ -237,6 +242,11 @@ __global__ void k_permute_out32(const zf *us, const int64_t *perm, int64_t n, in
             u[(int64_t)v * n + j] = conjugate ? conj(b) : b;
         }
     }
+}
+__global__ void k_inverse_perm(const int64_t *perm, int64_t n, int64_t *iperm)
+{
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) iperm[perm[i]] = i;
 }
 
 // S2M in FP32 (Eq. (multipole_coef), scaled): one block per leaf
@@ -449,36 +459,36 @@ __global__ void k_m2l_rest32(int64_t nbox, int P, const int64_t *rstart, const i
 //   J0 = sum_m (-t)^m/(m!)^2,  Y0 = (2/pi)[(ln(x/2) + gamma) J0 - sum_{m>=1} H_m (-t)^m/(m!)^2],
 // H_m the harmonic numbers; 11 terms keep the truncation below 1e-9.
 // Larger x use the library's j0f / y0f.
-// nterms: series length, chosen per tree from the largest k r of any direct
-// pair so that the truncation stays below 1e-9 (at most 11 terms, x <= 2)
-__device__ __forceinline__ zf green_free32(float x, int nterms)
+// (i/4) H0^(1)(x) in FP32 as a function of t = x^2/4.  For t <= 1 (x <= 2)
+// the ascending series of J0 and Y0 (Abramowitz & Stegun 9.1.12, 9.1.13),
+//   J0 = sum_m c_m t^m,  c_m = (-1)^m/(m!)^2,
+//   Y0 = (2/pi) [ (ln(x/2) + gamma) J0 - sum_{m>=1} H_m c_m t^m ],  ln(x/2) = ln(t)/2,
+// H_m the harmonic numbers, are evaluated by Horner's rule to degree 8
+// (truncation < 1e-11); no square root is needed.  Larger x use the
+// library's j0f / y0f.
+__device__ __forceinline__ zf green_free32_t(float t)
 {
-    // 1/m^2 and the harmonic numbers H_m, m = 1..11
-    constexpr float kInvM2[11] = {1.0f, 0.25f, 0.11111111f, 0.0625f, 0.04f, 0.027777778f,
-                                  0.020408163f, 0.015625f, 0.012345679f, 0.01f, 0.0082644628f};
-    constexpr float kHarm[11] = {1.0f, 1.5f, 1.8333333f, 2.0833333f, 2.2833333f, 2.45f,
-                                 2.5928571f, 2.7178571f, 2.8289683f, 2.9289683f, 3.0198773f};
     float j, y;
-    if (x <= 2.0f) {
-        const float mt = -0.25f * x * x;
-        float a = 1.0f, sj = 1.0f, sh = 0.0f;
-#pragma unroll
-        for (int m = 0; m < 11; ++m) {
-            if (m < nterms) {
-                a *= mt * kInvM2[m];
-                sj += a;
-                sh = fmaf(kHarm[m], a, sh);
-            }
-        }
-        j = sj;
-        // MUFU logarithm: absolute error ~1e-7 on (0, 1], well inside the 1e-6 budget
-        y = 0.63661977236758134f * ((__logf(0.5f * x) + 0.57721566490153286f) * sj - sh);
+    if (t <= 1.0f) {
+        // c_m and H_m c_m for m = 8 .. 1, from the series definitions
+        const float c8 = 6.15118733e-10f, c7 = -3.93675989e-08f, c6 = 1.92901235e-06f, c5 = -6.94444444e-05f,
+                    c4 = 1.73611111e-03f, c3 = -2.77777778e-02f, c2 = 0.25f, c1 = -1.0f;
+        const float e8 = 1.67180484e-09f, e7 = -1.02074560e-07f, e6 = 4.72608025e-06f, e5 = -1.58564815e-04f,
+                    e4 = 3.61689815e-03f, e3 = -5.09259259e-02f, e2 = 0.375f, e1 = -1.0f;
+        float pj = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(c8, t, c7), t, c6), t, c5), t, c4), t, c3), t, c2), t, c1);
+        j = fmaf(pj, t, 1.0f);
+        float ps = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(e8, t, e7), t, e6), t, e5), t, e4), t, e3), t, e2), t, e1);
+        const float sh = ps * t;
+        // MUFU logarithm: absolute error ~1e-7, well inside the 1e-6 budget
+        y = 0.63661977236758134f * (fmaf(0.5f, __logf(t), 0.57721566490153286f) * j - sh);
     } else {
+        const float x = 2.0f * sqrtf(t);
         j = j0f(x);
         y = y0f(x);
     }
     return zf{-0.25f * y, 0.25f * j};
 }
+__device__ __forceinline__ zf green_free32(float x, int) { return green_free32_t(0.25f * x * x); }
 
 // terms of the J0/Y0 series needed for arguments up to xmax (truncation < 1e-9)
 int lm_h0_terms(double xmax)
@@ -670,6 +680,7 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
     const zf *Lb = Lc + b * NP * LM_MAXV;
     const int lo = (int)ls[b], hi = (int)ls[b + 1];
     const int e0 = (int)ustart[b], e1 = (int)ustart[b + 1];
+    const float k24 = 0.25f * k * k;
 
     // chunk c of the U list -> (entry, first point, count); enumerated on the fly
     auto chunk_at = [&](int c) {
@@ -759,8 +770,7 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
                     if (term == 0) {
                         if (ch.j0 + jj == i) continue;
                         const float dy = (yi - sy[buf][jj]) + oy;
-                        const float r2 = dx * dx + dy * dy;
-                        g = green_free32(k * r2 * rsqrtf(r2), nterms);
+                        g = green_free32_t(k24 * fmaf(dx, dx, dy * dy));
                     } else {
                         // tail of a reflected direct term; its segment part is added by k_near_pw32
                         const float h = term == 1 ? -(ya + sya[buf][jj]) : ya + sya[buf][jj] + 2.0f * d;
@@ -852,7 +862,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         lm_phase_begin(t, PH_PERMUTE, st);
-        k_permute_in32<<<gridm(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->perm, n, nv, adjoint, t->qs32);
+        k_permute_in32<<<gridm(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->iperm, n, nv, adjoint, t->qs32);
         lm_phase_end(t, PH_PERMUTE, st, 1);
         lm_phase_begin(t, PH_S2M, st);
         {
@@ -907,7 +917,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
         }
         lm_phase_end(t, PH_LEAF, st, 2);
         lm_phase_begin(t, PH_PERMUTE, st);
-        k_permute_out32<<<gridm(n, 256), 256, 0, st>>>(t->us32, t->perm, n, nv, adjoint, u + (int64_t)v0 * n);
+        k_permute_out32<<<gridm(n, 256), 256, 0, st>>>(t->us32, t->iperm, n, nv, adjoint, u + (int64_t)v0 * n);
         lm_phase_end(t, PH_PERMUTE, st, 1);
         LM_CUDA(cudaGetLastError());
     }
