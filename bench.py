@@ -40,7 +40,7 @@ PHASES = ["permute", "s2m", "m2m", "m2l", "l2l", "l2t_s2t", "refine"]
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
@@ -309,6 +309,7 @@ def main():
     peaks = measured_peaks()
     dom = max(phase_ms, key=phase_ms.get)
     roof = roofline(lm, tree, dom, phase_ms[dom], npc, precision, dev, peaks)
+    roof_m2l = roofline(lm, tree, "m2l", phase_ms["m2l"], npc, precision, dev, peaks) if dom != "m2l" else None
 
     if rank != 0:
         return
@@ -337,6 +338,7 @@ def main():
         "gpu_launches": launches,
         "phase_ms": phase_ms,
         "roofline": roof,
+        "roofline_m2l": roof_m2l,
         "cpu_baseline": cpu,
     }
     if rel_err is not None:
@@ -347,27 +349,49 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def roofline(lm, tree, phase, ms, npc, precision, dev, peaks):
-    """Algorithmic work of the dominant phase per apply over its measured time."""
+def _probe(lm, kind, dev):
     import torch
 
+    rate = ctypes.c_double()
+    lm._lib.lm_peak_probe(kind, 20000, ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream),
+                          ctypes.byref(rate))
+    return rate.value / 1e12
+
+
+def roofline(lm, tree, phase, ms, npc, precision, dev, peaks):
+    """Algorithmic work of the dominant phase per apply over its measured time
+    (CUDA events the library records on the launching stream)."""
     info = tree.info
     L = info["depth"]
     if phase == "m2l":
         entries = sum(tree.list_export(0, l).shape[0] for l in range(L + 1))
         flops = 8.0 * npc * npc * entries * NVEC
-        kind = 0 if precision == "fp64" else 1
-        rate = ctypes.c_double()
-        lm._lib.lm_peak_probe(kind, 20000, ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream),
-                              ctypes.byref(rate))
+        if precision == "fp64":
+            peak, src = _probe(lm, 0, dev), "lm_peak_probe FP64 FMA chains on all SMs (measured live)"
+        else:
+            # tcgen05 kind::tf32: the measured bf16 dense peak x the nominal tf32/bf16 ratio (1.1/2.25)
+            bf = (peaks or {}).get("bf16_tflops")
+            peak = bf * 1.1 / 2.25 if bf else 1900 * 1.1 / 2.25
+            src = "MEASURED_PEAKS bf16_tflops x 1.1/2.25 (tf32 nominal ratio)" if bf else "fallback 1.9 PF bf16 x 1.1/2.25"
         ach = flops / (ms * 1e-3) / 1e12
-        return {"bound": "alu", "kernel": "k_m2l64" if precision == "fp64" else "m2l",
-                "achieved": ach, "peak": rate.value / 1e12, "unit": "TFLOP/s",
-                "frac": ach / (rate.value / 1e12), "traffic": recorded_traffic("m2l"),
-                "work": f"8 (2p+1)^2 flops per V-list entry per vector; {entries} entries",
-                "peak_source": "lm_peak_probe FP64 FMA chains, all SMs (measured live)"
-                if kind == 0 else "lm_peak_probe FP32 FMA chains (measured live)"}
-    # leaf / other phases: pair-kernel evaluations against the measured FP64 exp rate
+        return {"bound": "tensor" if precision != "fp64" else "alu", "kernel": "m2l", "achieved": ach,
+                "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": recorded_traffic("m2l"),
+                "work": f"8 (2p+1)^2 flop per V-list entry per vector; {entries} entries", "peak_source": src}
+    if phase == "l2t_s2t":
+        perm, ls = tree.export()
+        cnt = np.diff(ls)
+        U = tree.list_export(1)
+        pairs = int(np.sum(cnt[U[:, 0]] * cnt[U[:, 2]])) - tree.n
+        flops = 8.0 * NVEC * pairs + 8.0 * NVEC * npc * tree.n
+        peak = _probe(lm, 0 if precision == "fp64" else 1, dev)
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "kernel": "k_leaf64" if precision == "fp64" else "k_leaf32 + k_near_pw32",
+                "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": recorded_traffic("l2t_s2t"),
+                "work": f"8 flop per complex MAC x 16 vectors over {pairs} direct pairs and (2p+1) local terms "
+                        "per target (kernel evaluation itself not counted)",
+                "peak_source": "lm_peak_probe %s FMA chains on all SMs (measured live)" %
+                               ("FP64" if precision == "fp64" else "FP32")}
     return {"bound": "alu", "kernel": phase, "achieved": None, "peak": None, "unit": "TFLOP/s",
             "frac": None, "traffic": recorded_traffic(phase), "phase_ms": ms}
 
