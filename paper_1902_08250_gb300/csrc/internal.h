@@ -68,6 +68,8 @@ struct Level {
     int64_t nrest;
     int64_t *rstart; // [nbox + 1]
     int32_t *rsrc, *rslot;
+    int64_t nrtgt;   // targets with entries on the rest list
+    int32_t *rtgt;   // [nrtgt]
     // tensor-core M2L: real-block TF32 hi/lo table images and their (dc, dr) map
     float *rb;
     int32_t *rbslot;

@@ -151,6 +151,19 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
         TRYM(lm_dalloc(t, &lv.rslot, lv.nrest));
         k_rest<<<gridm(lv.nbox, 128), 128, 0, st>>>(l, lv.nbox, lv.vstart, lv.vsrc, lv.vslot, lv.vterm,
                                                      lv.rstart, lv.rsrc, lv.rslot, 1);
+        {
+            // targets that have entries on this list
+            std::vector<int64_t> hs(lv.nbox + 1);
+            LM_CUDA(cudaMemcpyAsync(hs.data(), lv.rstart, (lv.nbox + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            LM_CUDA(cudaStreamSynchronize(st));
+            std::vector<int32_t> tg;
+            for (int64_t b2 = 0; b2 < lv.nbox; ++b2)
+                if (hs[b2 + 1] > hs[b2]) tg.push_back((int32_t)b2);
+            lv.nrtgt = (int64_t)tg.size();
+            TRYM(lm_dalloc(t, &lv.rtgt, tg.size()));
+            if (!tg.empty())
+                LM_CUDA(cudaMemcpyAsync(lv.rtgt, tg.data(), tg.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        }
     }
     const int64_t n = t->n;
     TRYM(lm_dalloc(t, &t->xl32, n));
@@ -193,7 +206,7 @@ void lm_free_mixed(lm_tree_s *t)
         if (p) cudaFree(p);
     for (Level &lv : t->lev) {
         void *lp[] = {lv.tab32, lv.m2m32, lv.l2l32, lv.M32, lv.L32, lv.stencil, lv.rstart, lv.rsrc, lv.rslot,
-                      lv.rb, lv.rbslot};
+                      lv.rb, lv.rbslot, lv.rtgt};
         for (void *p : lp)
             if (p) cudaFree(p);
     }
@@ -310,43 +323,46 @@ __global__ void k_p2m32(int P, float k, float w, const float *xl, const float *y
     }
 }
 
-__global__ void k_m2m32(int64_t ncol, int64_t nbox, int P, const zf *tabs, const zf *Mc, zf *Mp)
+template <int NP>
+__global__ void k_m2m32(int64_t ncol, int64_t nbox, const zf *tabs, const zf *Mc, zf *Mp)
 {
-    const int np = 2 * P + 1;
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= nbox * np * LM_MAXV) return;
+    if (idx >= nbox * NP * LM_MAXV) return;
     int v = idx % LM_MAXV;
-    int p = (idx / LM_MAXV) % np;
-    int64_t b = idx / (LM_MAXV * np);
+    int p = (idx / LM_MAXV) % NP;
+    int64_t b = idx / (LM_MAXV * NP);
     int64_t r = b / ncol, c = b % ncol, ncc = 2 * ncol;
     zf acc = {0.f, 0.f};
+#pragma unroll
     for (int pos = 0; pos < 4; ++pos) {
         int dy = pos >> 1, dx = pos & 1;
         int64_t ch = (2 * r + dy) * ncc + 2 * c + dx;
-        const zf *T = tabs + ((int64_t)pos * np + p) * np;
-        const zf *m = Mc + ch * np * LM_MAXV + v;
+        const zf *T = tabs + ((int64_t)pos * NP + p) * NP;
+        const zf *m = Mc + ch * NP * LM_MAXV + v;
         zf tmp = {0.f, 0.f};
-        for (int q = 0; q < np; ++q) cfmaf(tmp, T[q], m[q * LM_MAXV]);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) cfmaf(tmp, T[q], m[q * LM_MAXV]);
         acc = acc + tmp;
     }
     Mp[idx] = acc;
 }
 
-__global__ void k_l2l32(int64_t ncol, int64_t nbox, int P, const zf *tabs, const zf *Lp, zf *Lc)
+template <int NP>
+__global__ void k_l2l32(int64_t ncol, int64_t nbox, const zf *tabs, const zf *Lp, zf *Lc)
 {
-    const int np = 2 * P + 1;
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= nbox * np * LM_MAXV) return;
+    if (idx >= nbox * NP * LM_MAXV) return;
     int v = idx % LM_MAXV;
-    int p = (idx / LM_MAXV) % np;
-    int64_t b = idx / (LM_MAXV * np);
+    int p = (idx / LM_MAXV) % NP;
+    int64_t b = idx / (LM_MAXV * NP);
     int64_t r = b / ncol, c = b % ncol;
     int pos = (int)((r & 1) * 2 + (c & 1));
     int64_t par = (r / 2) * (ncol / 2) + c / 2;
-    const zf *T = tabs + ((int64_t)pos * np + p) * np;
-    const zf *m = Lp + par * np * LM_MAXV + v;
+    const zf *T = tabs + ((int64_t)pos * NP + p) * NP;
+    const zf *m = Lp + par * NP * LM_MAXV + v;
     zf acc = {0.f, 0.f};
-    for (int q = 0; q < np; ++q) cfmaf(acc, T[q], m[q * LM_MAXV]);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) cfmaf(acc, T[q], m[q * LM_MAXV]);
     Lc[idx] = acc;
 }
 
@@ -430,35 +446,32 @@ __global__ void __launch_bounds__(64 * ((NP + ST_RG - 1) / ST_RG))
     }
 }
 
-// remaining V-list entries (level 0 and the image terms), one thread per (target, order, vector)
-__global__ void k_m2l_rest32(int64_t nbox, int P, const int64_t *rstart, const int32_t *rsrc,
+// remaining V-list entries (level 0 and the image terms), one thread per
+// (target with such entries, order, vector); the targets are listed in rtgt
+template <int NP>
+__global__ void k_m2l_rest32(int64_t ntgt, const int32_t *rtgt, const int64_t *rstart, const int32_t *rsrc,
                              const int32_t *rslot, const zf *tab, const zf *M, zf *Lc)
 {
-    const int np = 2 * P + 1;
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= nbox * np * LM_MAXV) return;
+    if (idx >= ntgt * NP * LM_MAXV) return;
     int v = idx % LM_MAXV;
-    int p = (idx / LM_MAXV) % np;
-    int64_t b = idx / (LM_MAXV * np);
+    int p = (idx / LM_MAXV) % NP;
+    int64_t b = rtgt[idx / (LM_MAXV * NP)];
     int64_t e0 = rstart[b], e1 = rstart[b + 1];
-    if (e0 == e1) return;
     zf acc = {0.f, 0.f};
     for (int64_t e = e0; e < e1; ++e) {
-        const zf *T = tab + ((int64_t)rslot[e] * np + p) * np;
-        const zf *m = M + (int64_t)rsrc[e] * np * LM_MAXV + v;
+        const zf *T = tab + ((int64_t)rslot[e] * NP + p) * NP;
+        const zf *m = M + (int64_t)rsrc[e] * NP * LM_MAXV + v;
         zf tmp = {0.f, 0.f};
-        for (int q = 0; q < np; ++q) cfmaf(tmp, T[q], m[q * LM_MAXV]);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) cfmaf(tmp, T[q], m[q * LM_MAXV]);
         acc = acc + tmp;
     }
-    zf o = Lc[idx];
-    Lc[idx] = zf{o.re + acc.re, o.im + acc.im};
+    const int64_t o = (b * NP + p) * LM_MAXV + v;
+    zf x = Lc[o];
+    Lc[o] = zf{x.re + acc.re, x.im + acc.im};
 }
 
-// (i/4) H0^(1)(x) in FP32.  For x <= 2 the ascending series of J0 and Y0
-// (Abramowitz & Stegun 9.1.12, 9.1.13) share one power series in t = x^2/4:
-//   J0 = sum_m (-t)^m/(m!)^2,  Y0 = (2/pi)[(ln(x/2) + gamma) J0 - sum_{m>=1} H_m (-t)^m/(m!)^2],
-// H_m the harmonic numbers; 11 terms keep the truncation below 1e-9.
-// Larger x use the library's j0f / y0f.
 // (i/4) H0^(1)(x) in FP32 as a function of t = x^2/4.  For t <= 1 (x <= 2)
 // the ascending series of J0 and Y0 (Abramowitz & Stegun 9.1.12, 9.1.13),
 //   J0 = sum_m c_m t^m,  c_m = (-1)^m/(m!)^2,
@@ -764,24 +777,37 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
                 zf part[LM_MAXV];
 #pragma unroll
                 for (int v = 0; v < LM_MAXV; ++v) part[v] = zf{0.f, 0.f};
-                for (int jj = 0; jj < ch.cnt; ++jj) {
-                    const float dx = (xi - sx[buf][jj]) + ox;
-                    zf g;
-                    if (term == 0) {
-                        if (ch.j0 + jj == i) continue;
-                        const float dy = (yi - sy[buf][jj]) + oy;
-                        g = green_free32_t(k24 * fmaf(dx, dx, dy * dy));
-                    } else {
-                        // tail of a reflected direct term; its segment part is added by k_near_pw32
-                        const float h = term == 1 ? -(ya + sya[buf][jj]) : ya + sya[buf][jj] + 2.0f * d;
-                        g = zf{near_tail32(nq, term - 1, fabsf(dx), h), 0.f};
-                    }
-                    const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
+                if (term == 0) {
+                    const int self = i - ch.j0; // this target's slot in the chunk, if it is a source here
+#pragma unroll 2
+                    for (int jj = 0; jj < ch.cnt; ++jj) {
+                        const float dx = (xi - sx[buf][jj]) + ox, dy = (yi - sy[buf][jj]) + oy;
+                        // the free-space self term is excluded: a dummy t = 1 keeps the
+                        // evaluation finite and the weight is zeroed
+                        const float t2 = jj == self ? 1.0f : k24 * fmaf(dx, dx, dy * dy);
+                        zf g = green_free32_t(t2);
+                        if (jj == self) g = zf{0.f, 0.f};
+                        const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
 #pragma unroll
-                    for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {
-                        const float4 t = qj[v2];
-                        cfmaf(part[2 * v2], g, zf{t.x, t.y});
-                        cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
+                        for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {
+                            const float4 t = qj[v2];
+                            cfmaf(part[2 * v2], g, zf{t.x, t.y});
+                            cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
+                        }
+                    }
+                } else {
+                    for (int jj = 0; jj < ch.cnt; ++jj) {
+                        // tail of a reflected direct term; its segment part is added by k_near_pw32
+                        const float dx = (xi - sx[buf][jj]) + ox;
+                        const float h = term == 1 ? -(ya + sya[buf][jj]) : ya + sya[buf][jj] + 2.0f * d;
+                        const zf g = zf{near_tail32(nq, term - 1, fabsf(dx), h), 0.f};
+                        const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
+#pragma unroll
+                        for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {
+                            const float4 t = qj[v2];
+                            cfmaf(part[2 * v2], g, zf{t.x, t.y});
+                            cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
+                        }
                     }
                 }
 #pragma unroll
@@ -807,6 +833,28 @@ static void launch_stencil(const Level &lv, cudaStream_t st)
     dim3 g((unsigned)((ncls + 15) / 16), 4);
     k_m2l_stencil32<NP><<<g, 64 * ((NP + ST_RG - 1) / ST_RG), 0, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32,
                                                                          lv.M32, lv.L32);
+}
+template <int P>
+static void launch_m2m(const Level &lv, const Level &child, cudaStream_t st)
+{
+    constexpr int NP = 2 * P + 1;
+    int64_t tot = lv.nbox * NP * LM_MAXV;
+    k_m2m32<NP><<<gridm(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, lv.m2m32, child.M32, lv.M32);
+}
+template <int P>
+static void launch_l2l(const Level &lv, const Level &par, cudaStream_t st)
+{
+    constexpr int NP = 2 * P + 1;
+    int64_t tot = lv.nbox * NP * LM_MAXV;
+    k_l2l32<NP><<<gridm(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, lv.l2l32, par.L32, lv.L32);
+}
+template <int P>
+static void launch_rest(const Level &lv, cudaStream_t st)
+{
+    constexpr int NP = 2 * P + 1;
+    int64_t tot = lv.nrtgt * NP * LM_MAXV;
+    k_m2l_rest32<NP><<<gridm(tot, 128), 128, 0, st>>>(lv.nrtgt, lv.rtgt, lv.rstart, lv.rsrc, lv.rslot, lv.tab32,
+                                                       lv.M32, lv.L32);
 }
 template <int P>
 static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st)
@@ -874,9 +922,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
         lm_phase_end(t, PH_S2M, st, 1);
         if (L > 0) lm_phase_begin(t, PH_M2M, st);
         for (int l = L - 1; l >= 0; --l) {
-            Level &lv = t->lev[l];
-            int64_t tot = lv.nbox * np * LM_MAXV;
-            k_m2m32<<<gridm(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, lv.m2m32, t->lev[l + 1].M32, lv.M32);
+            MX_DISPATCH(P, launch_m2m, t->lev[l], t->lev[l + 1], st);
         }
         if (L > 0) lm_phase_end(t, PH_M2M, st, L);
         for (int l = 0; l <= L; ++l) {
@@ -886,7 +932,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
             if (l == 0)
                 LM_CUDA(cudaMemsetAsync(lv.L32, 0, lv.nbox * np * LM_MAXV * sizeof(zf), st));
             else
-                k_l2l32<<<gridm(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, lv.l2l32, t->lev[l - 1].L32, lv.L32);
+                MX_DISPATCH(P, launch_l2l, lv, t->lev[l - 1], st);
             lm_phase_end(t, PH_L2L, st, l > 0);
             lm_phase_begin(t, PH_M2L, st);
             int launches = 0;
@@ -900,8 +946,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
                 ++launches;
             }
             if (lv.nrest > 0) {
-                k_m2l_rest32<<<gridm(tot, 128), 128, 0, st>>>(lv.nbox, P, lv.rstart, lv.rsrc, lv.rslot, lv.tab32,
-                                                              lv.M32, lv.L32);
+                MX_DISPATCH(P, launch_rest, lv, st);
                 ++launches;
             }
             lm_phase_end(t, PH_M2L, st, launches);
