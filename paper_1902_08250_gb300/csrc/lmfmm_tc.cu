@@ -25,78 +25,8 @@
 #define TC_TILE_B (TC_N * TC_K * 4)      // bytes of one B operand
 #define TC_PAD 0                         // no slack after the tiles
 #define TC_SMEM (2 * TC_TILE_A + 2 * TC_TILE_B + TC_PAD + 64)
-#define TC_WAIT_LIMIT (1 << 20)
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ float tf32_rna(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-// byte offset of element (row, k) of a K-major no-swizzle operand with K = 64
-__host__ __device__ __forceinline__ uint32_t tc_off(int row, int k)
-{
-    return (uint32_t)((row >> 3) * 2048 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
-}
-
-// shared-memory matrix descriptor: start, LBO (K-direction core-matrix
-// stride), SBO (8-row-group stride), fixed 0b001 at bits 46-48, no swizzle
-__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(128 >> 4) << 16;
-    d |= (uint64_t)(2048 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
-}
-
-// instruction descriptor: D = F32, A = B = TF32, both K-major, N = 64, M = 128
-__host__ __device__ constexpr uint32_t tc_idesc()
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_ROWS >> 4) << 24);
-}
-
-// bounded wait; gives up after TC_WAIT_LIMIT polls or as soon as another CTA
-// has reported a timeout
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, const volatile int *err)
-{
-    for (int i = 0; i < TC_WAIT_LIMIT; ++i) {
-        if ((i & 1023) == 1023 && *err) return false;
-        uint32_t ok;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}\n"
-                     : "=r"(ok)
-                     : "r"(addr), "r"(parity)
-                     : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
-{
-    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
-                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v)
-{
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-                 "%12, %13, %14, %15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
+#include "tc_common.cuh"
 
 // Real-block TF32 hi/lo images of the stencil tables, already in the shared
 // layout (row n = real output order, k = real input order).
@@ -157,7 +87,7 @@ __global__ void __launch_bounds__(128, 2) k_m2l_tc(int64_t ncol, int64_t nrow, c
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const uint32_t idesc = tc_idesc();
+    const uint32_t idesc = tc_idesc_mn(TC_ROWS, TC_N);
     const uint32_t mb = smem_u32(mbar);
     uint32_t phase = 0;
     bool ok = true;
