@@ -228,6 +228,25 @@ lm_status lm_tree_order_noalloc(const double *x, const double *y, int64_t n, dou
                                 int *R, void *stream);
 
 /*
+ * Batched apply: the applies of `count` built trees -- each with its own
+ * medium, size, expansion order and precision -- captured once into one CUDA
+ * graph and replayed as a single launch.  Inside the graph the trees are
+ * forked over up to 8 streams so that small instances run concurrently.
+ *   batch_create: trees[i], q[i] (device, complex128 [nvec[i]][n_i]), u[i]
+ *     (device, same layout, not overlapping q[i]) for i < count.  The buffer
+ *     addresses are bound at capture: every launch reads q[i] and writes u[i].
+ *     The trees must be distinct and outlive the batch, and no other apply may
+ *     use them while a launch is in flight.  Profiling must be off on them.
+ *   batch_launch: enqueue the whole batch on `stream`.
+ * Errors: LM_EINVAL for bad arguments, LM_ECUDA if capture or instantiation fails.
+ */
+typedef struct lm_batch_s *lm_batch;
+lm_status lm_batch_create(const lm_tree *trees, int count, const void *const *q, const int *nvec,
+                          void *const *u, lm_batch *out);
+lm_status lm_batch_launch(lm_batch b, void *stream);
+void lm_batch_destroy(lm_batch b);
+
+/*
  * sync_status -- synchronise `stream` and report device-side failures of the
  * applies enqueued so far on tree t: LM_ETIMEOUT if a bounded wait inside a
  * tensor-core kernel gave up (the result of that apply is invalid), LM_OK

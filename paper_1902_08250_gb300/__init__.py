@@ -22,8 +22,8 @@ from . import _build
 HAS_MIXED = True
 
 __all__ = [
-    "LMError", "Medium", "Tree", "create_medium", "build_tree", "apply", "apply_adjoint", "library_path",
-    "FP64", "MIXED",
+    "LMError", "Medium", "Tree", "create_medium", "build_tree", "apply", "apply_adjoint", "green_apply",
+    "sync_status", "Batch", "library_path", "FP64", "MIXED",
 ]
 
 FP64, MIXED = 0, 1
@@ -67,6 +67,9 @@ def _load():
         "lm_peak_probe": (I, [I, I64, P, P]),
         "lm_tree_order_noalloc": (I, [P, P, I64, D, I, P, P, I64, P, P, P]),
         "lm_sync_status": (I, [V, P]),
+        "lm_batch_create": (I, [P, I, P, P, P, P]),
+        "lm_batch_launch": (I, [V, P]),
+        "lm_batch_destroy": (None, [V]),
         "lm_destroy_tree": (None, [V]),
         "lm_destroy_medium": (None, [V]),
         "lm_status_string": (ctypes.c_char_p, [I]),
@@ -218,3 +221,68 @@ def sync_status(tree: Tree, stream=None):
 def apply_adjoint(tree: Tree, v, w=None, stream=None):
     """w = G^H v = conj(G conj(v)) (reciprocity)."""
     return _apply(_lib.lm_apply_adjoint, tree, v, w, stream)
+
+
+def _autograd_function():
+    import torch
+
+    class _LayeredGreen(torch.autograd.Function):
+        """u = G q with dL/dq = G^H dL/du (G is linear; its adjoint is lm_apply_adjoint)."""
+
+        @staticmethod
+        def forward(ctx, q, tree):
+            ctx.tree = tree
+            return apply(tree, q.contiguous())
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            return apply_adjoint(ctx.tree, grad_u.contiguous()), None
+
+    return _LayeredGreen
+
+
+_LG = None
+
+
+def green_apply(tree: Tree, q):
+    """Differentiable u = G q (PyTorch autograd): gradients with respect to the
+    complex densities q flow through the adjoint apply (Sec. 3 reciprocity:
+    G^H v = conj(G conj(v)))."""
+    global _LG
+    if _LG is None:
+        _LG = _autograd_function()
+    return _LG.apply(q, tree)
+
+
+class Batch:
+    """Applies of several trees captured into one CUDA graph (lm_batch_create);
+    launch() replays them, reading the bound q buffers and writing the u buffers."""
+
+    def __init__(self, trees, qs, us):
+        import torch
+
+        if not (len(trees) == len(qs) == len(us)) or not trees:
+            raise ValueError("Batch: trees, qs and us must be non-empty and of equal length")
+        self.trees, self.qs, self.us = list(trees), list(qs), list(us)   # keep buffers alive
+        n = len(trees)
+        for t, q, u in zip(trees, qs, us):
+            for a in (q, u):
+                if not (a.is_cuda and a.dtype == torch.complex128 and a.is_contiguous()):
+                    raise ValueError("Batch: buffers must be contiguous complex128 CUDA tensors")
+            if q.shape[-1] != t.n or u.shape != q.shape:
+                raise ValueError("Batch: buffer shape does not match its tree")
+        th = (ctypes.c_void_p * n)(*[t._h.value for t in trees])
+        qp = (ctypes.c_void_p * n)(*[q.data_ptr() for q in qs])
+        up = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
+        nv = (ctypes.c_int * n)(*[1 if q.dim() == 1 else q.shape[0] for q in qs])
+        h = ctypes.c_void_p()
+        _check(_lib.lm_batch_create(th, n, qp, nv, up, ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(_lib.lm_batch_launch(self._h, _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lm_batch_destroy(self._h)
+            self._h = None

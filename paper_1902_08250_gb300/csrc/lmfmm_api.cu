@@ -461,3 +461,106 @@ extern "C" lm_status lm_peak_probe(int kind, int64_t iters, void *stream, double
     cudaFree(sink);
     return LM_OK;
 }
+
+// ---------------------------------------------------------------------------
+// batched apply as one captured CUDA graph
+// ---------------------------------------------------------------------------
+struct lm_batch_s {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+extern "C" void lm_batch_destroy(lm_batch b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    delete b;
+}
+
+extern "C" lm_status lm_batch_create(const lm_tree *trees, int count, const void *const *q, const int *nvec,
+                                     void *const *u, lm_batch *out)
+{
+    if (!out || !trees || !q || !nvec || !u || count < 1) {
+        lm_set_error("batch_create: bad argument");
+        return LM_EINVAL;
+    }
+    *out = nullptr;
+    for (int i = 0; i < count; ++i) {
+        lm_status s = check_apply(trees[i], q[i], nvec[i], u[i]);
+        if (s != LM_OK) return s;
+        for (int j = 0; j < i; ++j)
+            if (trees[j] == trees[i]) { // one tree's scratch cannot serve two concurrent applies
+                lm_set_error("batch_create: tree %d appears twice", i);
+                return LM_EINVAL;
+            }
+        if (trees[i]->prof_max) {
+            lm_set_error("batch_create: profiling is enabled on tree %d", i);
+            return LM_EINVAL;
+        }
+    }
+    const int nstream = std::min(count, 8);
+    cudaStream_t cs, side[8];
+    cudaEvent_t fork, join[8];
+    LM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    for (int k = 0; k < nstream; ++k) {
+        LM_CUDA(cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking));
+        LM_CUDA(cudaEventCreateWithFlags(&join[k], cudaEventDisableTiming));
+    }
+    LM_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    lm_batch_s *b = new (std::nothrow) lm_batch_s();
+    if (!b) {
+        lm_set_error("batch_create: host allocation failed");
+        return LM_ENOMEM;
+    }
+    lm_status st = LM_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(fork, cs);
+        for (int k = 0; k < nstream; ++k) cudaStreamWaitEvent(side[k], fork, 0);
+        for (int i = 0; i < count && st == LM_OK; ++i)
+            st = lm_run_apply(trees[i], (const zd *)q[i], nvec[i], (zd *)u[i], false, side[i % nstream]);
+        for (int k = 0; k < nstream; ++k) {
+            cudaEventRecord(join[k], side[k]);
+            cudaStreamWaitEvent(cs, join[k], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+        if (st == LM_OK && e2 != cudaSuccess) {
+            lm_set_error("batch_create: capture failed: %s", cudaGetErrorString(e2));
+            st = LM_ECUDA;
+        }
+        if (st == LM_OK) {
+            e2 = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            if (e2 != cudaSuccess) {
+                lm_set_error("batch_create: graph instantiation failed: %s", cudaGetErrorString(e2));
+                st = LM_ECUDA;
+            }
+        }
+    } else {
+        lm_set_error("batch_create: cudaStreamBeginCapture failed: %s", cudaGetErrorString(e));
+        st = LM_ECUDA;
+    }
+    cudaEventDestroy(fork);
+    for (int k = 0; k < nstream; ++k) {
+        cudaEventDestroy(join[k]);
+        cudaStreamDestroy(side[k]);
+    }
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    if (st != LM_OK) {
+        lm_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LM_OK;
+}
+
+extern "C" lm_status lm_batch_launch(lm_batch b, void *stream)
+{
+    if (!b || !b->exec) {
+        lm_set_error("batch_launch: NULL batch");
+        return LM_EINVAL;
+    }
+    LM_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return LM_OK;
+}

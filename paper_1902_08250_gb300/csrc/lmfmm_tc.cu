@@ -198,11 +198,17 @@ __global__ void __launch_bounds__(128, 2) k_m2l_tc(int64_t ncol, int64_t nrow, c
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(64));
 }
 
+static lm_status lm_attr_tc(int P);
+
 // ---------------------------------------------------------------------------
 lm_status lm_setup_tc(lm_tree_s *t, cudaStream_t st)
 {
     const int P = t->p, np = 2 * P + 1;
     if (2 * np > TC_K) return LM_OK; // orders beyond the tensor-core tile: CUDA-core stencil only
+    {
+        lm_status sa = lm_attr_tc(P);
+        if (sa != LM_OK) return sa;
+    }
     for (int l = 1; l <= t->L; ++l) {
         Level &lv = t->lev[l];
         std::vector<int32_t> slots, map(49, -1);
@@ -229,30 +235,47 @@ lm_status lm_setup_tc(lm_tree_s *t, cudaStream_t st)
 }
 
 template <int NP>
-static lm_status launch_tc_np(lm_tree_s *t, const Level &lv, cudaStream_t st)
+static lm_status attr_tc_np()
 {
     LM_CUDA(cudaFuncSetAttribute(k_m2l_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    return LM_OK;
+}
+
+template <int NP>
+static lm_status launch_tc_np(lm_tree_s *t, const Level &lv, cudaStream_t st)
+{
     int64_t ncls = (lv.ncol / 2) * (lv.nrow / 2);
     dim3 g((unsigned)((ncls + 7) / 8), 4);
     k_m2l_tc<NP><<<g, 128, TC_SMEM, st>>>(lv.ncol, lv.nrow, lv.rbslot, lv.rb, lv.M32, lv.L32, t->dflag + 1);
     return LM_OK;
 }
 
+#define TC_SWITCH(P, FN, ...)                    \
+    switch (P) {                                 \
+    case 4: return FN<9>(__VA_ARGS__);           \
+    case 6: return FN<13>(__VA_ARGS__);          \
+    case 8: return FN<17>(__VA_ARGS__);          \
+    case 9: return FN<19>(__VA_ARGS__);          \
+    case 10: return FN<21>(__VA_ARGS__);         \
+    case 11: return FN<23>(__VA_ARGS__);         \
+    case 12: return FN<25>(__VA_ARGS__);         \
+    case 13: return FN<27>(__VA_ARGS__);         \
+    case 14: return FN<29>(__VA_ARGS__);         \
+    default: break;                              \
+    }
+
+// kernel attributes are set once at set-up, never while an apply may be captured
+static lm_status lm_attr_tc(int P)
+{
+    TC_SWITCH(P, attr_tc_np);
+    lm_set_error("tensor-core M2L: order %d not instantiated", P);
+    return LM_ENOTSUP;
+}
+
 lm_status lm_launch_m2l_tc(lm_tree_s *t, int l, cudaStream_t st)
 {
     const Level &lv = t->lev[l];
-    switch (t->p) {
-    case 4: return launch_tc_np<9>(t, lv, st);
-    case 6: return launch_tc_np<13>(t, lv, st);
-    case 8: return launch_tc_np<17>(t, lv, st);
-    case 9: return launch_tc_np<19>(t, lv, st);
-    case 10: return launch_tc_np<21>(t, lv, st);
-    case 11: return launch_tc_np<23>(t, lv, st);
-    case 12: return launch_tc_np<25>(t, lv, st);
-    case 13: return launch_tc_np<27>(t, lv, st);
-    case 14: return launch_tc_np<29>(t, lv, st);
-    default: break;
-    }
+    TC_SWITCH(t->p, launch_tc_np, t, lv, st);
     lm_set_error("tensor-core M2L: order %d not instantiated", t->p);
     return LM_ENOTSUP;
 }

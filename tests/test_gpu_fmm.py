@@ -165,3 +165,34 @@ def test_mixed_adjoint_and_chunking(lm):
     lhs = np.vdot(q[1], u[0])
     rhs = np.vdot(w[1], q[0])
     assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+
+
+def test_batched_graph_matches_individual_applies(lm):
+    """Many independent media and trees in one captured graph (the batched form)."""
+    import torch
+
+    rng = np.random.default_rng(4)
+    trees, qs, us, refs = [], [], [], []
+    for i in range(6):
+        k1, k2, k3 = rng.uniform(0.5, 4.0, 3)
+        d = rng.uniform(0.5, 2.0)
+        n = int(np.exp(rng.uniform(np.log(2000), np.log(30000))))
+        x = rng.uniform(0.0, 10.0, n)
+        y = -d * rng.uniform(0.1, 0.9, n)
+        q = rng.standard_normal((4, n)) + 1j * rng.standard_normal((4, n))
+        prec = "mixed" if i % 2 else "fp64"
+        m = lm.create_medium(k1, k2, k3, d, p=12 if prec == "mixed" else 16, precision=prec)
+        t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+        qd = torch.from_numpy(q).cuda()
+        refs.append(lm.apply(t, qd).cpu().numpy())
+        trees.append(t)
+        qs.append(qd)
+        us.append(torch.zeros_like(qd))
+    b = lm.Batch(trees, qs, us)
+    for _ in range(2):
+        for u in us:
+            u.zero_()
+        b.launch()
+        torch.cuda.synchronize()
+        for u, r in zip(us, refs):
+            assert np.array_equal(u.cpu().numpy(), r)

@@ -79,3 +79,34 @@ def test_tensor_core_m2l_matches_cuda_cores():
     err = np.linalg.norm(out[0] - out[1]) / np.linalg.norm(out[1])
     print(f"tensor-core vs CUDA-core M2L: rel-l2 {err:.3e}")
     assert err < 5e-7
+
+
+def test_clustered_fp64_sampled(oracle):
+    """100k points, half within 0.01 of the interface y = 0 (|x1 - x0| >> |y1 + y0|:
+    the alternative-direction tails carry the reflected near field)."""
+    import torch
+
+    import paper_1902_08250_gb300 as lm
+
+    n = 100_000
+    x, y, _ = workloads.clustered(n, 1, seed=0)
+    rng = np.random.default_rng(5)
+    perm = rng.permutation(n)
+    src = np.sort(perm[:1500])
+    near = np.nonzero(y > -0.01)[0]
+    tg = np.sort(np.concatenate([rng.choice(np.setdiff1d(near, src), 24, replace=False),
+                                 rng.choice(np.setdiff1d(np.arange(n), np.concatenate([src, near])), 24,
+                                            replace=False)]))
+    q = np.zeros((1, n), np.complex128)
+    q[:, src] = rng.standard_normal((1, src.size)) + 1j * rng.standard_normal((1, src.size))
+    xs = np.concatenate([x[src], x[tg]])
+    ys = np.concatenate([y[src], y[tg]])
+    qq = np.concatenate([q[:, src], np.zeros((1, tg.size))], axis=1)
+    ref = oracle.direct_apply(workloads.MEDIUM_A, xs, ys, qq, targets=np.arange(src.size, src.size + tg.size))
+    for prec, p, tol in (("fp64", 20, 1e-10), ("mixed", 14, 1e-6)):
+        m = lm.create_medium(*workloads.MEDIUM_A, p=p, precision=prec)
+        t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+        u = lm.apply(t, torch.from_numpy(q).cuda()).cpu().numpy()[:, tg]
+        err = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+        print(f"clustered {prec} p={p} depth={t.info['depth']}: rel-l2 {err:.3e} on {tg.size} targets")
+        assert err < tol
