@@ -71,6 +71,9 @@ def _declare(L):
         "orc_green_refl": (_I, [_D, _D, _D, _D, _D, _D, _D, _D, _I, _I, _P]),
         "orc_green_term": (_I, [_D, _D, _D, _D, _I, _D, _D, _D, _D, _P]),
         "orc_direct_apply": (_I, [_D, _D, _D, _D, _I64, _P, _P, _I, _P, _I64, _P, _I, _I, _P]),
+        "orc_direct_apply_deriv": (_I, [_D, _D, _D, _D, _I64, _P, _P, _I, _P, _I64, _P, _I, _I, _P]),
+        "orc_green_refl_deriv": (_I, [_D, _D, _D, _D, _D, _D, _D, _D, _I, _I, _P]),
+        "orc_green_free_grad": (None, [_D, _D, _D, _P]),
         "orc_tree_build": (_I, [_I64, _P, _P, _D, _I, _P, _P, _P]),
         "orc_vlist": (_I64, [_I, _I, _I64, _P]),
         "orc_ulist": (_I64, [_I, _I, _I64, _P]),
@@ -189,6 +192,22 @@ def green_refl(k1, k2, k3, d, x, y, x0, y0, mask=MASK_ALL, tailmode=AUTO):
     return _green_out(lib().orc_green_refl, k1, k2, k3, d, x, y, x0, y0, mask, tailmode)
 
 
+DX, DY, DD = 1, 2, 3
+
+
+def green_refl_deriv(k1, k2, k3, d, x, y, x0, y0, deriv, mask=MASK_ALL):
+    """d/dx or d/dy (target coordinates, deriv = DX, DY) or d/dd (deriv = DD) of G_r,
+    by the chain rule inside the Sommerfeld integrand."""
+    return _green_out(lib().orc_green_refl_deriv, k1, k2, k3, d, x, y, x0, y0, mask, deriv)
+
+
+def green_free_grad(k, dx, dy):
+    """Target gradient of (i/4) H0^(1)(k r) at offset (dx, dy): (i/4)(-k) H1^(1)(k r) (dx, dy)/r."""
+    o = np.zeros(4)
+    lib().orc_green_free_grad(k, dx, dy, _ptr(o))
+    return complex(o[0], o[1]), complex(o[2], o[3])
+
+
 def green_term(k1, k2, k3, d, term, x, y, x0, y0):
     """One image term G_m (term in 1..4 = tt, bb, tb, bt)."""
     return _green_out(lib().orc_green_term, k1, k2, k3, d, term, x, y, x0, y0)
@@ -227,6 +246,27 @@ def direct_apply(medium, x, y, q, targets=None, refl_mask=MASK_ALL, nthreads=0):
     u = np.zeros((nvec, nt), np.complex128)
     st = lib().orc_direct_apply(k1, k2, k3, d, n, _ptr(x), _ptr(y), nvec, _ptr(q2), nt,
                                 _ptr(tg) if tg is not None else None, refl_mask, nthreads, _ptr(u))
+    if st != 0:
+        raise RuntimeError("oracle quadrature did not converge")
+    return u[0] if one else u
+
+
+def direct_apply_deriv(medium, x, y, q, deriv, targets=None, nthreads=0):
+    """Derivative of the direct sum at the targets: d u_i/dx_i or d u_i/dy_i with the
+    sources fixed (deriv = DX, DY), or d u_i/dd (deriv = DD).  Layout as direct_apply."""
+    k1, k2, k3, d = medium
+    x = _c(x, np.float64)
+    y = _c(y, np.float64)
+    q = np.asarray(q)
+    one = q.ndim == 1
+    q2 = _c(q.reshape(1, -1) if one else q, np.complex128)
+    n = x.size
+    nvec = q2.shape[0]
+    tg = None if targets is None else _c(targets, np.int64)
+    nt = n if tg is None else tg.size
+    u = np.zeros((nvec, nt), np.complex128)
+    st = lib().orc_direct_apply_deriv(k1, k2, k3, d, n, _ptr(x), _ptr(y), nvec, _ptr(q2), nt,
+                                      _ptr(tg) if tg is not None else None, deriv, nthreads, _ptr(u))
     if st != 0:
         raise RuntimeError("oracle quadrature did not converge")
     return u[0] if one else u

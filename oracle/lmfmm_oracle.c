@@ -21,6 +21,9 @@
  *   - a uniform strip-forest quadtree and its interaction lists (Algorithm 1, step 1)
  *   - S2M, M2M, M2L (free space and layered), L2L, L2T, S2T and the FMM driver
  *     (Sec. 2.1 lemmas, Algorithm 1)
+ *   - derivatives of the direct sum for gradient checks: the target gradient
+ *     (free part through H1, reflected part by i lambda and -s2 dh/dy in the
+ *     Sommerfeld integrand) and d/dd (chain rule on sigma_m e^{-s2 h_m})
  *
  * Quadrature: adaptive Gauss-Kronrod (7/15) with a global error estimate.
  * Bessel functions: the C library's jn / yn (a library primitive used as a step).
@@ -376,44 +379,57 @@ void orc_gk15_pow(int n, double a, double b, double *out)
 /* ------------------------------------------------------------------------- */
 typedef cx (*specfun)(cx lam, void *ctx); /* F(lambda) */
 
+/* dX = 1 takes d/dX of the integral instead: e^{i lambda X} -> i lambda e^{i lambda X},
+ * so 2 cos(lambda X) -> -2 lambda sin(lambda X). */
 typedef struct {
     specfun F;
     void *fctx;
     double X, c, a, L;
+    int dX;
 } contour_ctx;
 
+static cx fold_cos(cx lam, const contour_ctx *c)
+{
+    return c->dX ? -2.0 * lam * csin(lam * c->X) : 2.0 * ccos(lam * c->X);
+}
 static cx f_segment(double t, void *vc)
 {
     contour_ctx *c = vc;
     double ph = M_PI * t / c->c;
     cx lam = t - I * c->a * sin(ph);
     cx dl = 1.0 - I * c->a * (M_PI / c->c) * cos(ph);
-    return 2.0 * ccos(lam * c->X) * c->F(lam, c->fctx) * dl;
+    return fold_cos(lam, c) * c->F(lam, c->fctx) * dl;
 }
 static cx f_north(double u, void *vc)
 {
     contour_ctx *c = vc;
     double t = c->L * u / (1.0 - u), dt = c->L / ((1.0 - u) * (1.0 - u));
     cx lam = c->c + t;
-    return 2.0 * ccos(lam * c->X) * c->F(lam, c->fctx) * dt;
+    return fold_cos(lam, c) * c->F(lam, c->fctx) * dt;
 }
 static cx f_east(double u, void *vc)
 {
     contour_ctx *c = vc;
     double tau = c->L * u / (1.0 - u), dt = c->L / ((1.0 - u) * (1.0 - u));
     cx lp = c->c + I * tau, lm = c->c - I * tau;
-    cx v = I * (cexp(I * lp * c->X) * c->F(lp, c->fctx) - cexp(-I * lm * c->X) * c->F(lm, c->fctx));
+    cx ep = cexp(I * lp * c->X), em = cexp(-I * lm * c->X);
+    if (c->dX) {
+        ep *= I * lp;
+        em *= -I * lm;
+    }
+    cx v = I * (ep * c->F(lp, c->fctx) - em * c->F(lm, c->fctx));
     return v * dt;
 }
 
 /* tail: 0 = north, 1 = east. rate = decay rate used to scale the tail map. */
-static int sommerfeld(specfun F, void *fctx, double kmax, double X, int tail, double rate,
-                      int do_segment, int do_tail, cx *out)
+static int sommerfeld_x(specfun F, void *fctx, double kmax, double X, int tail, double rate,
+                        int do_segment, int do_tail, int dX, cx *out)
 {
     contour_ctx c;
     c.F = F;
     c.fctx = fctx;
     c.X = X;
+    c.dX = dX;
     c.c = 1.5 * kmax + 1.0;
     c.a = fmin(0.5, 1.0 / fmax(X, 1e-3));
     c.L = 1.0 / (rate + 1.0 / c.c);
@@ -430,6 +446,11 @@ static int sommerfeld(specfun F, void *fctx, double kmax, double X, int tail, do
     }
     *out = (seg + tl) / (4.0 * M_PI);
     return st;
+}
+static int sommerfeld(specfun F, void *fctx, double kmax, double X, int tail, double rate,
+                      int do_segment, int do_tail, cx *out)
+{
+    return sommerfeld_x(F, fctx, kmax, X, tail, rate, do_segment, do_tail, 0, out);
 }
 
 /* --- free space: F = e^{-s|Y|}/s; equals (i/4) H0^(1)(k r) (Example 1) --- */
@@ -498,25 +519,58 @@ int orc_g2t_paper(double k1, double k2, double k3, double d, double x, double y,
 }
 
 /* --- middle-layer reflected field, any subset of the four terms --- */
+/* Derivatives of each term sigma_m(lambda; d) e^{-s2 h_m} / s2, by the chain rule:
+ *   d/dy (target):  -s2 (dh_m/dy) sigma_m e^{-s2 h_m}/s2
+ *   d/dd:           [d sigma_m/dd - s2 (dh_m/dd) sigma_m] e^{-s2 h_m}/s2
+ * with dh/dy = (-1, +1, -1, +1) and dh/dd = (0, 2, 2, 2) for (tt, bb, tb, bt);
+ * d/dx (target) is taken on the contour (dX) times sign(x - x0).           */
+enum { ORC_VALUE = 0, ORC_DX = 1, ORC_DY = 2, ORC_DD = 3 };
+static const double dh_dy[4] = {-1.0, 1.0, -1.0, 1.0};
+static const double dh_dd[4] = {0.0, 2.0, 2.0, 2.0};
+
+/* d sigma_m / dd at fixed lambda: only S = 1/D, D = 1 - R_t R_b e^{-2 d s2}, depends on d,
+ * dS/dd = -(dD/dd) S^2 = -2 s2 R_t R_b e^{-2 d s2} S^2. */
+static void sig_layer2_dd(cx l, const orc_medium *m, cx dsig[3])
+{
+    cx s1 = sroot(l, m->k1), s2 = sroot(l, m->k2), s3 = sroot(l, m->k3);
+    cx Rt = (m->k1 * m->k1 - m->k2 * m->k2) / ((s2 + s1) * (s2 + s1));
+    cx Rb = (m->k3 * m->k3 - m->k2 * m->k2) / ((s2 + s3) * (s2 + s3));
+    cx E = Rt * Rb * cexp(-2.0 * m->d * s2);
+    cx S = 1.0 / (1.0 - E);
+    cx dS = -2.0 * s2 * E * S * S;
+    dsig[0] = Rt * dS;
+    dsig[1] = Rb * dS;
+    dsig[2] = Rt * Rb * dS;
+}
+
 typedef struct {
     orc_medium m;
     double h[4];
-    int mask;
+    int mask, deriv;
 } refl_ctx;
 static cx F_refl(cx l, void *v)
 {
     refl_ctx *r = v;
-    cx s2, sig[3];
+    cx s2, sig[3], dsig[3];
     sig_layer2(l, &r->m, &s2, sig);
+    if (r->deriv == ORC_DD) sig_layer2_dd(l, &r->m, dsig);
     cx acc = 0.0;
-    for (int t = 0; t < 4; ++t)
-        if (r->mask & (1 << t)) acc += sig[term_sig[t]] * cexp(-s2 * r->h[t]);
+    for (int t = 0; t < 4; ++t) {
+        if (!(r->mask & (1 << t))) continue;
+        cx e = cexp(-s2 * r->h[t]), sg = sig[term_sig[t]];
+        if (r->deriv == ORC_DY)
+            acc += -s2 * dh_dy[t] * sg * e;
+        else if (r->deriv == ORC_DD)
+            acc += (dsig[term_sig[t]] - s2 * dh_dd[t] * sg) * e;
+        else
+            acc += sg * e;
+    }
     return acc / s2;
 }
 
 /* tailmode: -1 = per term (north if h_m >= X, else east), 0 = all north, 1 = all east */
-static int green_refl(const orc_medium *m, double x, double y, double x0, double y0, int mask,
-                      int tailmode, cx *out)
+static int green_refl_x(const orc_medium *m, double x, double y, double x0, double y0, int mask,
+                        int tailmode, int deriv, cx *out)
 {
     refl_ctx r;
     r.m = *m;
@@ -526,10 +580,12 @@ static int green_refl(const orc_medium *m, double x, double y, double x0, double
     int st = 0;
     cx seg = 0.0;
     r.mask = mask;
+    r.deriv = deriv;
+    const int dX = deriv == ORC_DX;
     /* the four terms can cancel in the sum: measure the error against the
      * integrand's L1 size, not against the (possibly much smaller) integral */
     g_l1 = 1;
-    st |= sommerfeld(F_refl, &r, km, X, 0, 0.0, 1, 0, &seg);
+    st |= sommerfeld_x(F_refl, &r, km, X, 0, 0.0, 1, 0, dX, &seg);
     cx tails = 0.0;
     for (int dir = 0; dir < 2; ++dir) {
         int sub = 0;
@@ -545,11 +601,29 @@ static int green_refl(const orc_medium *m, double x, double y, double x0, double
         if (!sub) continue;
         r.mask = sub;
         cx tl;
-        st |= sommerfeld(F_refl, &r, km, X, dir, dir == 0 ? hmin : X, 0, 1, &tl);
+        st |= sommerfeld_x(F_refl, &r, km, X, dir, dir == 0 ? hmin : X, 0, 1, dX, &tl);
         tails += tl;
     }
     g_l1 = 0;
     *out = seg + tails;
+    if (dX) *out *= (x > x0) ? 1.0 : (x < x0 ? -1.0 : 0.0);
+    return st;
+}
+static int green_refl(const orc_medium *m, double x, double y, double x0, double y0, int mask,
+                      int tailmode, cx *out)
+{
+    return green_refl_x(m, x, y, x0, y0, mask, tailmode, ORC_VALUE, out);
+}
+
+/* d/dx, d/dy (target) or d/dd of G_r; deriv = 1, 2, 3 */
+int orc_green_refl_deriv(double k1, double k2, double k3, double d, double x, double y, double x0,
+                         double y0, int mask, int deriv, double *out)
+{
+    orc_medium m = {k1, k2, k3, d};
+    cx r;
+    int st = green_refl_x(&m, x, y, x0, y0, mask, -1, deriv, &r);
+    out[0] = creal(r);
+    out[1] = cimag(r);
     return st;
 }
 
@@ -566,6 +640,23 @@ int orc_green_refl(double k1, double k2, double k3, double d, double x, double y
 
 /* free-space part (i/4) H0^(1)(k r) (Example 1) */
 static cx green_free(double k, double r) { return 0.25 * I * (j0(k * r) + I * y0(k * r)); }
+/* its target gradient: d/dr H0^(1)(k r) = -k H1^(1)(k r), times (dx, dy)/r */
+static void green_free_grad(double k, double dx, double dy, cx *gx, cx *gy)
+{
+    double r = hypot(dx, dy);
+    cx dr = 0.25 * I * (-k) * (j1(k * r) + I * y1(k * r));
+    *gx = dr * (dx / r);
+    *gy = dr * (dy / r);
+}
+void orc_green_free_grad(double k, double dx, double dy, double *out)
+{
+    cx gx, gy;
+    green_free_grad(k, dx, dy, &gx, &gy);
+    out[0] = creal(gx);
+    out[1] = cimag(gx);
+    out[2] = creal(gy);
+    out[3] = cimag(gy);
+}
 
 /* ------------------------------------------------------------------------- */
 /* Direct summation (Eq. (direct_sum)) for targets = sources = the points:    */
@@ -600,6 +691,46 @@ int orc_direct_apply(double k1, double k2, double k3, double d, int64_t n, const
                 fail |= green_refl(&m, x[i], y[i], x[j], y[j], refl_mask, -1, &gr);
                 g += gr;
             }
+            for (int v = 0; v < nvec; ++v) acc[v] += g * Q[(int64_t)v * n + j];
+        }
+        for (int v = 0; v < nvec; ++v) U[(int64_t)v * nt + ii] = acc[v];
+        free(acc);
+    }
+    return fail;
+}
+
+/* Derivatives of the direct sum (Eq. (direct_sum)) at the listed targets:
+ *   deriv 1, 2: d/dx_i, d/dy_i of u_i with the sources held fixed
+ *               (free part over j != i, reflected part over all j);
+ *   deriv 3:    d/dd of u_i (reflected part only; the free part has no d).
+ * Layouts as orc_direct_apply. */
+int orc_direct_apply_deriv(double k1, double k2, double k3, double d, int64_t n, const double *x,
+                           const double *y, int nvec, const double *q, int64_t ntgt,
+                           const int64_t *tgt, int deriv, int nthreads, double *u)
+{
+    orc_medium m = {k1, k2, k3, d};
+    const cx *Q = (const cx *)q;
+    cx *U = (cx *)u;
+    int64_t nt = tgt ? ntgt : n;
+    int fail = 0;
+    if (deriv < ORC_DX || deriv > ORC_DD) return 2;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : fail)
+    for (int64_t ii = 0; ii < nt; ++ii) {
+        int64_t i = tgt ? tgt[ii] : ii;
+        cx *acc = calloc(nvec, sizeof(cx));
+        for (int64_t j = 0; j < n; ++j) {
+            cx g = 0.0;
+            if (j != i && deriv != ORC_DD) {
+                cx gx, gy;
+                green_free_grad(m.k2, x[i] - x[j], y[i] - y[j], &gx, &gy);
+                g += deriv == ORC_DX ? gx : gy;
+            }
+            cx gr;
+            fail |= green_refl_x(&m, x[i], y[i], x[j], y[j], 15, -1, deriv, &gr);
+            g += gr;
             for (int v = 0; v < nvec; ++v) acc[v] += g * Q[(int64_t)v * n + j];
         }
         for (int v = 0; v < nvec; ++v) U[(int64_t)v * nt + ii] = acc[v];
