@@ -69,7 +69,17 @@ typedef struct {
     int tail_rays;   /* near-field tail: rays between the north and east directions; 0 -> 9 */
     int tensor_m2l;  /* mixed path, p <= 14: free-space M2L on the tcgen05 tensor cores
                         (TF32 hi/lo split, FP32 accumulation in tensor memory); 1 on, 0 off */
+    int kernel;      /* lm_kernel: the operator the tree applies; 0 -> LM_KERNEL_G */
 } lm_options;
+
+typedef enum {
+    LM_KERNEL_G = 0,     /* G = free space + reflected part (Sec. 3, Example 4; reading R1) */
+    LM_KERNEL_DG_DD = 1  /* dG/dd at fixed points: the reflected part with each image density
+                            sigma_m replaced by d/dd[sigma_m e^{-s2 c_m}] e^{s2 c_m}
+                            = -2 s2 (E/(1-E) + [m != tt]) sigma_m, E = R_t R_b e^{-2 d s2},
+                            c_m the d-dependent part of h_m (0 for tt, 2d otherwise); the free
+                            part has no d and is left out.  Same FMM, same lists. */
+} lm_kernel;
 
 typedef struct lm_medium_s *lm_medium; /* opaque, library-owned */
 typedef struct lm_tree_s *lm_tree;     /* opaque, library-owned */
@@ -245,6 +255,24 @@ lm_status lm_batch_create(const lm_tree *trees, int count, const void *const *q,
                           void *const *u, lm_batch *out);
 lm_status lm_batch_launch(lm_batch b, void *stream);
 void lm_batch_destroy(lm_batch b);
+
+/*
+ * apply_grad -- the field and its target gradient, FP64 trees only:
+ *   u_i  = sum_j G(x_i, x_j) q_j                (as lm_apply)
+ *   ux_i = sum_j d/dx G(x, x_j)|_{x = x_i} q_j  (sources held fixed)
+ *   uy_i = sum_j d/dy G(x, x_j)|_{x = x_i} q_j
+ * The far field differentiates the local expansion (Eq. (local)) with
+ * (d/dx +- i d/dy) J_n(kr) e^{i n theta} = -+k J_{n+-1}(kr) e^{i (n+-1) theta};
+ * the free near field uses (i/4)(-k) H1(k r); the reflected near field
+ * multiplies the Sommerfeld integrand by i lambda (x) and -s2 dh_m/dy (y).
+ * With reciprocity this gives every coordinate gradient of a misfit: for
+ * J(u), g = dJ/d(Re u) + i dJ/d(Im u), dJ/dx_j = Re[conj(g_j) ux(q)_j +
+ * q_j ux(conj g)_j] (and the same in y).
+ *   q: device [nvec][n] complex128, input order; u (may be NULL), ux, uy:
+ *   device [nvec][n] complex128, input order, not overlapping q.
+ * Errors: as lm_apply; LM_ENOTSUP on an LM_MIXED tree.
+ */
+lm_status lm_apply_grad(lm_tree t, const void *q, int nvec, void *u, void *ux, void *uy, void *stream);
 
 /*
  * sync_status -- synchronise `stream` and report device-side failures of the

@@ -22,11 +22,12 @@ from . import _build
 HAS_MIXED = True
 
 __all__ = [
-    "LMError", "Medium", "Tree", "create_medium", "build_tree", "apply", "apply_adjoint", "green_apply",
-    "sync_status", "Batch", "library_path", "FP64", "MIXED",
+    "LMError", "Medium", "Tree", "create_medium", "build_tree", "apply", "apply_adjoint", "apply_grad", "green_apply",
+    "sync_status", "Batch", "library_path", "FP64", "MIXED", "KERNEL_G", "KERNEL_DG_DD",
 ]
 
 FP64, MIXED = 0, 1
+KERNEL_G, KERNEL_DG_DD = 0, 1
 _STATUS = {0: "LM_OK", 1: "LM_EINVAL", 2: "LM_ENOMEM", 3: "LM_ECUDA", 4: "LM_ETIMEOUT", 5: "LM_ENOTSUP"}
 
 
@@ -39,7 +40,8 @@ class LMError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_target", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_nvec", ctypes.c_int), ("seg_order", ctypes.c_int),
-                ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int), ("tensor_m2l", ctypes.c_int)]
+                ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int), ("tensor_m2l", ctypes.c_int),
+                ("kernel", ctypes.c_int)]
 
 
 class _TreeInfo(ctypes.Structure):
@@ -58,6 +60,7 @@ def _load():
         "lm_build_tree": (I, [V, P, P, I64, P, P]),
         "lm_apply": (I, [V, P, I, P, P]),
         "lm_apply_adjoint": (I, [V, P, I, P, P]),
+        "lm_apply_grad": (I, [V, P, I, P, P, P, P]),
         "lm_get_tree_info": (I, [V, P]),
         "lm_tree_export": (I, [V, P, P, P]),
         "lm_list_export": (I, [V, I, I, P, I64, P, P]),
@@ -117,24 +120,40 @@ class Medium:
 
 
 def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
-                  seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1) -> Medium:
+                  seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1, kernel=KERNEL_G) -> Medium:
+    """kernel = KERNEL_G applies G; KERNEL_DG_DD applies dG/dd at fixed points."""
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
-    o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays, tensor_m2l)
+    o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays, tensor_m2l,
+                 kernel)
     h = ctypes.c_void_p()
     _check(_lib.lm_create_medium(k1, k2, k3, d, ctypes.byref(o), ctypes.byref(h)))
     return Medium(h.value, k1, k2, k3, d, dict(p=p, depth=depth, leaf_target=leaf_target,
-                                              precision=precision, max_nvec=max_nvec))
+                                              precision=precision, max_nvec=max_nvec, seg_order=seg_order,
+                                              tail_order=tail_order, tail_rays=tail_rays,
+                                              tensor_m2l=tensor_m2l, kernel=kernel))
 
 
 class Tree:
     """A built tree: points, lists and translation tables on the device."""
 
-    def __init__(self, handle, medium):
+    def __init__(self, handle, medium, x=None, y=None):
         self._h = ctypes.c_void_p(handle)
         self.medium = medium
         self.info = self._info()
         self.n = self.info["n"]
+        self._x, self._y = x, y   # the caller's coordinate tensors (not copied)
+        self._dtree = None
+
+    def d_tree(self):
+        """The tree of dG/dd over the same points and options (built once, cached)."""
+        if self._dtree is None:
+            m = self.medium
+            opts = dict(m.options)
+            opts["kernel"] = KERNEL_DG_DD
+            md = create_medium(m.k1, m.k2, m.k3, m.d, **opts)
+            self._dtree = build_tree(md, self._x, self._y)
+        return self._dtree
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
@@ -189,7 +208,7 @@ def build_tree(medium: Medium, x, y, stream=None) -> Tree:
     h = ctypes.c_void_p()
     _check(_lib.lm_build_tree(medium._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                               x.numel(), _stream(stream), ctypes.byref(h)))
-    return Tree(h.value, medium)
+    return Tree(h.value, medium, x, y)
 
 
 def _apply(fn, tree, q, u, stream):
@@ -223,20 +242,66 @@ def apply_adjoint(tree: Tree, v, w=None, stream=None):
     return _apply(_lib.lm_apply_adjoint, tree, v, w, stream)
 
 
+def apply_grad(tree: Tree, q, stream=None, want_u=True):
+    """(u, du/dx, du/dy) at the points, sources held fixed (lm_apply_grad; FP64 trees).
+    q: complex128 CUDA tensor [nvec, n] or [n]; u is None when want_u is False."""
+    import torch
+
+    if not (q.is_cuda and q.dtype == torch.complex128 and q.is_contiguous()):
+        raise ValueError("apply_grad: q must be a contiguous complex128 CUDA tensor")
+    one = q.dim() == 1
+    q2 = q.reshape(1, -1) if one else q
+    if q2.shape[-1] != tree.n:
+        raise ValueError(f"apply_grad: q has {q2.shape[-1]} points, tree has {tree.n}")
+    u = torch.empty_like(q2) if want_u else None
+    ux, uy = torch.empty_like(q2), torch.empty_like(q2)
+    _check(_lib.lm_apply_grad(tree._h, ctypes.c_void_p(q2.data_ptr()), q2.shape[0],
+                              ctypes.c_void_p(u.data_ptr()) if want_u else None, ctypes.c_void_p(ux.data_ptr()),
+                              ctypes.c_void_p(uy.data_ptr()), _stream(stream)))
+    if one:
+        return (u.reshape(-1) if want_u else None), ux.reshape(-1), uy.reshape(-1)
+    return u, ux, uy
+
+
 def _autograd_function():
     import torch
 
     class _LayeredGreen(torch.autograd.Function):
-        """u = G q with dL/dq = G^H dL/du (G is linear; its adjoint is lm_apply_adjoint)."""
+        """u = G(x, y, d) q.  With g = dL/du (PyTorch's convention for a real L):
+        dL/dq = G^H g (adjoint apply); dL/dx_j = Re[conj(g_j) ux(q)_j + q_j ux(conj g)_j]
+        and the same in y (target gradient + reciprocity G(a, b) = G(b, a));
+        dL/dd = Re sum_i conj(g_i) (dG/dd q)_i (the dG/dd tree)."""
 
         @staticmethod
-        def forward(ctx, q, tree):
+        def forward(ctx, q, x, y, d, tree):
             ctx.tree = tree
+            ctx.one = q.dim() == 1
+            ctx.save_for_backward(q)
             return apply(tree, q.contiguous())
 
         @staticmethod
         def backward(ctx, grad_u):
-            return apply_adjoint(ctx.tree, grad_u.contiguous()), None
+            (q,) = ctx.saved_tensors
+            t = ctx.tree
+            g = grad_u.contiguous()
+            g2 = g.reshape(1, -1) if ctx.one else g
+            q2 = q.reshape(1, -1) if ctx.one else q
+            gq = gx = gy = gd = None
+            if ctx.needs_input_grad[0]:
+                gq = apply_adjoint(t, g)
+            if ctx.needs_input_grad[1] or ctx.needs_input_grad[2]:
+                nv = q2.shape[0]
+                V = torch.cat([q2, torch.conj(g2)], 0).contiguous()
+                _, ux, uy = apply_grad(t, V, want_u=False)
+                gc = torch.conj(g2)
+                if ctx.needs_input_grad[1]:
+                    gx = torch.real(gc * ux[:nv] + q2 * ux[nv:]).sum(0)
+                if ctx.needs_input_grad[2]:
+                    gy = torch.real(gc * uy[:nv] + q2 * uy[nv:]).sum(0)
+            if ctx.needs_input_grad[3]:
+                dd = apply(t.d_tree(), q2.contiguous())
+                gd = torch.real(torch.sum(torch.conj(g2) * dd)).reshape(())
+            return gq, gx, gy, gd, None
 
     return _LayeredGreen
 
@@ -244,14 +309,25 @@ def _autograd_function():
 _LG = None
 
 
-def green_apply(tree: Tree, q):
-    """Differentiable u = G q (PyTorch autograd): gradients with respect to the
-    complex densities q flow through the adjoint apply (Sec. 3 reciprocity:
-    G^H v = conj(G conj(v)))."""
+def green_apply(tree: Tree, q, x=None, y=None, d=None):
+    """Differentiable u = G q (PyTorch autograd).
+
+    Gradients flow to the complex densities q (adjoint apply, Sec. 3
+    reciprocity: G^H v = conj(G conj(v))), and, when given, to the point
+    coordinates x, y (float64 CUDA tensors holding the values the tree was
+    built on) and to the layer thickness d (a 0-dim float64 tensor equal to the
+    medium's d).  Coordinate gradients need an FP64 tree."""
+    import torch
+
     global _LG
     if _LG is None:
         _LG = _autograd_function()
-    return _LG.apply(q, tree)
+    for a, ref in ((x, tree._x), (y, tree._y)):
+        if a is not None and a is not ref and not torch.equal(a.detach(), ref):
+            raise ValueError("green_apply: x and y must hold the coordinates the tree was built on")
+    if d is not None and float(d.detach()) != tree.medium.d:
+        raise ValueError("green_apply: d must equal the medium's thickness")
+    return _LG.apply(q, x, y, d, tree)
 
 
 class Batch:

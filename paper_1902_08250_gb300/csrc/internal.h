@@ -124,6 +124,7 @@ lm_status lm_list_to_host(lm_tree_s *t, int which, int level, std::vector<int64_
 void lm_free_tree_device(lm_tree_s *t);
 // apply (lmfmm_apply.cu)
 lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);
+lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, zd *uy, cudaStream_t st);
 // mixed precision (lmfmm_mixed.cu)
 lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st);
 lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);

@@ -52,6 +52,7 @@ extern "C" lm_status lm_options_default(lm_options *o)
     o->tail_order = 0;
     o->tail_rays = 9;
     o->tensor_m2l = 1;
+    o->kernel = LM_KERNEL_G;
     return LM_OK;
 }
 
@@ -88,6 +89,10 @@ extern "C" lm_status lm_create_medium(double k1, double k2, double k3, double d,
     }
     if (o.precision != LM_FP64 && o.precision != LM_MIXED) {
         lm_set_error("create_medium: unknown precision %d", o.precision);
+        return LM_EINVAL;
+    }
+    if (o.kernel != LM_KERNEL_G && o.kernel != LM_KERNEL_DG_DD) {
+        lm_set_error("create_medium: unknown kernel %d", o.kernel);
         return LM_EINVAL;
     }
     if (o.seg_order > 64 || o.tail_order > 256 || o.tail_rays > 64) {
@@ -188,6 +193,27 @@ extern "C" lm_status lm_apply_adjoint(lm_tree t, const void *v, int nvec, void *
     if (s != LM_OK) return s;
     lm_profile_apply_start(t);
     s = lm_run_apply(t, (const zd *)v, nvec, (zd *)w, true, (cudaStream_t)stream);
+    lm_profile_apply_stop(t);
+    return s;
+}
+
+extern "C" lm_status lm_apply_grad(lm_tree t, const void *q, int nvec, void *u, void *ux, void *uy,
+                                   void *stream)
+{
+    lm_status s = check_apply(t, q, nvec, ux);
+    if (s != LM_OK) return s;
+    s = check_apply(t, q, nvec, uy);
+    if (s != LM_OK) return s;
+    if (u) {
+        s = check_apply(t, q, nvec, u);
+        if (s != LM_OK) return s;
+    }
+    if (t->precision != LM_FP64) {
+        lm_set_error("apply_grad: FP64 trees only");
+        return LM_ENOTSUP;
+    }
+    lm_profile_apply_start(t);
+    s = lm_run_apply_grad(t, (const zd *)q, nvec, (zd *)u, (zd *)ux, (zd *)uy, (cudaStream_t)stream);
     lm_profile_apply_stop(t);
     return s;
 }

@@ -206,7 +206,7 @@ __device__ zd near_refl64(const NearQuadD &q, int m, double X, double h)
 __global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs, const double *ys,
                          const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
                          const int32_t *uterm, NearQuadD nq, const zd *Lc, const zd *qs, int64_t n,
-                         int nvec, zd *us)
+                         int nvec, int free_on, zd *us)
 {
     const int np = 2 * P + 1;
     const int64_t b = blockIdx.x;
@@ -237,6 +237,7 @@ __global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs
         }
         for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
             const int32_t s = usrc[e], term = uterm[e];
+            if (term == 0 && !free_on) continue;
             for (int64_t j = ls[s]; j < ls[s + 1]; ++j) {
                 zd gij;
                 if (term == 0) {
@@ -255,9 +256,153 @@ __global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs
     }
 }
 
+// ---------------------------------------------------------------------------
+// Target gradient of one reflected direct term: the value, d/dX and d/dh of
+// the near-field quadrature of near_refl64 (segment: e^{+-i lam X} -> +-i lam,
+// e^{-s2 h} -> -s2; tail: the same inside Re[.]).
+// ---------------------------------------------------------------------------
+__device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, zd *val, zd *dX, zd *dh)
+{
+    zd a0 = {0.0, 0.0}, a1 = {0.0, 0.0}, a2 = {0.0, 0.0};
+    const zd *W = q.seg_w + (int64_t)m * q.nseg;
+    for (int i = 0; i < q.nseg; ++i) {
+        zd lam = q.seg_lam[i], s2 = q.seg_s2[i];
+        double er = -s2.re * h, ei = -s2.im * h;
+        zd e1 = cexpd(zd{er - lam.im * X, ei + lam.re * X});
+        zd e2 = cexpd(zd{er + lam.im * X, ei - lam.re * X});
+        zd we = W[i] * (e1 + e2);
+        a0 = a0 + we;
+        cfma(a1, W[i] * zd{-lam.im, lam.re}, e1 - e2);
+        cfma(a2, -1.0 * s2, we);
+    }
+    int k = q.nray > 1 ? (int)rint(atan2(X, h) * (q.nray - 1) / (0.5 * M_PI)) : 0;
+    const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
+    const zd *tw = q.tail_w + ((int64_t)m * q.nray + k) * q.ntail;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    for (int i = 0; i < q.ntail; ++i) {
+        zd lam = tl[i], s2 = ts[i];
+        zd we = tw[i] * cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
+        t0 += we.re;
+        t1 += (zd{-lam.im, lam.re} * we).re;
+        t2 -= (s2 * we).re;
+    }
+    a0.re += t0;
+    a1.re += t1;
+    a2.re += t2;
+    *val = a0;
+    *dX = a1;
+    *dh = a2;
+}
+
+// ---------------------------------------------------------------------------
+// Step 4 with the target gradient: u, du/dx, du/dy for nv <= GV vectors
+// starting at v0, written straight to input order through perm.  Far field:
+// the local expansion differentiated with (d/dx + i d/dy) J_n e^{i n t} =
+// -k J_{n+1} e^{i(n+1)t} and (d/dx - i d/dy) J_n e^{i n t} = k J_{n-1}
+// e^{i(n-1)t}; in scaled coefficients the shifts carry S(|n|)/S(|n -+ 1|).
+// ---------------------------------------------------------------------------
+#define GV 4
+__global__ void k_leaf64_grad(LeafGeom g, int P, double k, double d, const double *xs, const double *ys,
+                              const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
+                              const int32_t *uterm, NearQuadD nq, const zd *Lc, const zd *qs, int64_t n,
+                              int v0, int nv, int free_on, const int64_t *perm, zd *u, zd *ux, zd *uy)
+{
+    const int64_t b = blockIdx.x;
+    double cx, cy;
+    leaf_centre(g, b, &cx, &cy);
+    const double sc = k * g.w, hs = 0.5 * sc;
+    const zd *Lb = Lc + b * (2 * P + 1) * LM_MAXV + v0;
+    for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
+        const double xi = xs[i], yi = ys[i];
+        zd a[GV], dp[GV], dm[GV], gxa[GV], gya[GV]; // dp = (d/dx - i d/dy) u, dm = (d/dx + i d/dy) u
+        for (int v = 0; v < GV; ++v) a[v] = dp[v] = dm[v] = zd{0.0, 0.0};
+        {
+            double rx = xi - cx, ry = yi - cy, r = hypot(rx, ry);
+            double J[LM_MAXP + 2];
+            bessel_j_scaled<double>(P + 1, k * r, sc, J);
+            zd z = r > 0.0 ? zd{rx / r, ry / r} : zd{1.0, 0.0}; // e^{i theta}
+            zd zp = {1.0, 0.0};
+            for (int m = 0; m <= P + 1; ++m) {
+                if (m > 0) zp = zp * z;
+                const zd bp = J[m] * zp;                           // Jhat_m e^{i m t}
+                const zd bn = ((m & 1) ? -J[m] : J[m]) * conj(zp); // Jhat_{-m} e^{-i m t}
+                const double rdn = m >= 1 ? hs / m : 0.0;          // S(m)/S(m-1)
+                const double rup = (m + 1) / hs;                   // S(m)/S(m+1)
+                for (int v = 0; v < nv; ++v) {
+                    const zd *Lv = Lb + P * LM_MAXV + v; // Lv[n * LM_MAXV] = Lhat_n
+                    if (m <= P) cfma(a[v], bp, Lv[m * LM_MAXV]);
+                    if (m >= 1 && m <= P) cfma(a[v], bn, Lv[-m * LM_MAXV]);
+                    // dm = -k sum_n L_{n-1} J_n e^{i n t}: n = m, and n = -m (m >= 1, -m-1 >= -P)
+                    if (m >= 1) cfma(dm[v], (-k * rdn) * bp, Lv[(m - 1) * LM_MAXV]);
+                    else cfma(dm[v], (-k / hs) * bp, Lv[-LM_MAXV]);
+                    if (m >= 1 && m <= P - 1) cfma(dm[v], (-k * rup) * bn, Lv[(-m - 1) * LM_MAXV]);
+                    // dp = k sum_n L_{n+1} J_n e^{i n t}: n = m (m + 1 <= P), and n = -m (m >= 1)
+                    if (m <= P - 1) cfma(dp[v], (k * rup) * bp, Lv[(m + 1) * LM_MAXV]);
+                    if (m >= 1) cfma(dp[v], (k * rdn) * bn, Lv[(1 - m) * LM_MAXV]);
+                }
+            }
+            for (int v = 0; v < GV; ++v) {
+                gxa[v] = 0.5 * (dp[v] + dm[v]);
+                const zd df = dp[v] - dm[v];
+                gya[v] = zd{-0.5 * df.im, 0.5 * df.re}; // i (dp - dm) / 2
+            }
+        }
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
+            const int32_t s = usrc[e], term = uterm[e];
+            if (term == 0 && !free_on) continue;
+            for (int64_t j = ls[s]; j < ls[s + 1]; ++j) {
+                zd gv, gx, gy;
+                const double Dx = xi - xs[j];
+                if (term == 0) {
+                    if (j == i) continue;
+                    const double Dy = yi - ys[j], r = hypot(Dx, Dy);
+                    gv = zd{-0.25 * y0(k * r), 0.25 * j0(k * r)};                // (i/4) H0
+                    const zd dr = zd{0.25 * k * y1(k * r), -0.25 * k * j1(k * r)}; // (i/4)(-k) H1
+                    gx = (Dx / r) * dr;
+                    gy = (Dy / r) * dr;
+                } else {
+                    const double X = fabs(Dx);
+                    const double h = term == 1 ? -(yi + ys[j]) : yi + ys[j] + 2.0 * d;
+                    zd dX, dh;
+                    near_refl64_grad(nq, term - 1, X, h, &gv, &dX, &dh);
+                    gx = (Dx > 0.0 ? 1.0 : (Dx < 0.0 ? -1.0 : 0.0)) * dX;
+                    gy = (term == 1 ? -1.0 : 1.0) * dh; // dh/dy: -1 (tt), +1 (bb)
+                }
+                for (int v = 0; v < nv; ++v) {
+                    const zd qj = qs[(int64_t)(v0 + v) * n + j];
+                    cfma(a[v], gv, qj);
+                    cfma(gxa[v], gx, qj);
+                    cfma(gya[v], gy, qj);
+                }
+            }
+        }
+        const int64_t o = perm[i];
+        for (int v = 0; v < nv; ++v) {
+            if (u) u[(int64_t)v * n + o] = a[v];
+            ux[(int64_t)v * n + o] = gxa[v];
+            uy[(int64_t)v * n + o] = gya[v];
+        }
+    }
+}
+
+static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, zd *ux, zd *uy,
+                          cudaStream_t st);
+
 lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st)
 {
     if (t->precision == LM_MIXED) return lm_run_apply_mixed(t, q, nvec, u, adjoint, st);
+    return run_fp64(t, q, nvec, u, adjoint, nullptr, nullptr, st);
+}
+
+lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, zd *uy, cudaStream_t st)
+{
+    return run_fp64(t, q, nvec, u, false, ux, uy, st);
+}
+
+// FP64 driver; with ux set, step 4 also evaluates the target gradient and writes u, ux, uy
+static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, zd *ux, zd *uy,
+                          cudaStream_t st)
+{
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const int64_t n = t->n;
     const double k = t->med.k2;
@@ -304,13 +449,29 @@ lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint,
             lm_phase_end(t, PH_M2L, st, lv.nv > 0);
         }
         // step 4: evaluation
+        const int free_on = t->med.opt.kernel == LM_KERNEL_G;
         lm_phase_begin(t, PH_LEAF, st);
+        if (ux) {
+            Level &lv = t->lev[L];
+            LeafGeom g{lv.ncol, t->x0, lv.w};
+            const int64_t off = (int64_t)v0 * n;
+            int nl = 0;
+            for (int w0 = 0; w0 < nv; w0 += GV, ++nl)
+                k_leaf64_grad<<<(unsigned)lv.nbox, 64, 0, st>>>(
+                    g, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, lv.Lc,
+                    t->qs, n, w0, std::min(GV, nv - w0), free_on, t->perm,
+                    u ? u + off + (int64_t)w0 * n : nullptr, ux + off + (int64_t)w0 * n,
+                    uy + off + (int64_t)w0 * n);
+            lm_phase_end(t, PH_LEAF, st, nl);
+            LM_CUDA(cudaGetLastError());
+            continue;
+        }
         {
             Level &lv = t->lev[L];
             LeafGeom g{lv.ncol, t->x0, lv.w};
             k_leaf64<<<(unsigned)lv.nbox, 64, 0, st>>>(g, P, k, t->med.d, t->xs, t->ys, t->leaf_start,
                                                        t->ustart, t->usrc, t->uterm, nq, lv.Lc, t->qs, n,
-                                                       nv, t->us);
+                                                       nv, free_on, t->us);
         }
         lm_phase_end(t, PH_LEAF, st, 1);
         lm_phase_begin(t, PH_PERMUTE, st);

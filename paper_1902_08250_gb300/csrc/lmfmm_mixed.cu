@@ -683,7 +683,8 @@ template <int P>
 __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
                                                   const float *yl, const float *y32, const int64_t *ls,
                                                   const int64_t *ustart, const int32_t *usrc, const int32_t *uterm,
-                                                  NearQuadF nq, const zf *Lc, const zf *qs, zf *us, int nterms)
+                                                  NearQuadF nq, const zf *Lc, const zf *qs, zf *us, int nterms,
+                                                  int free_on)
 {
     constexpr int NP = 2 * P + 1;
     __shared__ __align__(16) zf sq[2][LCAP * LM_MAXV];
@@ -777,7 +778,7 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
                 zf part[LM_MAXV];
 #pragma unroll
                 for (int v = 0; v < LM_MAXV; ++v) part[v] = zf{0.f, 0.f};
-                if (term == 0) {
+                if (term == 0 && free_on) {
                     const int self = i - ch.j0; // this target's slot in the chunk, if it is a source here
 #pragma unroll 2
                     for (int jj = 0; jj < ch.cnt; ++jj) {
@@ -795,7 +796,7 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
                             cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
                         }
                     }
-                } else {
+                } else if (term != 0) {
                     for (int jj = 0; jj < ch.cnt; ++jj) {
                         // tail of a reflected direct term; its segment part is added by k_near_pw32
                         const float dx = (xi - sx[buf][jj]) + ox;
@@ -864,7 +865,8 @@ static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st)
     const int nterms = lm_h0_terms(t->med.k2 * lv.w * 2.0 * 1.4142135623730951 * 1.0001);
     k_leaf32<P><<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
                                                    t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart, t->usrc,
-                                                   t->uterm, nq, lv.L32, t->qs32, t->us32, nterms);
+                                                   t->uterm, nq, lv.L32, t->qs32, t->us32, nterms,
+                                                   t->med.opt.kernel == LM_KERNEL_G);
 }
 
 int lm_h0_terms(double xmax);

@@ -305,8 +305,12 @@ __global__ void k_scan64(int64_t *c, int64_t m)
 // Sigma = 1/(1 - R_t R_b e^{-2 d s2}); sigma_tt = R_t Sigma, sigma_bb =
 // R_b Sigma, sigma_tb = R_t R_b Sigma.
 // ---------------------------------------------------------------------------
+// With deriv set (the kernel dG/dd): each density becomes
+// d/dd[sigma_m e^{-s2 c_m}] e^{s2 c_m} = -2 s2 (E S + [m != tt]) sigma_m, E = R_t R_b e^{-2 d s2},
+// since only S = 1/(1 - E) and c_m (0 for tt, 2d otherwise) depend on d.
 struct MediumD {
     double k1, k2, k3, d;
+    int deriv;
 };
 __device__ void densities(const MediumD &m, zd lam, zd *s2o, zd sig[3])
 {
@@ -314,11 +318,18 @@ __device__ void densities(const MediumD &m, zd lam, zd *s2o, zd sig[3])
     zd a = s2 + s1, b = s2 + s3;
     zd Rt = cdiv(zd{m.k1 * m.k1 - m.k2 * m.k2, 0.0}, a * a);
     zd Rb = cdiv(zd{m.k3 * m.k3 - m.k2 * m.k2, 0.0}, b * b);
-    zd E = cexpd(-2.0 * m.d * s2);
-    zd S = cdiv(zd{1.0, 0.0}, zd{1.0, 0.0} - Rt * Rb * E);
+    zd E = Rt * Rb * cexpd(-2.0 * m.d * s2);
+    zd S = cdiv(zd{1.0, 0.0}, zd{1.0, 0.0} - E);
     sig[0] = Rt * S;
     sig[1] = Rb * S;
     sig[2] = Rt * Rb * S;
+    if (m.deriv) {
+        zd f = -2.0 * s2 * (E * S);
+        zd g = f - 2.0 * s2;
+        sig[0] = f * sig[0];
+        sig[1] = g * sig[1];
+        sig[2] = g * sig[2];
+    }
     *s2o = s2;
 }
 
@@ -759,7 +770,7 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
 {
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const double k = t->med.k2, d = t->med.d;
-    MediumD md{t->med.k1, t->med.k2, t->med.k3, t->med.d};
+    MediumD md{t->med.k1, t->med.k2, t->med.k3, t->med.d, t->med.opt.kernel == LM_KERNEL_DG_DD};
     t->lev.resize(L + 1);
     // scale vectors
     for (int l = 0; l <= L; ++l) {
@@ -851,7 +862,9 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
         hb.insert(hb.end(), iidx.begin(), iidx.end());
         if (!hb.empty())
             LM_CUDA(cudaMemcpyAsync(dbuf, hb.data(), hb.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-        if (nf > 0) {
+        if (md.deriv) // the free part does not depend on d: its tables stay zero
+            LM_CUDA(cudaMemsetAsync(lv.tab, 0, (size_t)std::max(1, ncls) * np * np * sizeof(zd), st));
+        if (nf > 0 && !md.deriv) {
             dim3 g(grid_for(np * np, 256), nf);
             k_free_m2l<<<g, 256, 0, st>>>(k, P, lv.w, dbuf, dbuf + nf, dbuf + 2 * nf, nf, lv.scale, lv.tab);
         }

@@ -1,6 +1,8 @@
-"""Gradients of J = sum_i |u_i - u_obs_i|^2 with respect to the complex
-densities, u = G q through the FMM: autograd (adjoint apply) against central
-finite differences and against the oracle's gradient 2 G^H (u - u_obs)."""
+"""Gradients of J = sum_i |u_i - u_obs_i|^2, u = G(x, y, d) q through the FMM:
+with respect to the complex densities (adjoint apply), the point coordinates
+(target-gradient apply + reciprocity) and the layer thickness d (the dG/dd
+tree).  Checked against the oracle's gradients -- built from oracle-only
+residuals -- and against central differences of J (h = 1e-6)."""
 import numpy as np
 import pytest
 
@@ -8,41 +10,153 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
+MED = workloads.MEDIUM_A
+P, DEPTH = 22, 3
 
-def test_density_gradient_matches_fd_and_oracle(oracle):
+
+@pytest.fixture(scope="module")
+def lm():
     import torch
 
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests")
     import paper_1902_08250_gb300 as lm
 
-    med = workloads.MEDIUM_A
+    return lm
+
+
+def _setup(n, seed_q=0, seed_ref=1):
+    x, y, q = workloads.uniform_strip(n, 0.0, 4.0, -0.9, -0.1, nvec=1, seed=seed_q)
+    _, _, qref = workloads.uniform_strip(n, 0.0, 4.0, -0.9, -0.1, nvec=1, seed=seed_ref)
+    return x, y, q[0], qref[0]
+
+
+def test_apply_grad_matches_oracle(lm, oracle):
+    import torch
+
     n = 2000
-    x, y, q = workloads.uniform_strip(n, 0.0, 4.0, -0.9, -0.1, nvec=1, seed=0)
-    _, _, qref = workloads.uniform_strip(n, 0.0, 4.0, -0.9, -0.1, nvec=1, seed=1)
-    m = lm.create_medium(*med, p=22, depth=3)
+    x, y, q, qref = _setup(n)
+    V = np.stack([q, qref])
+    m = lm.create_medium(*MED, p=P, depth=DEPTH)
     t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
-    uobs = lm.apply(t, torch.from_numpy(qref[0]).cuda())
-    qd = torch.from_numpy(q[0]).cuda().requires_grad_(True)
-    u = lm.green_apply(t, qd)
+    u, ux, uy = (a.cpu().numpy() for a in lm.apply_grad(t, torch.from_numpy(V).cuda()))
+    u0 = lm.apply(t, torch.from_numpy(V).cuda()).cpu().numpy()
+    assert np.linalg.norm(u - u0) <= 1e-13 * np.linalg.norm(u0)
+    sub = np.sort(np.random.default_rng(3).choice(n, 64, replace=False))
+    rx = oracle.direct_apply_deriv(MED, x, y, V, oracle.DX, targets=sub)
+    ry = oracle.direct_apply_deriv(MED, x, y, V, oracle.DY, targets=sub)
+    for a, r in ((ux[:, sub], rx), (uy[:, sub], ry)):
+        assert np.linalg.norm(a - r) <= 1e-9 * np.linalg.norm(r), np.linalg.norm(a - r) / np.linalg.norm(r)
+
+
+@pytest.mark.parametrize("prec,p,tol", [("fp64", 22, 1e-9), ("mixed", 14, 1e-6)])
+def test_dG_dd_tree_matches_oracle(lm, oracle, prec, p, tol):
+    import torch
+
+    n = 2000
+    x, y, q, _ = _setup(n)
+    m = lm.create_medium(*MED, p=p, depth=DEPTH, precision=prec, kernel=lm.KERNEL_DG_DD)
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    du = lm.apply(t, torch.from_numpy(q).cuda()).cpu().numpy()
+    sub = np.sort(np.random.default_rng(4).choice(n, 64, replace=False))
+    ref = oracle.direct_apply_deriv(MED, x, y, q, oracle.DD, targets=sub)
+    assert np.linalg.norm(du[sub] - ref) <= tol * np.linalg.norm(ref), np.linalg.norm(du[sub] - ref) / np.linalg.norm(ref)
+
+
+def _grads(lm, t, x, y, q, uobs, d):
+    import torch
+
+    qd = torch.from_numpy(q).cuda().requires_grad_(True)
+    xd = t._x.clone().requires_grad_(True)
+    yd = t._y.clone().requires_grad_(True)
+    dd = torch.tensor(d, dtype=torch.float64, requires_grad=True)
+    u = lm.green_apply(t, qd, xd, yd, dd)
     J = torch.sum(torch.abs(u - uobs) ** 2)
-    (g,) = torch.autograd.grad(J, qd)
-    g = g.detach().cpu().numpy()
-    # oracle gradient: 2 G^H r = 2 conj(G conj(r)), r = u - u_obs, on a 64-point target subset
-    r = (u - uobs).detach().cpu().numpy()
+    gq, gx, gy, gd = torch.autograd.grad(J, (qd, xd, yd, dd))
+    return gq.cpu().numpy(), gx.cpu().numpy(), gy.cpu().numpy(), float(gd)
+
+
+def test_gradients_match_oracle_2k(lm, oracle):
+    """Densities and coordinates at N = 2000 against the oracle: r from the
+    oracle's own FMM (p = 22), gradients by oracle direct sums on 64 points."""
+    import torch
+
+    n = 2000
+    x, y, q, qref = _setup(n)
+    m = lm.create_medium(*MED, p=P, depth=DEPTH)
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    uobs = lm.apply(t, torch.from_numpy(qref).cuda())
+    gq, gx, gy, _ = _grads(lm, t, x, y, q, uobs, MED[3])
+    # oracle: g = dJ/du = 2 r, r = G q - G qref (oracle FMM at the same p and depth)
+    r = oracle.fmm_apply(MED, x, y, np.stack([q, qref]), DEPTH, P)
+    r = r[0] - r[1]
+    g = 2.0 * r
     sub = np.sort(np.random.default_rng(2).choice(n, 64, replace=False))
-    gref = 2 * np.conj(oracle.direct_apply(med, x, y, np.conj(r), targets=sub))
-    assert np.linalg.norm(g[sub] - gref) <= 1e-9 * np.linalg.norm(gref)
-    # central differences (h = 1e-6) of J in Re q_j and Im q_j for a few j
-    def J_of(qv):
-        uu = lm.apply(t, torch.from_numpy(qv).cuda())
-        return float(torch.sum(torch.abs(uu - uobs) ** 2))
+    gq_ref = np.conj(oracle.direct_apply(MED, x, y, np.conj(g), targets=sub))
+    assert np.linalg.norm(gq[sub] - gq_ref) <= 1e-9 * np.linalg.norm(gq_ref)
+    V = np.stack([q, np.conj(g)])
+    Dx = oracle.direct_apply_deriv(MED, x, y, V, oracle.DX, targets=sub)
+    Dy = oracle.direct_apply_deriv(MED, x, y, V, oracle.DY, targets=sub)
+    gx_ref = np.real(np.conj(g[sub]) * Dx[0] + q[sub] * Dx[1])
+    gy_ref = np.real(np.conj(g[sub]) * Dy[0] + q[sub] * Dy[1])
+    assert np.linalg.norm(gx[sub] - gx_ref) <= 1e-9 * np.linalg.norm(gx_ref)
+    assert np.linalg.norm(gy[sub] - gy_ref) <= 1e-9 * np.linalg.norm(gy_ref)
+
+
+def test_thickness_gradient_matches_oracle_500(lm, oracle):
+    """dJ/dd needs dG/dd q at every target: oracle direct sums at N = 500."""
+    import torch
+
+    n = 500
+    x, y, q, qref = _setup(n, 7, 8)
+    m = lm.create_medium(*MED, p=P, depth=2)
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    uobs = lm.apply(t, torch.from_numpy(qref).cuda())
+    _, _, _, gd = _grads(lm, t, x, y, q, uobs, MED[3])
+    u = oracle.direct_apply(MED, x, y, np.stack([q, qref]))
+    g = 2.0 * (u[0] - u[1])
+    dq = oracle.direct_apply_deriv(MED, x, y, q, oracle.DD)
+    gd_ref = float(np.real(np.vdot(g, dq)))
+    assert abs(gd - gd_ref) <= 1e-9 * abs(gd_ref), (gd, gd_ref)
+
+
+def test_gradients_match_central_differences(lm):
+    """Central differences (h = 1e-6) of J at N = 2000 for x_j, y_j and d.  The
+    difference J+ - J- is formed as sum Re[(u+ - u-) conj(r+ + r-)], which
+    keeps the rounding of J itself out of it."""
+    import torch
+
+    n = 2000
+    x, y, q, qref = _setup(n)
+    m = lm.create_medium(*MED, p=P, depth=DEPTH)
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    uobs = lm.apply(t, torch.from_numpy(qref).cuda())
+    gq, gx, gy, gd = _grads(lm, t, x, y, q, uobs, MED[3])
+    qd = torch.from_numpy(q).cuda()
+    uo = uobs.cpu().numpy()
+
+    def u_at(xx, yy, d):
+        mm = lm.create_medium(MED[0], MED[1], MED[2], d, p=P, depth=DEPTH)
+        tt = lm.build_tree(mm, torch.from_numpy(xx).cuda(), torch.from_numpy(yy).cuda())
+        return lm.apply(tt, qd).cpu().numpy()
+
+    def dJ(up, um, h):
+        return float(np.sum(np.real((up - um) * np.conj(up + um - 2 * uo)))) / (2 * h)
 
     h = 1e-6
     for j in (3, 777, 1999):
-        for part, unit in ((0, 1.0), (1, 1j)):
-            qp = q[0].copy()
-            qm = q[0].copy()
-            qp[j] += h * unit
-            qm[j] -= h * unit
-            fd = (J_of(qp) - J_of(qm)) / (2 * h)
-            an = g[j].real if part == 0 else g[j].imag
-            assert abs(fd - an) <= 1e-5 * (abs(an) + 1e-3), (j, part, fd, an)
+        for arr, an in ((0, gx[j]), (1, gy[j])):
+            xp, yp, xm, ym = x.copy(), y.copy(), x.copy(), y.copy()
+            (xp if arr == 0 else yp)[j] += h
+            (xm if arr == 0 else ym)[j] -= h
+            fd = dJ(u_at(xp, yp, MED[3]), u_at(xm, ym, MED[3]), h)
+            assert abs(fd - an) <= 1e-5 * (abs(an) + 1e-2 * np.max(np.abs(gx))), (j, arr, fd, an)
+    fd = dJ(u_at(x, y, MED[3] + h), u_at(x, y, MED[3] - h), h)
+    assert abs(fd - gd) <= 1e-5 * abs(gd), (fd, gd)
+    # densities: J is quadratic in q, so the difference is exact up to rounding
+    for j in (5, 1500):
+        e = np.zeros(n, complex)
+        e[j] = h
+        up = lm.apply(t, torch.from_numpy(q + e).cuda()).cpu().numpy()
+        um = lm.apply(t, torch.from_numpy(q - e).cuda()).cpu().numpy()
+        assert abs(dJ(up, um, h) - gq[j].real) <= 1e-5 * (abs(gq[j].real) + 1e-3)
