@@ -488,10 +488,16 @@ __device__ __forceinline__ zf green_free32_t(float t)
                     c4 = 1.73611111e-03f, c3 = -2.77777778e-02f, c2 = 0.25f, c1 = -1.0f;
         const float e8 = 1.67180484e-09f, e7 = -1.02074560e-07f, e6 = 4.72608025e-06f, e5 = -1.58564815e-04f,
                     e4 = 3.61689815e-03f, e3 = -5.09259259e-02f, e2 = 0.375f, e1 = -1.0f;
-        float pj = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(c8, t, c7), t, c6), t, c5), t, c4), t, c3), t, c2), t, c1);
-        j = fmaf(pj, t, 1.0f);
-        float ps = fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(fmaf(e8, t, e7), t, e6), t, e5), t, e4), t, e3), t, e2), t, e1);
-        const float sh = ps * t;
+        const float2 tt = make_float2(t, t);
+        float2 pp = __ffma2_rn(make_float2(c8, e8), tt, make_float2(c7, e7));
+        pp = __ffma2_rn(pp, tt, make_float2(c6, e6));
+        pp = __ffma2_rn(pp, tt, make_float2(c5, e5));
+        pp = __ffma2_rn(pp, tt, make_float2(c4, e4));
+        pp = __ffma2_rn(pp, tt, make_float2(c3, e3));
+        pp = __ffma2_rn(pp, tt, make_float2(c2, e2));
+        pp = __ffma2_rn(pp, tt, make_float2(c1, e1));
+        j = fmaf(pp.x, t, 1.0f);
+        const float sh = pp.y * t;
         // MUFU logarithm: absolute error ~1e-7, well inside the 1e-6 budget
         y = 0.63661977236758134f * (fmaf(0.5f, __logf(t), 0.57721566490153286f) * j - sh);
     } else {
