@@ -446,32 +446,6 @@ __global__ void __launch_bounds__(64 * ((NP + ST_RG - 1) / ST_RG))
     }
 }
 
-// remaining V-list entries (level 0 and the image terms), one thread per
-// (target with such entries, order, vector); the targets are listed in rtgt
-template <int NP>
-__global__ void k_m2l_rest32(int64_t ntgt, const int32_t *rtgt, const int64_t *rstart, const int32_t *rsrc,
-                             const int32_t *rslot, const zf *tab, const zf *M, zf *Lc)
-{
-    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= ntgt * NP * LM_MAXV) return;
-    int v = idx % LM_MAXV;
-    int p = (idx / LM_MAXV) % NP;
-    int64_t b = rtgt[idx / (LM_MAXV * NP)];
-    int64_t e0 = rstart[b], e1 = rstart[b + 1];
-    zf acc = {0.f, 0.f};
-    for (int64_t e = e0; e < e1; ++e) {
-        const zf *T = tab + ((int64_t)rslot[e] * NP + p) * NP;
-        const zf *m = M + (int64_t)rsrc[e] * NP * LM_MAXV + v;
-        zf tmp = {0.f, 0.f};
-#pragma unroll
-        for (int q = 0; q < NP; ++q) cfmaf(tmp, T[q], m[q * LM_MAXV]);
-        acc = acc + tmp;
-    }
-    const int64_t o = (b * NP + p) * LM_MAXV + v;
-    zf x = Lc[o];
-    Lc[o] = zf{x.re + acc.re, x.im + acc.im};
-}
-
 // (i/4) H0^(1)(x) in FP32 as a function of t = x^2/4.  For t <= 1 (x <= 2)
 // the ascending series of J0 and Y0 (Abramowitz & Stegun 9.1.12, 9.1.13),
 //   J0 = sum_m c_m t^m,  c_m = (-1)^m/(m!)^2,
@@ -680,6 +654,90 @@ __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+                 "l"(gsrc)
+                 : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Remaining V-list entries (level 0 and the image terms): one block per target
+// box with such entries.  Each entry's table (NP x NP) and source multipoles
+// (NP x 16 vectors) are staged in shared memory, the next entry's copies in
+// flight (double-buffered cp.async) while the current one is contracted.
+// Thread (v, g) owns vector v and rows g, g + 8, g + 16, ...; the sum over an
+// entry is formed on its own before it is added (blocked FP32 accumulation).
+// ---------------------------------------------------------------------------
+template <int NP>
+__global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const int64_t *rstart,
+                                                    const int32_t *rsrc, const int32_t *rslot, const zf *tab,
+                                                    const zf *M, zf *Lc)
+{
+    constexpr int NR = (NP + 7) / 8;
+    // two buffers while they fit the 48 KB of static shared memory (all orders but p = 24)
+    constexpr int NB = 2 * (NP * NP + NP * LM_MAXV) * 8 <= 48 * 1024 ? 2 : 1;
+    __shared__ __align__(16) zf Ts[NB][NP * NP];
+    __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
+    const int64_t b = rtgt[blockIdx.x];
+    const int64_t e0 = rstart[b], e1 = rstart[b + 1];
+    const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
+    auto stage = [&](int64_t e, int buf) {
+        // table slots are NP*NP*8 bytes apart (8-byte aligned); multipole rows are 16-byte aligned
+        const zf *T = tab + (int64_t)rslot[e] * NP * NP;
+        for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) cp_async8(&Ts[buf][i], T + i);
+        const zf *Mm = M + (int64_t)rsrc[e] * NP * LM_MAXV;
+        for (int i = threadIdx.x; i < NP * LM_MAXV / 2; i += blockDim.x)
+            cp_async16(&Ms[buf][2 * i], Mm + 2 * i);
+    };
+    zf acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = zf{0.f, 0.f};
+    if (NB == 2) {
+        stage(e0, 0);
+        cp_commit();
+    }
+    for (int64_t e = e0; e < e1; ++e) {
+        const int buf = NB == 2 ? (int)((e - e0) & 1) : 0;
+        if (NB == 1) {
+            stage(e, 0);
+            cp_commit();
+            cp_wait<0>();
+        } else if (e + 1 < e1) {
+            stage(e + 1, buf ^ 1);
+            cp_commit();
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        zf tmp[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) tmp[r] = zf{0.f, 0.f};
+        const zf *Tb = Ts[buf];
+        const zf *Mb = Ms[buf] + v;
+#pragma unroll 4
+        for (int q = 0; q < NP; ++q) {
+            const zf m = Mb[q * LM_MAXV];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) {
+                const int p = g + 8 * r;
+                if (p < NP) cfmaf(tmp[r], Tb[p * NP + q], m);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = acc[r] + tmp[r];
+        __syncthreads(); // buffer `buf` is refilled by the stage of entry e + NB
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        const int p = g + 8 * r;
+        if (p < NP) {
+            zf *o = Lc + (b * NP + p) * LM_MAXV + v;
+            *o = *o + acc[r];
+        }
+    }
+}
 
 struct LeafChunk {
     int e, j0, cnt;
@@ -859,8 +917,7 @@ template <int P>
 static void launch_rest(const Level &lv, cudaStream_t st)
 {
     constexpr int NP = 2 * P + 1;
-    int64_t tot = lv.nrtgt * NP * LM_MAXV;
-    k_m2l_rest32<NP><<<gridm(tot, 128), 128, 0, st>>>(lv.nrtgt, lv.rtgt, lv.rstart, lv.rsrc, lv.rslot, lv.tab32,
+    k_m2l_rest32<NP><<<(unsigned)lv.nrtgt, 128, 0, st>>>(lv.rtgt, lv.rstart, lv.rsrc, lv.rslot, lv.tab32,
                                                        lv.M32, lv.L32);
 }
 template <int P>
