@@ -70,9 +70,6 @@ struct Level {
     int32_t *rsrc, *rslot;
     int64_t nrtgt;   // targets with entries on the rest list
     int32_t *rtgt;   // [nrtgt]
-    // tensor-core M2L: real-block TF32 hi/lo table images and their (dc, dr) map
-    float *rb;
-    int32_t *rbslot;
 };
 
 struct lm_tree_s {

@@ -206,7 +206,7 @@ void lm_free_mixed(lm_tree_s *t)
         if (p) cudaFree(p);
     for (Level &lv : t->lev) {
         void *lp[] = {lv.tab32, lv.m2m32, lv.l2l32, lv.M32, lv.L32, lv.stencil, lv.rstart, lv.rsrc, lv.rslot,
-                      lv.rb, lv.rbslot, lv.rtgt};
+                      lv.rtgt};
         for (void *p : lp)
             if (p) cudaFree(p);
     }
@@ -1002,7 +1002,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
             lm_phase_begin(t, PH_M2L, st);
             int launches = 0;
             if (l > 0) {
-                if (t->tc_ready && lv.rb) {
+                if (t->tc_ready) {
                     lm_status s = lm_launch_m2l_tc(t, l, st);
                     if (s != LM_OK) return s;
                 } else {

@@ -42,12 +42,12 @@ __host__ __device__ constexpr uint32_t tc_idesc_mn(int m, int n)
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
-// bounded wait; gives up after TC_WAIT_LIMIT polls or as soon as another CTA
-// has reported a timeout
+// bounded wait; gives up after TC_WAIT_LIMIT polls or, when err is given, as
+// soon as another CTA has reported a timeout
 __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity, const volatile int *err)
 {
     for (int i = 0; i < TC_WAIT_LIMIT; ++i) {
-        if ((i & 1023) == 1023 && *err) return false;
+        if ((i & 1023) == 1023 && err && *err) return false;
         uint32_t ok;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}\n"
