@@ -70,6 +70,7 @@ typedef struct {
     int tensor_m2l;  /* mixed path, p <= 14: free-space M2L on the tcgen05 tensor cores
                         (TF32 hi/lo split, FP32 accumulation in tensor memory); 1 on, 0 off */
     int kernel;      /* lm_kernel: the operator the tree applies; 0 -> LM_KERNEL_G */
+    int autotune;    /* LM_MIXED: run lm_autotune at the end of lm_build_tree; 0 off (default) */
 } lm_options;
 
 typedef enum {
@@ -243,7 +244,8 @@ lm_status lm_tree_order_noalloc(const double *x, const double *y, int64_t n, dou
  * graph and replayed as a single launch.  Inside the graph the trees are
  * forked over up to 8 streams so that small instances run concurrently.
  *   batch_create: trees[i], q[i] (device, complex128 [nvec[i]][n_i]), u[i]
- *     (device, same layout, not overlapping q[i]) for i < count.  The buffer
+ *     (device, same layout, not overlapping q[i]) for i < count; c64 (host,
+ *     nullable): c64[i] != 0 makes entry i's buffers complex64 (LM_MIXED trees).  The buffer
  *     addresses are bound at capture: every launch reads q[i] and writes u[i].
  *     The trees must be distinct and outlive the batch, and no other apply may
  *     use them while a launch is in flight.  Profiling must be off on them.
@@ -252,9 +254,32 @@ lm_status lm_tree_order_noalloc(const double *x, const double *y, int64_t n, dou
  */
 typedef struct lm_batch_s *lm_batch;
 lm_status lm_batch_create(const lm_tree *trees, int count, const void *const *q, const int *nvec,
-                          void *const *u, lm_batch *out);
+                          void *const *u, const int *c64, lm_batch *out);
 lm_status lm_batch_launch(lm_batch b, void *stream);
 void lm_batch_destroy(lm_batch b);
+
+/*
+ * autotune -- choose, per level, the tile shape of the free-space M2L of an
+ * LM_MIXED tree: the tcgen05 kernel (8 boxes x 16 vectors x 64 real orders
+ * per tile) or the CUDA-core kernel with 2, 4 or 8 orders per thread (16
+ * boxes x 4 vectors per row group), by timing each on the tree's own buffers
+ * with CUDA events on `stream` (synchronises it).  The choice stays with the
+ * tree.  choice, ms: host arrays of depth + 1 entries, or NULL; choice[l] =
+ * -1 (no stencil at level 0), 0 (tensor cores) or the orders per thread;
+ * ms[l] = the chosen kernel's time per launch.  On an LM_FP64 tree nothing
+ * is tuned and every choice is -1.  Not to be called while an apply of the
+ * tree is in flight.  Errors: LM_EINVAL (NULL tree), LM_ECUDA.
+ */
+lm_status lm_autotune(lm_tree t, void *stream, int *choice, float *ms);
+
+/*
+ * apply_c64, apply_adjoint_c64 -- lm_apply and lm_apply_adjoint with
+ * complex64 (interleaved float re, im) densities and potentials, [nvec][n],
+ * for LM_MIXED trees, whose arithmetic is FP32 already: halves the bytes moved
+ * and copied per point.  Errors as lm_apply; LM_EINVAL on an LM_FP64 tree.
+ */
+lm_status lm_apply_c64(lm_tree t, const void *q, int nvec, void *u, void *stream);
+lm_status lm_apply_adjoint_c64(lm_tree t, const void *v, int nvec, void *w, void *stream);
 
 /*
  * apply_grad -- the field and its target gradient, FP64 trees only:

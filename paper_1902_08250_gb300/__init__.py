@@ -41,7 +41,7 @@ class _Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_target", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_nvec", ctypes.c_int), ("seg_order", ctypes.c_int),
                 ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int), ("tensor_m2l", ctypes.c_int),
-                ("kernel", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("autotune", ctypes.c_int)]
 
 
 class _TreeInfo(ctypes.Structure):
@@ -61,6 +61,9 @@ def _load():
         "lm_apply": (I, [V, P, I, P, P]),
         "lm_apply_adjoint": (I, [V, P, I, P, P]),
         "lm_apply_grad": (I, [V, P, I, P, P, P, P]),
+        "lm_apply_c64": (I, [V, P, I, P, P]),
+        "lm_autotune": (I, [V, P, P, P]),
+        "lm_apply_adjoint_c64": (I, [V, P, I, P, P]),
         "lm_get_tree_info": (I, [V, P]),
         "lm_tree_export": (I, [V, P, P, P]),
         "lm_list_export": (I, [V, I, I, P, I64, P, P]),
@@ -70,7 +73,7 @@ def _load():
         "lm_peak_probe": (I, [I, I64, P, P]),
         "lm_tree_order_noalloc": (I, [P, P, I64, D, I, P, P, I64, P, P, P]),
         "lm_sync_status": (I, [V, P]),
-        "lm_batch_create": (I, [P, I, P, P, P, P]),
+        "lm_batch_create": (I, [P, I, P, P, P, P, P]),
         "lm_batch_launch": (I, [V, P]),
         "lm_batch_destroy": (None, [V]),
         "lm_destroy_tree": (None, [V]),
@@ -120,18 +123,20 @@ class Medium:
 
 
 def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
-                  seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1, kernel=KERNEL_G) -> Medium:
-    """kernel = KERNEL_G applies G; KERNEL_DG_DD applies dG/dd at fixed points."""
+                  seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1, kernel=KERNEL_G,
+                  autotune=0) -> Medium:
+    """kernel = KERNEL_G applies G; KERNEL_DG_DD applies dG/dd at fixed points.
+    autotune = 1 tunes the M2L tile shapes of mixed-precision trees at build time."""
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
     o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays, tensor_m2l,
-                 kernel)
+                 kernel, autotune)
     h = ctypes.c_void_p()
     _check(_lib.lm_create_medium(k1, k2, k3, d, ctypes.byref(o), ctypes.byref(h)))
     return Medium(h.value, k1, k2, k3, d, dict(p=p, depth=depth, leaf_target=leaf_target,
                                               precision=precision, max_nvec=max_nvec, seg_order=seg_order,
                                               tail_order=tail_order, tail_rays=tail_rays,
-                                              tensor_m2l=tensor_m2l, kernel=kernel))
+                                              tensor_m2l=tensor_m2l, kernel=kernel, autotune=autotune))
 
 
 class Tree:
@@ -144,6 +149,15 @@ class Tree:
         self.n = self.info["n"]
         self._x, self._y = x, y   # the caller's coordinate tensors (not copied)
         self._dtree = None
+
+    def autotune(self, stream=None):
+        """Tune the M2L tile shape per level (lm_autotune); returns [(choice, ms)] per level:
+        choice -1 = no stencil, 0 = tensor cores, r = CUDA cores with r orders per thread."""
+        nl = self.info["depth"] + 1
+        ch = (ctypes.c_int * nl)()
+        ms = (ctypes.c_float * nl)()
+        _check(_lib.lm_autotune(self._h, _stream(stream), ch, ms))
+        return [(ch[i], ms[i]) for i in range(nl)]
 
     def d_tree(self):
         """The tree of dG/dd over the same points and options (built once, cached)."""
@@ -211,11 +225,15 @@ def build_tree(medium: Medium, x, y, stream=None) -> Tree:
     return Tree(h.value, medium, x, y)
 
 
-def _apply(fn, tree, q, u, stream):
+def _apply(fn, tree, q, u, stream, fn64=None):
     import torch
 
-    if not (q.is_cuda and q.dtype == torch.complex128 and q.is_contiguous()):
-        raise ValueError("apply: q must be a contiguous complex128 CUDA tensor")
+    if fn64 is not None and q.dtype == torch.complex64:
+        fn = fn64  # complex64 buffers (LM_MIXED trees)
+    elif q.dtype != torch.complex128:
+        raise ValueError("apply: q must be complex128 (or complex64 on a mixed-precision tree)")
+    if not (q.is_cuda and q.is_contiguous()):
+        raise ValueError("apply: q must be a contiguous CUDA tensor")
     one = q.dim() == 1
     q2 = q.reshape(1, -1) if one else q
     if q2.shape[-1] != tree.n:
@@ -228,8 +246,9 @@ def _apply(fn, tree, q, u, stream):
 
 
 def apply(tree: Tree, q, u=None, stream=None):
-    """u = G q (Algorithm 1). q: complex128 CUDA tensor [nvec, n] or [n]."""
-    return _apply(_lib.lm_apply, tree, q, u, stream)
+    """u = G q (Algorithm 1). q: complex128 CUDA tensor [nvec, n] or [n] (complex64 on a
+    mixed-precision tree; u then has the same dtype)."""
+    return _apply(_lib.lm_apply, tree, q, u, stream, _lib.lm_apply_c64)
 
 
 def sync_status(tree: Tree, stream=None):
@@ -239,7 +258,7 @@ def sync_status(tree: Tree, stream=None):
 
 def apply_adjoint(tree: Tree, v, w=None, stream=None):
     """w = G^H v = conj(G conj(v)) (reciprocity)."""
-    return _apply(_lib.lm_apply_adjoint, tree, v, w, stream)
+    return _apply(_lib.lm_apply_adjoint, tree, v, w, stream, _lib.lm_apply_adjoint_c64)
 
 
 def apply_grad(tree: Tree, q, stream=None, want_u=True):
@@ -343,16 +362,17 @@ class Batch:
         n = len(trees)
         for t, q, u in zip(trees, qs, us):
             for a in (q, u):
-                if not (a.is_cuda and a.dtype == torch.complex128 and a.is_contiguous()):
-                    raise ValueError("Batch: buffers must be contiguous complex128 CUDA tensors")
-            if q.shape[-1] != t.n or u.shape != q.shape:
-                raise ValueError("Batch: buffer shape does not match its tree")
+                if not (a.is_cuda and a.dtype in (torch.complex128, torch.complex64) and a.is_contiguous()):
+                    raise ValueError("Batch: buffers must be contiguous complex128 or complex64 CUDA tensors")
+            if q.shape[-1] != t.n or u.shape != q.shape or u.dtype != q.dtype:
+                raise ValueError("Batch: buffer shape or dtype does not match its tree")
         th = (ctypes.c_void_p * n)(*[t._h.value for t in trees])
         qp = (ctypes.c_void_p * n)(*[q.data_ptr() for q in qs])
         up = (ctypes.c_void_p * n)(*[u.data_ptr() for u in us])
         nv = (ctypes.c_int * n)(*[1 if q.dim() == 1 else q.shape[0] for q in qs])
+        c64 = (ctypes.c_int * n)(*[int(q.dtype == torch.complex64) for q in qs])
         h = ctypes.c_void_p()
-        _check(_lib.lm_batch_create(th, n, qp, nv, up, ctypes.byref(h)))
+        _check(_lib.lm_batch_create(th, n, qp, nv, up, c64, ctypes.byref(h)))
         self._h = h
 
     def launch(self, stream=None):

@@ -14,6 +14,12 @@
 
 void lm_set_error(const char *fmt, ...);
 
+// Dynamic shared-memory limits are per kernel and per device, shared by every
+// tree: raise one (never lower it) so that trees built earlier, with larger
+// needs, still launch.  slot names the kernel in a small per-device cache.
+enum { LM_SMEM_NEAR_PW = 0, LM_SMEM_IMAGE_M2L = 1, LM_SMEM_SLOTS = 2 };
+cudaError_t lm_raise_smem(const void *func, int slot, int bytes);
+
 #define LM_CUDA(call)                                                                       \
     do {                                                                                    \
         cudaError_t e_ = (call);                                                            \
@@ -68,6 +74,8 @@ struct Level {
     int64_t nrest;
     int64_t *rstart; // [nbox + 1]
     int32_t *rsrc, *rslot;
+    int m2l_impl;    // free-space stencil M2L at this level: 0 tensor cores, else CUDA cores with
+                     // this many orders per thread (set at build, changed by the autotuner)
     int64_t nrtgt;   // targets with entries on the rest list
     int32_t *rtgt;   // [nrtgt]
 };
@@ -124,7 +132,8 @@ lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint,
 lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, zd *uy, cudaStream_t st);
 // mixed precision (lmfmm_mixed.cu)
 lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st);
-lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);
+lm_status lm_autotune_mixed(lm_tree_s *t, cudaStream_t st, int *choice, float *ms);
+lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st);
 void lm_free_mixed(lm_tree_s *t);
 // tensor-core M2L (lmfmm_tc.cu)
 lm_status lm_setup_tc(lm_tree_s *t, cudaStream_t st);

@@ -1,6 +1,7 @@
 // lmfmm_api.cu -- the C ABI declared in include/lmfmm.h: argument checks,
 // handle management and error reporting around the setup and apply code.
 #include <math.h>
+#include <mutex>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -53,6 +54,7 @@ extern "C" lm_status lm_options_default(lm_options *o)
     o->tail_rays = 9;
     o->tensor_m2l = 1;
     o->kernel = LM_KERNEL_G;
+    o->autotune = 0;
     return LM_OK;
 }
 
@@ -153,6 +155,7 @@ extern "C" lm_status lm_build_tree(lm_medium m, const double *x, const double *y
     t->max_nvec = m->opt.max_nvec;
     lm_status s = lm_setup_tree(t, x, y, st);
     if (s == LM_OK) s = lm_setup_tables(t, st);
+    if (s == LM_OK && t->precision == LM_MIXED && m->opt.autotune) s = lm_autotune_mixed(t, st, nullptr, nullptr);
     if (s != LM_OK) {
         cudaStreamSynchronize(st);
         lm_destroy_tree(t);
@@ -162,14 +165,14 @@ extern "C" lm_status lm_build_tree(lm_medium m, const double *x, const double *y
     return LM_OK;
 }
 
-static lm_status check_apply(lm_tree t, const void *q, int nvec, void *u)
+static lm_status check_apply(lm_tree t, const void *q, int nvec, void *u, size_t esize = sizeof(zd))
 {
     if (!t || !q || !u || nvec < 1) {
         lm_set_error("apply: NULL tree or buffer, or nvec < 1");
         return LM_EINVAL;
     }
     const char *a = (const char *)q, *b = (const char *)u;
-    size_t bytes = (size_t)nvec * t->n * sizeof(zd);
+    size_t bytes = (size_t)nvec * t->n * esize;
     if (a < b + bytes && b < a + bytes) {
         lm_set_error("apply: q and u overlap");
         return LM_EINVAL;
@@ -195,6 +198,46 @@ extern "C" lm_status lm_apply_adjoint(lm_tree t, const void *v, int nvec, void *
     s = lm_run_apply(t, (const zd *)v, nvec, (zd *)w, true, (cudaStream_t)stream);
     lm_profile_apply_stop(t);
     return s;
+}
+
+extern "C" lm_status lm_autotune(lm_tree t, void *stream, int *choice, float *ms)
+{
+    if (!t) {
+        lm_set_error("autotune: NULL tree");
+        return LM_EINVAL;
+    }
+    if (t->precision != LM_MIXED) {
+        for (int l = 0; l <= t->L; ++l) {
+            if (choice) choice[l] = -1;
+            if (ms) ms[l] = 0.f;
+        }
+        return LM_OK;
+    }
+    return lm_autotune_mixed(t, (cudaStream_t)stream, choice, ms);
+}
+
+static lm_status apply_c64(lm_tree t, const void *q, int nvec, void *u, bool adjoint, void *stream)
+{
+    lm_status s = check_apply(t, q, nvec, u, sizeof(zf));
+    if (s != LM_OK) return s;
+    if (t->precision != LM_MIXED) {
+        lm_set_error("apply_c64: complex64 buffers need an LM_MIXED tree");
+        return LM_EINVAL;
+    }
+    lm_profile_apply_start(t);
+    s = lm_run_apply_mixed(t, q, nvec, u, adjoint, true, (cudaStream_t)stream);
+    lm_profile_apply_stop(t);
+    return s;
+}
+
+extern "C" lm_status lm_apply_c64(lm_tree t, const void *q, int nvec, void *u, void *stream)
+{
+    return apply_c64(t, q, nvec, u, false, stream);
+}
+
+extern "C" lm_status lm_apply_adjoint_c64(lm_tree t, const void *v, int nvec, void *w, void *stream)
+{
+    return apply_c64(t, v, nvec, w, true, stream);
 }
 
 extern "C" lm_status lm_apply_grad(lm_tree t, const void *q, int nvec, void *u, void *ux, void *uy,
@@ -505,7 +548,7 @@ extern "C" void lm_batch_destroy(lm_batch b)
 }
 
 extern "C" lm_status lm_batch_create(const lm_tree *trees, int count, const void *const *q, const int *nvec,
-                                     void *const *u, lm_batch *out)
+                                     void *const *u, const int *c64, lm_batch *out)
 {
     if (!out || !trees || !q || !nvec || !u || count < 1) {
         lm_set_error("batch_create: bad argument");
@@ -513,8 +556,13 @@ extern "C" lm_status lm_batch_create(const lm_tree *trees, int count, const void
     }
     *out = nullptr;
     for (int i = 0; i < count; ++i) {
-        lm_status s = check_apply(trees[i], q[i], nvec[i], u[i]);
+        const bool f = c64 && c64[i];
+        lm_status s = check_apply(trees[i], q[i], nvec[i], u[i], f ? sizeof(zf) : sizeof(zd));
         if (s != LM_OK) return s;
+        if (f && trees[i]->precision != LM_MIXED) {
+            lm_set_error("batch_create: complex64 buffers of entry %d need an LM_MIXED tree", i);
+            return LM_EINVAL;
+        }
         for (int j = 0; j < i; ++j)
             if (trees[j] == trees[i]) { // one tree's scratch cannot serve two concurrent applies
                 lm_set_error("batch_create: tree %d appears twice", i);
@@ -544,8 +592,15 @@ extern "C" lm_status lm_batch_create(const lm_tree *trees, int count, const void
     if (e == cudaSuccess) {
         cudaEventRecord(fork, cs);
         for (int k = 0; k < nstream; ++k) cudaStreamWaitEvent(side[k], fork, 0);
-        for (int i = 0; i < count && st == LM_OK; ++i)
-            st = lm_run_apply(trees[i], (const zd *)q[i], nvec[i], (zd *)u[i], false, side[i % nstream]);
+        for (int i = 0; i < count && st == LM_OK; ++i) {
+            st = (c64 && c64[i]) ? lm_run_apply_mixed(trees[i], q[i], nvec[i], u[i], false, true, side[i % nstream])
+                                 : lm_run_apply(trees[i], (const zd *)q[i], nvec[i], (zd *)u[i], false,
+                                                side[i % nstream]);
+            if (st != LM_OK) {
+                std::string why = lm_last_error();
+                lm_set_error("batch_create: capturing the apply of tree %d failed: %s", i, why.c_str());
+            }
+        }
         for (int k = 0; k < nstream; ++k) {
             cudaEventRecord(join[k], side[k]);
             cudaStreamWaitEvent(cs, join[k], 0);
@@ -589,4 +644,25 @@ extern "C" lm_status lm_batch_launch(lm_batch b, void *stream)
     }
     LM_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
     return LM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// monotone dynamic shared-memory limits (per device, per kernel slot)
+// ---------------------------------------------------------------------------
+#define LM_SMEM_MAXDEV 64
+static int g_smem_set[LM_SMEM_MAXDEV][LM_SMEM_SLOTS];
+static std::mutex g_smem_mutex;
+
+cudaError_t lm_raise_smem(const void *func, int slot, int bytes)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= LM_SMEM_MAXDEV || slot < 0 || slot >= LM_SMEM_SLOTS)
+        return cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    std::lock_guard<std::mutex> lock(g_smem_mutex);
+    if (bytes <= g_smem_set[dev][slot]) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) g_smem_set[dev][slot] = bytes;
+    return e;
 }

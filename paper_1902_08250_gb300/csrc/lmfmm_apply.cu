@@ -390,7 +390,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
 
 lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st)
 {
-    if (t->precision == LM_MIXED) return lm_run_apply_mixed(t, q, nvec, u, adjoint, st);
+    if (t->precision == LM_MIXED) return lm_run_apply_mixed(t, q, nvec, u, adjoint, false, st);
     return run_fp64(t, q, nvec, u, adjoint, nullptr, nullptr, st);
 }
 

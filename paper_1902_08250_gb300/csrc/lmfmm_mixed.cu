@@ -191,8 +191,9 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
         lm_set_error("build_tree: near-field segment of %d nodes is too long for the factorised kernel", q.nseg);
         return LM_ENOTSUP;
     }
-    LM_CUDA(cudaFuncSetAttribute(k_near_pw32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+    LM_CUDA(lm_raise_smem((const void *)k_near_pw32, LM_SMEM_NEAR_PW, (int)shm));
     if (t->med.opt.tensor_m2l) TRYM(lm_setup_tc(t, st));
+    for (Level &lv : t->lev) lv.m2l_impl = t->tc_ready ? 0 : 4;
     LM_CUDA(cudaGetLastError());
     LM_CUDA(cudaStreamSynchronize(st));
     return LM_OK;
@@ -217,7 +218,8 @@ void lm_free_mixed(lm_tree_s *t)
 // ---------------------------------------------------------------------------
 // input order -> tree order: one thread per input point, coalesced reads of
 // q[v][j], one 128-byte row written at the point's tree position
-__global__ void k_permute_in32(const zd *q, const int64_t *iperm, int64_t n, int nvec, int conjugate, zf *qs)
+template <typename TIO>
+__global__ void k_permute_in32(const TIO *q, const int64_t *iperm, int64_t n, int nvec, int conjugate, zf *qs)
 {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -227,8 +229,8 @@ __global__ void k_permute_in32(const zd *q, const int64_t *iperm, int64_t n, int
     for (int v = 0; v < LM_MAXV; ++v) {
         a[v] = zf{0.f, 0.f};
         if (v < nvec) {
-            zd b = q[(int64_t)v * n + j];
-            a[v] = f2(conjugate ? conj(b) : b);
+            const TIO b = q[(int64_t)v * n + j];
+            a[v] = zf{(float)b.re, (float)(conjugate ? -b.im : b.im)};
         }
     }
     float4 *o = (float4 *)(qs + i * LM_MAXV);
@@ -238,7 +240,8 @@ __global__ void k_permute_in32(const zd *q, const int64_t *iperm, int64_t n, int
 }
 // tree order -> input order: one thread per input point, one 128-byte row
 // read at its tree position, coalesced writes of u[v][j]
-__global__ void k_permute_out32(const zf *us, const int64_t *iperm, int64_t n, int nvec, int conjugate, zd *u)
+template <typename TIO>
+__global__ void k_permute_out32(const zf *us, const int64_t *iperm, int64_t n, int nvec, int conjugate, TIO *u)
 {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -251,8 +254,11 @@ __global__ void k_permute_out32(const zf *us, const int64_t *iperm, int64_t n, i
     for (int v = 0; v < LM_MAXV; ++v) {
         if (v < nvec) {
             const float4 t = a[v / 2];
-            zd b = (v & 1) ? zd{(double)t.z, (double)t.w} : zd{(double)t.x, (double)t.y};
-            u[(int64_t)v * n + j] = conjugate ? conj(b) : b;
+            const float re = (v & 1) ? t.z : t.x, im = (v & 1) ? t.w : t.y;
+            TIO b;
+            b.re = re;
+            b.im = conjugate ? -im : im;
+            u[(int64_t)v * n + j] = b;
         }
     }
 }
@@ -374,9 +380,10 @@ __global__ void k_l2l32(int64_t ncol, int64_t nbox, const zf *tabs, const zf *Lp
 // shared memory (transposed: warp-uniform broadcast reads) and the gathered
 // source multipoles stream from L2 as 32-byte vector loads.  Each offset's
 // contraction accumulates in fresh registers before joining the sum.
-#define ST_RG 4
-template <int NP>
-__global__ void __launch_bounds__(64 * ((NP + ST_RG - 1) / ST_RG))
+// RG (orders per thread, hence the block's row tiling) is the tile shape the
+// autotuner chooses among, together with the tensor-core kernel.
+template <int NP, int RG>
+__global__ void __launch_bounds__(64 * ((NP + RG - 1) / RG))
     k_m2l_stencil32(int64_t ncol, int64_t nrow, const int32_t *stencil, const zf *tab, const zf *M, zf *Lc)
 {
     __shared__ zf At[NP * NP]; // At[q][p]
@@ -388,10 +395,10 @@ __global__ void __launch_bounds__(64 * ((NP + ST_RG - 1) / ST_RG))
     const int64_t cidx = (int64_t)blockIdx.x * 16 + lb;
     const bool active = cidx < hc * hr;
     const int64_t c = 2 * (active ? cidx % hc : 0) + pc, r = 2 * (active ? cidx / hc : 0) + pr;
-    const int p0 = rg * ST_RG;
-    zf acc[ST_RG][4];
+    const int p0 = rg * RG;
+    zf acc[RG][4];
 #pragma unroll
-    for (int i = 0; i < ST_RG; ++i)
+    for (int i = 0; i < RG; ++i)
 #pragma unroll
         for (int u = 0; u < 4; ++u) acc[i][u] = zf{0.f, 0.f};
     for (int dc = pc - 3; dc <= pc + 2; ++dc)
@@ -409,9 +416,9 @@ __global__ void __launch_bounds__(64 * ((NP + ST_RG - 1) / ST_RG))
             const int64_t cs = c - dc, rs = r - dr;
             if (!active || cs < 0 || cs >= ncol || rs < 0 || rs >= nrow) continue;
             const zf *m = M + (rs * ncol + cs) * NP * LM_MAXV + vq;
-            zf tmp[ST_RG][4];
+            zf tmp[RG][4];
 #pragma unroll
-            for (int i = 0; i < ST_RG; ++i)
+            for (int i = 0; i < RG; ++i)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) tmp[i][u] = zf{0.f, 0.f};
 #pragma unroll 2
@@ -421,7 +428,7 @@ __global__ void __launch_bounds__(64 * ((NP + ST_RG - 1) / ST_RG))
                 const zf mv[4] = {{m01.x, m01.y}, {m01.z, m01.w}, {m23.x, m23.y}, {m23.z, m23.w}};
                 const zf *a = At + q * NP + p0;
 #pragma unroll
-                for (int i = 0; i < ST_RG; ++i) {
+                for (int i = 0; i < RG; ++i) {
                     if (p0 + i < NP) {
                         const zf ai = a[i];
 #pragma unroll
@@ -430,14 +437,14 @@ __global__ void __launch_bounds__(64 * ((NP + ST_RG - 1) / ST_RG))
                 }
             }
 #pragma unroll
-            for (int i = 0; i < ST_RG; ++i)
+            for (int i = 0; i < RG; ++i)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) acc[i][u] = acc[i][u] + tmp[i][u];
         }
     if (!active) return;
     zf *out = Lc + (r * ncol + c) * NP * LM_MAXV + vq;
 #pragma unroll
-    for (int i = 0; i < ST_RG; ++i) {
+    for (int i = 0; i < RG; ++i) {
         if (p0 + i >= NP) break;
         float4 *o = (float4 *)(out + (p0 + i) * LM_MAXV);
         float4 x0 = o[0], x1 = o[1];
@@ -890,14 +897,24 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
 }
 
 // ---------------------------------------------------------------------------
-template <int P>
-static void launch_stencil(const Level &lv, cudaStream_t st)
+template <int NP, int RG>
+static void launch_stencil_rg(const Level &lv, cudaStream_t st)
 {
-    constexpr int NP = 2 * P + 1;
     int64_t ncls = (lv.ncol / 2) * (lv.nrow / 2);
     dim3 g((unsigned)((ncls + 15) / 16), 4);
-    k_m2l_stencil32<NP><<<g, 64 * ((NP + ST_RG - 1) / ST_RG), 0, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32,
-                                                                         lv.M32, lv.L32);
+    k_m2l_stencil32<NP, RG><<<g, 64 * ((NP + RG - 1) / RG), 0, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32,
+                                                                       lv.M32, lv.L32);
+}
+// rg = 2 only while the block stays within 1024 threads (2p + 1 <= 32)
+template <int P>
+static void launch_stencil(const Level &lv, cudaStream_t st, int rg)
+{
+    constexpr int NP = 2 * P + 1;
+    if constexpr (NP <= 32) {
+        if (rg == 2) return launch_stencil_rg<NP, 2>(lv, st);
+    }
+    if (rg == 8) return launch_stencil_rg<NP, 8>(lv, st);
+    launch_stencil_rg<NP, 4>(lv, st);
 }
 template <int P>
 static void launch_m2m(const Level &lv, const Level &child, cudaStream_t st)
@@ -965,7 +982,7 @@ bool lm_mixed_order_supported(int P)
     }
 }
 
-lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st)
+lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st)
 {
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const int64_t n = t->n;
@@ -975,7 +992,12 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         lm_phase_begin(t, PH_PERMUTE, st);
-        k_permute_in32<<<gridm(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->iperm, n, nv, adjoint, t->qs32);
+        if (c64)
+            k_permute_in32<zf><<<gridm(n, 256), 256, 0, st>>>((const zf *)q + (int64_t)v0 * n, t->iperm, n, nv,
+                                                             adjoint, t->qs32);
+        else
+            k_permute_in32<zd><<<gridm(n, 256), 256, 0, st>>>((const zd *)q + (int64_t)v0 * n, t->iperm, n, nv,
+                                                             adjoint, t->qs32);
         lm_phase_end(t, PH_PERMUTE, st, 1);
         lm_phase_begin(t, PH_S2M, st);
         {
@@ -1002,11 +1024,11 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
             lm_phase_begin(t, PH_M2L, st);
             int launches = 0;
             if (l > 0) {
-                if (t->tc_ready) {
+                if (lv.m2l_impl == 0 && t->tc_ready) {
                     lm_status s = lm_launch_m2l_tc(t, l, st);
                     if (s != LM_OK) return s;
                 } else {
-                    MX_DISPATCH(P, launch_stencil, lv, st);
+                    MX_DISPATCH(P, launch_stencil, lv, st, lv.m2l_impl > 0 ? lv.m2l_impl : 4);
                 }
                 ++launches;
             }
@@ -1027,9 +1049,81 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const zd *q, int nvec, zd *u, bool ad
         }
         lm_phase_end(t, PH_LEAF, st, 2);
         lm_phase_begin(t, PH_PERMUTE, st);
-        k_permute_out32<<<gridm(n, 256), 256, 0, st>>>(t->us32, t->iperm, n, nv, adjoint, u + (int64_t)v0 * n);
+        if (c64)
+            k_permute_out32<zf><<<gridm(n, 256), 256, 0, st>>>(t->us32, t->iperm, n, nv, adjoint,
+                                                              (zf *)u + (int64_t)v0 * n);
+        else
+            k_permute_out32<zd><<<gridm(n, 256), 256, 0, st>>>(t->us32, t->iperm, n, nv, adjoint,
+                                                              (zd *)u + (int64_t)v0 * n);
         lm_phase_end(t, PH_PERMUTE, st, 1);
         LM_CUDA(cudaGetLastError());
     }
     return LM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// M2L autotuner: per level >= 1, time the free-space stencil with each tile
+// shape -- the tcgen05 kernel (8 boxes x 16 vectors x 64 real orders) and the
+// CUDA-core kernel with 2, 4 or 8 orders per thread (16 boxes x 4 vectors per
+// row group) -- on the tree's own buffers (zeroed first: an apply rewrites
+// them), one warm-up and three timed launches each, CUDA events on `st`, and
+// keep the fastest.  choice[l] receives 0 (tensor cores) or the rows per
+// thread; ms[l] its time per launch.
+// ---------------------------------------------------------------------------
+lm_status lm_autotune_mixed(lm_tree_s *t, cudaStream_t st, int *choice, float *ms)
+{
+    const int P = t->p, np = 2 * P + 1;
+    cudaEvent_t e0, e1;
+    LM_CUDA(cudaEventCreate(&e0));
+    LM_CUDA(cudaEventCreate(&e1));
+    lm_status status = LM_OK;
+    for (int l = 0; l <= t->L && status == LM_OK; ++l) {
+        Level &lv = t->lev[l];
+        if (choice) choice[l] = -1;
+        if (ms) ms[l] = 0.f;
+        if (l == 0) continue; // level 0 has no stencil: its entries are on the rest list
+        if (cudaMemsetAsync(lv.M32, 0, lv.nbox * np * LM_MAXV * sizeof(zf), st) != cudaSuccess ||
+            cudaMemsetAsync(lv.L32, 0, lv.nbox * np * LM_MAXV * sizeof(zf), st) != cudaSuccess) {
+            status = LM_ECUDA;
+            break;
+        }
+        int cand[4], nc = 0;
+        if (t->tc_ready) cand[nc++] = 0;
+        if (np <= 32) cand[nc++] = 2;
+        cand[nc++] = 4;
+        cand[nc++] = 8;
+        int best = cand[0];
+        float best_ms = 1e30f;
+        for (int ci = 0; ci < nc && status == LM_OK; ++ci) {
+            lv.m2l_impl = cand[ci];
+            auto run = [&]() -> lm_status {
+                if (cand[ci] == 0) return lm_launch_m2l_tc(t, l, st);
+                MX_DISPATCH(P, launch_stencil, lv, st, cand[ci]);
+                return LM_OK;
+            };
+            status = run();
+            if (status != LM_OK) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && status == LM_OK; ++r) status = run();
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+                lm_set_error("autotune: a candidate launch failed at level %d", l);
+                status = LM_ECUDA;
+                break;
+            }
+            float el = 0.f;
+            cudaEventElapsedTime(&el, e0, e1);
+            el /= 3.f;
+            if (el < best_ms) {
+                best_ms = el;
+                best = cand[ci];
+            }
+        }
+        lv.m2l_impl = best;
+        if (choice) choice[l] = best;
+        if (ms) ms[l] = best_ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return status;
 }

@@ -870,7 +870,7 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
         }
         if (ni > 0) {
             size_t shm = (2 * TB_CHUNK * np + TB_CHUNK) * sizeof(zd);
-            LM_CUDA(cudaFuncSetAttribute(k_image_m2l, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
+            LM_CUDA(lm_raise_smem((const void *)k_image_m2l, LM_SMEM_IMAGE_M2L, (int)shm));
             k_image_m2l<<<ni, 256, shm, st>>>(md, P, lv.w, k * lv.w, dbuf + 3 * nf, dbuf + 3 * nf + ni,
                                               dbuf + 3 * nf + 2 * ni, dbuf + 3 * nf + 3 * ni, ni, lv.tab,
                                               t->dflag);

@@ -44,3 +44,20 @@ def clustered(n=100_000, nvec=1, seed=0):
 def wide_uniform(n=1_000_000, nvec=16, seed=0):
     """N uniform in x in [0,20], y in [-0.95,-0.05] (medium B), nvec densities."""
     return uniform_strip(n, 0.0, 20.0, -0.95, -0.05, nvec, seed)
+
+
+def batched_instances(count=48, n_lo=10_000, n_hi=500_000, nvec=4, seed=0, dtype=np.complex64):
+    """Independent instances: per instance N log-uniform in [n_lo, n_hi], wave numbers
+    k1, k2, k3 ~ U[0.5, 4], thickness d ~ U[0.5, 2], points x ~ U[0, 10], y ~ U[-0.9 d, -0.1 d],
+    nvec N(0,1) complex densities.  Returns a list of (medium, x, y, q); drawn in order
+    (N, k1, k2, k3, d, x, y, q) per instance from one generator."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        k1, k2, k3 = rng.uniform(0.5, 4.0, 3)
+        d = rng.uniform(0.5, 2.0)
+        x = rng.uniform(0.0, 10.0, n)
+        y = rng.uniform(-0.9 * d, -0.1 * d, n)
+        out.append(((float(k1), float(k2), float(k3), float(d)), x, y, densities(rng, nvec, n, dtype)))
+    return out
