@@ -64,6 +64,7 @@ def _declare(L):
         "orc_spectral_refl": (None, [_P, _D, _D, _D, _D, _D, _D, _P]),
         "orc_spectral_refl_solve": (None, [_P, _D, _D, _D, _D, _D, _D, _P]),
         "orc_set_tolerance": (None, [_D, _D]),
+        "orc_set_boundaries": (None, [_I, _D, _I, _D]),
         "orc_gk15_pow": (None, [_I, _D, _D, _P]),
         "orc_sommerfeld_free": (_I, [_D, _D, _D, _I, _P]),
         "orc_dirichlet": (_I, [_D, _D, _D, _D, _D, _I, _P]),
@@ -108,6 +109,16 @@ def _cplx_in(z):
 
 def set_tolerance(atol=1e-15, rtol=1e-13):
     lib().orc_set_tolerance(atol, rtol)
+
+
+BC = {"transmission": 0, "dirichlet": 1, "neumann": 2, "impedance": 3}
+
+
+def set_boundaries(top="transmission", top_alpha=0.0, bottom="transmission", bottom_alpha=0.0):
+    """Kinds of the middle layer's interfaces (y = 0 top, y = -d bottom) for every later
+    oracle call: transmission (the outer wave number k1 / k3), or a wall -- Dirichlet
+    (R = -1), Neumann (R = +1), impedance (R = (s2 + i k2 alpha)/(s2 - i k2 alpha))."""
+    lib().orc_set_boundaries(BC[top], float(top_alpha), BC[bottom], float(bottom_alpha))
 
 
 # --- branch and densities ---------------------------------------------------

@@ -169,11 +169,44 @@ void orc_sigma2t_safe(const double *lam, double k1, double k2, double k3, double
  * R_t and R_b are written as (k1^2-k2^2)/(s2+s1)^2 and (k3^2-k2^2)/(s2+s3)^2
  * (the same numbers, without cancellation at large lambda).                 */
 /* ------------------------------------------------------------------------- */
+/* Other media (Sec. 3, Examples 2 and 3): either interface of the middle
+ * layer may instead be a wall with a one-sided condition.  Its reflection
+ * coefficient replaces R_t or R_b in the formulas above:
+ *   Dirichlet (u = 0): -1;  Neumann (du/dn = 0): +1;
+ *   impedance: the image term of Eq. (halfspace), (s2 + i k2 alpha)/(s2 - i k2 alpha)
+ *   (reading: the printed image term defines the condition, du/dn - i k2 alpha u = 0
+ *   with n the layer's outward normal; it tends to the Dirichlet value as alpha
+ *   grows and equals the Neumann value at alpha = 0).
+ * The kinds are process-wide settings of the oracle (orc_set_boundaries). */
+enum { ORC_BC_TRANSMISSION = 0, ORC_BC_DIRICHLET = 1, ORC_BC_NEUMANN = 2, ORC_BC_IMPEDANCE = 3 };
+static int g_bc_kind[2] = {ORC_BC_TRANSMISSION, ORC_BC_TRANSMISSION}; /* top (y = 0), bottom (y = -d) */
+static double g_bc_alpha[2] = {0.0, 0.0};
+void orc_set_boundaries(int top, double top_alpha, int bottom, double bottom_alpha)
+{
+    g_bc_kind[0] = top;
+    g_bc_alpha[0] = top_alpha;
+    g_bc_kind[1] = bottom;
+    g_bc_alpha[1] = bottom_alpha;
+}
+/* reflection coefficient of boundary b (0 top, 1 bottom); kj, sj: the outer layer's */
+static cx refl_coef(int b, cx s2, double k2, cx sj, double kj)
+{
+    switch (g_bc_kind[b]) {
+    case ORC_BC_DIRICHLET: return -1.0;
+    case ORC_BC_NEUMANN: return 1.0;
+    case ORC_BC_IMPEDANCE: {
+        cx beta = I * k2 * g_bc_alpha[b];
+        return (s2 + beta) / (s2 - beta);
+    }
+    default: return (kj * kj - k2 * k2) / ((s2 + sj) * (s2 + sj));
+    }
+}
+
 static void sig_layer2(cx l, const orc_medium *m, cx *s2o, cx sig[3])
 {
     cx s1 = sroot(l, m->k1), s2 = sroot(l, m->k2), s3 = sroot(l, m->k3);
-    cx Rt = (m->k1 * m->k1 - m->k2 * m->k2) / ((s2 + s1) * (s2 + s1));
-    cx Rb = (m->k3 * m->k3 - m->k2 * m->k2) / ((s2 + s3) * (s2 + s3));
+    cx Rt = refl_coef(0, s2, m->k2, s1, m->k1);
+    cx Rb = refl_coef(1, s2, m->k2, s3, m->k3);
     cx S = 1.0 / (1.0 - Rt * Rb * cexp(-2.0 * m->d * s2));
     sig[0] = Rt * S;
     sig[1] = Rb * S;
@@ -533,8 +566,8 @@ static const double dh_dd[4] = {0.0, 2.0, 2.0, 2.0};
 static void sig_layer2_dd(cx l, const orc_medium *m, cx dsig[3])
 {
     cx s1 = sroot(l, m->k1), s2 = sroot(l, m->k2), s3 = sroot(l, m->k3);
-    cx Rt = (m->k1 * m->k1 - m->k2 * m->k2) / ((s2 + s1) * (s2 + s1));
-    cx Rb = (m->k3 * m->k3 - m->k2 * m->k2) / ((s2 + s3) * (s2 + s3));
+    cx Rt = refl_coef(0, s2, m->k2, s1, m->k1);
+    cx Rb = refl_coef(1, s2, m->k2, s3, m->k3);
     cx E = Rt * Rb * cexp(-2.0 * m->d * s2);
     cx S = 1.0 / (1.0 - E);
     cx dS = -2.0 * s2 * E * S * S;
