@@ -71,7 +71,24 @@ typedef struct {
                         (TF32 hi/lo split, FP32 accumulation in tensor memory); 1 on, 0 off */
     int kernel;      /* lm_kernel: the operator the tree applies; 0 -> LM_KERNEL_G */
     int autotune;    /* LM_MIXED: run lm_autotune at the end of lm_build_tree; 0 off (default) */
+    int top_bc;      /* lm_boundary of the interface y = 0; 0 -> LM_BC_TRANSMISSION (layer 1, k1) */
+    int bottom_bc;   /* lm_boundary of the interface y = -d; 0 -> LM_BC_TRANSMISSION (layer 3, k3) */
+    double top_alpha;    /* LM_BC_IMPEDANCE at y = 0: alpha (real, finite) */
+    double bottom_alpha; /* LM_BC_IMPEDANCE at y = -d: alpha */
 } lm_options;
+
+/* Other media (Sec. 3, Examples 2 and 3): an interface of the middle layer
+ * may be a wall with a one-sided condition instead of a transmission to an
+ * outer layer.  Its reflection coefficient replaces R_t or R_b:
+ *   LM_BC_DIRICHLET  u = 0          R = -1
+ *   LM_BC_NEUMANN    du/dn = 0      R = +1
+ *   LM_BC_IMPEDANCE  du/dn - i k2 alpha u = 0, n the layer's outward normal:
+ *                    R = (s2 + i k2 alpha)/(s2 - i k2 alpha), the image term
+ *                    of Eq. (halfspace)
+ * A half-space is a wall on top and k3 = k2 below (R_b = 0), with d any
+ * depth below the points.  With a wall, k1 (or k3) is not used but must
+ * still be finite and positive. */
+typedef enum { LM_BC_TRANSMISSION = 0, LM_BC_DIRICHLET = 1, LM_BC_NEUMANN = 2, LM_BC_IMPEDANCE = 3 } lm_boundary;
 
 typedef enum {
     LM_KERNEL_G = 0,     /* G = free space + reflected part (Sec. 3, Example 4; reading R1) */

@@ -28,6 +28,7 @@ __all__ = [
 
 FP64, MIXED = 0, 1
 KERNEL_G, KERNEL_DG_DD = 0, 1
+BC = {"transmission": 0, "dirichlet": 1, "neumann": 2, "impedance": 3}
 _STATUS = {0: "LM_OK", 1: "LM_EINVAL", 2: "LM_ENOMEM", 3: "LM_ECUDA", 4: "LM_ETIMEOUT", 5: "LM_ENOTSUP"}
 
 
@@ -41,7 +42,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("depth", ctypes.c_int), ("leaf_target", ctypes.c_int),
                 ("precision", ctypes.c_int), ("max_nvec", ctypes.c_int), ("seg_order", ctypes.c_int),
                 ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int), ("tensor_m2l", ctypes.c_int),
-                ("kernel", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("top_bc", ctypes.c_int),
+                ("bottom_bc", ctypes.c_int), ("top_alpha", ctypes.c_double), ("bottom_alpha", ctypes.c_double)]
 
 
 class _TreeInfo(ctypes.Structure):
@@ -124,19 +126,28 @@ class Medium:
 
 def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
                   seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1, kernel=KERNEL_G,
-                  autotune=0) -> Medium:
+                  autotune=0, top_bc="transmission", top_alpha=0.0, bottom_bc="transmission",
+                  bottom_alpha=0.0) -> Medium:
     """kernel = KERNEL_G applies G; KERNEL_DG_DD applies dG/dd at fixed points.
-    autotune = 1 tunes the M2L tile shapes of mixed-precision trees at build time."""
+    autotune = 1 tunes the M2L tile shapes of mixed-precision trees at build time.
+    top_bc / bottom_bc: "transmission" (to the outer layer, k1 / k3), or a wall --
+    "dirichlet", "neumann", "impedance" (du/dn - i k2 alpha u = 0, alpha = top_alpha /
+    bottom_alpha)."""
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
+    for b in (top_bc, bottom_bc):
+        if b not in BC:
+            raise ValueError(f"create_medium: unknown boundary kind {b!r} (one of {sorted(BC)})")
     o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays, tensor_m2l,
-                 kernel, autotune)
+                 kernel, autotune, BC[top_bc], BC[bottom_bc], float(top_alpha), float(bottom_alpha))
     h = ctypes.c_void_p()
     _check(_lib.lm_create_medium(k1, k2, k3, d, ctypes.byref(o), ctypes.byref(h)))
     return Medium(h.value, k1, k2, k3, d, dict(p=p, depth=depth, leaf_target=leaf_target,
                                               precision=precision, max_nvec=max_nvec, seg_order=seg_order,
                                               tail_order=tail_order, tail_rays=tail_rays,
-                                              tensor_m2l=tensor_m2l, kernel=kernel, autotune=autotune))
+                                              tensor_m2l=tensor_m2l, kernel=kernel, autotune=autotune,
+                                              top_bc=top_bc, top_alpha=top_alpha, bottom_bc=bottom_bc,
+                                              bottom_alpha=bottom_alpha))
 
 
 class Tree:

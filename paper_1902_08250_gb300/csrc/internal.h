@@ -45,7 +45,7 @@ struct NearQuad {
     double c;    // segment end
     // device arrays
     zd *seg_lam, *seg_s2, *seg_w;    // [nseg], [nseg], [2][nseg]: w * lambda' * sigma_m / s2 / 4pi
-    zd *tail_lam, *tail_s2, *tail_w; // [nray][ntail], ..., [2][nray][ntail]: 2 w dlambda sigma_m/s2/4pi
+    zd *tail_lam, *tail_s2, *tail_w; // [nray][ntail], ..., [2 terms][P, M][nray][ntail] (see k_near_tail)
 };
 
 struct Level {

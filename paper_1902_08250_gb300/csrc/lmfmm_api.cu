@@ -55,6 +55,10 @@ extern "C" lm_status lm_options_default(lm_options *o)
     o->tensor_m2l = 1;
     o->kernel = LM_KERNEL_G;
     o->autotune = 0;
+    o->top_bc = LM_BC_TRANSMISSION;
+    o->bottom_bc = LM_BC_TRANSMISSION;
+    o->top_alpha = 0.0;
+    o->bottom_alpha = 0.0;
     return LM_OK;
 }
 
@@ -91,6 +95,11 @@ extern "C" lm_status lm_create_medium(double k1, double k2, double k3, double d,
     }
     if (o.precision != LM_FP64 && o.precision != LM_MIXED) {
         lm_set_error("create_medium: unknown precision %d", o.precision);
+        return LM_EINVAL;
+    }
+    if (o.top_bc < LM_BC_TRANSMISSION || o.top_bc > LM_BC_IMPEDANCE || o.bottom_bc < LM_BC_TRANSMISSION ||
+        o.bottom_bc > LM_BC_IMPEDANCE || !isfinite(o.top_alpha) || !isfinite(o.bottom_alpha)) {
+        lm_set_error("create_medium: unknown boundary kind or non-finite impedance alpha");
         return LM_EINVAL;
     }
     if (o.kernel != LM_KERNEL_G && o.kernel != LM_KERNEL_DG_DD) {

@@ -188,15 +188,13 @@ __device__ zd near_refl64(const NearQuadD &q, int m, double X, double h)
     }
     int k = q.nray > 1 ? (int)rint(atan2(X, h) * (q.nray - 1) / (0.5 * M_PI)) : 0;
     const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
-    const zd *tw = q.tail_w + ((int64_t)m * q.nray + k) * q.ntail;
-    double tre = 0.0;
+    const int64_t tot = (int64_t)q.nray * q.ntail;
+    const zd *tP = q.tail_w + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
     for (int i = 0; i < q.ntail; ++i) {
         zd lam = tl[i], s2 = ts[i];
         zd e = cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
-        zd w = tw[i];
-        tre += w.re * e.re - w.im * e.im;
+        acc = acc + e.re * tP[i] + e.im * zd{-tM[i].im, tM[i].re}; // P Re(E) + i M Im(E)
     }
-    acc.re += tre;
     return acc;
 }
 
@@ -259,7 +257,7 @@ __global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs
 // ---------------------------------------------------------------------------
 // Target gradient of one reflected direct term: the value, d/dX and d/dh of
 // the near-field quadrature of near_refl64 (segment: e^{+-i lam X} -> +-i lam,
-// e^{-s2 h} -> -s2; tail: the same inside Re[.]).
+// e^{-s2 h} -> -s2; tail: Z = E -> i lam E, -s2 E in P Re(Z) + i M Im(Z)).
 // ---------------------------------------------------------------------------
 __device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, zd *val, zd *dX, zd *dh)
 {
@@ -277,18 +275,17 @@ __device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, 
     }
     int k = q.nray > 1 ? (int)rint(atan2(X, h) * (q.nray - 1) / (0.5 * M_PI)) : 0;
     const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
-    const zd *tw = q.tail_w + ((int64_t)m * q.nray + k) * q.ntail;
-    double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+    const int64_t tot = (int64_t)q.nray * q.ntail;
+    const zd *tP = q.tail_w + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
     for (int i = 0; i < q.ntail; ++i) {
         zd lam = tl[i], s2 = ts[i];
-        zd we = tw[i] * cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
-        t0 += we.re;
-        t1 += (zd{-lam.im, lam.re} * we).re;
-        t2 -= (s2 * we).re;
+        const zd e = cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
+        const zd P = tP[i], iM = zd{-tM[i].im, tM[i].re};
+        const zd z1 = zd{-lam.im, lam.re} * e, z2 = -1.0 * (s2 * e); // i lam E, -s2 E
+        a0 = a0 + e.re * P + e.im * iM;
+        a1 = a1 + z1.re * P + z1.im * iM;
+        a2 = a2 + z2.re * P + z2.im * iM;
     }
-    a0.re += t0;
-    a1.re += t1;
-    a2.re += t2;
     *val = a0;
     *dX = a1;
     *dh = a2;

@@ -185,7 +185,7 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
     int64_t nt = (int64_t)q.nray * q.ntail;
     TRYM(conv(t, q.tail_lam, &t->nq_tail_lam, nt, st));
     TRYM(conv(t, q.tail_s2, &t->nq_tail_s2, nt, st));
-    TRYM(conv(t, q.tail_w, &t->nq_tail_w, 2 * nt, st));
+    TRYM(conv(t, q.tail_w, &t->nq_tail_w, 4 * nt, st));
     size_t shm = near_pw_smem(t);
     if (shm > 200 * 1024) {
         lm_set_error("build_tree: near-field segment of %d nodes is too long for the factorised kernel", q.nseg);
@@ -510,20 +510,22 @@ struct NearQuadF {
 // horizontal distance X and image height h: the rays lambda = c + t e^{i phi_k}
 // nearest the steepest-descent direction atan2(X, h) (Sec. 4.2, alternative
 // directions); 2 Re is taken because sigma(conj lambda) = conj(sigma(lambda)).
-__device__ float near_tail32(const NearQuadF &q, int m, float X, float h)
+__device__ zf near_tail32(const NearQuadF &q, int m, float X, float h)
 {
     int k = q.nray > 1 ? (int)rintf(atan2f(X, h) * (q.nray - 1) * 0.63661977236758134f) : 0;
     const zf *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
-    const zf *tw = q.tail_w + ((int64_t)m * q.nray + k) * q.ntail;
-    float tre = 0.f;
+    const int64_t tot = (int64_t)q.nray * q.ntail;
+    const zf *tP = q.tail_w + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
+    float re = 0.f, im = 0.f; // sum P Re(E) + i M Im(E)
     for (int i = 0; i < q.ntail; ++i) {
         zf lam = tl[i], s2 = ts[i];
         float a = expf(-lam.im * X - s2.re * h), sn, cs;
         sincosf(lam.re * X - s2.im * h, &sn, &cs);
-        zf w = tw[i];
-        tre += a * (w.re * cs - w.im * sn);
+        const zf P = tP[i], M = tM[i];
+        re += a * (P.re * cs - M.im * sn);
+        im += a * (P.im * cs + M.re * sn);
     }
-    return tre;
+    return zf{re, im};
 }
 
 // Segment part of the reflected direct terms, factorised per target leaf.
@@ -872,7 +874,7 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
                         // tail of a reflected direct term; its segment part is added by k_near_pw32
                         const float dx = (xi - sx[buf][jj]) + ox;
                         const float h = term == 1 ? -(ya + sya[buf][jj]) : ya + sya[buf][jj] + 2.0f * d;
-                        const zf g = zf{near_tail32(nq, term - 1, fabsf(dx), h), 0.f};
+                        const zf g = near_tail32(nq, term - 1, fabsf(dx), h);
                         const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
 #pragma unroll
                         for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {

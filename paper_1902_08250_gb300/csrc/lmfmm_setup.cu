@@ -311,13 +311,32 @@ __global__ void k_scan64(int64_t *c, int64_t m)
 struct MediumD {
     double k1, k2, k3, d;
     int deriv;
+    int bc[2];       // lm_boundary of the top (y = 0) and bottom (y = -d) interfaces
+    double alpha[2]; // impedance parameters
 };
+// reflection coefficient of interface b: a wall's (Dirichlet -1, Neumann +1,
+// impedance (s2 + i k2 alpha)/(s2 - i k2 alpha)) or the transmission value
+// (kj^2 - k2^2)/(s2 + sj)^2 to the outer layer of wave number kj
+__device__ zd refl_coef(const MediumD &m, int b, zd s2, zd sj, double kj)
+{
+    switch (m.bc[b]) {
+    case LM_BC_DIRICHLET: return zd{-1.0, 0.0};
+    case LM_BC_NEUMANN: return zd{1.0, 0.0};
+    case LM_BC_IMPEDANCE: {
+        const zd beta = {0.0, m.k2 * m.alpha[b]};
+        return cdiv(s2 + beta, s2 - beta);
+    }
+    default: {
+        zd a = s2 + sj;
+        return cdiv(zd{kj * kj - m.k2 * m.k2, 0.0}, a * a);
+    }
+    }
+}
 __device__ void densities(const MediumD &m, zd lam, zd *s2o, zd sig[3])
 {
     zd s1 = sbranch(lam, m.k1), s2 = sbranch(lam, m.k2), s3 = sbranch(lam, m.k3);
-    zd a = s2 + s1, b = s2 + s3;
-    zd Rt = cdiv(zd{m.k1 * m.k1 - m.k2 * m.k2, 0.0}, a * a);
-    zd Rb = cdiv(zd{m.k3 * m.k3 - m.k2 * m.k2, 0.0}, b * b);
+    zd Rt = refl_coef(m, 0, s2, s1, m.k1);
+    zd Rb = refl_coef(m, 1, s2, s3, m.k3);
     zd E = Rt * Rb * cexpd(-2.0 * m.d * s2);
     zd S = cdiv(zd{1.0, 0.0}, zd{1.0, 0.0} - E);
     sig[0] = Rt * S;
@@ -339,9 +358,13 @@ __device__ void densities(const MediumD &m, zd lam, zd *s2o, zd sig[3])
 //  along -i a to c - delta - i a, and up to c; the negative half is folded
 //  onto it (integrand 2 cos(lambda X) ...).  Gauss-Legendre panels.
 //  Tail: rays lambda = c + t e^{i phi_k}, phi_k = k (pi/2) / (nray - 1),
-//  t = c v/(1-v), Gauss-Legendre in v; since sigma(conj lambda) =
-//  conj(sigma(lambda)) for real wave numbers, the two half-line tails sum to
-//  2 Re Int_ray e^{i lambda X} F(lambda) d lambda.
+//  t = c v/(1-v), Gauss-Legendre in v.  The half-line integrals of
+//  e^{+i lambda X} F and e^{-i lambda X} F go to the ray and its mirror image
+//  below the axis, with weights W_u, W_l; with E = e^{i lambda X - s2 h} the
+//  mirror's factor is conj(E), so the tail is sum P Re(Z) + i M Im(Z) with
+//  P = W_u + W_l, M = W_u - W_l and Z = E (or its X- or h-derivative).  For
+//  transmission and Dirichlet/Neumann walls sigma(conj lambda) = conj(sigma)
+//  and the tail is real; an impedance wall makes it complex.
 // ---------------------------------------------------------------------------
 __global__ void k_near_seg(MediumD m, double c, double a, double delta, int nflat, int order,
                            zd *lam_o, zd *s2_o, zd *w_o, int nseg)
@@ -385,15 +408,20 @@ __global__ void k_near_tail(MediumD m, double c, int nray, int order, zd *lam_o,
     double v = 0.5 * (x + 1.0), wv = 0.5 * w;
     double t = c * v / (1.0 - v), dt = c / ((1.0 - v) * (1.0 - v));
     double phi = (nray > 1) ? k * (0.5 * M_PI) / (nray - 1) : 0.0;
+    // upper ray (for e^{+i lam X}) and its mirror below the axis (for e^{-i lam X})
     zd e = {cos(phi), sin(phi)};
-    zd lam = zd{c, 0.0} + t * e;
-    zd s2, sig[3];
+    zd lam = zd{c, 0.0} + t * e, laml = conj(lam);
+    zd s2, sig[3], s2l, sigl[3];
     densities(m, lam, &s2, sig);
-    zd base = cdiv((2.0 * wv * dt / (4.0 * M_PI)) * e, s2);
+    densities(m, laml, &s2l, sigl);
+    zd bu = cdiv((wv * dt / (4.0 * M_PI)) * e, s2), bl = cdiv((wv * dt / (4.0 * M_PI)) * conj(e), s2l);
     lam_o[i] = lam;
     s2_o[i] = s2;
-    w_o[i] = base * sig[0];
-    w_o[tot + i] = base * sig[1];
+    for (int mm = 0; mm < 2; ++mm) {
+        const zd wu = bu * sig[mm], wl = bl * sigl[mm];
+        w_o[((size_t)(2 * mm) * tot) + i] = wu + wl;     // P
+        w_o[((size_t)(2 * mm + 1) * tot) + i] = wu - wl; // M
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -770,7 +798,13 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
 {
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const double k = t->med.k2, d = t->med.d;
-    MediumD md{t->med.k1, t->med.k2, t->med.k3, t->med.d, t->med.opt.kernel == LM_KERNEL_DG_DD};
+    MediumD md{t->med.k1,
+               t->med.k2,
+               t->med.k3,
+               t->med.d,
+               t->med.opt.kernel == LM_KERNEL_DG_DD,
+               {t->med.opt.top_bc, t->med.opt.bottom_bc},
+               {t->med.opt.top_alpha, t->med.opt.bottom_alpha}};
     t->lev.resize(L + 1);
     // scale vectors
     for (int l = 0; l <= L; ++l) {
@@ -910,7 +944,7 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
         int nt = q.nray * q.ntail;
         TRY(dalloc(t, &q.tail_lam, nt));
         TRY(dalloc(t, &q.tail_s2, nt));
-        TRY(dalloc(t, &q.tail_w, 2 * nt));
+        TRY(dalloc(t, &q.tail_w, 4 * nt));
         k_near_seg<<<grid_for(q.nseg, 64), 64, 0, st>>>(md, q.c, a, delta, nflat, order, q.seg_lam,
                                                          q.seg_s2, q.seg_w, q.nseg);
         k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2,

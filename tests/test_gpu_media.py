@@ -1,0 +1,85 @@
+"""Other media (Sec. 3, Examples 2 and 3): Dirichlet, Neumann and impedance
+walls in place of the interfaces, through the same FMM, against the oracle's
+direct sums (FP64 path 1e-10, mixed path 1e-6) on sampled targets."""
+import numpy as np
+import pytest
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+MEDIA = {
+    # name: ((k1, k2, k3, d), top, top_alpha, bottom, bottom_alpha)
+    "dirichlet_half_space": ((1.0, 1.5, 1.5, 1.0), "dirichlet", 0.0, "transmission", 0.0),
+    "neumann_over_dirichlet": ((1.0, 1.5, 2.0, 1.0), "neumann", 0.0, "dirichlet", 0.0),
+    "impedance_walls": ((1.0, 1.5, 2.0, 1.0), "impedance", 0.7, "impedance", -0.3),
+    "impedance_over_layer": ((1.0, 1.5, 2.0, 1.0), "impedance", 1.0, "transmission", 0.0),
+}
+
+
+@pytest.fixture(scope="module")
+def lm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA GPU is required for -m gpu tests")
+    import paper_1902_08250_gb300 as lm
+
+    return lm
+
+
+@pytest.fixture
+def case(oracle):
+    x, y, q = workloads.uniform_strip(1500, 0.0, 3.0, -0.95, -0.05, nvec=2, seed=21)
+    sub = np.sort(np.random.default_rng(22).choice(x.size, 64, replace=False))
+    yield x, y, q, sub
+    oracle.set_boundaries()
+
+
+def _ref(oracle, spec, x, y, q, sub, deriv=None):
+    med, tb, ta, bb, ba = spec
+    oracle.set_boundaries(tb, ta, bb, ba)
+    if deriv is None:
+        return oracle.direct_apply(med, x, y, q, targets=sub)
+    return oracle.direct_apply_deriv(med, x, y, q, deriv, targets=sub)
+
+
+@pytest.mark.parametrize("name", list(MEDIA))
+@pytest.mark.parametrize("prec,p,tol", [("fp64", 24, 1e-10), ("mixed", 14, 1e-6)])
+def test_media_fmm_matches_oracle(lm, oracle, case, name, prec, p, tol):
+    import torch
+
+    x, y, q, sub = case
+    med, tb, ta, bb, ba = MEDIA[name]
+    m = lm.create_medium(*med, p=p, depth=2, precision=prec, top_bc=tb, top_alpha=ta, bottom_bc=bb,
+                         bottom_alpha=ba)
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    u = lm.apply(t, torch.from_numpy(q).cuda()).cpu().numpy()[:, sub]
+    ref = _ref(oracle, MEDIA[name], x, y, q, sub)
+    err = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+    print(f"{name} {prec} p={p}: rel-l2 {err:.2e}")
+    assert err < tol
+
+
+def test_impedance_target_gradient_matches_oracle(lm, oracle, case):
+    import torch
+
+    x, y, q, sub = case
+    spec = MEDIA["impedance_walls"]
+    med, tb, ta, bb, ba = spec
+    m = lm.create_medium(*med, p=24, depth=2, top_bc=tb, top_alpha=ta, bottom_bc=bb, bottom_alpha=ba)
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    _, ux, uy = (None if a is None else a.cpu().numpy()[:, sub]
+                 for a in lm.apply_grad(t, torch.from_numpy(q).cuda(), want_u=False))
+    for got, deriv in ((ux, oracle.DX), (uy, oracle.DY)):
+        ref = _ref(oracle, spec, x, y, q, sub, deriv)
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        print(f"impedance gradient {deriv}: rel-l2 {err:.2e}")
+        assert err < 1e-9
+
+
+def test_invalid_boundary_rejected(lm):
+    with pytest.raises(ValueError):
+        lm.create_medium(1.0, 1.5, 2.0, 1.0, top_bc="absorbing")
+    with pytest.raises(lm.LMError):
+        lm.create_medium(1.0, 1.5, 2.0, 1.0, top_bc="impedance", top_alpha=float("nan"))
