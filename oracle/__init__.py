@@ -65,6 +65,8 @@ def _declare(L):
         "orc_spectral_refl_solve": (None, [_P, _D, _D, _D, _D, _D, _D, _P]),
         "orc_set_tolerance": (None, [_D, _D]),
         "orc_set_boundaries": (None, [_I, _D, _I, _D]),
+        "orc_cross_field": (_I, [_D, _D, _D, _D, _D, _D, _D, _D, _I, _I, _P]),
+        "orc_cross_direct": (_I, [_D, _D, _D, _D, _I64, _P, _P, _I64, _P, _P, _I, _P, _I64, _P, _I, _P]),
         "orc_gk15_pow": (None, [_I, _D, _D, _P]),
         "orc_sommerfeld_free": (_I, [_D, _D, _D, _I, _P]),
         "orc_dirichlet": (_I, [_D, _D, _D, _D, _D, _I, _P]),
@@ -382,3 +384,34 @@ def psi_e4(medium, p, X, Y):
     """Evanescent part of the three-layer local basis Psi_p (Sec. 5, Fig. order3layer)."""
     k1, k2, k3, d = medium
     return _green_out(lib().orc_psi_e4, k1, k2, k3, d, p, X, Y)
+
+
+# --- cross-layer operator (Example 4 as printed: layer-1 sources, layer-2 targets) ---
+G2T, G2B, G1 = 1, 2, 4
+
+
+def cross_field(medium, x, y, x0, y0, which=G2T | G2B, dy=False):
+    """The printed Example 4 fields for a source (x0, y0 > 0) in layer 1: g_2^t, g_2^b (target
+    in layer 2) or g_1^s (target in layer 1), selected by the bits of `which`; dy=True gives
+    the target y-derivative."""
+    k1, k2, k3, d = medium
+    return _green_out(lib().orc_cross_field, k1, k2, k3, d, x, y, x0, y0, which, int(dy))
+
+
+def cross_direct(medium, xs, ys, xt, yt, q, targets=None, nthreads=0):
+    """u_i = sum_j q_j (g_2^t + g_2^b)(x_i, x_j), sources in layer 1, targets in layer 2.
+    q: [nvec, ns] or [ns]; returns [nvec, ntargets] (or [ntargets])."""
+    k1, k2, k3, d = medium
+    xs, ys, xt, yt = (_c(a, np.float64) for a in (xs, ys, xt, yt))
+    q = np.asarray(q)
+    one = q.ndim == 1
+    q2 = _c(q.reshape(1, -1) if one else q, np.complex128)
+    tg = None if targets is None else _c(targets, np.int64)
+    nt = xt.size if tg is None else tg.size
+    u = np.zeros((q2.shape[0], nt), np.complex128)
+    st = lib().orc_cross_direct(k1, k2, k3, d, xs.size, _ptr(xs), _ptr(ys), xt.size, _ptr(xt), _ptr(yt),
+                                q2.shape[0], _ptr(q2), nt, _ptr(tg) if tg is not None else None, nthreads,
+                                _ptr(u))
+    if st != 0:
+        raise RuntimeError("oracle quadrature did not converge")
+    return u[0] if one else u

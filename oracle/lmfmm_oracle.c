@@ -551,6 +551,98 @@ int orc_g2t_paper(double k1, double k2, double k3, double d, double x, double y,
     return st;
 }
 
+/* --- Example 4 as printed, layer-1 source (y0 > 0): the cross-layer fields --- */
+/* Closed forms of sigma_1, sigma_2^t, sigma_2^b with numerator and denominator
+ * divided by e^{d s2} / 2 (the same functions, no overflow):
+ *   D' = (1 - E)(lambda^2 + s1 s3 - k2^2) + s2 (s1 + s3)(1 + E),  E = e^{-2 d s2}
+ *   sigma_1   = [(1 - E)(-lambda^2 + s1 s3 + k2^2) + s2 (s1 - s3)(1 + E)] / D'
+ *   sigma_2^t = 2 (lambda^2 + s2 s3 - k2^2) / D'
+ *   sigma_2^b = -2 (-lambda^2 + s2 s3 + k2^2) / D'                            */
+static void sigma_cross_safe(cx l, const orc_medium *m, cx *s1o, cx *s2o, cx sig[3])
+{
+    cx s1 = sroot(l, m->k1), s2 = sroot(l, m->k2), s3 = sroot(l, m->k3);
+    cx E = cexp(-2.0 * m->d * s2);
+    cx l2 = l * l, K2 = m->k2 * m->k2;
+    cx den = (1.0 - E) * (l2 + s1 * s3 - K2) + s2 * (s1 + s3) * (1.0 + E);
+    sig[0] = ((1.0 - E) * (-l2 + s1 * s3 + K2) + s2 * (s1 - s3) * (1.0 + E)) / den;
+    sig[1] = 2.0 * (l2 + s2 * s3 - K2) / den;
+    sig[2] = -2.0 * (-l2 + s2 * s3 + K2) / den;
+    *s1o = s1;
+    *s2o = s2;
+}
+
+/* which = bit 0: g_2^t, bit 1: g_2^b (target in layer 2), bit 2: g_1^s (target in
+ * layer 1); dy = 1 takes d/dy (target) inside the integrand */
+typedef struct {
+    orc_medium m;
+    double y, y0;
+    int which, dy;
+} cross_ctx;
+static cx F_cross(cx l, void *v)
+{
+    cross_ctx *c = v;
+    cx s1, s2, sig[3];
+    sigma_cross_safe(l, &c->m, &s1, &s2, sig);
+    cx acc = 0.0, src = cexp(-s1 * c->y0);
+    if (c->which & 1) acc += (c->dy ? s2 : 1.0) * cexp(s2 * c->y) * sig[1] / s2;
+    if (c->which & 2) acc += (c->dy ? -s2 : 1.0) * cexp(-s2 * (c->y + 2.0 * c->m.d)) * sig[2] / s2;
+    if (c->which & 4) acc += (c->dy ? -s1 : 1.0) * cexp(-s1 * c->y) * sig[0] / s1;
+    return acc * src;
+}
+/* the printed fields of Example 4 by the Sommerfeld quadrature of this file;
+ * the tail decays like e^{-lambda h}, h = y0 - y (layer 2) or y0 + y (layer 1) */
+static int cross_field(const orc_medium *m, double x, double y, double x0, double y0, int which, int dy,
+                       cx *out)
+{
+    cross_ctx c = {*m, y, y0, which, dy};
+    double X = fabs(x - x0), h = (which & 4) ? y0 + y : y0 - y;
+    double km = fmax(m->k1, fmax(m->k2, m->k3));
+    g_l1 = 1;
+    int st = sommerfeld(F_cross, &c, km, X, h >= X ? 0 : 1, h >= X ? h : X, 1, 1, out);
+    g_l1 = 0;
+    return st;
+}
+int orc_cross_field(double k1, double k2, double k3, double d, double x, double y, double x0, double y0,
+                    int which, int dy, double *out)
+{
+    orc_medium m = {k1, k2, k3, d};
+    cx r;
+    int st = cross_field(&m, x, y, x0, y0, which, dy, &r);
+    out[0] = creal(r);
+    out[1] = cimag(r);
+    return st;
+}
+
+/* Direct sum of the cross-layer operator: sources (xs, ys) in layer 1
+ * (0 < ys), targets (xt, yt) in layer 2:  u_i = sum_j q_j (g_2^t + g_2^b)(x_i, x_j).
+ * q: [nvec][ns]; u: [nvec][ntgt] at targets tgt[] (NULL = all nt). */
+int orc_cross_direct(double k1, double k2, double k3, double d, int64_t ns, const double *xs,
+                     const double *ys, int64_t nt, const double *xt, const double *yt, int nvec,
+                     const double *q, int64_t ntgt, const int64_t *tgt, int nthreads, double *u)
+{
+    orc_medium m = {k1, k2, k3, d};
+    const cx *Q = (const cx *)q;
+    cx *U = (cx *)u;
+    int64_t n = tgt ? ntgt : nt;
+    int fail = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : fail)
+    for (int64_t ii = 0; ii < n; ++ii) {
+        int64_t i = tgt ? tgt[ii] : ii;
+        cx *acc = calloc(nvec, sizeof(cx));
+        for (int64_t j = 0; j < ns; ++j) {
+            cx g;
+            fail |= cross_field(&m, xt[i], yt[i], xs[j], ys[j], 3, 0, &g);
+            for (int v = 0; v < nvec; ++v) acc[v] += g * Q[(int64_t)v * ns + j];
+        }
+        for (int v = 0; v < nvec; ++v) U[(int64_t)v * n + ii] = acc[v];
+        free(acc);
+    }
+    return fail;
+}
+
 /* --- middle-layer reflected field, any subset of the four terms --- */
 /* Derivatives of each term sigma_m(lambda; d) e^{-s2 h_m} / s2, by the chain rule:
  *   d/dy (target):  -s2 (dh_m/dy) sigma_m e^{-s2 h_m}/s2
