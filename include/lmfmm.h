@@ -317,6 +317,29 @@ lm_status lm_apply_adjoint_c64(lm_tree t, const void *v, int nvec, void *w, void
 lm_status lm_apply_grad(lm_tree t, const void *q, int nvec, void *u, void *ux, void *uy, void *stream);
 
 /*
+ * Cross-layer operator (Sec. 3, Example 4 as printed): sources in layer 1,
+ * targets in the middle layer,
+ *     u_i = sum_j q_j [g_2^t + g_2^b](x_i, x_j),
+ * g_2^t, g_2^b with the printed densities sigma_2^t, sigma_2^b, through the
+ * FMM with two wave numbers: multipoles in k1 about the source boxes, local
+ * expansions in k2 about the target boxes (Sec. 2.1), on a source and a target
+ * tree sharing one lattice of d x d roots.  FP64; the medium must have
+ * precision LM_FP64, kernel LM_KERNEL_G and transmission interfaces.
+ *   build_cross: xs, ys (device, [ns]) sources with 0 < ys < d; xt, yt
+ *     (device, [nt]) targets with -d < yt < 0.  Copies what it needs.
+ *   cross_apply: q device complex128 [nvec][ns]; u device complex128 [nvec][nt].
+ *   cross_info: sizes and the shared lattice (any output may be NULL).
+ * Errors: LM_EINVAL for bad points or arguments, LM_ENOTSUP for another
+ * medium kind or precision, LM_ENOMEM, LM_ECUDA.
+ */
+typedef struct lm_cross_s *lm_cross;
+lm_status lm_build_cross(lm_medium m, const double *xs, const double *ys, int64_t ns, const double *xt,
+                         const double *yt, int64_t nt, void *stream, lm_cross *out);
+lm_status lm_cross_apply(lm_cross c, const void *q, int nvec, void *u, void *stream);
+lm_status lm_cross_info(lm_cross c, int64_t *ns, int64_t *nt, int *R, int *depth, double *x_origin);
+void lm_destroy_cross(lm_cross c);
+
+/*
  * sync_status -- synchronise `stream` and report device-side failures of the
  * applies enqueued so far on tree t: LM_ETIMEOUT if a bounded wait inside a
  * tensor-core kernel gave up (the result of that apply is invalid), LM_OK

@@ -23,7 +23,7 @@ HAS_MIXED = True
 
 __all__ = [
     "LMError", "Medium", "Tree", "create_medium", "build_tree", "apply", "apply_adjoint", "apply_grad", "green_apply",
-    "sync_status", "Batch", "library_path", "FP64", "MIXED", "KERNEL_G", "KERNEL_DG_DD",
+    "sync_status", "Batch", "Cross", "build_cross", "library_path", "FP64", "MIXED", "KERNEL_G", "KERNEL_DG_DD",
 ]
 
 FP64, MIXED = 0, 1
@@ -77,6 +77,10 @@ def _load():
         "lm_sync_status": (I, [V, P]),
         "lm_batch_create": (I, [P, I, P, P, P, P, P]),
         "lm_batch_launch": (I, [V, P]),
+        "lm_build_cross": (I, [V, P, P, I64, P, P, I64, P, P]),
+        "lm_cross_apply": (I, [V, P, I, P, P]),
+        "lm_cross_info": (I, [V, P, P, P, P, P]),
+        "lm_destroy_cross": (None, [V]),
         "lm_batch_destroy": (None, [V]),
         "lm_destroy_tree": (None, [V]),
         "lm_destroy_medium": (None, [V]),
@@ -393,3 +397,51 @@ class Batch:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.lm_batch_destroy(self._h)
             self._h = None
+
+
+class Cross:
+    """Cross-layer operator (Example 4 as printed): layer-1 sources -> middle-layer targets."""
+
+    def __init__(self, handle, medium, ns, nt):
+        self._h = ctypes.c_void_p(handle)
+        self.medium, self.ns, self.nt = medium, ns, nt
+        R, L, x0 = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(_lib.lm_cross_info(self._h, None, None, ctypes.byref(R), ctypes.byref(L), ctypes.byref(x0)))
+        self.info = {"R": R.value, "depth": L.value, "x_origin": x0.value, "ns": ns, "nt": nt}
+
+    def apply(self, q, u=None, stream=None):
+        """u = (g_2^t + g_2^b) q: q complex128 CUDA [nvec, ns] or [ns] -> [nvec, nt] or [nt]."""
+        import torch
+
+        if not (q.is_cuda and q.dtype == torch.complex128 and q.is_contiguous()):
+            raise ValueError("Cross.apply: q must be a contiguous complex128 CUDA tensor")
+        one = q.dim() == 1
+        q2 = q.reshape(1, -1) if one else q
+        if q2.shape[-1] != self.ns:
+            raise ValueError(f"Cross.apply: q has {q2.shape[-1]} sources, the operator has {self.ns}")
+        if u is None:
+            u = torch.empty((q2.shape[0], self.nt), dtype=torch.complex128, device=q.device)
+        _check(_lib.lm_cross_apply(self._h, ctypes.c_void_p(q2.data_ptr()), q2.shape[0],
+                                   ctypes.c_void_p(u.data_ptr()), _stream(stream)))
+        return u.reshape(-1) if one else u
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.lm_destroy_cross(self._h)
+            self._h = None
+
+
+def build_cross(medium: Medium, xs, ys, xt, yt, stream=None) -> Cross:
+    """Sources (xs, ys), 0 < ys < d, in layer 1; targets (xt, yt), -d < yt < 0; float64 CUDA tensors."""
+    import torch
+
+    for a in (xs, ys, xt, yt):
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+            raise ValueError("build_cross: coordinates must be contiguous float64 CUDA tensors")
+    if xs.numel() != ys.numel() or xt.numel() != yt.numel():
+        raise ValueError("build_cross: coordinate arrays differ in length")
+    h = ctypes.c_void_p()
+    _check(_lib.lm_build_cross(medium._h, ctypes.c_void_p(xs.data_ptr()), ctypes.c_void_p(ys.data_ptr()),
+                               xs.numel(), ctypes.c_void_p(xt.data_ptr()), ctypes.c_void_p(yt.data_ptr()),
+                               xt.numel(), _stream(stream), ctypes.byref(h)))
+    return Cross(h.value, medium, xs.numel(), xt.numel())

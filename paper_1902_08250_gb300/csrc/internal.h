@@ -17,7 +17,7 @@ void lm_set_error(const char *fmt, ...);
 // Dynamic shared-memory limits are per kernel and per device, shared by every
 // tree: raise one (never lower it) so that trees built earlier, with larger
 // needs, still launch.  slot names the kernel in a small per-device cache.
-enum { LM_SMEM_NEAR_PW = 0, LM_SMEM_IMAGE_M2L = 1, LM_SMEM_SLOTS = 2 };
+enum { LM_SMEM_NEAR_PW = 0, LM_SMEM_IMAGE_M2L = 1, LM_SMEM_CROSS_M2L = 2, LM_SMEM_SLOTS = 3 };
 cudaError_t lm_raise_smem(const void *func, int slot, int bytes);
 
 #define LM_CUDA(call)                                                                       \
@@ -29,6 +29,18 @@ cudaError_t lm_raise_smem(const void *func, int slot, int bytes);
             return LM_ECUDA;                                                                \
         }                                                                                   \
     } while (0)
+
+// leaf lattice of one level: ncol columns from x0, boxes of width w, row 0 touching y = 0
+struct LeafGeom {
+    int64_t ncol;
+    double x0, w;
+};
+__device__ inline void leaf_centre(const LeafGeom &g, int64_t b, double *cx, double *cy)
+{
+    int64_t r = b / g.ncol, c = b % g.ncol;
+    *cx = g.x0 + (c + 0.5) * g.w;
+    *cy = -(r + 0.5) * g.w;
+}
 
 struct lm_medium_s {
     double k1, k2, k3, d;

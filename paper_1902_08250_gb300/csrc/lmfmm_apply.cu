@@ -30,16 +30,6 @@ __global__ void k_permute_out(const zd *us, const int64_t *perm, int64_t n, int 
     }
 }
 
-struct LeafGeom {
-    int64_t ncol;
-    double x0, w;
-};
-__device__ inline void leaf_centre(const LeafGeom &g, int64_t b, double *cx, double *cy)
-{
-    int64_t r = b / g.ncol, c = b % g.ncol;
-    *cx = g.x0 + (c + 0.5) * g.w;
-    *cy = -(r + 0.5) * g.w;
-}
 
 // ---------------------------------------------------------------------------
 // S2M (Eq. (multipole_coef)), scaled: Mhat_q = sum_j q_j Jhat_q(k r_j) e^{-i q theta_j}
