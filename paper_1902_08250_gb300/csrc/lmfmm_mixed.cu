@@ -329,49 +329,6 @@ __global__ void k_p2m32(int P, float k, float w, const float *xl, const float *y
     }
 }
 
-template <int NP>
-__global__ void k_m2m32(int64_t ncol, int64_t nbox, const zf *tabs, const zf *Mc, zf *Mp)
-{
-    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= nbox * NP * LM_MAXV) return;
-    int v = idx % LM_MAXV;
-    int p = (idx / LM_MAXV) % NP;
-    int64_t b = idx / (LM_MAXV * NP);
-    int64_t r = b / ncol, c = b % ncol, ncc = 2 * ncol;
-    zf acc = {0.f, 0.f};
-#pragma unroll
-    for (int pos = 0; pos < 4; ++pos) {
-        int dy = pos >> 1, dx = pos & 1;
-        int64_t ch = (2 * r + dy) * ncc + 2 * c + dx;
-        const zf *T = tabs + ((int64_t)pos * NP + p) * NP;
-        const zf *m = Mc + ch * NP * LM_MAXV + v;
-        zf tmp = {0.f, 0.f};
-#pragma unroll
-        for (int q = 0; q < NP; ++q) cfmaf(tmp, T[q], m[q * LM_MAXV]);
-        acc = acc + tmp;
-    }
-    Mp[idx] = acc;
-}
-
-template <int NP>
-__global__ void k_l2l32(int64_t ncol, int64_t nbox, const zf *tabs, const zf *Lp, zf *Lc)
-{
-    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= nbox * NP * LM_MAXV) return;
-    int v = idx % LM_MAXV;
-    int p = (idx / LM_MAXV) % NP;
-    int64_t b = idx / (LM_MAXV * NP);
-    int64_t r = b / ncol, c = b % ncol;
-    int pos = (int)((r & 1) * 2 + (c & 1));
-    int64_t par = (r / 2) * (ncol / 2) + c / 2;
-    const zf *T = tabs + ((int64_t)pos * NP + p) * NP;
-    const zf *m = Lp + par * NP * LM_MAXV + v;
-    zf acc = {0.f, 0.f};
-#pragma unroll
-    for (int q = 0; q < NP; ++q) cfmaf(acc, T[q], m[q * LM_MAXV]);
-    Lc[idx] = acc;
-}
-
 // Free-space M2L over the fixed 27-offset stencil of the V list (levels >= 1).
 // Boxes of one parity class share their offsets.  A block takes 16 boxes of
 // one class; its threads form (row group of 4 orders) x (box, 4 vectors)
@@ -505,18 +462,30 @@ int lm_h0_terms(double xmax)
 struct NearQuadF {
     int nseg, nray, ntail;
     const zf *seg_lam, *seg_s2, *seg_w, *tail_lam, *tail_s2, *tail_w;
+    int sym; // sigma(conj lambda) = conj(sigma(lambda)) (no impedance wall): the tail is real
 };
 // Tail of one reflected direct term (tt: m = 0, bb: m = 1) for a pair at
 // horizontal distance X and image height h: the rays lambda = c + t e^{i phi_k}
 // nearest the steepest-descent direction atan2(X, h) (Sec. 4.2, alternative
 // directions); 2 Re is taken because sigma(conj lambda) = conj(sigma(lambda)).
-__device__ zf near_tail32(const NearQuadF &q, int m, float X, float h)
+// Kept out of line: inlined into k_leaf32 it pushes the kernel to its
+// 128-register cap and slows the free-space loop by 9 % (measured).
+__device__ __noinline__ zf near_tail32(const NearQuadF &q, int m, float X, float h)
 {
     int k = q.nray > 1 ? (int)rintf(atan2f(X, h) * (q.nray - 1) * 0.63661977236758134f) : 0;
     const zf *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
     const int64_t tot = (int64_t)q.nray * q.ntail;
     const zf *tP = q.tail_w + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
     float re = 0.f, im = 0.f; // sum P Re(E) + i M Im(E)
+    if (q.sym) { // P real, M imaginary: only the real part survives
+        for (int i = 0; i < q.ntail; ++i) {
+            zf lam = tl[i], s2 = ts[i];
+            float a = expf(-lam.im * X - s2.re * h), sn, cs;
+            sincosf(lam.re * X - s2.im * h, &sn, &cs);
+            re += a * (tP[i].re * cs - tM[i].im * sn);
+        }
+        return zf{re, 0.f};
+    }
     for (int i = 0; i < q.ntail; ++i) {
         zf lam = tl[i], s2 = ts[i];
         float a = expf(-lam.im * X - s2.re * h), sn, cs;
@@ -671,48 +640,50 @@ __device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
 }
 
 // ---------------------------------------------------------------------------
-// Remaining V-list entries (level 0 and the image terms): one block per target
-// box with such entries.  Each entry's table (NP x NP) and source multipoles
-// (NP x 16 vectors) are staged in shared memory, the next entry's copies in
-// flight (double-buffered cp.async) while the current one is contracted.
-// Thread (v, g) owns vector v and rows g, g + 8, g + 16, ...; the sum over an
-// entry is formed on its own before it is added (blocked FP32 accumulation).
+// Staged contraction of one output box: acc = sum over its entries e of
+// T[slot(e)] M[src(e)], each (NP x NP) x (NP x 16 vectors).  Each entry's table
+// and source coefficients are staged in shared memory with the next entry's
+// copies in flight (double-buffered cp.async).  Thread (v, g) of 128 owns
+// vector v and rows g, g + 8, g + 16, ...; each entry's sum is formed on its
+// own before it is added (blocked FP32 accumulation).  Used by the rest-list
+// M2L, M2M (4 child entries) and L2L (1 parent entry).
 // ---------------------------------------------------------------------------
 template <int NP>
-__global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const int64_t *rstart,
-                                                    const int32_t *rsrc, const int32_t *rslot, const zf *tab,
-                                                    const zf *M, zf *Lc)
-{
-    constexpr int NR = (NP + 7) / 8;
+struct Staged {
+    static constexpr int NR = (NP + 7) / 8;
     // two buffers while they fit the 48 KB of static shared memory (all orders but p = 24)
-    constexpr int NB = 2 * (NP * NP + NP * LM_MAXV) * 8 <= 48 * 1024 ? 2 : 1;
-    __shared__ __align__(16) zf Ts[NB][NP * NP];
-    __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
-    const int64_t b = rtgt[blockIdx.x];
-    const int64_t e0 = rstart[b], e1 = rstart[b + 1];
+    static constexpr int NB = 2 * (NP * NP + NP * LM_MAXV) * 8 <= 48 * 1024 ? 2 : 1;
+};
+template <int NP, class EntryF>
+__device__ __forceinline__ void staged_contract(int ne, EntryF entry, const zf *tab, const zf *M,
+                                                zf (&acc)[Staged<NP>::NR], zf (*Ts)[NP * NP],
+                                                zf (*Ms)[NP * LM_MAXV])
+{
+    constexpr int NR = Staged<NP>::NR, NB = Staged<NP>::NB;
     const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
-    auto stage = [&](int64_t e, int buf) {
-        // table slots are NP*NP*8 bytes apart (8-byte aligned); multipole rows are 16-byte aligned
-        const zf *T = tab + (int64_t)rslot[e] * NP * NP;
+    auto stage = [&](int e, int buf) {
+        int slot;
+        int64_t src;
+        entry(e, &slot, &src);
+        // table slots are NP*NP*8 bytes apart (8-byte aligned); coefficient rows are 16-byte aligned
+        const zf *T = tab + (int64_t)slot * NP * NP;
         for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) cp_async8(&Ts[buf][i], T + i);
-        const zf *Mm = M + (int64_t)rsrc[e] * NP * LM_MAXV;
-        for (int i = threadIdx.x; i < NP * LM_MAXV / 2; i += blockDim.x)
-            cp_async16(&Ms[buf][2 * i], Mm + 2 * i);
+        const zf *Mm = M + src * NP * LM_MAXV;
+        for (int i = threadIdx.x; i < NP * LM_MAXV / 2; i += blockDim.x) cp_async16(&Ms[buf][2 * i], Mm + 2 * i);
     };
-    zf acc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = zf{0.f, 0.f};
-    if (NB == 2) {
-        stage(e0, 0);
+    if (NB == 2 && ne > 0) {
+        stage(0, 0);
         cp_commit();
     }
-    for (int64_t e = e0; e < e1; ++e) {
-        const int buf = NB == 2 ? (int)((e - e0) & 1) : 0;
+    for (int e = 0; e < ne; ++e) {
+        const int buf = NB == 2 ? (e & 1) : 0;
         if (NB == 1) {
             stage(e, 0);
             cp_commit();
             cp_wait<0>();
-        } else if (e + 1 < e1) {
+        } else if (e + 1 < ne) {
             stage(e + 1, buf ^ 1);
             cp_commit();
             cp_wait<1>();
@@ -738,6 +709,27 @@ __global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const i
         for (int r = 0; r < NR; ++r) acc[r] = acc[r] + tmp[r];
         __syncthreads(); // buffer `buf` is refilled by the stage of entry e + NB
     }
+}
+
+// Remaining V-list entries (level 0 and the image terms): one block per target
+// box with such entries; adds into L
+template <int NP>
+__global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const int64_t *rstart,
+                                                    const int32_t *rsrc, const int32_t *rslot, const zf *tab,
+                                                    const zf *M, zf *Lc)
+{
+    constexpr int NR = Staged<NP>::NR, NB = Staged<NP>::NB;
+    __shared__ __align__(16) zf Ts[NB][NP * NP];
+    __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
+    const int64_t b = rtgt[blockIdx.x];
+    const int64_t e0 = rstart[b];
+    auto entry = [&](int e, int *slot, int64_t *src) {
+        *slot = rslot[e0 + e];
+        *src = rsrc[e0 + e];
+    };
+    zf acc[NR];
+    staged_contract<NP>((int)(rstart[b + 1] - e0), entry, tab, M, acc, Ts, Ms);
+    const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
         const int p = g + 8 * r;
@@ -745,6 +737,52 @@ __global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const i
             zf *o = Lc + (b * NP + p) * LM_MAXV + v;
             *o = *o + acc[r];
         }
+    }
+}
+
+// M2M (Lemma M2M): a parent (this level) from its four children (level l + 1),
+// table slot = child position (dy, dx); writes the parent's coefficients
+template <int NP>
+__global__ void __launch_bounds__(128) k_m2m32(int64_t ncol, const zf *tabs, const zf *Mc, zf *Mp)
+{
+    constexpr int NR = Staged<NP>::NR, NB = Staged<NP>::NB;
+    __shared__ __align__(16) zf Ts[NB][NP * NP];
+    __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
+    const int64_t b = blockIdx.x, r = b / ncol, c = b % ncol, ncc = 2 * ncol;
+    auto entry = [&](int pos, int *slot, int64_t *src) {
+        *slot = pos;
+        *src = (2 * r + (pos >> 1)) * ncc + 2 * c + (pos & 1);
+    };
+    zf acc[NR];
+    staged_contract<NP>(4, entry, tabs, Mc, acc, Ts, Ms);
+    const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int p = g + 8 * k;
+        if (p < NP) Mp[(b * NP + p) * LM_MAXV + v] = acc[k];
+    }
+}
+
+// L2L (Lemma L2L): a child (this level) from its parent (level l - 1), table
+// slot = the child's position in the parent; writes the child's coefficients
+template <int NP>
+__global__ void __launch_bounds__(128) k_l2l32(int64_t ncol, const zf *tabs, const zf *Lp, zf *Lc)
+{
+    constexpr int NR = Staged<NP>::NR, NB = Staged<NP>::NB;
+    __shared__ __align__(16) zf Ts[NB][NP * NP];
+    __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
+    const int64_t b = blockIdx.x, r = b / ncol, c = b % ncol;
+    auto entry = [&](int, int *slot, int64_t *src) {
+        *slot = (int)((r & 1) * 2 + (c & 1));
+        *src = (r / 2) * (ncol / 2) + c / 2;
+    };
+    zf acc[NR];
+    staged_contract<NP>(1, entry, tabs, Lp, acc, Ts, Ms);
+    const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int p = g + 8 * k;
+        if (p < NP) Lc[(b * NP + p) * LM_MAXV + v] = acc[k];
     }
 }
 
@@ -922,15 +960,13 @@ template <int P>
 static void launch_m2m(const Level &lv, const Level &child, cudaStream_t st)
 {
     constexpr int NP = 2 * P + 1;
-    int64_t tot = lv.nbox * NP * LM_MAXV;
-    k_m2m32<NP><<<gridm(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, lv.m2m32, child.M32, lv.M32);
+    k_m2m32<NP><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.m2m32, child.M32, lv.M32);
 }
 template <int P>
 static void launch_l2l(const Level &lv, const Level &par, cudaStream_t st)
 {
     constexpr int NP = 2 * P + 1;
-    int64_t tot = lv.nbox * NP * LM_MAXV;
-    k_l2l32<NP><<<gridm(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, lv.l2l32, par.L32, lv.L32);
+    k_l2l32<NP><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
 }
 template <int P>
 static void launch_rest(const Level &lv, cudaStream_t st)
@@ -989,8 +1025,9 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const int64_t n = t->n;
     const float k = (float)t->med.k2;
-    NearQuadF nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq_seg_lam, t->nq_seg_s2,
-                 t->nq_seg_w, t->nq_tail_lam, t->nq_tail_s2, t->nq_tail_w};
+    NearQuadF nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w, t->nq_tail_lam,
+                 t->nq_tail_s2, t->nq_tail_w,
+                 t->med.opt.top_bc != LM_BC_IMPEDANCE && t->med.opt.bottom_bc != LM_BC_IMPEDANCE};
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         lm_phase_begin(t, PH_PERMUTE, st);
