@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--depth", type=int, default=-2, help="tree depth (-1 automatic; default per precision)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
-    ap.add_argument("--workload", default="strip", choices=["strip", "batched"],
-                    help="strip: the 1M-point headline apply; batched: 48 independent instances in one graph")
+    ap.add_argument("--workload", default="strip", choices=["strip", "batched", "adjoint"],
+                    help="strip: the 1M-point headline apply; batched: 48 independent instances in one graph; "
+                         "adjoint: J = sum |u - u_obs|^2 and its gradients in q, x, y, d at N = 200k (FP64)")
     return ap.parse_args()
 
 
@@ -294,12 +295,79 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args):
+    """One step = the forward apply and the backward pass of J = sum |G q - u_obs|^2 with respect
+    to the densities, the coordinates and the thickness (FP64, N = 200k, medium k = (1, 1.5, 2))."""
+    import torch
+
+    import paper_1902_08250_gb300 as lm
+    import workloads
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    n = 200_000
+    med = workloads.MEDIUM_A
+    x, y, q = workloads.uniform_strip(n, 0.0, 40.0, -0.9, -0.1, nvec=1, seed=0)
+    _, _, qref = workloads.uniform_strip(n, 0.0, 40.0, -0.9, -0.1, nvec=1, seed=1)
+    p = args.p or 20
+    t0 = time.time()
+    m = lm.create_medium(*med, p=p)
+    tree = lm.build_tree(m, torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev))
+    tree.d_tree()
+    torch.cuda.synchronize(dev)
+    setup_s = time.time() - t0
+    uobs = lm.apply(tree, torch.from_numpy(qref[0]).to(dev))
+    q0 = torch.from_numpy(q[0]).to(dev)
+
+    def step():
+        qd = q0.clone().requires_grad_(True)
+        xd = tree._x.clone().requires_grad_(True)
+        yd = tree._y.clone().requires_grad_(True)
+        dd = torch.tensor(med[3], dtype=torch.float64, requires_grad=True)
+        u = lm.green_apply(tree, qd, xd, yd, dd)
+        J = torch.sum(torch.abs(u - uobs) ** 2)
+        return torch.autograd.grad(J, (qd, xd, yd, dd))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(0)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g = step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    line = {
+        "metric": "targets/s, loss + gradients (densities, coordinates, thickness) through the FMM, FP64",
+        "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "N=200k uniform x in [0,40], y in [-0.9,-0.1]; medium k=(1,1.5,2), d=1; "
+                               "J = sum |u - u_obs|^2, u_obs from a seed-1 density",
+                   "n": n, "p": p, "depth": tree.info["depth"], "setup_s": setup_s,
+                   "calls_per_step": "apply + apply_adjoint + apply_grad (2 vectors) + dG/dd apply",
+                   "parallelism": "replicas x1"},
+        "clocks": ck,
+        "gradient_norms": {"q": float(torch.linalg.norm(g[0])), "x": float(torch.linalg.norm(g[1])),
+                           "y": float(torch.linalg.norm(g[2])), "d": float(g[3])},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     import torch
 
     rank, world, local = dist_env()

@@ -160,3 +160,40 @@ def test_gradients_match_central_differences(lm):
         up = lm.apply(t, torch.from_numpy(q + e).cuda()).cpu().numpy()
         um = lm.apply(t, torch.from_numpy(q - e).cuda()).cpu().numpy()
         assert abs(dJ(up, um, h) - gq[j].real) <= 1e-5 * (abs(gq[j].real) + 1e-3)
+
+
+def test_gradients_at_200k_match_central_differences(lm):
+    """The gradient workload at full size (N = 200k): autograd coordinate and
+    thickness gradients against central differences (h = 1e-6) of J."""
+    import torch
+
+    n = 200_000
+    x, y, q = workloads.uniform_strip(n, 0.0, 40.0, -0.9, -0.1, nvec=1, seed=0)
+    _, _, qref = workloads.uniform_strip(n, 0.0, 40.0, -0.9, -0.1, nvec=1, seed=1)
+    q, qref = q[0], qref[0]
+    p = 20
+    m = lm.create_medium(*MED, p=p)
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    uobs = lm.apply(t, torch.from_numpy(qref).cuda())
+    _, gx, gy, gd = _grads(lm, t, x, y, q, uobs, MED[3])
+    qd = torch.from_numpy(q).cuda()
+    uo = uobs.cpu().numpy()
+
+    def u_at(xx, yy, d):
+        mm = lm.create_medium(MED[0], MED[1], MED[2], d, p=p, depth=t.info["depth"])
+        tt = lm.build_tree(mm, torch.from_numpy(xx).cuda(), torch.from_numpy(yy).cuda())
+        return lm.apply(tt, qd).cpu().numpy()
+
+    def dJ(up, um, h):
+        return float(np.sum(np.real((up - um) * np.conj(up + um - 2 * uo)))) / (2 * h)
+
+    h = 1e-6
+    for j in (11, 123_456):
+        for arr, an in ((0, gx[j]), (1, gy[j])):
+            xp, yp, xm, ym = x.copy(), y.copy(), x.copy(), y.copy()
+            (xp if arr == 0 else yp)[j] += h
+            (xm if arr == 0 else ym)[j] -= h
+            fd = dJ(u_at(xp, yp, MED[3]), u_at(xm, ym, MED[3]), h)
+            assert abs(fd - an) <= 1e-5 * (abs(an) + 1e-2 * np.max(np.abs(gx))), (j, arr, fd, an)
+    fd = dJ(u_at(x, y, MED[3] + h), u_at(x, y, MED[3] - h), h)
+    assert abs(fd - gd) <= 1e-5 * abs(gd), (fd, gd)
