@@ -790,7 +790,8 @@ struct LeafChunk {
     int e, j0, cnt;
 };
 
-template <int P>
+// NV: vectors computed (4 or 16); buffers keep the 16-vector layout
+template <int P, int NV>
 __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
                                                   const float *yl, const float *y32, const int64_t *ls,
                                                   const int64_t *ustart, const int32_t *usrc, const int32_t *uterm,
@@ -830,8 +831,8 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
     }
     auto issue = [&](int c, int buf) {
         const LeafChunk ch = chunk_at(c);
-        for (int t = threadIdx.x; t < ch.cnt * (LM_MAXV / 2); t += blockDim.x) {
-            const int j = t / (LM_MAXV / 2), part = t % (LM_MAXV / 2);
+        for (int t = threadIdx.x; t < ch.cnt * (NV / 2); t += blockDim.x) {
+            const int j = t / (NV / 2), part = t % (NV / 2);
             cp_async16(&sq[buf][j * LM_MAXV + 2 * part], qs + (int64_t)(ch.j0 + j) * LM_MAXV + 2 * part);
         }
         for (int t = threadIdx.x; t < ch.cnt; t += blockDim.x) {
@@ -845,9 +846,9 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
         const int i = i0 + threadIdx.x;
         const bool act = i < hi;
         const float xi = act ? xl[i] : 0.f, yi = act ? yl[i] : 0.f, ya = act ? y32[i] : -0.5f;
-        zf acc[LM_MAXV];
+        zf acc[NV];
 #pragma unroll
-        for (int v = 0; v < LM_MAXV; ++v) acc[v] = zf{0.f, 0.f};
+        for (int v = 0; v < NV; ++v) acc[v] = zf{0.f, 0.f};
         if (nch > 0) {
             issue(0, 0);
             cp_commit();
@@ -859,13 +860,13 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
             zf z = r > 0.f ? zf{xi / r, yi / r} : zf{1.f, 0.f};
             zf zp = {1.f, 0.f};
 #pragma unroll
-            for (int v = 0; v < LM_MAXV; ++v) cfmaf(acc[v], zf{J[0], 0.f}, Lb[P * LM_MAXV + v]);
+            for (int v = 0; v < NV; ++v) cfmaf(acc[v], zf{J[0], 0.f}, Lb[P * LM_MAXV + v]);
             for (int m = 1; m <= P; ++m) {
                 zp = zp * z;
                 zf bp = J[m] * zp;
                 zf bn = ((m & 1) ? -J[m] : J[m]) * conj(zp);
 #pragma unroll
-                for (int v = 0; v < LM_MAXV; ++v) {
+                for (int v = 0; v < NV; ++v) {
                     cfmaf(acc[v], bp, Lb[(P + m) * LM_MAXV + v]);
                     cfmaf(acc[v], bn, Lb[(P - m) * LM_MAXV + v]);
                 }
@@ -886,9 +887,9 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
             const int rs = s / (int)ncol, cs = s % (int)ncol;
             const float ox = (float)(ct - cs) * w, oy = -(float)(rt - rs) * w; // centre_t - centre_s
             if (act) {
-                zf part[LM_MAXV];
+                zf part[NV];
 #pragma unroll
-                for (int v = 0; v < LM_MAXV; ++v) part[v] = zf{0.f, 0.f};
+                for (int v = 0; v < NV; ++v) part[v] = zf{0.f, 0.f};
                 if (term == 0 && free_on) {
                     const int self = i - ch.j0; // this target's slot in the chunk, if it is a source here
 #pragma unroll 2
@@ -901,7 +902,7 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
                         if (jj == self) g = zf{0.f, 0.f};
                         const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
 #pragma unroll
-                        for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {
+                        for (int v2 = 0; v2 < NV / 2; ++v2) {
                             const float4 t = qj[v2];
                             cfmaf(part[2 * v2], g, zf{t.x, t.y});
                             cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
@@ -915,7 +916,7 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
                         const zf g = near_tail32(nq, term - 1, fabsf(dx), h);
                         const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
 #pragma unroll
-                        for (int v2 = 0; v2 < LM_MAXV / 2; ++v2) {
+                        for (int v2 = 0; v2 < NV / 2; ++v2) {
                             const float4 t = qj[v2];
                             cfmaf(part[2 * v2], g, zf{t.x, t.y});
                             cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
@@ -923,14 +924,14 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
                     }
                 }
 #pragma unroll
-                for (int v = 0; v < LM_MAXV; ++v) acc[v] = acc[v] + part[v];
+                for (int v = 0; v < NV; ++v) acc[v] = acc[v] + part[v];
             }
             __syncthreads(); // buffer `buf` is refilled by the issue of chunk c + 2
         }
         if (act) {
             float4 *o = (float4 *)(us + (int64_t)i * LM_MAXV);
 #pragma unroll
-            for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
+            for (int v2 = 0; v2 < NV / 2; ++v2)
                 o[v2] = make_float4(acc[2 * v2].re, acc[2 * v2].im, acc[2 * v2 + 1].re, acc[2 * v2 + 1].im);
         }
     }
@@ -976,15 +977,22 @@ static void launch_rest(const Level &lv, cudaStream_t st)
                                                        lv.M32, lv.L32);
 }
 template <int P>
-static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st)
+static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st, int nv)
 {
     const Level &lv = t->lev[t->L];
     // largest k r of a direct pair: two leaves apart diagonally
     const int nterms = lm_h0_terms(t->med.k2 * lv.w * 2.0 * 1.4142135623730951 * 1.0001);
-    k_leaf32<P><<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
-                                                   t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart, t->usrc,
-                                                   t->uterm, nq, lv.L32, t->qs32, t->us32, nterms,
-                                                   t->med.opt.kernel == LM_KERNEL_G);
+    const int free_on = t->med.opt.kernel == LM_KERNEL_G;
+    if (nv <= 4) // the batched form's 4-vector applies: a quarter of the contraction
+        k_leaf32<P, 4><<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
+                                                         t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart,
+                                                         t->usrc, t->uterm, nq, lv.L32, t->qs32, t->us32, nterms,
+                                                         free_on);
+    else
+        k_leaf32<P, LM_MAXV><<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2,
+                                                               (float)t->med.d, t->xl32, t->yl32, t->y32,
+                                                               t->leaf_start, t->ustart, t->usrc, t->uterm, nq,
+                                                               lv.L32, t->qs32, t->us32, nterms, free_on);
 }
 
 int lm_h0_terms(double xmax);
@@ -1078,7 +1086,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
             lm_phase_end(t, PH_M2L, st, launches);
         }
         lm_phase_begin(t, PH_LEAF, st);
-        MX_DISPATCH(P, launch_leaf, t, nq, st);
+        MX_DISPATCH(P, launch_leaf, t, nq, st, nv);
         {
             const Level &lv = t->lev[L];
             const unsigned nb = (unsigned)(lv.nrow == 1 ? lv.ncol : 2 * lv.ncol);

@@ -92,3 +92,18 @@ def test_batched_instances_match_oracle(lm, oracle):
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         print(f"instance k={np.round(med[:3], 2)} d={med[3]:.2f}: rel-l2 {err:.2e}")
         assert err < 1e-6
+
+
+def test_few_vectors_match_full_width(lm):
+    """Applies of up to 4 vectors take the 4-vector leaf kernel; they agree with the
+    same vectors computed inside a 16-vector apply (same FP32 arithmetic per vector,
+    other kernels around it)."""
+    import torch
+
+    x, y, q = workloads.uniform_strip(60_000, 0.0, 8.0, -0.95, -0.05, nvec=16, seed=9)
+    m = lm.create_medium(*workloads.MEDIUM_B, p=14, precision="mixed")
+    t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
+    qd = torch.from_numpy(q).cuda()
+    full = lm.apply(t, qd).cpu().numpy()
+    few = lm.apply(t, qd[:3].contiguous()).cpu().numpy()
+    assert np.linalg.norm(few - full[:3]) <= 1e-7 * np.linalg.norm(full[:3])
