@@ -157,12 +157,20 @@ def cpu_baseline(x, y, q, medium, budget_s=12.0, ntgt=None, nsrc=None, seed=1):
     src = np.sort(rng.choice(n, size=nsrc, replace=False))
     tg = np.arange(ntgt)
     t0 = time.time()
-    oracle.direct_apply(medium, x[src], y[src], q[:1, src], targets=tg)
+    oracle.direct_apply(medium, x[src], y[src], q[:1, src], targets=tg, nthreads=cores)
     dt = time.time() - t0
     per_target_full = dt / ntgt * (n / nsrc)
+    # the same oracle on one core: one target over a tenth of the sampled sources
+    src1 = src[: max(50, nsrc // 10)]
+    t0 = time.time()
+    oracle.direct_apply(medium, x[src1], y[src1], q[:1, src1], targets=np.arange(1), nthreads=1)
+    dt1 = time.time() - t0
+    oracle.direct_apply(medium, x[src1[:2]], y[src1[:2]], q[:1, src1[:2]], targets=np.arange(1), nthreads=cores)
     return {"value": 1.0 / per_target_full, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": 1.0 / (dt1 * (n / src1.size)),
             "sample": f"{ntgt} targets x {nsrc} of {n} sources (1 density vector), "
-                      f"{dt:.1f} s wall on {cores} threads, extrapolated to full source sums"}
+                      f"{dt:.1f} s wall on {cores} threads, extrapolated to full source sums; single core: "
+                      f"1 target x {src1.size} sources, {dt1:.2f} s"}
 
 
 def run_reference(args):
