@@ -107,7 +107,24 @@ __device__ inline void m2l_table_body(SigF sigf, double km, double kmin, double 
     int nseg_half = (nflat + 2) * ORD;
     double rho = hypot(dx, h);
     double tmax = 1.5 * (2.0 * P + 60.0) / rho;
-    const int TPAN = P + 8 > 24 ? P + 8 : 24; // panels of ORD nodes resolving t^{2P} e^{-t rho}
+    // Panels of ORD nodes on [0, tmax], geometrically graded: the first is at
+    // most 1 wide (low orders vary on the scale of c near the start of the ray),
+    // later ones widen by the ratio g (high orders peak near t = 2P / rho).
+    // Uniform panels lost accuracy for small boxes, where tmax ~ 1/rho is large.
+    const int TPAN = P + 16 > 32 ? P + 16 : 32;
+    const double h0 = fmin(1.0, tmax / TPAN);
+    double g = 1.0;
+    if (h0 * TPAN < tmax) { // solve h0 (g^TPAN - 1)/(g - 1) = tmax for g > 1 by bisection
+        double lo = 1.0, hi = 2.0;
+        while (h0 * (pow(hi, TPAN) - 1.0) / (hi - 1.0) < tmax) hi *= 2.0;
+        for (int it = 0; it < 100; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (h0 * (pow(mid, TPAN) - 1.0) / (mid - 1.0) < tmax) lo = mid;
+            else hi = mid;
+        }
+        g = hi;
+    }
+    auto tpan = [&](int j) { return g == 1.0 ? h0 * j : h0 * (pow(g, j) - 1.0) / (g - 1.0); };
     int ntail = TPAN * ORD;
     int ntot = 2 * nseg_half + 2 * ntail;
     double phi = atan2(dx, h);
@@ -163,7 +180,7 @@ __device__ inline void m2l_table_body(SigF sigf, double km, double kmin, double 
                     int pan = ii / ORD, j = ii % ORD;
                     double x, gw;
                     gl_node(ORD, j, &x, &gw);
-                    double t0 = tmax * pan / TPAN, t1 = tmax * (pan + 1) / TPAN;
+                    double t0 = tpan(pan), t1 = tpan(pan + 1);
                     double t = t0 + 0.5 * (x + 1.0) * (t1 - t0), wt = 0.5 * gw * (t1 - t0);
                     if (side > 0) {
                         lam = zd{c, 0.0} + t * er;

@@ -196,3 +196,29 @@ def test_batched_graph_matches_individual_applies(lm):
         torch.cuda.synchronize()
         for u, r in zip(us, refs):
             assert np.array_equal(u.cpu().numpy(), r)
+
+
+def test_small_box_image_tables_and_deep_clustered_fmm(lm, oracle):
+    """Points within 0.01 of y = 0 in a depth-6 tree: the image M2L tables of the
+    small leaf-level boxes (h and dx of a few hundredths) against the oracle's
+    adaptive quadrature, and the whole FMM against the direct sum.  With tail
+    panels of uniform width these tables lost accuracy as the boxes shrank
+    (1.5e-9 at depth 4, 6e-5 at depth 6)."""
+    x, y, q = workloads.clustered(6000, 1, seed=3)
+    P, L = 20, 6
+    m = lm.create_medium(*MED_A, p=P, depth=L)
+    t = lm.build_tree(m, *_dev(x, y))
+    k, d = MED_A[1], MED_A[3]
+    for lev in (5, 6):
+        w = d / 2 ** lev
+        sc = np.array([(0.5 * k * w) ** abs(n) / factorial(abs(n)) for n in range(-P, P + 1)])
+        S = np.outer(sc, sc)
+        for term, dc, dr in ((1, 2, 1), (1, 3, 1), (1, 2, 2)):
+            A = t.m2l_table(lev, term, dc, dr)
+            ref = oracle.m2l_image_table(MED_A, term, dc * w, dr * w, P)
+            err = np.max(np.abs((A - ref) * S)) / np.max(np.abs(ref * S))
+            assert err < 1e-12, (lev, term, dc, dr, err)
+    sub = np.sort(np.random.default_rng(4).choice(x.size, 32, replace=False))
+    u = lm.apply(t, _dev(q)[0]).cpu().numpy()[:, sub]
+    ref = oracle.direct_apply(MED_A, x, y, q, targets=sub)
+    assert np.linalg.norm(u - ref) <= 1e-10 * np.linalg.norm(ref)
