@@ -60,7 +60,9 @@ typedef enum {
 typedef struct {
     int p;           /* expansion order: coefficients -p..p (Sec. 4.1); 0 -> 20 */
     int depth;       /* quadtree depth below the d x d roots; -1 -> automatic */
-    int leaf_target; /* automatic depth: least L >= 0 with n <= leaf_target * R * 4^L; 0 -> 48 */
+    int leaf_target; /* automatic depth: from the least L with n <= leaf_target * R * 4^L, deeper
+                        while sum(n_leaf^2)/n > 1.5 leaf_target (clustered points), keeping the
+                        leaves fewer than twice the points; 0 -> 48 */
     int precision;   /* lm_precision */
     int max_nvec;    /* largest nvec one apply processes at once (larger nvec is
                         processed in chunks); 0 -> 16 */

@@ -504,9 +504,35 @@ lm_status lm_setup_tree(lm_tree_s *t, const double *x, const double *y, cudaStre
     if (t->med.opt.depth >= 0) {
         t->L = t->med.opt.depth;
     } else {
+        // least L with n <= leaf_target R 4^L, then deeper while the points share
+        // a leaf with more than 1.5 leaf_target points on average over the points
+        // (sum n_leaf^2 / n: what the direct interactions cost), as long as the
+        // leaves stay fewer than twice the points (clustered inputs)
         int L = 0;
         while ((double)n > (double)t->med.opt.leaf_target * t->R * pow(4.0, L)) ++L;
-        t->L = L;
+        int32_t *key = nullptr, *cnt = nullptr;
+        TRY(dalloc(t, &key, n));
+        for (;; ++L) {
+            const int64_t ncol = (int64_t)t->R << L, nrow = (int64_t)1 << L, nl = ncol * nrow;
+            if (L >= 14 || nl > std::max<int64_t>(2 * n, t->R)) {
+                --L;
+                break;
+            }
+            TRY(dalloc(t, &cnt, nl));
+            LM_CUDA(cudaMemsetAsync(cnt, 0, nl * sizeof(int32_t), st));
+            k_keys<<<grid_for(n, 256), 256, 0, st>>>(x, y, n, t->x0, ldexp(d, -L), ncol, nrow, key, cnt);
+            std::vector<int32_t> hc(nl);
+            LM_CUDA(cudaMemcpyAsync(hc.data(), cnt, nl * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            LM_CUDA(cudaStreamSynchronize(st));
+            cudaFree(cnt);
+            t->bytes -= nl * sizeof(int32_t);
+            double s2 = 0.0;
+            for (int32_t c : hc) s2 += (double)c * c;
+            if (s2 / n <= 1.5 * t->med.opt.leaf_target) break;
+        }
+        cudaFree(key);
+        t->bytes -= n * sizeof(int32_t);
+        t->L = std::max(L, 0);
     }
     const int L = t->L;
     const int64_t ncol = (int64_t)t->R << L, nrow = (int64_t)1 << L;
