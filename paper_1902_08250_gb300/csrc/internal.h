@@ -17,7 +17,7 @@ void lm_set_error(const char *fmt, ...);
 // Dynamic shared-memory limits are per kernel and per device, shared by every
 // tree: raise one (never lower it) so that trees built earlier, with larger
 // needs, still launch.  slot names the kernel in a small per-device cache.
-enum { LM_SMEM_NEAR_PW = 0, LM_SMEM_IMAGE_M2L = 1, LM_SMEM_CROSS_M2L = 2, LM_SMEM_SLOTS = 3 };
+enum { LM_SMEM_NEAR_PW = 0, LM_SMEM_IMAGE_M2L = 1, LM_SMEM_CROSS_M2L = 2, LM_SMEM_NEAR_PW64 = 3, LM_SMEM_SLOTS = 4 };
 cudaError_t lm_raise_smem(const void *func, int slot, int bytes);
 
 #define LM_CUDA(call)                                                                       \
@@ -117,6 +117,7 @@ struct lm_tree_s {
     zf *qs32, *us32;           // [n][LM_MAXV]
     zf *nq_seg_lam, *nq_seg_s2, *nq_seg_w, *nq_tail_lam, *nq_tail_s2, *nq_tail_w;
     bool tc_ready; // tensor-core M2L tables built
+    bool near_pw64; // FP64 reflected near field: segment factorised per leaf (k_near_pw64)
     int *dflag;  // device error flag
     int64_t bytes;
     // phase profiling
@@ -141,6 +142,8 @@ lm_status lm_list_to_host(lm_tree_s *t, int which, int level, std::vector<int64_
 void lm_free_tree_device(lm_tree_s *t);
 // apply (lmfmm_apply.cu)
 lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);
+size_t lm_near_pw64_smem(int nseg);
+lm_status lm_near_pw64_attr(size_t bytes);
 lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, zd *uy, cudaStream_t st);
 // mixed precision (lmfmm_mixed.cu)
 lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st);

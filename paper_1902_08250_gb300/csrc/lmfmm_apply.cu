@@ -164,11 +164,11 @@ struct NearQuadD {
     int nseg, nray, ntail;
     const zd *seg_lam, *seg_s2, *seg_w, *tail_lam, *tail_s2, *tail_w;
 };
-__device__ zd near_refl64(const NearQuadD &q, int m, double X, double h)
+__device__ zd near_refl64(const NearQuadD &q, int m, double X, double h, bool seg = true)
 {
     zd acc = {0.0, 0.0};
     const zd *W = q.seg_w + (int64_t)m * q.nseg;
-    for (int i = 0; i < q.nseg; ++i) {
+    for (int i = 0; i < (seg ? q.nseg : 0); ++i) {
         zd lam = q.seg_lam[i], s2 = q.seg_s2[i];
         // e^{+i lam X - s2 h} + e^{-i lam X - s2 h}
         double er = -s2.re * h, ei = -s2.im * h;
@@ -194,7 +194,7 @@ __device__ zd near_refl64(const NearQuadD &q, int m, double X, double h)
 __global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs, const double *ys,
                          const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
                          const int32_t *uterm, NearQuadD nq, const zd *Lc, const zd *qs, int64_t n,
-                         int nvec, int free_on, zd *us)
+                         int nvec, int free_on, int pw, zd *us)
 {
     const int np = 2 * P + 1;
     const int64_t b = blockIdx.x;
@@ -235,12 +235,97 @@ __global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs
                 } else {
                     double X = fabs(xi - xs[j]);
                     double h = term == 1 ? -(yi + ys[j]) : yi + ys[j] + 2.0 * d;
-                    gij = near_refl64(nq, term - 1, X, h);
+                    gij = near_refl64(nq, term - 1, X, h, !pw); // segment added by k_near_pw64
                 }
                 for (int v = 0; v < nvec; ++v) cfma(acc[v], gij, qs[(int64_t)v * n + j]);
             }
         }
         for (int v = 0; v < nvec; ++v) us[(int64_t)v * n + i] = acc[v];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Segment part of the reflected direct terms, factorised per target leaf (FP64
+// form of the mixed path's k_near_pw32).  On the fixed segment the folded
+// integrand of a pair separates,
+//   2 cos(lambda (x_i - x_j)) e^{-s2 h_ij} = sum_{s=+-1} e^{s i lambda (x_i - x_T)} E(y_i) e^{-s i lambda (x_j - x_T)} E(y_j),
+// E(y) = e^{s2 y} (tt) or e^{-s2 (y + d)} (bb), x_T the target leaf centre:
+// phase A sums the near sources into B_{n,s}[v], phase B evaluates them at the
+// leaf's targets and adds to us.  One block per leaf of the top (and bottom) row.
+// ---------------------------------------------------------------------------
+#define PW64_SRC 64
+size_t lm_near_pw64_smem(int nseg) { return ((size_t)2 * nseg * LM_MAXV + PW64_SRC * LM_MAXV) * sizeof(zd) + 2 * PW64_SRC * sizeof(double); }
+__global__ void __launch_bounds__(256) k_near_pw64(LeafGeom g, int64_t nrow, double d, const double *xs,
+                                                   const double *ys, const int64_t *ls, const int64_t *ustart,
+                                                   const int32_t *usrc, const int32_t *uterm, NearQuadD nq,
+                                                   const zd *qs, int64_t n, int nvec, zd *us)
+{
+    extern __shared__ unsigned char smem[];
+    const int nk = 2 * nq.nseg;
+    zd *B = (zd *)smem;                              // [nk][LM_MAXV]
+    zd *SQ = B + (size_t)nk * LM_MAXV;               // [PW64_SRC][LM_MAXV]
+    double *SX = (double *)(SQ + PW64_SRC * LM_MAXV); // [PW64_SRC]
+    double *SY = SX + PW64_SRC;                      // [PW64_SRC]
+    const int64_t ncol = g.ncol;
+    const int64_t row = (nrow == 1 || blockIdx.x < ncol) ? 0 : nrow - 1;
+    const int64_t col = blockIdx.x % ncol;
+    const int64_t b = row * ncol + col;
+    const double xT = g.x0 + (col + 0.5) * g.w;
+    for (int term = 1; term <= 2; ++term) {
+        bool any = false;
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) any |= (uterm[e] == term);
+        if (!any) continue; // block-uniform
+        const int m = term - 1;
+        const zd *W = nq.seg_w + (int64_t)m * nq.nseg;
+        __syncthreads();
+        for (int k = threadIdx.x; k < nk * LM_MAXV; k += blockDim.x) B[k] = zd{0.0, 0.0};
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
+            if (uterm[e] != term) continue;
+            const int64_t s = usrc[e];
+            for (int64_t j0 = ls[s]; j0 < ls[s + 1]; j0 += PW64_SRC) {
+                const int cnt = (int)min((int64_t)PW64_SRC, ls[s + 1] - j0);
+                __syncthreads();
+                for (int t = threadIdx.x; t < cnt * nvec; t += blockDim.x) {
+                    const int jj = t % cnt, v = t / cnt;
+                    SQ[jj * LM_MAXV + v] = qs[(int64_t)v * n + j0 + jj];
+                }
+                for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                    SX[t] = xs[j0 + t] - xT;
+                    SY[t] = ys[j0 + t];
+                }
+                __syncthreads();
+                for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+                    const zd lam = nq.seg_lam[k >> 1], s2 = nq.seg_s2[k >> 1];
+                    const double sg = (k & 1) ? -1.0 : 1.0;
+                    zd part[LM_MAXV];
+                    for (int v = 0; v < nvec; ++v) part[v] = zd{0.0, 0.0};
+                    for (int t = 0; t < cnt; ++t) {
+                        const double x = SX[t], y = SY[t];
+                        zd ex = {sg * lam.im * x, -sg * lam.re * x}; // -s i lambda x
+                        ex = ex + (m == 0 ? y * s2 : -(y + d) * s2);
+                        const zd f = cexpd(ex);
+                        for (int v = 0; v < nvec; ++v) cfma(part[v], f, SQ[t * LM_MAXV + v]);
+                    }
+                    for (int v = 0; v < nvec; ++v) B[k * LM_MAXV + v] = B[k * LM_MAXV + v] + part[v];
+                }
+            }
+        }
+        __syncthreads();
+        const int64_t lo = ls[b], cntT = ls[b + 1] - lo;
+        for (int64_t t = threadIdx.x; t < cntT * nvec; t += blockDim.x) {
+            const int64_t i = lo + t % cntT;
+            const int v = (int)(t / cntT);
+            const double x = xs[i] - xT, y = ys[i];
+            zd acc = {0.0, 0.0};
+            for (int k = 0; k < nk; ++k) {
+                const zd lam = nq.seg_lam[k >> 1], s2 = nq.seg_s2[k >> 1];
+                const double sg = (k & 1) ? -1.0 : 1.0;
+                zd ex = {-sg * lam.im * x, sg * lam.re * x}; // s i lambda x
+                ex = ex + (m == 0 ? y * s2 : -(y + d) * s2);
+                cfma(acc, cexpd(ex) * W[k >> 1], B[k * LM_MAXV + v]);
+            }
+            us[(int64_t)v * n + i] = us[(int64_t)v * n + i] + acc;
+        }
     }
 }
 
@@ -456,15 +541,28 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
         {
             Level &lv = t->lev[L];
             LeafGeom g{lv.ncol, t->x0, lv.w};
+            const int pw = t->near_pw64 ? 1 : 0;
             k_leaf64<<<(unsigned)lv.nbox, 64, 0, st>>>(g, P, k, t->med.d, t->xs, t->ys, t->leaf_start,
                                                        t->ustart, t->usrc, t->uterm, nq, lv.Lc, t->qs, n,
-                                                       nv, free_on, t->us);
+                                                       nv, free_on, pw, t->us);
+            if (pw)
+                k_near_pw64<<<(unsigned)(lv.nrow == 1 ? lv.ncol : 2 * lv.ncol), 256,
+                              lm_near_pw64_smem(t->nq.nseg), st>>>(g, lv.nrow, t->med.d, t->xs, t->ys,
+                                                                   t->leaf_start, t->ustart, t->usrc, t->uterm,
+                                                                   nq, t->qs, n, nv, t->us);
         }
-        lm_phase_end(t, PH_LEAF, st, 1);
+        lm_phase_end(t, PH_LEAF, st, t->near_pw64 ? 2 : 1);
         lm_phase_begin(t, PH_PERMUTE, st);
         k_permute_out<<<gridn(n, 256), 256, 0, st>>>(t->us, t->perm, n, nv, adjoint, u + (int64_t)v0 * n);
         lm_phase_end(t, PH_PERMUTE, st, 1);
         LM_CUDA(cudaGetLastError());
     }
+    return LM_OK;
+}
+
+// dynamic shared-memory limit of k_near_pw64 (raised, never lowered: shared by all trees)
+lm_status lm_near_pw64_attr(size_t bytes)
+{
+    LM_CUDA(lm_raise_smem((const void *)k_near_pw64, LM_SMEM_NEAR_PW64, (int)bytes));
     return LM_OK;
 }

@@ -759,6 +759,13 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
                                                          q.seg_s2, q.seg_w, q.nseg);
         k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2,
                                                       q.tail_w);
+        // FP64: factorise the segment per leaf when its coefficients fit in shared memory
+        const size_t pw = lm_near_pw64_smem(q.nseg);
+        t->near_pw64 = false;
+        if (t->precision == LM_FP64 && pw <= 200 * 1024) {
+            TRY(lm_near_pw64_attr(pw));
+            t->near_pw64 = true;
+        }
     }
     // tree-order scratch for densities and potentials
     TRY(dalloc(t, &t->qs, (size_t)LM_MAXV * t->n));
