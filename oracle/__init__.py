@@ -79,6 +79,8 @@ def _declare(L):
         "orc_green_free_grad": (None, [_D, _D, _D, _P]),
         "orc_tree_build": (_I, [_I64, _P, _P, _D, _I, _P, _P, _P]),
         "orc_vlist": (_I64, [_I, _I, _I64, _P]),
+        "orc_adaptive_tree": (_I64, [_I64, _P, _P, _D, _I, _I, _I64, _P, _P, _P, _P]),
+        "orc_adaptive_lists": (_I64, [_I64, _P, _P, _D, _I, _I, _I, _I64, _P]),
         "orc_ulist": (_I64, [_I, _I, _I64, _P]),
         "orc_m2l_image_table": (_I, [_D, _D, _D, _D, _I, _D, _D, _I, _P]),
         "orc_m2l_free_table": (None, [_D, _D, _D, _I, _P]),
@@ -415,3 +417,33 @@ def cross_direct(medium, xs, ys, xt, yt, q, targets=None, nthreads=0):
     if st != 0:
         raise RuntimeError("oracle quadrature did not converge")
     return u[0] if one else u
+
+
+# --- adaptive tree (Algorithm 1 step 1) ------------------------------------------
+def adaptive_tree(x, y, d, s, Lmax):
+    """Adaptive strip-forest tree: a box with more than s points below level Lmax is split.
+    Returns (hdr = (x_origin, R), boxes [nbox, 4] = (level, col, row, leaf), perm, pstart)."""
+    x = _c(x, np.float64)
+    y = _c(y, np.float64)
+    cap = 1024
+    while True:
+        hdr = np.zeros(2)
+        boxes = np.zeros((cap, 4), np.int64)
+        perm = np.zeros(x.size, np.int64)
+        pstart = np.zeros(cap + 1, np.int64)
+        nb = lib().orc_adaptive_tree(x.size, _ptr(x), _ptr(y), d, s, Lmax, cap, _ptr(hdr), _ptr(boxes),
+                                     _ptr(perm), _ptr(pstart))
+        if nb >= 0:
+            return (hdr[0], int(hdr[1])), boxes[:nb].copy(), perm, pstart[:nb + 1].copy()
+        cap *= 4
+
+
+def adaptive_lists(x, y, d, s, Lmax, which):
+    """V (which = 0) or U (which = 1) rows (target box, term, source box) of the adaptive tree,
+    by dual traversal from every pair of roots; sorted."""
+    x = _c(x, np.float64)
+    y = _c(y, np.float64)
+    cnt = lib().orc_adaptive_lists(x.size, _ptr(x), _ptr(y), d, s, Lmax, which, 0, None)
+    out = np.zeros((max(cnt, 1), 3), np.int64)
+    lib().orc_adaptive_lists(x.size, _ptr(x), _ptr(y), d, s, Lmax, which, cnt, _ptr(out))
+    return out[:cnt]

@@ -1013,6 +1013,252 @@ int64_t orc_ulist(int R, int L, int64_t cap, int64_t *out)
 }
 
 /* ------------------------------------------------------------------------- */
+/* Adaptive tree (Algorithm 1, step 1: "an adaptive hierarchical tree").     */
+/* Reading: the strip forest of d x d roots as for the uniform tree; a box    */
+/* (level l, column c, row r) holding more than s points with l < Lmax is     */
+/* split into its four children (all four exist, empty or not).  A point's   */
+/* cell at level l is (floor((x - x0)/w_l), floor(-y/w_l)), clamped, as       */
+/* before.  Boxes are numbered level by level and, within a level, by         */
+/* r * ncol_l + c.  Points are ordered by the number of their leaf, then by   */
+/* input index; boxes that are not leaves own no points.                      */
+/*                                                                            */
+/* Lists by dual traversal, per term m (0 free, 1 tt, 2 bb, 3 tb, 4 bt), from */
+/* every pair of roots.  A target box t and the image of a source box s (its  */
+/* row mapped as for the uniform lists, at the source's level) are well       */
+/* separated when the larger of |dx|, |dy| between their centres is at least  */
+/* w_t + w_s: then (t, m, s) is a V entry (M2L).  Otherwise two leaves give a */
+/* U entry (direct); otherwise the larger box is split -- never a leaf; both  */
+/* when the levels are equal -- and the traversal goes on with the child      */
+/* pairs.  On a uniform tree this is exactly the uniform V and U lists.       */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int level;
+    int64_t col, row, npts;
+    int leaf;
+} orc_abox;
+
+typedef struct {
+    orc_grid g; /* d, x0, R */
+    int Lmax;
+    int64_t nbox, *lev_start; /* boxes of level l: [lev_start[l], lev_start[l + 1]) */
+    orc_abox *box;
+} orc_atree;
+
+static int64_t a_key(const orc_atree *T, int l, int64_t c, int64_t r) { return r * ((int64_t)T->g.R << l) + c; }
+
+/* id of box (l, c, r), or -1 */
+static int64_t a_find(const orc_atree *T, int l, int64_t c, int64_t r)
+{
+    if (l > T->Lmax) return -1;
+    int64_t a = T->lev_start[l], b = T->lev_start[l + 1] - 1, key = a_key(T, l, c, r);
+    while (a <= b) {
+        int64_t mid = (a + b) / 2, k = a_key(T, l, T->box[mid].col, T->box[mid].row);
+        if (k == key) return mid;
+        if (k < key) a = mid + 1;
+        else b = mid - 1;
+    }
+    return -1;
+}
+
+static void a_cell(const orc_grid *g, int l, double x, double y, int64_t *c, int64_t *r)
+{
+    double w = ldexp(g->d, -l);
+    int64_t ncol = (int64_t)g->R << l, nrow = (int64_t)1 << l;
+    *c = (int64_t)floor((x - g->x0) / w);
+    *r = (int64_t)floor(-y / w);
+    if (*c < 0) *c = 0;
+    if (*c > ncol - 1) *c = ncol - 1;
+    if (*r < 0) *r = 0;
+    if (*r > nrow - 1) *r = nrow - 1;
+}
+
+static void atree_build(int64_t n, const double *x, const double *y, double d, int s, int Lmax, orc_atree *T)
+{
+    make_grid(n, x, d, 0, &T->g);
+    T->Lmax = Lmax;
+    int64_t cap = 64 + 8 * (int64_t)T->g.R, nb = 0;
+    T->box = malloc(sizeof(orc_abox) * cap);
+    T->lev_start = calloc(Lmax + 2, sizeof(int64_t));
+    for (int64_t c = 0; c < T->g.R; ++c) {
+        orc_abox b = {0, c, 0, 0, 1};
+        T->box[nb++] = b;
+    }
+    T->lev_start[1] = nb;
+    for (int l = 0; l <= Lmax; ++l) {
+        const int64_t lo = T->lev_start[l], hi = T->lev_start[l + 1];
+        for (int64_t i = 0; i < n; ++i) { /* count each point in its box of this level, if present */
+            int64_t c, r;
+            a_cell(&T->g, l, x[i], y[i], &c, &r);
+            int64_t b = a_find(T, l, c, r);
+            if (b >= 0) T->box[b].npts++;
+        }
+        if (l == Lmax) break;
+        int64_t first = nb;
+        for (int64_t b = lo; b < hi; ++b) {
+            if (T->box[b].npts <= s) continue;
+            T->box[b].leaf = 0;
+            for (int k = 0; k < 4; ++k) {
+                if (nb == cap) {
+                    cap *= 2;
+                    T->box = realloc(T->box, sizeof(orc_abox) * cap);
+                }
+                orc_abox ch = {l + 1, 2 * T->box[b].col + (k & 1), 2 * T->box[b].row + (k >> 1), 0, 1};
+                T->box[nb++] = ch;
+            }
+        }
+        const int64_t m = nb - first, ncol1 = (int64_t)T->g.R << (l + 1);
+        kv *ord = malloc(sizeof(kv) * (m ? m : 1));
+        orc_abox *tmp = malloc(sizeof(orc_abox) * (m ? m : 1));
+        for (int64_t i = 0; i < m; ++i) {
+            ord[i].key = T->box[first + i].row * ncol1 + T->box[first + i].col;
+            ord[i].idx = first + i;
+        }
+        qsort(ord, m, sizeof(kv), kv_cmp);
+        for (int64_t i = 0; i < m; ++i) tmp[i] = T->box[ord[i].idx];
+        memcpy(T->box + first, tmp, sizeof(orc_abox) * m);
+        free(tmp);
+        free(ord);
+        T->lev_start[l + 2] = nb;
+    }
+    T->nbox = nb;
+}
+
+/* separation of target t and the image of source s under term m, in units of half
+ * the finest width of the pair: centres (2c + 1) S, S = 2^(lmax - l), image rows */
+static int a_separated(const orc_atree *T, int64_t t, int64_t s, int m)
+{
+    const orc_abox *A = &T->box[t], *B = &T->box[s];
+    int lm = A->level > B->level ? A->level : B->level;
+    int64_t SA = (int64_t)1 << (lm - A->level), SB = (int64_t)1 << (lm - B->level);
+    int64_t ri = img_row(m, B->row, (int64_t)1 << B->level);
+    int64_t X2 = llabs((2 * A->col + 1) * SA - (2 * B->col + 1) * SB);
+    int64_t Y2 = llabs((2 * A->row + 1) * SA - (2 * ri + 1) * SB);
+    int64_t M2 = X2 > Y2 ? X2 : Y2;
+    return M2 >= 2 * (SA + SB);
+}
+
+typedef struct {
+    int64_t *rows, cnt, cap;
+} a_list;
+static void a_push(a_list *L, int64_t t, int m, int64_t s)
+{
+    if (L->cnt == L->cap) {
+        L->cap = L->cap ? 2 * L->cap : 1024;
+        L->rows = realloc(L->rows, sizeof(int64_t) * 3 * L->cap);
+    }
+    L->rows[3 * L->cnt] = t;
+    L->rows[3 * L->cnt + 1] = m;
+    L->rows[3 * L->cnt + 2] = s;
+    L->cnt++;
+}
+static int64_t a_child(const orc_atree *T, int64_t b, int k)
+{
+    const orc_abox *B = &T->box[b];
+    return a_find(T, B->level + 1, 2 * B->col + (k & 1), 2 * B->row + (k >> 1));
+}
+static void a_visit(const orc_atree *T, int64_t t, int64_t s, int m, a_list *V, a_list *U)
+{
+    if (a_separated(T, t, s, m)) {
+        a_push(V, t, m, s);
+        return;
+    }
+    const orc_abox *A = &T->box[t], *B = &T->box[s];
+    if (A->leaf && B->leaf) {
+        a_push(U, t, m, s);
+        return;
+    }
+    if (A->leaf || (!B->leaf && B->level < A->level)) {
+        for (int k = 0; k < 4; ++k) a_visit(T, t, a_child(T, s, k), m, V, U);
+    } else if (B->leaf || A->level < B->level) {
+        for (int k = 0; k < 4; ++k) a_visit(T, a_child(T, t, k), s, m, V, U);
+    } else {
+        for (int k = 0; k < 4; ++k)
+            for (int j = 0; j < 4; ++j) a_visit(T, a_child(T, t, k), a_child(T, s, j), m, V, U);
+    }
+}
+typedef struct {
+    int64_t a, b, c;
+} i3;
+static int i3_cmp(const void *p, const void *q)
+{
+    const i3 *u = p, *v = q;
+    if (u->a != v->a) return u->a < v->a ? -1 : 1;
+    if (u->b != v->b) return u->b < v->b ? -1 : 1;
+    return u->c < v->c ? -1 : (u->c > v->c);
+}
+static void a_sort(a_list *L)
+{
+    qsort(L->rows, L->cnt, sizeof(i3), i3_cmp);
+}
+
+/* Tree: returns the box count (or -1 if cap is too small); boxes[nbox][4] =
+ * (level, col, row, leaf); hdr = {x_origin, R}; perm[n] (position -> input
+ * index); pstart[nbox + 1] (points of box b: [pstart[b], pstart[b + 1])). */
+int64_t orc_adaptive_tree(int64_t n, const double *x, const double *y, double d, int s, int Lmax, int64_t cap,
+                          double *hdr, int64_t *boxes, int64_t *perm, int64_t *pstart)
+{
+    orc_atree T;
+    atree_build(n, x, y, d, s, Lmax, &T);
+    int64_t nb = T.nbox;
+    if (nb <= cap) {
+        for (int64_t b = 0; b < nb; ++b) {
+            boxes[4 * b] = T.box[b].level;
+            boxes[4 * b + 1] = T.box[b].col;
+            boxes[4 * b + 2] = T.box[b].row;
+            boxes[4 * b + 3] = T.box[b].leaf;
+        }
+        /* leaf of each point: descend from its root */
+        kv *a = malloc(sizeof(kv) * (n ? n : 1));
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t b = -1;
+            for (int l = 0; l <= Lmax; ++l) {
+                int64_t c, r;
+                a_cell(&T.g, l, x[i], y[i], &c, &r);
+                b = a_find(&T, l, c, r);
+                if (T.box[b].leaf) break;
+            }
+            a[i].key = b;
+            a[i].idx = i;
+        }
+        qsort(a, n, sizeof(kv), kv_cmp);
+        for (int64_t b = 0; b <= nb; ++b) pstart[b] = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            perm[i] = a[i].idx;
+            pstart[a[i].key + 1]++;
+        }
+        for (int64_t b = 0; b < nb; ++b) pstart[b + 1] += pstart[b];
+        free(a);
+        hdr[0] = T.g.x0;
+        hdr[1] = T.g.R;
+    }
+    free(T.box);
+    free(T.lev_start);
+    return nb <= cap ? nb : -1;
+}
+
+/* Lists: which = 0 (V) or 1 (U); rows (target, term, source) sorted; returns the
+ * count (rows written only if count <= cap). */
+int64_t orc_adaptive_lists(int64_t n, const double *x, const double *y, double d, int s, int Lmax, int which,
+                           int64_t cap, int64_t *out)
+{
+    orc_atree T;
+    atree_build(n, x, y, d, s, Lmax, &T);
+    a_list V = {0, 0, 0}, U = {0, 0, 0};
+    for (int64_t t = 0; t < T.g.R; ++t)
+        for (int64_t sb = 0; sb < T.g.R; ++sb)
+            for (int m = 0; m < 5; ++m) a_visit(&T, t, sb, m, &V, &U);
+    a_list *L = which ? &U : &V;
+    a_sort(L);
+    int64_t cnt = L->cnt;
+    if (cnt <= cap) memcpy(out, L->rows, sizeof(int64_t) * 3 * cnt);
+    free(V.rows);
+    free(U.rows);
+    free(T.box);
+    free(T.lev_start);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Expansions (Sec. 2.1).  Orders -p..p, stored at index p + P0 (P0 = p).     */
 /*   S2M:  M_q = sum_j q_j J_q(k r_j) e^{-i q theta_j}        (Eq. (multipole_coef))
  *   L2T:  u(x) = sum_p L_p J_p(k r) e^{i p theta}            (Eq. (local))
