@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--n", type=int, default=N_POINTS)
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--depth", type=int, default=-2, help="tree depth (-1 automatic; default per precision)")
+    ap.add_argument("--tree", default="adaptive", choices=["adaptive", "uniform"],
+                    help="clustered workload: adaptive tree (boxes refined where the points are) or uniform depth")
+    ap.add_argument("--leaf-target", type=int, default=0, help="points per leaf (0: library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--workload", default="strip", choices=["strip", "batched", "adjoint", "clustered"],
@@ -388,8 +391,9 @@ def run_adjoint(args):
 
 def run_clustered(args):
     """N = 100k: half the points uniform in the middle layer, half within 0.01 of y = 0 (x spread
-    10), one complex128 vector, FP64 at p = 24 with the automatic (occupancy-driven) depth; the
-    error is measured against the oracle's direct sum on 16 targets x all sources."""
+    10), one complex128 vector, FP64 at p = 24, on the adaptive tree (--tree adaptive, default) or
+    the uniform tree of automatic (occupancy-driven) depth; the error is measured against the
+    oracle's direct sum on 16 targets x all sources."""
     import torch
 
     import oracle
@@ -404,7 +408,12 @@ def run_clustered(args):
     x, y, q = workloads.clustered(n, 1, seed=0)
     p = args.p or 24  # the order that meets 1e-10 on this workload (p = 20 gives 1.4e-10)
     t0 = time.time()
-    m = lm.create_medium(*med, p=p)
+    opt = dict(p=p, adaptive=args.tree == "adaptive")
+    if args.leaf_target > 0:
+        opt["leaf_target"] = args.leaf_target
+    if args.depth >= -1:
+        opt["depth"] = args.depth
+    m = lm.create_medium(*med, **opt)
     tree = lm.build_tree(m, torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev))
     torch.cuda.synchronize(dev)
     setup_s = time.time() - t0
@@ -424,6 +433,17 @@ def run_clustered(args):
     torch.cuda.synchronize(dev)
     ck = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    # phase times from two further applies with per-phase events (outside the timed region)
+    lib = lm._lib
+    lib.lm_profile_begin(tree._h, 2)
+    for _ in range(2):
+        lm.apply(tree, qd, ud)
+    torch.cuda.synchronize(dev)
+    ph_ms = (ctypes.c_double * len(PHASES))()
+    ph_n = (ctypes.c_int64 * len(PHASES))()
+    napp = ctypes.c_int()
+    lib.lm_profile_end(tree._h, ph_ms, ph_n, len(PHASES), ctypes.byref(napp))
+    phase_ms = {PHASES[i]: ph_ms[i] / max(1, napp.value) for i in range(len(PHASES))}
     sub = np.sort(np.random.default_rng(0).choice(n, 16, replace=False))
     err = None
     if not args.no_fp64_compare:
@@ -436,8 +456,11 @@ def run_clustered(args):
         "data": "synthetic",
         "config": {"workload": "N=100k: 50k x in [0,10], y in [-0.9,-0.1]; 50k x in [0,10], y in [-0.01,0); "
                                "medium k=(1,1.5,2), d=1; 1 complex N(0,1) vector",
-                   "n": n, "p": p, "depth": tree.info["depth"], "setup_s": setup_s, "parallelism": "replicas x1"},
+                   "n": n, "p": p, "tree": args.tree, "depth": tree.info["depth"], "nbox": tree.info["nbox"],
+                   "nleaf": tree.info["nleaf"], "leaf_target": m.options["leaf_target"], "setup_s": setup_s,
+                   "parallelism": "replicas x1"},
         "clocks": ck,
+        "phase_ms": phase_ms,
         "rel_err_vs_oracle_direct": err,
         "rel_err_sample": "16 random targets x all 100k sources (oracle direct sum, FP64 adaptive quadrature)",
     }

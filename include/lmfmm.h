@@ -77,6 +77,11 @@ typedef struct {
     int bottom_bc;   /* lm_boundary of the interface y = -d; 0 -> LM_BC_TRANSMISSION (layer 3, k3) */
     double top_alpha;    /* LM_BC_IMPEDANCE at y = 0: alpha (real, finite) */
     double bottom_alpha; /* LM_BC_IMPEDANCE at y = -d: alpha */
+    int adaptive;    /* 1: adaptive tree (Algorithm 1, step 1) -- a box holding more than
+                        leaf_target points is split into its four children while its level is
+                        below depth (-1 -> 14); boxes of different levels interact through
+                        lists built by a dual traversal (see lm_build_tree).  LM_FP64 only
+                        (LM_ENOTSUP otherwise).  0 (default): uniform depth. */
 } lm_options;
 
 /* Other media (Sec. 3, Examples 2 and 3): an interface of the middle layer
@@ -114,6 +119,9 @@ typedef struct {
     int precision;    /* lm_precision */
     int max_nvec;
     int64_t device_bytes; /* device memory held by the tree handle */
+    int64_t nbox;     /* boxes of every level (uniform: sum over l of R 4^l) */
+    int adaptive;     /* 1 for an adaptive tree: depth is then its deepest level and
+                         nleaf its number of leaves */
 } lm_tree_info;
 
 /* Fill *opt with the defaults listed above. LM_EINVAL if opt is NULL. */
@@ -142,6 +150,18 @@ lm_status lm_create_medium(double k1, double k2, double k3, double d, const lm_o
  *         during the call only.
  *   n >= 1.
  * Synchronises `stream` (host needs the x extent and a validity flag).
+ *
+ * With opt.adaptive = 1 the roots are refined only where the points are: a box
+ * (level l, column c, row r) with more than leaf_target points and l < depth
+ * has all four children; boxes are numbered level by level, within a level by
+ * r * (R 2^l) + c; points are ordered by leaf number, then input index.  The
+ * lists come from a dual traversal per term from every pair of roots: a target
+ * box and the image of a source box (row mapped as for the uniform lists, at
+ * the source's level) with max(|dx|, |dy|) >= w_t + w_s between centres are a
+ * V entry (M2L between their levels); two leaves that are not are a U entry;
+ * otherwise the larger box is split (both when the levels are equal).  This
+ * tree and its lists are built on the host (the points are copied back once);
+ * tables, lists and expansions are on the device.
  * Errors: LM_EINVAL if a point is non-finite or not strictly inside
  * -d < y < 0; LM_ENOMEM; LM_ENOTSUP if a leaf holds more than 8192 points;
  * LM_ECUDA.
@@ -173,7 +193,9 @@ lm_status lm_get_tree_info(lm_tree t, lm_tree_info *info);
 /*
  * tree_export -- copy the tree order to host memory (synchronises `stream`).
  *   perm: host int64[n], tree position -> input index (may be NULL).
- *   leaf_start: host int64[nleaf + 1], first tree position of each leaf (may be NULL).
+ *   leaf_start: host int64[nleaf + 1], first tree position of each leaf (may be NULL);
+ *               adaptive trees: int64[nbox + 1], the points of box b are tree positions
+ *               leaf_start[b] .. leaf_start[b + 1] - 1 (none for a box that is not a leaf).
  */
 lm_status lm_tree_export(lm_tree t, int64_t *perm, int64_t *leaf_start, void *stream);
 
@@ -184,6 +206,8 @@ lm_status lm_tree_export(lm_tree t, int64_t *perm, int64_t *leaf_start, void *st
  * then term, then source (Algorithm 1: the interaction list of step 3 and
  * the direct-interaction list of step 4).
  *   which: 0 = V list of `level` (0..L), 1 = U list (leaf level; level ignored).
+ *   Adaptive trees: box ids are those of lm_box_export, which = 0 gives the V
+ *   list of every level at once and `level` is ignored.
  *   out: host int64[3 * cap]; *count receives the full length (rows written:
  *   min(cap, *count)).  Synchronises `stream`.
  */
@@ -191,12 +215,22 @@ lm_status lm_list_export(lm_tree t, int which, int level, int64_t *out, int64_t 
                          int64_t *count, void *stream);
 
 /*
+ * box_export -- the boxes of a tree as rows (level, column, row, leaf) in box-id
+ * order: level by level, within a level by row * (R 2^l) + column (the uniform
+ * tree lists every box of every level; leaf = 1 at level L).
+ *   boxes: host int64[4 * cap]; *count receives the number of boxes (rows
+ *   written: min(cap, *count)).  Host-only; no device work.
+ */
+lm_status lm_box_export(lm_tree t, int64_t *boxes, int64_t cap, int64_t *count);
+
+/*
  * m2l_table_export -- copy one M2L translation matrix A_pq (Lemma M2L for
  * term 1..4, the free-space translation for term 0), unscaled, p, q in
  * -P..P, to host memory as complex128 [(2P+1)][(2P+1)] (row p, column q).
  * The class is given by level, term, column offset dc = target col - source
  * col and row offset dr = target row - image row (image rows as in
- * lm_list_export's lists).  LM_EINVAL if that class is not in any list.
+ * lm_list_export's lists).  LM_EINVAL if that class is not in any list;
+ * LM_ENOTSUP for an adaptive tree.
  * Synchronises `stream`.
  */
 lm_status lm_m2l_table_export(lm_tree t, int level, int term, int dc, int dr, double *out,

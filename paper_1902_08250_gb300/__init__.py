@@ -43,13 +43,15 @@ class _Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("max_nvec", ctypes.c_int), ("seg_order", ctypes.c_int),
                 ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int), ("tensor_m2l", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("top_bc", ctypes.c_int),
-                ("bottom_bc", ctypes.c_int), ("top_alpha", ctypes.c_double), ("bottom_alpha", ctypes.c_double)]
+                ("bottom_bc", ctypes.c_int), ("top_alpha", ctypes.c_double), ("bottom_alpha", ctypes.c_double),
+                ("adaptive", ctypes.c_int)]
 
 
 class _TreeInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("R", ctypes.c_int), ("depth", ctypes.c_int), ("p", ctypes.c_int),
                 ("x_origin", ctypes.c_double), ("nleaf", ctypes.c_int64), ("precision", ctypes.c_int),
-                ("max_nvec", ctypes.c_int), ("device_bytes", ctypes.c_int64)]
+                ("max_nvec", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("nbox", ctypes.c_int64),
+                ("adaptive", ctypes.c_int)]
 
 
 def _load():
@@ -69,6 +71,7 @@ def _load():
         "lm_get_tree_info": (I, [V, P]),
         "lm_tree_export": (I, [V, P, P, P]),
         "lm_list_export": (I, [V, I, I, P, I64, P, P]),
+        "lm_box_export": (I, [V, P, I64, P]),
         "lm_m2l_table_export": (I, [V, I, I, I, I, P, P]),
         "lm_profile_begin": (I, [V, I]),
         "lm_profile_end": (I, [V, P, P, I, P]),
@@ -131,19 +134,22 @@ class Medium:
 def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
                   seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1, kernel=KERNEL_G,
                   autotune=0, top_bc="transmission", top_alpha=0.0, bottom_bc="transmission",
-                  bottom_alpha=0.0) -> Medium:
+                  bottom_alpha=0.0, adaptive=False) -> Medium:
     """kernel = KERNEL_G applies G; KERNEL_DG_DD applies dG/dd at fixed points.
     autotune = 1 tunes the M2L tile shapes of mixed-precision trees at build time.
     top_bc / bottom_bc: "transmission" (to the outer layer, k1 / k3), or a wall --
     "dirichlet", "neumann", "impedance" (du/dn - i k2 alpha u = 0, alpha = top_alpha /
-    bottom_alpha)."""
+    bottom_alpha).
+    adaptive = True builds adaptive trees (FP64): a box with more than leaf_target points is
+    split while its level is below depth (-1 -> 14)."""
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
     for b in (top_bc, bottom_bc):
         if b not in BC:
             raise ValueError(f"create_medium: unknown boundary kind {b!r} (one of {sorted(BC)})")
     o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays, tensor_m2l,
-                 kernel, autotune, BC[top_bc], BC[bottom_bc], float(top_alpha), float(bottom_alpha))
+                 kernel, autotune, BC[top_bc], BC[bottom_bc], float(top_alpha), float(bottom_alpha),
+                 int(bool(adaptive)))
     h = ctypes.c_void_p()
     _check(_lib.lm_create_medium(k1, k2, k3, d, ctypes.byref(o), ctypes.byref(h)))
     return Medium(h.value, k1, k2, k3, d, dict(p=p, depth=depth, leaf_target=leaf_target,
@@ -151,7 +157,7 @@ def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP
                                               tail_order=tail_order, tail_rays=tail_rays,
                                               tensor_m2l=tensor_m2l, kernel=kernel, autotune=autotune,
                                               top_bc=top_bc, top_alpha=top_alpha, bottom_bc=bottom_bc,
-                                              bottom_alpha=bottom_alpha))
+                                              bottom_alpha=bottom_alpha, adaptive=bool(adaptive)))
 
 
 class Tree:
@@ -195,14 +201,26 @@ class Tree:
         return {f: getattr(i, f) for f, _ in _TreeInfo._fields_}
 
     def export(self, stream=None):
-        """(perm, leaf_start) as numpy int64 arrays (tree order)."""
+        """(perm, leaf_start) as numpy int64 arrays (tree order); for an adaptive tree
+        leaf_start has one entry per box (boxes that are not leaves own no points)."""
         import numpy as np
 
+        info = self.info
         perm = np.zeros(self.n, np.int64)
-        ls = np.zeros(self.info["nleaf"] + 1, np.int64)
+        ls = np.zeros((info["nbox"] if info["adaptive"] else info["nleaf"]) + 1, np.int64)
         _check(_lib.lm_tree_export(self._h, perm.ctypes.data_as(ctypes.c_void_p),
                                    ls.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
         return perm, ls
+
+    def boxes(self):
+        """Rows (level, column, row, leaf) of every box, in box-id order."""
+        import numpy as np
+
+        cnt = ctypes.c_int64()
+        _check(_lib.lm_box_export(self._h, None, 0, ctypes.byref(cnt)))
+        out = np.zeros((max(cnt.value, 1), 4), np.int64)
+        _check(_lib.lm_box_export(self._h, out.ctypes.data_as(ctypes.c_void_p), cnt.value, ctypes.byref(cnt)))
+        return out[:cnt.value]
 
     def list_export(self, which, level=0, stream=None):
         """Rows (target box, term, source box) of the V list of `level` (which=0) or the U list (1)."""

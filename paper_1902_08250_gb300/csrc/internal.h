@@ -17,7 +17,8 @@ void lm_set_error(const char *fmt, ...);
 // Dynamic shared-memory limits are per kernel and per device, shared by every
 // tree: raise one (never lower it) so that trees built earlier, with larger
 // needs, still launch.  slot names the kernel in a small per-device cache.
-enum { LM_SMEM_NEAR_PW = 0, LM_SMEM_IMAGE_M2L = 1, LM_SMEM_CROSS_M2L = 2, LM_SMEM_NEAR_PW64 = 3, LM_SMEM_SLOTS = 4 };
+enum { LM_SMEM_NEAR_PW = 0, LM_SMEM_IMAGE_M2L = 1, LM_SMEM_CROSS_M2L = 2, LM_SMEM_NEAR_PW64 = 3,
+       LM_SMEM_IMAGE_M2L_A = 4, LM_SMEM_NEAR_PW64_A = 5, LM_SMEM_SLOTS = 6 };
 cudaError_t lm_raise_smem(const void *func, int slot, int bytes);
 
 #define LM_CUDA(call)                                                                       \
@@ -40,6 +41,20 @@ __device__ inline void leaf_centre(const LeafGeom &g, int64_t b, double *cx, dou
     int64_t r = b / g.ncol, c = b % g.ncol;
     *cx = g.x0 + (c + 0.5) * g.w;
     *cy = -(r + 0.5) * g.w;
+}
+
+// Image row of source row r for term m at a level with nrow rows: free r;
+// tt -1-r (mirror in y = 0); bb 2nrow-1-r (mirror in y = -d); tb r-2nrow
+// (shift +2d); bt r+2nrow (shift -2d).
+__host__ __device__ inline int64_t img_row(int term, int64_t r, int64_t nrow)
+{
+    switch (term) {
+    case 0: return r;
+    case 1: return -1 - r;
+    case 2: return 2 * nrow - 1 - r;
+    case 3: return r - 2 * nrow;
+    default: return r + 2 * nrow;
+    }
 }
 
 struct lm_medium_s {
@@ -92,6 +107,31 @@ struct Level {
     int32_t *rtgt;   // [nrtgt]
 };
 
+// Adaptive tree (Algorithm 1, step 1): boxes of every level in one array,
+// numbered level by level and, within a level, by row * (R 2^l) + column.  A
+// box holding more than leaf_target points above the depth limit has all four
+// children; points are ordered by leaf, then input index (leaf_start then has
+// one entry per box, empty for boxes that are not leaves).  Lists come from a
+// dual traversal and hold entries between boxes of any two levels.
+struct AdaptTree {
+    int64_t nbox = 0, nleaf = 0, npw = 0;
+    std::vector<int64_t> lev_start;  // [L + 2] boxes of level l: [lev_start[l], lev_start[l + 1])
+    std::vector<int64_t> nl_start;   // [L + 1] non-leaf boxes of level l: nonleaf[nl_start[l] .. nl_start[l + 1])
+    std::vector<int64_t> hbox;       // host copy [nbox][4]: level, column, row, leaf
+    std::vector<int> cls_term, cls_lt, cls_ls; // V-list classes: term, target and source level,
+    std::vector<int64_t> cls_dx, cls_dy;       // centre offsets in half-widths of the finer level
+    double *cx = nullptr, *cy = nullptr, *w = nullptr; // [nbox] box centres and widths
+    int32_t *parent = nullptr, *pos = nullptr;         // [nbox] parent id (-1 for roots), child position
+    int32_t *child = nullptr;                          // [nbox][4] (-1 for leaves)
+    int32_t *leaves = nullptr, *nonleaf = nullptr, *pwleaves = nullptr; // box id lists
+    int64_t nv = 0;
+    std::vector<int64_t> lev_nv;                       // [L + 1] V entries of the targets of level l
+    int64_t *vstart = nullptr;                         // [nbox + 1] V list, target-major
+    int32_t *vsrc = nullptr, *vslot = nullptr, *vterm = nullptr;
+    zd *tab = nullptr;                                 // [nclass][np][np] scaled M2L tables
+    zd *M = nullptr, *Lc = nullptr;                    // [nbox][np][LM_MAXV]
+};
+
 struct lm_tree_s {
     lm_medium_s med;
     int64_t n;
@@ -118,6 +158,8 @@ struct lm_tree_s {
     zf *nq_seg_lam, *nq_seg_s2, *nq_seg_w, *nq_tail_lam, *nq_tail_s2, *nq_tail_w;
     bool tc_ready; // tensor-core M2L tables built
     bool near_pw64; // FP64 reflected near field: segment factorised per leaf (k_near_pw64)
+    bool adaptive;  // boxes refined where the points are (AdaptTree), FP64 only
+    AdaptTree at;
     int *dflag;  // device error flag
     int64_t bytes;
     // phase profiling
@@ -137,6 +179,12 @@ void lm_phase_end(lm_tree_s *t, int ph, cudaStream_t st, int launches);
 // setup (lmfmm_setup.cu)
 lm_status lm_setup_tree(lm_tree_s *t, const double *x, const double *y, cudaStream_t st);
 lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st);
+lm_status lm_setup_levels(lm_tree_s *t, int L, bool boxes, cudaStream_t st); // scales, M2M/L2L tables
+lm_status lm_setup_near(lm_tree_s *t, cudaStream_t st);                      // near-field quadrature
+// adaptive tree (lmfmm_adaptive.cu)
+lm_status lm_setup_adaptive(lm_tree_s *t, const double *x, const double *y, cudaStream_t st);
+lm_status lm_adaptive_lists_to_host(lm_tree_s *t, int which, std::vector<int64_t> &rows, cudaStream_t st);
+void lm_free_adaptive(lm_tree_s *t);
 lm_status lm_list_to_host(lm_tree_s *t, int which, int level, std::vector<int64_t> &rows,
                           cudaStream_t st);
 void lm_free_tree_device(lm_tree_s *t);

@@ -59,6 +59,7 @@ extern "C" lm_status lm_options_default(lm_options *o)
     o->bottom_bc = LM_BC_TRANSMISSION;
     o->top_alpha = 0.0;
     o->bottom_alpha = 0.0;
+    o->adaptive = 0;
     return LM_OK;
 }
 
@@ -105,6 +106,14 @@ extern "C" lm_status lm_create_medium(double k1, double k2, double k3, double d,
     if (o.kernel != LM_KERNEL_G && o.kernel != LM_KERNEL_DG_DD) {
         lm_set_error("create_medium: unknown kernel %d", o.kernel);
         return LM_EINVAL;
+    }
+    if (o.adaptive != 0 && o.adaptive != 1) {
+        lm_set_error("create_medium: adaptive must be 0 or 1");
+        return LM_EINVAL;
+    }
+    if (o.adaptive && o.precision != LM_FP64) {
+        lm_set_error("create_medium: the adaptive tree is built for LM_FP64 only");
+        return LM_ENOTSUP;
     }
     if (o.seg_order > 64 || o.tail_order > 256 || o.tail_rays > 64) {
         lm_set_error("create_medium: quadrature orders out of range");
@@ -162,8 +171,13 @@ extern "C" lm_status lm_build_tree(lm_medium m, const double *x, const double *y
     t->np = 2 * t->p + 1;
     t->precision = m->opt.precision;
     t->max_nvec = m->opt.max_nvec;
-    lm_status s = lm_setup_tree(t, x, y, st);
-    if (s == LM_OK) s = lm_setup_tables(t, st);
+    lm_status s;
+    if (m->opt.adaptive) {
+        s = lm_setup_adaptive(t, x, y, st);
+    } else {
+        s = lm_setup_tree(t, x, y, st);
+        if (s == LM_OK) s = lm_setup_tables(t, st);
+    }
     if (s == LM_OK && t->precision == LM_MIXED && m->opt.autotune) s = lm_autotune_mixed(t, st, nullptr, nullptr);
     if (s != LM_OK) {
         cudaStreamSynchronize(st);
@@ -304,6 +318,14 @@ extern "C" lm_status lm_get_tree_info(lm_tree t, lm_tree_info *info)
     info->precision = t->precision;
     info->max_nvec = t->max_nvec;
     info->device_bytes = t->bytes;
+    info->adaptive = t->adaptive ? 1 : 0;
+    if (t->adaptive) {
+        info->nbox = t->at.nbox;
+    } else {
+        int64_t nb = 0;
+        for (int l = 0; l <= t->L; ++l) nb += ((int64_t)t->R << l) << l;
+        info->nbox = nb;
+    }
     return LM_OK;
 }
 
@@ -316,9 +338,37 @@ extern "C" lm_status lm_tree_export(lm_tree t, int64_t *perm, int64_t *leaf_star
     cudaStream_t st = (cudaStream_t)stream;
     if (perm) LM_CUDA(cudaMemcpyAsync(perm, t->perm, t->n * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     if (leaf_start)
-        LM_CUDA(cudaMemcpyAsync(leaf_start, t->leaf_start, (t->nleaf + 1) * sizeof(int64_t),
+        LM_CUDA(cudaMemcpyAsync(leaf_start, t->leaf_start,
+                                ((t->adaptive ? t->at.nbox : t->nleaf) + 1) * sizeof(int64_t),
                                 cudaMemcpyDeviceToHost, st));
     LM_CUDA(cudaStreamSynchronize(st));
+    return LM_OK;
+}
+
+extern "C" lm_status lm_box_export(lm_tree t, int64_t *boxes, int64_t cap, int64_t *count)
+{
+    if (!t || !count || cap < 0 || (cap > 0 && !boxes)) {
+        lm_set_error("box_export: bad argument");
+        return LM_EINVAL;
+    }
+    if (t->adaptive) {
+        const int64_t nb = t->at.nbox;
+        *count = nb;
+        if (cap > 0) memcpy(boxes, t->at.hbox.data(), std::min(cap, nb) * 4 * sizeof(int64_t));
+        return LM_OK;
+    }
+    int64_t e = 0;
+    for (int l = 0; l <= t->L; ++l) {
+        const int64_t ncol = (int64_t)t->R << l, nrow = (int64_t)1 << l;
+        for (int64_t b = 0; b < ncol * nrow; ++b, ++e)
+            if (e < cap) {
+                boxes[4 * e] = l;
+                boxes[4 * e + 1] = b % ncol;
+                boxes[4 * e + 2] = b / ncol;
+                boxes[4 * e + 3] = l == t->L;
+            }
+    }
+    *count = e;
     return LM_OK;
 }
 
@@ -330,7 +380,8 @@ extern "C" lm_status lm_list_export(lm_tree t, int which, int level, int64_t *ou
         return LM_EINVAL;
     }
     std::vector<int64_t> rows;
-    lm_status s = lm_list_to_host(t, which, level, rows, (cudaStream_t)stream);
+    lm_status s = t->adaptive ? lm_adaptive_lists_to_host(t, which, rows, (cudaStream_t)stream)
+                              : lm_list_to_host(t, which, level, rows, (cudaStream_t)stream);
     if (s != LM_OK) return s;
     int64_t ne = (int64_t)rows.size() / 3;
     *count = ne;
@@ -344,6 +395,10 @@ extern "C" lm_status lm_m2l_table_export(lm_tree t, int level, int term, int dc,
     if (!t || !out || level < 0 || level > t->L) {
         lm_set_error("m2l_table_export: bad argument");
         return LM_EINVAL;
+    }
+    if (t->adaptive) {
+        lm_set_error("m2l_table_export: classes of an adaptive tree are not keyed by (level, dc, dr)");
+        return LM_ENOTSUP;
     }
     Level &lv = t->lev[level];
     int slot = -1;

@@ -6,6 +6,39 @@
 
 static int gridn(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
+// Box geometry of a launch: block i works on box id(i), whose centre and width
+// come from centre().
+struct GridLeaves { // uniform tree: leaf i of the leaf lattice
+    LeafGeom g;
+    __device__ int64_t id(int64_t i) const { return i; }
+    __device__ void centre(int64_t b, double *cx, double *cy, double *w) const
+    {
+        leaf_centre(g, b, cx, cy);
+        *w = g.w;
+    }
+};
+struct EdgeRowLeaves { // uniform tree: the leaves of the top row, then (nrow > 1) of the bottom row
+    LeafGeom g;
+    int64_t nrow;
+    __device__ int64_t id(int64_t i) const { return ((nrow == 1 || i < g.ncol) ? 0 : nrow - 1) * g.ncol + i % g.ncol; }
+    __device__ void centre(int64_t b, double *cx, double *cy, double *w) const
+    {
+        leaf_centre(g, b, cx, cy);
+        *w = g.w;
+    }
+};
+struct ListBoxes { // adaptive tree: box ids[i], centres and widths from arrays
+    const int32_t *ids;
+    const double *bx, *by, *bw;
+    __device__ int64_t id(int64_t i) const { return ids[i]; }
+    __device__ void centre(int64_t b, double *cx, double *cy, double *w) const
+    {
+        *cx = bx[b];
+        *cy = by[b];
+        *w = bw[b];
+    }
+};
+
 // q (input order, [nvec][n]) -> qs (tree order, [nvec][n]), optionally conjugated
 __global__ void k_permute_in(const zd *q, const int64_t *perm, int64_t n, int nvec, int conjugate,
                              zd *qs)
@@ -36,18 +69,19 @@ __global__ void k_permute_out(const zd *us, const int64_t *perm, int64_t n, int 
 // One block per leaf; points staged 16 at a time.
 // ---------------------------------------------------------------------------
 #define P2M_CHUNK 16
-__global__ void k_p2m64(LeafGeom g, int P, double k, const double *xs, const double *ys,
-                        const int64_t *ls, const zd *qs, int64_t n, int nvec, zd *M)
+template <class Geo>
+__device__ __forceinline__ void p2m64_body(Geo geo, int P, double k, const double *xs, const double *ys,
+                                           const int64_t *ls, const zd *qs, int64_t n, int nvec, zd *M)
 {
     extern __shared__ unsigned char smem[];
     const int np = 2 * P + 1;
     zd *B = (zd *)smem;                      // [P2M_CHUNK][np]
     zd *Q = B + P2M_CHUNK * np;              // [P2M_CHUNK][LM_MAXV]
-    const int64_t b = blockIdx.x;
+    const int64_t b = geo.id(blockIdx.x);
     const int64_t lo = ls[b], hi = ls[b + 1];
-    double cx, cy;
-    leaf_centre(g, b, &cx, &cy);
-    const double sc = k * g.w;
+    double cx, cy, bw;
+    geo.centre(b, &cx, &cy, &bw);
+    const double sc = k * bw;
     const int nent = np * nvec;
     zd acc[12];
     for (int e = 0; e < 12; ++e) acc[e] = zd{0.0, 0.0};
@@ -92,6 +126,53 @@ __global__ void k_p2m64(LeafGeom g, int P, double k, const double *xs, const dou
         int qi = idx / nvec, v = idx % nvec;
         M[(b * np + qi) * LM_MAXV + v] = acc[e];
     }
+}
+__global__ void k_p2m64(LeafGeom g, int P, double k, const double *xs, const double *ys,
+                        const int64_t *ls, const zd *qs, int64_t n, int nvec, zd *M)
+{
+    p2m64_body(GridLeaves{g}, P, k, xs, ys, ls, qs, n, nvec, M);
+}
+__global__ void k_p2m64_list(ListBoxes geo, int P, double k, const double *xs, const double *ys,
+                             const int64_t *ls, const zd *qs, int64_t n, int nvec, zd *M)
+{
+    p2m64_body(geo, P, k, xs, ys, ls, qs, n, nvec, M);
+}
+
+// M2M over the parents of one level of the adaptive tree: parent par[i] from its four children
+__global__ void k_m2m64a(int64_t npar, const int32_t *par, const int32_t *child, int P, int nvec,
+                         const zd *tabs, zd *M)
+{
+    const int np = 2 * P + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= npar * np * nvec) return;
+    int v = idx % nvec;
+    int p = (idx / nvec) % np;
+    const int64_t b = par[idx / (nvec * np)];
+    zd acc = {0.0, 0.0};
+    for (int pos = 0; pos < 4; ++pos) {
+        const int64_t ch = child[4 * b + pos];
+        const zd *T = tabs + ((int64_t)pos * np + p) * np;
+        const zd *m = M + ch * np * LM_MAXV + v;
+        for (int q = 0; q < np; ++q) cfma(acc, T[q], m[q * LM_MAXV]);
+    }
+    M[(b * np + p) * LM_MAXV + v] = acc;
+}
+
+// L2L over the boxes b0 .. b0 + nb - 1 of one level (>= 1) of the adaptive tree; initialises L
+__global__ void k_l2l64a(int64_t b0, int64_t nb, const int32_t *parent, const int32_t *bpos, int P, int nvec,
+                         const zd *tabs, zd *Lc)
+{
+    const int np = 2 * P + 1;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nb * np * nvec) return;
+    int v = idx % nvec;
+    int p = (idx / nvec) % np;
+    const int64_t b = b0 + idx / (nvec * np);
+    const zd *T = tabs + ((int64_t)bpos[b] * np + p) * np;
+    const zd *m = Lc + (int64_t)parent[b] * np * LM_MAXV + v;
+    zd acc = {0.0, 0.0};
+    for (int q = 0; q < np; ++q) cfma(acc, T[q], m[q * LM_MAXV]);
+    Lc[(b * np + p) * LM_MAXV + v] = acc;
 }
 
 // M2M (Lemma M2M): parent (level l) from its four children (level l+1)
@@ -191,16 +272,17 @@ __device__ zd near_refl64(const NearQuadD &q, int m, double X, double h, bool se
 // ---------------------------------------------------------------------------
 // Step 4: L2T (Eq. (local)) and S2T for every target of a leaf.
 // ---------------------------------------------------------------------------
-__global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs, const double *ys,
+template <class Geo>
+__global__ void k_leaf64(Geo geo, int P, double k, double d, const double *xs, const double *ys,
                          const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
                          const int32_t *uterm, NearQuadD nq, const zd *Lc, const zd *qs, int64_t n,
                          int nvec, int free_on, int pw, zd *us)
 {
     const int np = 2 * P + 1;
-    const int64_t b = blockIdx.x;
-    double cx, cy;
-    leaf_centre(g, b, &cx, &cy);
-    const double sc = k * g.w;
+    const int64_t b = geo.id(blockIdx.x);
+    double cx, cy, bw;
+    geo.centre(b, &cx, &cy, &bw);
+    const double sc = k * bw;
     const zd *Lb = Lc + b * np * LM_MAXV;
     for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
         const double xi = xs[i], yi = ys[i];
@@ -255,7 +337,8 @@ __global__ void k_leaf64(LeafGeom g, int P, double k, double d, const double *xs
 // ---------------------------------------------------------------------------
 #define PW64_SRC 64
 size_t lm_near_pw64_smem(int nseg) { return ((size_t)2 * nseg * LM_MAXV + PW64_SRC * LM_MAXV) * sizeof(zd) + 2 * PW64_SRC * sizeof(double); }
-__global__ void __launch_bounds__(256) k_near_pw64(LeafGeom g, int64_t nrow, double d, const double *xs,
+template <class Geo>
+__global__ void __launch_bounds__(256) k_near_pw64(Geo geo, double d, const double *xs,
                                                    const double *ys, const int64_t *ls, const int64_t *ustart,
                                                    const int32_t *usrc, const int32_t *uterm, NearQuadD nq,
                                                    const zd *qs, int64_t n, int nvec, zd *us)
@@ -266,11 +349,9 @@ __global__ void __launch_bounds__(256) k_near_pw64(LeafGeom g, int64_t nrow, dou
     zd *SQ = B + (size_t)nk * LM_MAXV;               // [PW64_SRC][LM_MAXV]
     double *SX = (double *)(SQ + PW64_SRC * LM_MAXV); // [PW64_SRC]
     double *SY = SX + PW64_SRC;                      // [PW64_SRC]
-    const int64_t ncol = g.ncol;
-    const int64_t row = (nrow == 1 || blockIdx.x < ncol) ? 0 : nrow - 1;
-    const int64_t col = blockIdx.x % ncol;
-    const int64_t b = row * ncol + col;
-    const double xT = g.x0 + (col + 0.5) * g.w;
+    const int64_t b = geo.id(blockIdx.x);
+    double xT, yT, wT;
+    geo.centre(b, &xT, &yT, &wT);
     for (int term = 1; term <= 2; ++term) {
         bool any = false;
         for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) any |= (uterm[e] == term);
@@ -374,15 +455,16 @@ __device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, 
 // e^{i(n-1)t}; in scaled coefficients the shifts carry S(|n|)/S(|n -+ 1|).
 // ---------------------------------------------------------------------------
 #define GV 4
-__global__ void k_leaf64_grad(LeafGeom g, int P, double k, double d, const double *xs, const double *ys,
+template <class Geo>
+__global__ void k_leaf64_grad(Geo geo, int P, double k, double d, const double *xs, const double *ys,
                               const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
                               const int32_t *uterm, NearQuadD nq, const zd *Lc, const zd *qs, int64_t n,
                               int v0, int nv, int free_on, const int64_t *perm, zd *u, zd *ux, zd *uy)
 {
-    const int64_t b = blockIdx.x;
-    double cx, cy;
-    leaf_centre(g, b, &cx, &cy);
-    const double sc = k * g.w, hs = 0.5 * sc;
+    const int64_t b = geo.id(blockIdx.x);
+    double cx, cy, bw;
+    geo.centre(b, &cx, &cy, &bw);
+    const double sc = k * bw, hs = 0.5 * sc;
     const zd *Lb = Lc + b * (2 * P + 1) * LM_MAXV + v0;
     for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
         const double xi = xs[i], yi = ys[i];
@@ -471,10 +553,89 @@ lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, 
     return run_fp64(t, q, nvec, u, false, ux, uy, st);
 }
 
+// FP64 driver of the adaptive tree: the same steps over the box lists of each level
+static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, zd *ux, zd *uy,
+                                   cudaStream_t st)
+{
+    const AdaptTree &A = t->at;
+    const int L = t->L, P = t->p, np = 2 * P + 1;
+    const int64_t n = t->n;
+    const double k = t->med.k2;
+    NearQuadD nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq.seg_lam, t->nq.seg_s2,
+                 t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w};
+    const ListBoxes leaves{A.leaves, A.cx, A.cy, A.w}, pwl{A.pwleaves, A.cx, A.cy, A.w};
+    const int free_on = t->med.opt.kernel == LM_KERNEL_G;
+    for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
+        const int nv = std::min(LM_MAXV, nvec - v0);
+        lm_phase_begin(t, PH_PERMUTE, st);
+        k_permute_in<<<gridn(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->perm, n, nv, adjoint, t->qs);
+        lm_phase_end(t, PH_PERMUTE, st, 1);
+        // step 2: S2M at every leaf, M2M up the levels
+        lm_phase_begin(t, PH_S2M, st);
+        const size_t shm = (P2M_CHUNK * np + P2M_CHUNK * LM_MAXV) * sizeof(zd);
+        k_p2m64_list<<<(unsigned)A.nleaf, 256, shm, st>>>(leaves, P, k, t->xs, t->ys, t->leaf_start, t->qs, n, nv,
+                                                           A.M);
+        lm_phase_end(t, PH_S2M, st, 1);
+        int nl = 0;
+        lm_phase_begin(t, PH_M2M, st);
+        for (int l = L - 1; l >= 0; --l) {
+            const int64_t npar = A.nl_start[l + 1] - A.nl_start[l];
+            if (npar == 0) continue;
+            k_m2m64a<<<gridn(npar * np * nv, 128), 128, 0, st>>>(npar, A.nonleaf + A.nl_start[l], A.child, P, nv,
+                                                                 t->lev[l].m2m, A.M);
+            ++nl;
+        }
+        lm_phase_end(t, PH_M2M, st, nl);
+        // step 3: level by level, L2L from the parent then M2L from the V list
+        for (int l = 0; l <= L; ++l) {
+            const int64_t b0 = A.lev_start[l], nb = A.lev_start[l + 1] - b0;
+            lm_phase_begin(t, PH_L2L, st);
+            if (l == 0)
+                LM_CUDA(cudaMemsetAsync(A.Lc, 0, nb * np * LM_MAXV * sizeof(zd), st));
+            else
+                k_l2l64a<<<gridn(nb * np * nv, 128), 128, 0, st>>>(b0, nb, A.parent, A.pos, P, nv, t->lev[l].l2l,
+                                                                   A.Lc);
+            lm_phase_end(t, PH_L2L, st, l > 0);
+            lm_phase_begin(t, PH_M2L, st);
+            if (A.lev_nv[l] > 0)
+                k_m2l64<<<gridn(nb * np * nv, 128), 128, 0, st>>>(nb, P, nv, A.vstart + b0, A.vsrc, A.vslot, A.tab,
+                                                                  A.M, A.Lc + b0 * np * LM_MAXV);
+            lm_phase_end(t, PH_M2L, st, A.lev_nv[l] > 0);
+        }
+        // step 4: L2T and the direct list at every leaf
+        lm_phase_begin(t, PH_LEAF, st);
+        if (ux) {
+            const int64_t off = (int64_t)v0 * n;
+            int ng = 0;
+            for (int w0 = 0; w0 < nv; w0 += GV, ++ng)
+                k_leaf64_grad<<<(unsigned)A.nleaf, 64, 0, st>>>(
+                    leaves, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, A.Lc,
+                    t->qs, n, w0, std::min(GV, nv - w0), free_on, t->perm, u ? u + off + (int64_t)w0 * n : nullptr,
+                    ux + off + (int64_t)w0 * n, uy + off + (int64_t)w0 * n);
+            lm_phase_end(t, PH_LEAF, st, ng);
+            LM_CUDA(cudaGetLastError());
+            continue;
+        }
+        const int pw = t->near_pw64 ? 1 : 0;
+        k_leaf64<<<(unsigned)A.nleaf, 64, 0, st>>>(leaves, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart,
+                                                   t->usrc, t->uterm, nq, A.Lc, t->qs, n, nv, free_on, pw, t->us);
+        if (pw && A.npw > 0)
+            k_near_pw64<<<(unsigned)A.npw, 256, lm_near_pw64_smem(t->nq.nseg), st>>>(
+                pwl, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, t->qs, n, nv, t->us);
+        lm_phase_end(t, PH_LEAF, st, (pw && A.npw > 0) ? 2 : 1);
+        lm_phase_begin(t, PH_PERMUTE, st);
+        k_permute_out<<<gridn(n, 256), 256, 0, st>>>(t->us, t->perm, n, nv, adjoint, u + (int64_t)v0 * n);
+        lm_phase_end(t, PH_PERMUTE, st, 1);
+        LM_CUDA(cudaGetLastError());
+    }
+    return LM_OK;
+}
+
 // FP64 driver; with ux set, step 4 also evaluates the target gradient and writes u, ux, uy
 static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, zd *ux, zd *uy,
                           cudaStream_t st)
 {
+    if (t->adaptive) return run_fp64_adaptive(t, q, nvec, u, adjoint, ux, uy, st);
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const int64_t n = t->n;
     const double k = t->med.k2;
@@ -530,7 +691,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             int nl = 0;
             for (int w0 = 0; w0 < nv; w0 += GV, ++nl)
                 k_leaf64_grad<<<(unsigned)lv.nbox, 64, 0, st>>>(
-                    g, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, lv.Lc,
+                    GridLeaves{g}, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, lv.Lc,
                     t->qs, n, w0, std::min(GV, nv - w0), free_on, t->perm,
                     u ? u + off + (int64_t)w0 * n : nullptr, ux + off + (int64_t)w0 * n,
                     uy + off + (int64_t)w0 * n);
@@ -542,12 +703,12 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             Level &lv = t->lev[L];
             LeafGeom g{lv.ncol, t->x0, lv.w};
             const int pw = t->near_pw64 ? 1 : 0;
-            k_leaf64<<<(unsigned)lv.nbox, 64, 0, st>>>(g, P, k, t->med.d, t->xs, t->ys, t->leaf_start,
+            k_leaf64<<<(unsigned)lv.nbox, 64, 0, st>>>(GridLeaves{g}, P, k, t->med.d, t->xs, t->ys, t->leaf_start,
                                                        t->ustart, t->usrc, t->uterm, nq, lv.Lc, t->qs, n,
                                                        nv, free_on, pw, t->us);
             if (pw)
                 k_near_pw64<<<(unsigned)(lv.nrow == 1 ? lv.ncol : 2 * lv.ncol), 256,
-                              lm_near_pw64_smem(t->nq.nseg), st>>>(g, lv.nrow, t->med.d, t->xs, t->ys,
+                              lm_near_pw64_smem(t->nq.nseg), st>>>(EdgeRowLeaves{g, lv.nrow}, t->med.d, t->xs, t->ys,
                                                                    t->leaf_start, t->ustart, t->usrc, t->uterm,
                                                                    nq, t->qs, n, nv, t->us);
         }
@@ -563,6 +724,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
 // dynamic shared-memory limit of k_near_pw64 (raised, never lowered: shared by all trees)
 lm_status lm_near_pw64_attr(size_t bytes)
 {
-    LM_CUDA(lm_raise_smem((const void *)k_near_pw64, LM_SMEM_NEAR_PW64, (int)bytes));
+    LM_CUDA(lm_raise_smem((const void *)k_near_pw64<EdgeRowLeaves>, LM_SMEM_NEAR_PW64, (int)bytes));
+    LM_CUDA(lm_raise_smem((const void *)k_near_pw64<ListBoxes>, LM_SMEM_NEAR_PW64_A, (int)bytes));
     return LM_OK;
 }

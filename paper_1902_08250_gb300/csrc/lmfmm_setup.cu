@@ -139,16 +139,6 @@ __global__ void k_gather_pts(const double *x, const double *y, const int64_t *pe
 // nrow rows: free r; tt -1-r (mirror in y = 0); bb 2nrow-1-r (mirror in
 // y = -d); tb r-2nrow (shift +2d); bt r+2nrow (shift -2d).
 // ---------------------------------------------------------------------------
-__host__ __device__ inline int64_t img_row(int term, int64_t r, int64_t nrow)
-{
-    switch (term) {
-    case 0: return r;
-    case 1: return -1 - r;
-    case 2: return 2 * nrow - 1 - r;
-    case 3: return r - 2 * nrow;
-    default: return r + 2 * nrow;
-    }
-}
 // inverse: source row whose image row is ri
 __host__ __device__ inline int64_t src_row(int term, int64_t ri, int64_t nrow)
 {
@@ -604,19 +594,13 @@ static void enumerate_classes(int l, int R, std::vector<std::tuple<int, int, int
     for (auto &kv : seen) out.push_back(kv.first);
 }
 
-lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
+// Levels 0..L of the strip forest: scale vectors, the M2M / L2L tables and,
+// with boxes set, the per-level expansion arrays of the uniform tree.
+lm_status lm_setup_levels(lm_tree_s *t, int L, bool boxes, cudaStream_t st)
 {
-    const int L = t->L, P = t->p, np = 2 * P + 1;
+    const int P = t->p, np = 2 * P + 1;
     const double k = t->med.k2, d = t->med.d;
-    MediumD md{t->med.k1,
-               t->med.k2,
-               t->med.k3,
-               t->med.d,
-               t->med.opt.kernel == LM_KERNEL_DG_DD,
-               {t->med.opt.top_bc, t->med.opt.bottom_bc},
-               {t->med.opt.top_alpha, t->med.opt.bottom_alpha}};
     t->lev.resize(L + 1);
-    // scale vectors
     for (int l = 0; l <= L; ++l) {
         Level &lv = t->lev[l];
         lv.l = l;
@@ -632,8 +616,10 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
         }
         TRY(dalloc(t, &lv.scale, P + 1));
         LM_CUDA(cudaMemcpyAsync(lv.scale, sc.data(), (P + 1) * sizeof(double), cudaMemcpyHostToDevice, st));
-        TRY(dalloc(t, &lv.M, lv.nbox * np * LM_MAXV));
-        TRY(dalloc(t, &lv.Lc, lv.nbox * np * LM_MAXV));
+        if (boxes) {
+            TRY(dalloc(t, &lv.M, lv.nbox * np * LM_MAXV));
+            TRY(dalloc(t, &lv.Lc, lv.nbox * np * LM_MAXV));
+        }
     }
     // shift tables
     for (int l = 0; l <= L; ++l) {
@@ -649,6 +635,62 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
         k_shift_tables<<<grid_for(4 * np * np, 128), 128, 0, st>>>(k, P, ch.w, ch.scale, par.scale,
                                                                    par.m2m, ch.l2l);
     }
+    LM_CUDA(cudaGetLastError());
+    return LM_OK;
+}
+
+// Near-field quadrature tables of the reflected direct terms (shared by both tree kinds)
+lm_status lm_setup_near(lm_tree_s *t, cudaStream_t st)
+{
+    MediumD md{t->med.k1,
+               t->med.k2,
+               t->med.k3,
+               t->med.d,
+               t->med.opt.kernel == LM_KERNEL_DG_DD,
+               {t->med.opt.top_bc, t->med.opt.bottom_bc},
+               {t->med.opt.top_alpha, t->med.opt.bottom_alpha}};
+    NearQuad &q = t->nq;
+    double km = fmax(md.k1, fmax(md.k2, md.k3)), kmin = fmin(md.k1, fmin(md.k2, md.k3));
+    q.c = 1.5 * km + 1.0;
+    double a = 0.5, delta = fmin(0.25, 0.5 * kmin);
+    int nflat = (int)ceil((q.c - 2.0 * delta) / 1.0);
+    int order = t->med.opt.seg_order;
+    q.nseg = (nflat + 2) * order;
+    q.nray = t->med.opt.tail_rays;
+    q.ntail = t->med.opt.tail_order;
+    TRY(dalloc(t, &q.seg_lam, q.nseg));
+    TRY(dalloc(t, &q.seg_s2, q.nseg));
+    TRY(dalloc(t, &q.seg_w, 2 * q.nseg));
+    int nt = q.nray * q.ntail;
+    TRY(dalloc(t, &q.tail_lam, nt));
+    TRY(dalloc(t, &q.tail_s2, nt));
+    TRY(dalloc(t, &q.tail_w, 4 * nt));
+    k_near_seg<<<grid_for(q.nseg, 64), 64, 0, st>>>(md, q.c, a, delta, nflat, order, q.seg_lam, q.seg_s2,
+                                                     q.seg_w, q.nseg);
+    k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2, q.tail_w);
+    LM_CUDA(cudaGetLastError());
+    // FP64: factorise the segment per leaf when its coefficients fit in shared memory
+    const size_t pw = lm_near_pw64_smem(q.nseg);
+    t->near_pw64 = false;
+    if (t->precision == LM_FP64 && pw <= 200 * 1024) {
+        TRY(lm_near_pw64_attr(pw));
+        t->near_pw64 = true;
+    }
+    return LM_OK;
+}
+
+lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
+{
+    const int L = t->L, P = t->p, np = 2 * P + 1;
+    const double k = t->med.k2;
+    MediumD md{t->med.k1,
+               t->med.k2,
+               t->med.k3,
+               t->med.d,
+               t->med.opt.kernel == LM_KERNEL_DG_DD,
+               {t->med.opt.top_bc, t->med.opt.bottom_bc},
+               {t->med.opt.top_alpha, t->med.opt.bottom_alpha}};
+    TRY(lm_setup_levels(t, L, true, st));
     // lists and M2L classes
     for (int l = 0; l <= L; ++l) {
         Level &lv = t->lev[l];
@@ -737,36 +779,7 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
         TRY(dalloc(t, &t->uterm, t->nu));
         k_ulist<<<grid_for(t->nleaf, 128), 128, 0, st>>>(ncol, nrow, t->ustart, t->usrc, t->uterm, 1);
     }
-    // near-field quadrature
-    {
-        NearQuad &q = t->nq;
-        double km = fmax(md.k1, fmax(md.k2, md.k3)), kmin = fmin(md.k1, fmin(md.k2, md.k3));
-        q.c = 1.5 * km + 1.0;
-        double a = 0.5, delta = fmin(0.25, 0.5 * kmin);
-        int nflat = (int)ceil((q.c - 2.0 * delta) / 1.0);
-        int order = t->med.opt.seg_order;
-        q.nseg = (nflat + 2) * order;
-        q.nray = t->med.opt.tail_rays;
-        q.ntail = t->med.opt.tail_order;
-        TRY(dalloc(t, &q.seg_lam, q.nseg));
-        TRY(dalloc(t, &q.seg_s2, q.nseg));
-        TRY(dalloc(t, &q.seg_w, 2 * q.nseg));
-        int nt = q.nray * q.ntail;
-        TRY(dalloc(t, &q.tail_lam, nt));
-        TRY(dalloc(t, &q.tail_s2, nt));
-        TRY(dalloc(t, &q.tail_w, 4 * nt));
-        k_near_seg<<<grid_for(q.nseg, 64), 64, 0, st>>>(md, q.c, a, delta, nflat, order, q.seg_lam,
-                                                         q.seg_s2, q.seg_w, q.nseg);
-        k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2,
-                                                      q.tail_w);
-        // FP64: factorise the segment per leaf when its coefficients fit in shared memory
-        const size_t pw = lm_near_pw64_smem(q.nseg);
-        t->near_pw64 = false;
-        if (t->precision == LM_FP64 && pw <= 200 * 1024) {
-            TRY(lm_near_pw64_attr(pw));
-            t->near_pw64 = true;
-        }
-    }
+    TRY(lm_setup_near(t, st));
     // tree-order scratch for densities and potentials
     TRY(dalloc(t, &t->qs, (size_t)LM_MAXV * t->n));
     TRY(dalloc(t, &t->us, (size_t)LM_MAXV * t->n));
@@ -835,6 +848,7 @@ lm_status lm_list_to_host(lm_tree_s *t, int which, int level, std::vector<int64_
 void lm_free_tree_device(lm_tree_s *t)
 {
     lm_free_mixed(t);
+    lm_free_adaptive(t);
     void *ptrs[] = {t->xs, t->ys, t->perm, t->leaf_start, t->ustart, t->usrc, t->uterm, t->qs, t->us,
                     t->dflag, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
                     t->nq.tail_w};
