@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--workload", default="strip", choices=["strip", "batched", "adjoint", "clustered"],
                     help="strip: the 1M-point headline apply; batched: 48 independent instances in one graph; "
                          "adjoint: J = sum |u - u_obs|^2 and its gradients in q, x, y, d at N = 200k (FP64); "
-                         "clustered: N = 100k, half within 0.01 of y = 0, FP64 at p = 24")
+                         "clustered: N = 100k, half within 0.01 of y = 0, FP64 on the adaptive tree")
     return ap.parse_args()
 
 
@@ -391,9 +391,9 @@ def run_adjoint(args):
 
 def run_clustered(args):
     """N = 100k: half the points uniform in the middle layer, half within 0.01 of y = 0 (x spread
-    10), one complex128 vector, FP64 at p = 24, on the adaptive tree (--tree adaptive, default) or
-    the uniform tree of automatic (occupancy-driven) depth; the error is measured against the
-    oracle's direct sum on 16 targets x all sources."""
+    10), one complex128 vector, FP64, on the adaptive tree (--tree adaptive, default: 16 points
+    per leaf, p = 22) or the uniform tree of automatic (occupancy-driven) depth (p = 24); the
+    error is measured against the oracle's direct sum on 16 targets x all sources."""
     import torch
 
     import oracle
@@ -406,11 +406,15 @@ def run_clustered(args):
     n = 100_000
     med = workloads.MEDIUM_A
     x, y, q = workloads.clustered(n, 1, seed=0)
-    p = args.p or 24  # the order that meets 1e-10 on this workload (p = 20 gives 1.4e-10)
+    # the least order that meets 1e-10 on this workload: adaptive p = 22 (1.7e-11; p = 20 gives
+    # 1.35e-10), uniform p = 24 (4.5e-12; p = 20 gives 1.4e-10)
+    p = args.p or (22 if args.tree == "adaptive" else 24)
     t0 = time.time()
     opt = dict(p=p, adaptive=args.tree == "adaptive")
     if args.leaf_target > 0:
         opt["leaf_target"] = args.leaf_target
+    elif args.tree == "adaptive":
+        opt["leaf_target"] = 16  # fastest of 8, 12, 16, 24, 32, 64, 128
     if args.depth >= -1:
         opt["depth"] = args.depth
     m = lm.create_medium(*med, **opt)

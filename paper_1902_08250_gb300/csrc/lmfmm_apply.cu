@@ -270,59 +270,100 @@ __device__ zd near_refl64(const NearQuadD &q, int m, double X, double h, bool se
 }
 
 // ---------------------------------------------------------------------------
-// Step 4: L2T (Eq. (local)) and S2T for every target of a leaf.
+// Step 4: L2T (Eq. (local)) and S2T for every target of a leaf.  L2T takes one
+// thread per target.  The direct interactions take one warp per target: the
+// leaf's U entries are flattened (in chunks) into one list of near sources,
+// the lanes split it, and a butterfly of shuffles sums the lanes in a fixed
+// order.  A thread per target left most lanes idle on small leaves while the
+// FP64 pipes stepped through the per-pair tails.
 // ---------------------------------------------------------------------------
+#define LEAF64_THREADS 128
+#define LEAF64_UCHUNK 64
 template <class Geo>
-__global__ void k_leaf64(Geo geo, int P, double k, double d, const double *xs, const double *ys,
-                         const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
-                         const int32_t *uterm, NearQuadD nq, const zd *Lc, const zd *qs, int64_t n,
-                         int nvec, int free_on, int pw, zd *us)
+__global__ void __launch_bounds__(LEAF64_THREADS)
+    k_leaf64(Geo geo, int P, double k, double d, const double *xs, const double *ys, const int64_t *ls,
+             const int64_t *ustart, const int32_t *usrc, const int32_t *uterm, NearQuadD nq, const zd *Lc,
+             const zd *qs, int64_t n, int nvec, int free_on, int pw, zd *us)
 {
+    __shared__ int64_t fj0[LEAF64_UCHUNK]; // first tree position of each entry's source leaf
+    __shared__ int fpre[LEAF64_UCHUNK + 1]; // running count of near sources before each entry
+    __shared__ int fterm[LEAF64_UCHUNK];
     const int np = 2 * P + 1;
     const int64_t b = geo.id(blockIdx.x);
     double cx, cy, bw;
     geo.centre(b, &cx, &cy, &bw);
     const double sc = k * bw;
     const zd *Lb = Lc + b * np * LM_MAXV;
-    for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
+    const int64_t lo = ls[b], hi = ls[b + 1];
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
         const double xi = xs[i], yi = ys[i];
         zd acc[LM_MAXV];
         for (int v = 0; v < nvec; ++v) acc[v] = zd{0.0, 0.0};
-        {
-            double rx = xi - cx, ry = yi - cy, r = hypot(rx, ry);
-            double J[LM_MAXP + 1];
-            bessel_j_scaled<double>(P, k * r, sc, J);
-            zd z = r > 0.0 ? zd{rx / r, ry / r} : zd{1.0, 0.0}; // e^{i theta}
-            zd zp = {1.0, 0.0};
-            for (int v = 0; v < nvec; ++v) cfma(acc[v], zd{J[0], 0.0}, Lb[P * LM_MAXV + v]);
-            for (int m = 1; m <= P; ++m) {
-                zp = zp * z;
-                zd bp = J[m] * zp;
-                zd bn = ((m & 1) ? -J[m] : J[m]) * conj(zp);
-                for (int v = 0; v < nvec; ++v) {
-                    cfma(acc[v], bp, Lb[(P + m) * LM_MAXV + v]);
-                    cfma(acc[v], bn, Lb[(P - m) * LM_MAXV + v]);
-                }
+        double rx = xi - cx, ry = yi - cy, r = hypot(rx, ry);
+        double J[LM_MAXP + 1];
+        bessel_j_scaled<double>(P, k * r, sc, J);
+        zd z = r > 0.0 ? zd{rx / r, ry / r} : zd{1.0, 0.0}; // e^{i theta}
+        zd zp = {1.0, 0.0};
+        for (int v = 0; v < nvec; ++v) cfma(acc[v], zd{J[0], 0.0}, Lb[P * LM_MAXV + v]);
+        for (int m = 1; m <= P; ++m) {
+            zp = zp * z;
+            zd bp = J[m] * zp;
+            zd bn = ((m & 1) ? -J[m] : J[m]) * conj(zp);
+            for (int v = 0; v < nvec; ++v) {
+                cfma(acc[v], bp, Lb[(P + m) * LM_MAXV + v]);
+                cfma(acc[v], bn, Lb[(P - m) * LM_MAXV + v]);
             }
         }
-        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
-            const int32_t s = usrc[e], term = uterm[e];
-            if (term == 0 && !free_on) continue;
-            for (int64_t j = ls[s]; j < ls[s + 1]; ++j) {
+        for (int v = 0; v < nvec; ++v) us[(int64_t)v * n + i] = acc[v];
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int64_t u0 = ustart[b], u1 = ustart[b + 1];
+    for (int64_t c0 = u0; c0 < u1; c0 += LEAF64_UCHUNK) {
+        const int nc = (int)min((int64_t)LEAF64_UCHUNK, u1 - c0);
+        __syncthreads(); // L2T values written, previous chunk finished
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int e = 0; e < nc; ++e) {
+                const int32_t s = usrc[c0 + e], term = uterm[c0 + e];
+                fj0[e] = ls[s];
+                fterm[e] = term;
+                fpre[e] = run;
+                run += (term == 0 && !free_on) ? 0 : (int)(ls[s + 1] - ls[s]);
+            }
+            fpre[nc] = run;
+        }
+        __syncthreads();
+        const int tot = fpre[nc];
+        for (int64_t i = lo + warp; i < hi; i += nwarp) {
+            const double xi = xs[i], yi = ys[i];
+            zd acc[LM_MAXV];
+            for (int v = 0; v < nvec; ++v) acc[v] = zd{0.0, 0.0};
+            int e = 0;
+            for (int f = lane; f < tot; f += 32) {
+                while (fpre[e + 1] <= f) ++e; // f < tot = fpre[nc] keeps e < nc
+                const int64_t j = fj0[e] + (f - fpre[e]);
+                const int term = fterm[e];
                 zd gij;
                 if (term == 0) {
                     if (j == i) continue;
-                    double r = hypot(xi - xs[j], yi - ys[j]);
+                    const double r = hypot(xi - xs[j], yi - ys[j]);
                     gij = zd{-0.25 * y0(k * r), 0.25 * j0(k * r)}; // (i/4) H0^(1)(k r)
                 } else {
-                    double X = fabs(xi - xs[j]);
-                    double h = term == 1 ? -(yi + ys[j]) : yi + ys[j] + 2.0 * d;
+                    const double X = fabs(xi - xs[j]);
+                    const double h = term == 1 ? -(yi + ys[j]) : yi + ys[j] + 2.0 * d;
                     gij = near_refl64(nq, term - 1, X, h, !pw); // segment added by k_near_pw64
                 }
                 for (int v = 0; v < nvec; ++v) cfma(acc[v], gij, qs[(int64_t)v * n + j]);
             }
+            for (int v = 0; v < nvec; ++v) {
+                double re = acc[v].re, im = acc[v].im;
+                for (int o = 16; o > 0; o >>= 1) {
+                    re += __shfl_xor_sync(0xffffffffu, re, o);
+                    im += __shfl_xor_sync(0xffffffffu, im, o);
+                }
+                if (lane == 0) us[(int64_t)v * n + i] = us[(int64_t)v * n + i] + zd{re, im};
+            }
         }
-        for (int v = 0; v < nvec; ++v) us[(int64_t)v * n + i] = acc[v];
     }
 }
 
@@ -617,7 +658,7 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
             continue;
         }
         const int pw = t->near_pw64 ? 1 : 0;
-        k_leaf64<<<(unsigned)A.nleaf, 64, 0, st>>>(leaves, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart,
+        k_leaf64<<<(unsigned)A.nleaf, LEAF64_THREADS, 0, st>>>(leaves, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart,
                                                    t->usrc, t->uterm, nq, A.Lc, t->qs, n, nv, free_on, pw, t->us);
         if (pw && A.npw > 0)
             k_near_pw64<<<(unsigned)A.npw, 256, lm_near_pw64_smem(t->nq.nseg), st>>>(
@@ -703,7 +744,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             Level &lv = t->lev[L];
             LeafGeom g{lv.ncol, t->x0, lv.w};
             const int pw = t->near_pw64 ? 1 : 0;
-            k_leaf64<<<(unsigned)lv.nbox, 64, 0, st>>>(GridLeaves{g}, P, k, t->med.d, t->xs, t->ys, t->leaf_start,
+            k_leaf64<<<(unsigned)lv.nbox, LEAF64_THREADS, 0, st>>>(GridLeaves{g}, P, k, t->med.d, t->xs, t->ys, t->leaf_start,
                                                        t->ustart, t->usrc, t->uterm, nq, lv.Lc, t->qs, n,
                                                        nv, free_on, pw, t->us);
             if (pw)
