@@ -497,7 +497,7 @@ __device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, 
 // ---------------------------------------------------------------------------
 #define GV 4
 template <class Geo>
-__global__ void k_leaf64_grad(Geo geo, int P, double k, double d, const double *xs, const double *ys,
+__global__ void __launch_bounds__(LEAF64_THREADS) k_leaf64_grad(Geo geo, int P, double k, double d, const double *xs, const double *ys,
                               const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
                               const int32_t *uterm, NearQuadD nq, const zd *Lc, const zd *qs, int64_t n,
                               int v0, int nv, int free_on, const int64_t *perm, zd *u, zd *ux, zd *uy)
@@ -507,6 +507,9 @@ __global__ void k_leaf64_grad(Geo geo, int P, double k, double d, const double *
     geo.centre(b, &cx, &cy, &bw);
     const double sc = k * bw, hs = 0.5 * sc;
     const zd *Lb = Lc + b * (2 * P + 1) * LM_MAXV + v0;
+    __shared__ int64_t fj0[LEAF64_UCHUNK];
+    __shared__ int fpre[LEAF64_UCHUNK + 1];
+    __shared__ int fterm[LEAF64_UCHUNK];
     for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
         const double xi = xs[i], yi = ys[i];
         zd a[GV], dp[GV], dm[GV], gxa[GV], gya[GV]; // dp = (d/dx - i d/dy) u, dm = (d/dx + i d/dy) u
@@ -542,10 +545,41 @@ __global__ void k_leaf64_grad(Geo geo, int P, double k, double d, const double *
                 gya[v] = zd{-0.5 * df.im, 0.5 * df.re}; // i (dp - dm) / 2
             }
         }
-        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
-            const int32_t s = usrc[e], term = uterm[e];
-            if (term == 0 && !free_on) continue;
-            for (int64_t j = ls[s]; j < ls[s + 1]; ++j) {
+        const int64_t o = perm[i];
+        for (int v = 0; v < nv; ++v) {
+            if (u) u[(int64_t)v * n + o] = a[v];
+            ux[(int64_t)v * n + o] = gxa[v];
+            uy[(int64_t)v * n + o] = gya[v];
+        }
+    }
+    // direct interactions: one warp per target over the flattened near sources (as k_leaf64)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int64_t lo = ls[b], hi = ls[b + 1], u0 = ustart[b], u1 = ustart[b + 1];
+    for (int64_t c0 = u0; c0 < u1; c0 += LEAF64_UCHUNK) {
+        const int nc = (int)min((int64_t)LEAF64_UCHUNK, u1 - c0);
+        __syncthreads(); // far-field values written, previous chunk finished
+        if (threadIdx.x == 0) {
+            int run = 0;
+            for (int e = 0; e < nc; ++e) {
+                const int32_t s = usrc[c0 + e], term = uterm[c0 + e];
+                fj0[e] = ls[s];
+                fterm[e] = term;
+                fpre[e] = run;
+                run += (term == 0 && !free_on) ? 0 : (int)(ls[s + 1] - ls[s]);
+            }
+            fpre[nc] = run;
+        }
+        __syncthreads();
+        const int tot = fpre[nc];
+        for (int64_t i = lo + warp; i < hi; i += nwarp) {
+            const double xi = xs[i], yi = ys[i];
+            zd a[GV], gxa[GV], gya[GV];
+            for (int v = 0; v < GV; ++v) a[v] = gxa[v] = gya[v] = zd{0.0, 0.0};
+            int e = 0;
+            for (int f = lane; f < tot; f += 32) {
+                while (fpre[e + 1] <= f) ++e; // f < tot = fpre[nc] keeps e < nc
+                const int64_t j = fj0[e] + (f - fpre[e]);
+                const int term = fterm[e];
                 zd gv, gx, gy;
                 const double Dx = xi - xs[j];
                 if (term == 0) {
@@ -570,12 +604,17 @@ __global__ void k_leaf64_grad(Geo geo, int P, double k, double d, const double *
                     cfma(gya[v], gy, qj);
                 }
             }
-        }
-        const int64_t o = perm[i];
-        for (int v = 0; v < nv; ++v) {
-            if (u) u[(int64_t)v * n + o] = a[v];
-            ux[(int64_t)v * n + o] = gxa[v];
-            uy[(int64_t)v * n + o] = gya[v];
+            const int64_t o = perm[i];
+            for (int v = 0; v < nv; ++v) {
+                double r6[6] = {a[v].re, a[v].im, gxa[v].re, gxa[v].im, gya[v].re, gya[v].im};
+                for (int c = 0; c < 6; ++c)
+                    for (int off = 16; off > 0; off >>= 1) r6[c] += __shfl_xor_sync(0xffffffffu, r6[c], off);
+                if (lane == 0) {
+                    if (u) u[(int64_t)v * n + o] = u[(int64_t)v * n + o] + zd{r6[0], r6[1]};
+                    ux[(int64_t)v * n + o] = ux[(int64_t)v * n + o] + zd{r6[2], r6[3]};
+                    uy[(int64_t)v * n + o] = uy[(int64_t)v * n + o] + zd{r6[4], r6[5]};
+                }
+            }
         }
     }
 }
@@ -649,7 +688,7 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
             const int64_t off = (int64_t)v0 * n;
             int ng = 0;
             for (int w0 = 0; w0 < nv; w0 += GV, ++ng)
-                k_leaf64_grad<<<(unsigned)A.nleaf, 64, 0, st>>>(
+                k_leaf64_grad<<<(unsigned)A.nleaf, LEAF64_THREADS, 0, st>>>(
                     leaves, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, A.Lc,
                     t->qs, n, w0, std::min(GV, nv - w0), free_on, t->perm, u ? u + off + (int64_t)w0 * n : nullptr,
                     ux + off + (int64_t)w0 * n, uy + off + (int64_t)w0 * n);
@@ -731,7 +770,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             const int64_t off = (int64_t)v0 * n;
             int nl = 0;
             for (int w0 = 0; w0 < nv; w0 += GV, ++nl)
-                k_leaf64_grad<<<(unsigned)lv.nbox, 64, 0, st>>>(
+                k_leaf64_grad<<<(unsigned)lv.nbox, LEAF64_THREADS, 0, st>>>(
                     GridLeaves{g}, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, lv.Lc,
                     t->qs, n, w0, std::min(GV, nv - w0), free_on, t->perm,
                     u ? u + off + (int64_t)w0 * n : nullptr, ux + off + (int64_t)w0 * n,
