@@ -82,6 +82,12 @@ typedef struct {
                         below depth (-1 -> 14); boxes of different levels interact through
                         lists built by a dual traversal (see lm_build_tree).  LM_FP64 only
                         (LM_ENOTSUP otherwise).  0 (default): uniform depth. */
+    int m2l_fp64;    /* LM_FP64 trees: 1 runs the M2L contraction in IEEE FP64; 0 (default)
+                        runs it in double-float on the FP32 pipes -- each value a pair of
+                        FP32 numbers (48-bit significand), exact products by fma and
+                        error-free sums, densities scaled by a power of two per apply so
+                        the expansions stay inside FP32's exponent range; about 1e-14
+                        relative, and several times the FP64 pipe's rate on GB300. */
 } lm_options;
 
 /* Other media (Sec. 3, Examples 2 and 3): an interface of the middle layer

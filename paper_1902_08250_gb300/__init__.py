@@ -44,7 +44,7 @@ class _Options(ctypes.Structure):
                 ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int), ("tensor_m2l", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("top_bc", ctypes.c_int),
                 ("bottom_bc", ctypes.c_int), ("top_alpha", ctypes.c_double), ("bottom_alpha", ctypes.c_double),
-                ("adaptive", ctypes.c_int)]
+                ("adaptive", ctypes.c_int), ("m2l_fp64", ctypes.c_int)]
 
 
 class _TreeInfo(ctypes.Structure):
@@ -134,14 +134,16 @@ class Medium:
 def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
                   seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1, kernel=KERNEL_G,
                   autotune=0, top_bc="transmission", top_alpha=0.0, bottom_bc="transmission",
-                  bottom_alpha=0.0, adaptive=False) -> Medium:
+                  bottom_alpha=0.0, adaptive=False, m2l_fp64=False) -> Medium:
     """kernel = KERNEL_G applies G; KERNEL_DG_DD applies dG/dd at fixed points.
     autotune = 1 tunes the M2L tile shapes of mixed-precision trees at build time.
     top_bc / bottom_bc: "transmission" (to the outer layer, k1 / k3), or a wall --
     "dirichlet", "neumann", "impedance" (du/dn - i k2 alpha u = 0, alpha = top_alpha /
     bottom_alpha).
     adaptive = True builds adaptive trees (FP64): a box with more than leaf_target points is
-    split while its level is below depth (-1 -> 14)."""
+    split while its level is below depth (-1 -> 14).
+    m2l_fp64 = True runs the FP64 form's M2L contraction in IEEE FP64 instead of double-float
+    on the FP32 pipes."""
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
     for b in (top_bc, bottom_bc):
@@ -149,7 +151,7 @@ def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP
             raise ValueError(f"create_medium: unknown boundary kind {b!r} (one of {sorted(BC)})")
     o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays, tensor_m2l,
                  kernel, autotune, BC[top_bc], BC[bottom_bc], float(top_alpha), float(bottom_alpha),
-                 int(bool(adaptive)))
+                 int(bool(adaptive)), int(bool(m2l_fp64)))
     h = ctypes.c_void_p()
     _check(_lib.lm_create_medium(k1, k2, k3, d, ctypes.byref(o), ctypes.byref(h)))
     return Medium(h.value, k1, k2, k3, d, dict(p=p, depth=depth, leaf_target=leaf_target,
@@ -157,7 +159,8 @@ def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP
                                               tail_order=tail_order, tail_rays=tail_rays,
                                               tensor_m2l=tensor_m2l, kernel=kernel, autotune=autotune,
                                               top_bc=top_bc, top_alpha=top_alpha, bottom_bc=bottom_bc,
-                                              bottom_alpha=bottom_alpha, adaptive=bool(adaptive)))
+                                              bottom_alpha=bottom_alpha, adaptive=bool(adaptive),
+                                              m2l_fp64=bool(m2l_fp64)))
 
 
 class Tree:

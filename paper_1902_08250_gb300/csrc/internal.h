@@ -92,6 +92,9 @@ struct Level {
     zd *m2m;         // [4][np][np]: child (level l+1) -> this level's box (l < L)
     zd *l2l;         // [4][np][np]: parent (level l-1) -> child at this level (l > 0)
     zd *M, *Lc;      // [nbox][np][LM_MAXV]
+    // FP64 form, double-float M2L: tables and multipoles as (re hi, re lo, im hi, im lo)
+    float4 *tabdf;   // [nclass][np][np]
+    float4 *Mdf;     // [nbox][np][LM_MAXV], scaled by 2^-qexp
     // mixed-precision copies (FP32, rounded from the FP64 tables)
     zf *tab32;       // [nclass][np][np]
     zf *m2m32, *l2l32; // [4][np][np]
@@ -130,6 +133,7 @@ struct AdaptTree {
     int32_t *vsrc = nullptr, *vslot = nullptr, *vterm = nullptr;
     zd *tab = nullptr;                                 // [nclass][np][np] scaled M2L tables
     zd *M = nullptr, *Lc = nullptr;                    // [nbox][np][LM_MAXV]
+    float4 *tabdf = nullptr, *Mdf = nullptr;           // double-float copies (as Level)
 };
 
 struct lm_tree_s {
@@ -161,6 +165,8 @@ struct lm_tree_s {
     bool adaptive;  // boxes refined where the points are (AdaptTree), FP64 only
     AdaptTree at;
     int *dflag;  // device error flag
+    bool m2l_df; // FP64 form: M2L contraction in double-float on the FP32 pipes
+    int *qexp;   // device: binary exponent of the largest |density| component of the apply
     int64_t bytes;
     // phase profiling
     int prof_max, prof_used;
@@ -192,6 +198,7 @@ void lm_free_tree_device(lm_tree_s *t);
 lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);
 size_t lm_near_pw64_smem(int nseg);
 lm_status lm_near_pw64_attr(size_t bytes);
+lm_status lm_setup_df(lm_tree_s *t, cudaStream_t st); // double-float tables and multipole buffers
 lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, zd *uy, cudaStream_t st);
 // mixed precision (lmfmm_mixed.cu)
 lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st);

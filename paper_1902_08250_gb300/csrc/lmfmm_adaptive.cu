@@ -532,7 +532,7 @@ lm_status lm_setup_adaptive(lm_tree_s *t, const double *x, const double *y, cuda
         lm_set_error("build_tree: a layered M2L table overflowed; lower p");
         return LM_ENOTSUP;
     }
-    return LM_OK;
+    return lm_setup_df(t, st);
 }
 
 // V (which = 0, every level) or U (which = 1) rows (target box, term, source box)
@@ -564,7 +564,8 @@ void lm_free_adaptive(lm_tree_s *t)
 {
     AdaptTree &A = t->at;
     void *ptrs[] = {A.cx,     A.cy,     A.w,      A.parent, A.pos,   A.child, A.leaves, A.nonleaf,
-                    A.pwleaves, A.vstart, A.vsrc, A.vslot,  A.vterm, A.tab,   A.M,      A.Lc};
+                    A.pwleaves, A.vstart, A.vsrc, A.vslot,  A.vterm, A.tab,   A.M,      A.Lc,
+                    A.tabdf,  A.Mdf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     A = AdaptTree();

@@ -60,6 +60,7 @@ extern "C" lm_status lm_options_default(lm_options *o)
     o->top_alpha = 0.0;
     o->bottom_alpha = 0.0;
     o->adaptive = 0;
+    o->m2l_fp64 = 0;
     return LM_OK;
 }
 
@@ -105,6 +106,10 @@ extern "C" lm_status lm_create_medium(double k1, double k2, double k3, double d,
     }
     if (o.kernel != LM_KERNEL_G && o.kernel != LM_KERNEL_DG_DD) {
         lm_set_error("create_medium: unknown kernel %d", o.kernel);
+        return LM_EINVAL;
+    }
+    if (o.m2l_fp64 != 0 && o.m2l_fp64 != 1) {
+        lm_set_error("create_medium: m2l_fp64 must be 0 or 1");
         return LM_EINVAL;
     }
     if (o.adaptive != 0 && o.adaptive != 1) {
@@ -171,6 +176,7 @@ extern "C" lm_status lm_build_tree(lm_medium m, const double *x, const double *y
     t->np = 2 * t->p + 1;
     t->precision = m->opt.precision;
     t->max_nvec = m->opt.max_nvec;
+    t->m2l_df = t->precision == LM_FP64 && m->opt.m2l_fp64 == 0;
     lm_status s;
     if (m->opt.adaptive) {
         s = lm_setup_adaptive(t, x, y, st);

@@ -237,6 +237,107 @@ __global__ void k_m2l64(int64_t nbox, int P, int nvec, const int64_t *vstart, co
 }
 
 // ---------------------------------------------------------------------------
+// M2L in double-float on the FP32 pipes (Dekker's representation: a value is
+// hi + lo, two FP32 numbers with |lo| <= ulp(hi)/2, 48 significand bits).  A
+// product is exact as p + e with p = hi*hi rounded and e = fma(hi, hi, -p),
+// plus the two cross terms; a sum is made exact by Knuth's TwoSum, whose
+// error joins the running low word.  The FP64 form keeps every other step in
+// IEEE FP64; GB300 issues FP32 at about 60 times its FP64 rate, so the
+// 48 FP32 instructions of a complex multiply-add cost less than its 4 DFMAs.
+// Multipoles are scaled by 2^-qexp (qexp: the binary exponent of the largest
+// density component of the apply), so that they stay inside FP32's exponent
+// range; tables are scaled (S_l) and of order one already.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float4 df_split(zd a)
+{
+    const float rh = __double2float_rn(a.re), ih = __double2float_rn(a.im);
+    return make_float4(rh, __double2float_rn(a.re - (double)rh), ih, __double2float_rn(a.im - (double)ih));
+}
+// (sh, sl) += (ah + al)(bh + bl)
+__device__ __forceinline__ void df_mac(float &sh, float &sl, float ah, float al, float bh, float bl)
+{
+    const float p = __fmul_rn(ah, bh);
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    const float s = __fadd_rn(sh, p);
+    const float bb = __fsub_rn(s, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+// complex: acc += t m, each part a double-float (x, y) = real, (z, w) = imaginary
+__device__ __forceinline__ void dfc_mac(float4 &acc, const float4 t, const float4 m)
+{
+    df_mac(acc.x, acc.y, t.x, t.y, m.x, m.y);
+    df_mac(acc.x, acc.y, -t.z, -t.w, m.z, m.w);
+    df_mac(acc.z, acc.w, t.x, t.y, m.z, m.w);
+    df_mac(acc.z, acc.w, t.z, t.w, m.x, m.y);
+}
+
+__global__ void k_tab_df(const zd *tab, int64_t count, float4 *out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) out[i] = df_split(tab[i]);
+}
+
+// largest |re|, |im| of the densities [nvec][n] -> its binary exponent, max-reduced into *qexp
+__global__ void k_qexp(const zd *qs, int64_t n, int nvec, int *qexp)
+{
+    double mx = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n * nvec; i += (int64_t)gridDim.x * blockDim.x) {
+        const zd a = qs[i];
+        mx = fmax(mx, fmax(fabs(a.re), fabs(a.im)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0 && mx > 0.0) {
+        int e;
+        frexp(mx, &e);
+        atomicMax(qexp, e);
+    }
+}
+__device__ __forceinline__ int qexp_of(const int *qexp)
+{
+    const int e = *qexp;
+    return e < -1000 ? 0 : e; // all densities zero: no scaling
+}
+
+// multipoles of boxes b0 .. b0 + nb - 1 -> double-float, scaled by 2^-qexp
+__global__ void k_m_df(int64_t b0, int64_t nb, int P, int nvec, const zd *M, const int *qexp, float4 *Mdf)
+{
+    const int np = 2 * P + 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nb * np * nvec) return;
+    const int v = idx % nvec;
+    const int64_t r = (b0 * np + idx / nvec) * LM_MAXV + v; // row (box, q), vector v
+    const int e = -qexp_of(qexp);
+    const zd a = M[r];
+    Mdf[r] = df_split(zd{ldexp(a.re, e), ldexp(a.im, e)});
+}
+
+// M2L over the V list, double-float: one thread per (target box, order p, vector)
+__global__ void __launch_bounds__(128) k_m2l_df(int64_t nbox, int P, int nvec, const int64_t *vstart,
+                                                const int32_t *vsrc, const int32_t *vslot, const float4 *tab,
+                                                const float4 *Mdf, const int *qexp, zd *Lc)
+{
+    const int np = 2 * P + 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * nvec) return;
+    const int v = idx % nvec;
+    const int p = (idx / nvec) % np;
+    const int64_t b = idx / (nvec * np);
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int64_t e = vstart[b]; e < vstart[b + 1]; ++e) {
+        const float4 *T = tab + ((int64_t)vslot[e] * np + p) * np;
+        const float4 *m = Mdf + (int64_t)vsrc[e] * np * LM_MAXV + v;
+        for (int q = 0; q < np; ++q) dfc_mac(acc, T[q], m[q * LM_MAXV]);
+    }
+    const int ex = qexp_of(qexp);
+    zd &o = Lc[(b * np + p) * LM_MAXV + v];
+    o = o + zd{ldexp((double)acc.x + (double)acc.y, ex), ldexp((double)acc.z + (double)acc.w, ex)};
+}
+
+// ---------------------------------------------------------------------------
 // Direct interaction of one reflected term (tt: term 1, bb: term 2) for a
 // pair at horizontal distance X and image height h, by the near-field
 // quadrature tables (segment + nearest steepest-descent ray).
@@ -649,7 +750,11 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
         const int nv = std::min(LM_MAXV, nvec - v0);
         lm_phase_begin(t, PH_PERMUTE, st);
         k_permute_in<<<gridn(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->perm, n, nv, adjoint, t->qs);
-        lm_phase_end(t, PH_PERMUTE, st, 1);
+        if (t->m2l_df) {
+            LM_CUDA(cudaMemsetAsync(t->qexp, 0x80, sizeof(int), st)); // below any exponent
+            k_qexp<<<std::min(1024, gridn(n * nv, 256)), 256, 0, st>>>(t->qs, n, nv, t->qexp);
+        }
+        lm_phase_end(t, PH_PERMUTE, st, t->m2l_df ? 2 : 1);
         // step 2: S2M at every leaf, M2M up the levels
         lm_phase_begin(t, PH_S2M, st);
         const size_t shm = (P2M_CHUNK * np + P2M_CHUNK * LM_MAXV) * sizeof(zd);
@@ -666,6 +771,11 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
             ++nl;
         }
         lm_phase_end(t, PH_M2M, st, nl);
+        if (t->m2l_df) {
+            lm_phase_begin(t, PH_M2L, st);
+            k_m_df<<<gridn(A.nbox * np * nv, 256), 256, 0, st>>>(0, A.nbox, P, nv, A.M, t->qexp, A.Mdf);
+            lm_phase_end(t, PH_M2L, st, 1);
+        }
         // step 3: level by level, L2L from the parent then M2L from the V list
         for (int l = 0; l <= L; ++l) {
             const int64_t b0 = A.lev_start[l], nb = A.lev_start[l + 1] - b0;
@@ -677,7 +787,10 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
                                                                    A.Lc);
             lm_phase_end(t, PH_L2L, st, l > 0);
             lm_phase_begin(t, PH_M2L, st);
-            if (A.lev_nv[l] > 0)
+            if (A.lev_nv[l] > 0 && t->m2l_df)
+                k_m2l_df<<<gridn(nb * np * nv, 128), 128, 0, st>>>(nb, P, nv, A.vstart + b0, A.vsrc, A.vslot, A.tabdf,
+                                                                   A.Mdf, t->qexp, A.Lc + b0 * np * LM_MAXV);
+            else if (A.lev_nv[l] > 0)
                 k_m2l64<<<gridn(nb * np * nv, 128), 128, 0, st>>>(nb, P, nv, A.vstart + b0, A.vsrc, A.vslot, A.tab,
                                                                   A.M, A.Lc + b0 * np * LM_MAXV);
             lm_phase_end(t, PH_M2L, st, A.lev_nv[l] > 0);
@@ -725,7 +838,11 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
         const int nv = std::min(LM_MAXV, nvec - v0);
         lm_phase_begin(t, PH_PERMUTE, st);
         k_permute_in<<<gridn(n, 256), 256, 0, st>>>(q + (int64_t)v0 * n, t->perm, n, nv, adjoint, t->qs);
-        lm_phase_end(t, PH_PERMUTE, st, 1);
+        if (t->m2l_df) {
+            LM_CUDA(cudaMemsetAsync(t->qexp, 0x80, sizeof(int), st)); // below any exponent
+            k_qexp<<<std::min(1024, gridn(n * nv, 256)), 256, 0, st>>>(t->qs, n, nv, t->qexp);
+        }
+        lm_phase_end(t, PH_PERMUTE, st, t->m2l_df ? 2 : 1);
         // step 2: upward pass
         lm_phase_begin(t, PH_S2M, st);
         {
@@ -743,6 +860,14 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             k_m2m64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.m2m, t->lev[l + 1].M, lv.M);
         }
         if (L > 0) lm_phase_end(t, PH_M2M, st, L);
+        if (t->m2l_df) {
+            lm_phase_begin(t, PH_M2L, st);
+            for (int l = 0; l <= L; ++l) {
+                Level &lv = t->lev[l];
+                k_m_df<<<gridn(lv.nbox * np * nv, 256), 256, 0, st>>>(0, lv.nbox, P, nv, lv.M, t->qexp, lv.Mdf);
+            }
+            lm_phase_end(t, PH_M2L, st, L + 1);
+        }
 
         // step 3: downward pass
         for (int l = 0; l <= L; ++l) {
@@ -756,7 +881,10 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
                                                          lv.Lc);
             lm_phase_end(t, PH_L2L, st, l > 0);
             lm_phase_begin(t, PH_M2L, st);
-            if (lv.nv > 0)
+            if (lv.nv > 0 && t->m2l_df)
+                k_m2l_df<<<gridn(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot, lv.tabdf,
+                                                          lv.Mdf, t->qexp, lv.Lc);
+            else if (lv.nv > 0)
                 k_m2l64<<<gridn(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot, lv.tab,
                                                          lv.M, lv.Lc);
             lm_phase_end(t, PH_M2L, st, lv.nv > 0);
@@ -806,5 +934,36 @@ lm_status lm_near_pw64_attr(size_t bytes)
 {
     LM_CUDA(lm_raise_smem((const void *)k_near_pw64<EdgeRowLeaves>, LM_SMEM_NEAR_PW64, (int)bytes));
     LM_CUDA(lm_raise_smem((const void *)k_near_pw64<ListBoxes>, LM_SMEM_NEAR_PW64_A, (int)bytes));
+    return LM_OK;
+}
+
+// double-float copies of the M2L tables, multipole buffers and the exponent slot (FP64 form)
+lm_status lm_setup_df(lm_tree_s *t, cudaStream_t st)
+{
+    if (!t->m2l_df) return LM_OK;
+    const int np = 2 * t->p + 1;
+    LM_CUDA(cudaMalloc((void **)&t->qexp, sizeof(int)));
+    t->bytes += sizeof(int);
+    auto conv = [&](const zd *tab, int64_t ncls, float4 **out) -> lm_status {
+        const int64_t cnt = std::max<int64_t>(1, ncls) * np * np;
+        lm_status s = lm_dalloc(t, out, cnt);
+        if (s != LM_OK) return s;
+        k_tab_df<<<gridn(cnt, 256), 256, 0, st>>>(tab, cnt, *out);
+        return LM_OK;
+    };
+    if (t->adaptive) {
+        lm_status s = conv(t->at.tab, (int64_t)t->at.cls_term.size(), &t->at.tabdf);
+        if (s != LM_OK) return s;
+        s = lm_dalloc(t, &t->at.Mdf, (size_t)t->at.nbox * np * LM_MAXV);
+        if (s != LM_OK) return s;
+    } else {
+        for (Level &lv : t->lev) {
+            lm_status s = conv(lv.tab, (int64_t)lv.cls_term.size(), &lv.tabdf);
+            if (s != LM_OK) return s;
+            s = lm_dalloc(t, &lv.Mdf, (size_t)lv.nbox * np * LM_MAXV);
+            if (s != LM_OK) return s;
+        }
+    }
+    LM_CUDA(cudaGetLastError());
     return LM_OK;
 }

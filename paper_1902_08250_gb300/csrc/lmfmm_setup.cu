@@ -800,7 +800,7 @@ lm_status lm_setup_tables(lm_tree_s *t, cudaStream_t st)
         return LM_ENOTSUP;
     }
     if (t->precision == LM_MIXED) return lm_setup_mixed(t, st);
-    return LM_OK;
+    return lm_setup_df(t, st);
 }
 
 lm_status lm_list_to_host(lm_tree_s *t, int which, int level, std::vector<int64_t> &rows,
@@ -850,12 +850,13 @@ void lm_free_tree_device(lm_tree_s *t)
     lm_free_mixed(t);
     lm_free_adaptive(t);
     void *ptrs[] = {t->xs, t->ys, t->perm, t->leaf_start, t->ustart, t->usrc, t->uterm, t->qs, t->us,
-                    t->dflag, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
+                    t->dflag, t->qexp, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
                     t->nq.tail_w};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (Level &lv : t->lev) {
-        void *lp[] = {lv.vstart, lv.vsrc, lv.vslot, lv.vterm, lv.tab, lv.scale, lv.m2m, lv.l2l, lv.M, lv.Lc};
+        void *lp[] = {lv.vstart, lv.vsrc, lv.vslot, lv.vterm, lv.tab, lv.scale, lv.m2m, lv.l2l, lv.M, lv.Lc,
+                      lv.tabdf, lv.Mdf};
         for (void *p : lp)
             if (p) cudaFree(p);
     }

@@ -164,7 +164,10 @@ def test_gradients_match_central_differences(lm):
 
 def test_gradients_at_200k_match_central_differences(lm):
     """The gradient workload at full size (N = 200k): autograd coordinate and
-    thickness gradients against central differences (h = 1e-6) of J."""
+    thickness gradients against central differences (h = 1e-6) of J.  Both use
+    the IEEE FP64 M2L: central differences divide the apply's rounding by 2h,
+    and the double-float M2L's (2e-13, from rounding at 2^-48 rather than 2^-53)
+    changes with the moved point and would dominate the difference."""
     import torch
 
     n = 200_000
@@ -172,7 +175,7 @@ def test_gradients_at_200k_match_central_differences(lm):
     _, _, qref = workloads.uniform_strip(n, 0.0, 40.0, -0.9, -0.1, nvec=1, seed=1)
     q, qref = q[0], qref[0]
     p = 20
-    m = lm.create_medium(*MED, p=p)
+    m = lm.create_medium(*MED, p=p, m2l_fp64=True)
     t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     uobs = lm.apply(t, torch.from_numpy(qref).cuda())
     _, gx, gy, gd = _grads(lm, t, x, y, q, uobs, MED[3])
@@ -180,7 +183,7 @@ def test_gradients_at_200k_match_central_differences(lm):
     uo = uobs.cpu().numpy()
 
     def u_at(xx, yy, d):
-        mm = lm.create_medium(MED[0], MED[1], MED[2], d, p=p, depth=t.info["depth"])
+        mm = lm.create_medium(MED[0], MED[1], MED[2], d, p=p, depth=t.info["depth"], m2l_fp64=True)
         tt = lm.build_tree(mm, torch.from_numpy(xx).cuda(), torch.from_numpy(yy).cuda())
         return lm.apply(tt, qd).cpu().numpy()
 
