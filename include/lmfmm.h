@@ -82,8 +82,8 @@ typedef struct {
                         below depth (-1 -> 14); boxes of different levels interact through
                         lists built by a dual traversal (see lm_build_tree).  LM_FP64 only
                         (LM_ENOTSUP otherwise).  0 (default): uniform depth. */
-    int m2l_fp64;    /* LM_FP64 trees: 1 runs the M2L contraction in IEEE FP64; 0 (default)
-                        runs it in double-float on the FP32 pipes -- each value a pair of
+    int m2l_fp64;    /* LM_FP64 trees: 1 runs the M2L, M2M and L2L contractions in IEEE FP64;
+                        0 (default) runs them in double-float on the FP32 pipes -- each value a pair of
                         FP32 numbers (48-bit significand), exact products by fma and
                         error-free sums, densities scaled by a power of two per apply so
                         the expansions stay inside FP32's exponent range; about 1e-14

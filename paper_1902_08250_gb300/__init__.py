@@ -142,8 +142,8 @@ def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP
     bottom_alpha).
     adaptive = True builds adaptive trees (FP64): a box with more than leaf_target points is
     split while its level is below depth (-1 -> 14).
-    m2l_fp64 = True runs the FP64 form's M2L contraction in IEEE FP64 instead of double-float
-    on the FP32 pipes."""
+    m2l_fp64 = True runs the FP64 form's M2L, M2M and L2L contractions in IEEE FP64 instead of
+    double-float on the FP32 pipes."""
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
     for b in (top_bc, bottom_bc):

@@ -95,6 +95,7 @@ struct Level {
     // FP64 form, double-float M2L: tables and multipoles as (re hi, re lo, im hi, im lo)
     float4 *tabdf;   // [nclass][np][np]
     float4 *Mdf;     // [nbox][np][LM_MAXV], scaled by 2^-qexp
+    float4 *m2mdf, *l2ldf; // [4][np][np] copies of m2m, l2l
     // mixed-precision copies (FP32, rounded from the FP64 tables)
     zf *tab32;       // [nclass][np][np]
     zf *m2m32, *l2l32; // [4][np][np]

@@ -337,6 +337,88 @@ __global__ void __launch_bounds__(128) k_m2l_df(int64_t nbox, int P, int nvec, c
     o = o + zd{ldexp((double)acc.x + (double)acc.y, ex), ldexp((double)acc.z + (double)acc.w, ex)};
 }
 
+// M2M and L2L in double-float: one block per parent box.  The parent's children
+// (M2M: their multipoles, one child position at a time) or the parent's local
+// expansion (L2L) are converted once into shared memory, scaled by 2^-qexp;
+// each thread accumulates up to DF_MAXO outputs (order, vector).
+#define DF_THREADS 128
+#define DF_MAXO 13 // (2 * LM_MAXP + 1) * LM_MAXV / DF_THREADS, rounded up
+struct GridParents { // uniform tree: parent i of a level with ncol columns; children one level down
+    int64_t ncol;
+    __device__ int64_t parent(int64_t i) const { return i; }
+    __device__ int64_t child(int64_t b, int pos) const
+    {
+        const int64_t r = b / ncol, c = b % ncol;
+        return (2 * r + (pos >> 1)) * (2 * ncol) + 2 * c + (pos & 1);
+    }
+};
+struct ListParents { // adaptive tree: parent ids[i], children from the box links
+    const int32_t *ids, *kids;
+    __device__ int64_t parent(int64_t i) const { return ids[i]; }
+    __device__ int64_t child(int64_t b, int pos) const { return kids[4 * b + pos]; }
+};
+
+template <class Geo>
+__global__ void __launch_bounds__(DF_THREADS) k_m2m_df(Geo geo, int P, int nvec, const float4 *tabs, const zd *Mc,
+                                                       const int *qexp, zd *Mp)
+{
+    extern __shared__ float4 sm4[]; // [np][nvec]: one child's multipole
+    const int np = 2 * P + 1, nout = np * nvec;
+    const int64_t b = geo.parent(blockIdx.x);
+    const int e = qexp_of(qexp);
+    float4 acc[DF_MAXO];
+#pragma unroll
+    for (int k = 0; k < DF_MAXO; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int pos = 0; pos < 4; ++pos) {
+        const int64_t ch = geo.child(b, pos);
+        __syncthreads();
+        for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+            const zd a = Mc[(ch * np + i / nvec) * LM_MAXV + i % nvec];
+            sm4[i] = df_split(zd{ldexp(a.re, -e), ldexp(a.im, -e)});
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < DF_MAXO; ++k) {
+            const int o = threadIdx.x + k * DF_THREADS;
+            if (o < nout) {
+                const int p = o / nvec, v = o % nvec;
+                const float4 *T = tabs + ((int64_t)pos * np + p) * np;
+                for (int q = 0; q < np; ++q) dfc_mac(acc[k], T[q], sm4[q * nvec + v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DF_MAXO; ++k) {
+        const int o = threadIdx.x + k * DF_THREADS;
+        if (o < nout)
+            Mp[(b * np + o / nvec) * LM_MAXV + o % nvec] =
+                zd{ldexp((double)acc[k].x + (double)acc[k].y, e), ldexp((double)acc[k].z + (double)acc[k].w, e)};
+    }
+}
+
+template <class Geo>
+__global__ void __launch_bounds__(DF_THREADS) k_l2l_df(Geo geo, int P, int nvec, const float4 *tabs, const zd *Lp,
+                                                       const int *qexp, zd *Lc)
+{
+    extern __shared__ float4 sm4[]; // [np][nvec]: the parent's local expansion
+    const int np = 2 * P + 1, nout = np * nvec;
+    const int64_t b = geo.parent(blockIdx.x);
+    const int e = qexp_of(qexp);
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+        const zd a = Lp[(b * np + i / nvec) * LM_MAXV + i % nvec];
+        sm4[i] = df_split(zd{ldexp(a.re, -e), ldexp(a.im, -e)});
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < 4 * nout; o += blockDim.x) {
+        const int pos = o / nout, r = o % nout, p = r / nvec, v = r % nvec;
+        const float4 *T = tabs + ((int64_t)pos * np + p) * np;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < np; ++q) dfc_mac(acc, T[q], sm4[q * nvec + v]);
+        Lc[(geo.child(b, pos) * np + p) * LM_MAXV + v] =
+            zd{ldexp((double)acc.x + (double)acc.y, e), ldexp((double)acc.z + (double)acc.w, e)};
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Direct interaction of one reflected term (tt: term 1, bb: term 2) for a
 // pair at horizontal distance X and image height h, by the near-field
@@ -766,8 +848,12 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
         for (int l = L - 1; l >= 0; --l) {
             const int64_t npar = A.nl_start[l + 1] - A.nl_start[l];
             if (npar == 0) continue;
-            k_m2m64a<<<gridn(npar * np * nv, 128), 128, 0, st>>>(npar, A.nonleaf + A.nl_start[l], A.child, P, nv,
-                                                                 t->lev[l].m2m, A.M);
+            if (t->m2l_df)
+                k_m2m_df<<<(unsigned)npar, DF_THREADS, np * nv * sizeof(float4), st>>>(
+                    ListParents{A.nonleaf + A.nl_start[l], A.child}, P, nv, t->lev[l].m2mdf, A.M, t->qexp, A.M);
+            else
+                k_m2m64a<<<gridn(npar * np * nv, 128), 128, 0, st>>>(npar, A.nonleaf + A.nl_start[l], A.child, P,
+                                                                     nv, t->lev[l].m2m, A.M);
             ++nl;
         }
         lm_phase_end(t, PH_M2M, st, nl);
@@ -782,7 +868,11 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
             lm_phase_begin(t, PH_L2L, st);
             if (l == 0)
                 LM_CUDA(cudaMemsetAsync(A.Lc, 0, nb * np * LM_MAXV * sizeof(zd), st));
-            else
+            else if (t->m2l_df) {
+                const int64_t npar = A.nl_start[l] - A.nl_start[l - 1]; // the parents of level l
+                k_l2l_df<<<(unsigned)npar, DF_THREADS, np * nv * sizeof(float4), st>>>(
+                    ListParents{A.nonleaf + A.nl_start[l - 1], A.child}, P, nv, t->lev[l].l2ldf, A.Lc, t->qexp, A.Lc);
+            } else
                 k_l2l64a<<<gridn(nb * np * nv, 128), 128, 0, st>>>(b0, nb, A.parent, A.pos, P, nv, t->lev[l].l2l,
                                                                    A.Lc);
             lm_phase_end(t, PH_L2L, st, l > 0);
@@ -857,7 +947,11 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
         for (int l = L - 1; l >= 0; --l) {
             Level &lv = t->lev[l];
             int64_t tot = lv.nbox * np * nv;
-            k_m2m64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.m2m, t->lev[l + 1].M, lv.M);
+            if (t->m2l_df)
+                k_m2m_df<<<(unsigned)lv.nbox, DF_THREADS, np * nv * sizeof(float4), st>>>(
+                    GridParents{lv.ncol}, P, nv, lv.m2mdf, t->lev[l + 1].M, t->qexp, lv.M);
+            else
+                k_m2m64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.m2m, t->lev[l + 1].M, lv.M);
         }
         if (L > 0) lm_phase_end(t, PH_M2M, st, L);
         if (t->m2l_df) {
@@ -876,6 +970,9 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             lm_phase_begin(t, PH_L2L, st);
             if (l == 0)
                 LM_CUDA(cudaMemsetAsync(lv.Lc, 0, lv.nbox * np * LM_MAXV * sizeof(zd), st));
+            else if (t->m2l_df)
+                k_l2l_df<<<(unsigned)t->lev[l - 1].nbox, DF_THREADS, np * nv * sizeof(float4), st>>>(
+                    GridParents{t->lev[l - 1].ncol}, P, nv, lv.l2ldf, t->lev[l - 1].Lc, t->qexp, lv.Lc);
             else
                 k_l2l64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.l2l, t->lev[l - 1].Lc,
                                                          lv.Lc);
@@ -951,6 +1048,16 @@ lm_status lm_setup_df(lm_tree_s *t, cudaStream_t st)
         k_tab_df<<<gridn(cnt, 256), 256, 0, st>>>(tab, cnt, *out);
         return LM_OK;
     };
+    for (Level &lv : t->lev) {
+        if (lv.m2m) {
+            lm_status s = conv(lv.m2m, 4, &lv.m2mdf); // 4 child positions
+            if (s != LM_OK) return s;
+        }
+        if (lv.l2l) {
+            lm_status s = conv(lv.l2l, 4, &lv.l2ldf);
+            if (s != LM_OK) return s;
+        }
+    }
     if (t->adaptive) {
         lm_status s = conv(t->at.tab, (int64_t)t->at.cls_term.size(), &t->at.tabdf);
         if (s != LM_OK) return s;

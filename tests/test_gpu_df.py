@@ -1,5 +1,5 @@
-"""The FP64 form's double-float M2L (pairs of FP32 numbers on the FP32 pipes)
-against the IEEE FP64 contraction, on uniform and adaptive trees, and its
+"""The FP64 form's double-float M2L, M2M and L2L (pairs of FP32 numbers on the
+FP32 pipes) against the IEEE FP64 contractions, on uniform and adaptive trees, and its
 exponent scaling over the whole FP64 range of density magnitudes."""
 import numpy as np
 import pytest
