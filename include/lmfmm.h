@@ -230,6 +230,28 @@ lm_status lm_list_export(lm_tree t, int which, int level, int64_t *out, int64_t 
 lm_status lm_box_export(lm_tree t, int64_t *boxes, int64_t cap, int64_t *count);
 
 /*
+ * adaptive_plan -- the host half of lm_build_tree with opt.adaptive = 1, from
+ * HOST arrays and without device work (no GPU needed): validation, the grid of
+ * roots, the adaptive boxes, the point order and the V and U lists, exactly as
+ * the tree that lm_build_tree builds from the same points and options.
+ *   x, y: host double[n], n >= 1; d > 0: the layer thickness; leaf_target >= 1;
+ *   depth: the depth limit, -1 (14) or 0..14.
+ *   x_origin, R, nbox, nv, nu: receive the grid and the counts (each may be NULL).
+ *   boxes: int64[4 * box_cap], rows (level, column, row, leaf) in box-id order
+ *   (min(box_cap, nbox) rows written); pstart: int64[nbox + 1], written only when
+ *   box_cap >= nbox (may be NULL); perm: int64[n] (may be NULL).
+ *   vrows / urows: int64[3 * v_cap] / [3 * u_cap], rows (target box, term, source
+ *   box) sorted, min(cap, count) written; a cap of 0 with a NULL array asks only
+ *   for the count.
+ * Errors: LM_EINVAL for bad arguments or a point that is non-finite or not
+ * strictly inside -d < y < 0; LM_ENOTSUP beyond 2^22 roots.
+ */
+lm_status lm_adaptive_plan(const double *x, const double *y, int64_t n, double d, int leaf_target, int depth,
+                           double *x_origin, int *R, int64_t *nbox, int64_t *boxes, int64_t box_cap,
+                           int64_t *perm, int64_t *pstart, int64_t *nv, int64_t *vrows, int64_t v_cap,
+                           int64_t *nu, int64_t *urows, int64_t u_cap);
+
+/*
  * m2l_table_export -- copy one M2L translation matrix A_pq (Lemma M2L for
  * term 1..4, the free-space translation for term 0), unscaled, p, q in
  * -P..P, to host memory as complex128 [(2P+1)][(2P+1)] (row p, column q).

@@ -72,6 +72,7 @@ def _load():
         "lm_tree_export": (I, [V, P, P, P]),
         "lm_list_export": (I, [V, I, I, P, I64, P, P]),
         "lm_box_export": (I, [V, P, I64, P]),
+        "lm_adaptive_plan": (I, [P, P, I64, D, I, I, P, P, P, P, I64, P, P, P, P, I64, P, P, I64]),
         "lm_m2l_table_export": (I, [V, I, I, I, I, P, P]),
         "lm_profile_begin": (I, [V, I]),
         "lm_profile_end": (I, [V, P, P, I, P]),
@@ -244,6 +245,32 @@ class Tree:
         _check(_lib.lm_m2l_table_export(self._h, level, term, dc, dr, out.ctypes.data_as(ctypes.c_void_p),
                                         _stream(stream)))
         return out
+
+
+def adaptive_plan(x, y, d, leaf_target=48, depth=-1):
+    """The adaptive tree of build_tree (adaptive=True) planned on the host from numpy
+    arrays, without a GPU: ((x_origin, R), boxes [nbox, 4] = (level, column, row, leaf),
+    perm, pstart [nbox + 1], V rows, U rows), rows (target box, term, source box)."""
+    import numpy as np
+
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.ascontiguousarray(y, np.float64)
+    if x.shape != y.shape or x.ndim != 1:
+        raise ValueError("adaptive_plan: x and y must be 1-D arrays of the same length")
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    x0, R = ctypes.c_double(), ctypes.c_int()
+    nb, nv, nu = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    args = (ptr(x), ptr(y), x.size, float(d), int(leaf_target), int(depth))
+    _check(_lib.lm_adaptive_plan(*args, ctypes.byref(x0), ctypes.byref(R), ctypes.byref(nb), None, 0, None, None,
+                                 ctypes.byref(nv), None, 0, ctypes.byref(nu), None, 0))
+    boxes = np.zeros((nb.value, 4), np.int64)
+    pstart = np.zeros(nb.value + 1, np.int64)
+    perm = np.zeros(x.size, np.int64)
+    V = np.zeros((max(nv.value, 1), 3), np.int64)
+    U = np.zeros((max(nu.value, 1), 3), np.int64)
+    _check(_lib.lm_adaptive_plan(*args, None, None, None, ptr(boxes), nb.value, ptr(perm), ptr(pstart), None,
+                                 ptr(V), nv.value, None, ptr(U), nu.value))
+    return (x0.value, R.value), boxes, perm, pstart, V[:nv.value], U[:nu.value]
 
 
 def build_tree(medium: Medium, x, y, stream=None) -> Tree:

@@ -175,6 +175,62 @@ struct Builder {
     }
 };
 
+typedef std::vector<std::tuple<int64_t, int, int64_t>> Rows;
+
+// The whole host side of the build: validates the points, sets the grid of
+// roots, builds the boxes, the point order (by leaf, then input index) and the
+// sorted V and U lists.  No device work.
+lm_status plan(const double *hx, const double *hy, int64_t n, double d, int s, int Lmax, const char *who,
+               Builder &B, std::vector<int64_t> &perm, std::vector<int64_t> &pstart, Rows &V, Rows &U)
+{
+    double mn = hx[0], mx = hx[0];
+    for (int64_t i = 0; i < n; ++i) {
+        if (!isfinite(hx[i]) || !isfinite(hy[i]) || !(hy[i] < 0.0) || !(hy[i] > -d)) {
+            lm_set_error("%s: a point is non-finite or not strictly inside -d < y < 0", who);
+            return LM_EINVAL;
+        }
+        mn = fmin(mn, hx[i]);
+        mx = fmax(mx, hx[i]);
+    }
+    const double f0 = floor(mn / d), f1 = floor(mx / d);
+    if (f1 - f0 + 1.0 > (double)(1 << 22)) {
+        lm_set_error("%s: the points span more than 2^22 roots; not supported by the adaptive tree", who);
+        return LM_ENOTSUP;
+    }
+    B.n = n;
+    B.d = d;
+    B.x0 = f0 * d;
+    B.R = (int)(f1 - f0) + 1;
+    B.Lmax = Lmax;
+    B.s = s;
+    std::vector<double> x(hx, hx + n), y(hy, hy + n);
+    B.build(x, y);
+    const int64_t nbox = (int64_t)B.box.size();
+    if (nbox >= INT32_MAX / 4) {
+        lm_set_error("%s: %lld boxes is beyond this build", who, (long long)nbox);
+        return LM_ENOTSUP;
+    }
+    perm.resize(n);
+    pstart.resize(nbox + 1);
+    int64_t pos = 0;
+    for (int64_t b = 0; b < nbox; ++b) {
+        pstart[b] = pos;
+        if (!B.box[b].leaf) continue;
+        std::vector<int64_t> idx(B.order.begin() + B.box[b].lo, B.order.begin() + B.box[b].hi);
+        std::sort(idx.begin(), idx.end());
+        for (int64_t i : idx) perm[pos++] = i;
+    }
+    pstart[nbox] = pos;
+    V.clear();
+    U.clear();
+    for (int64_t tb = 0; tb < B.R; ++tb)
+        for (int64_t sb = 0; sb < B.R; ++sb)
+            for (int m = 0; m < 5; ++m) B.visit(tb, sb, m, V, U);
+    std::sort(V.begin(), V.end());
+    std::sort(U.begin(), U.end());
+    return LM_OK;
+}
+
 template <typename T>
 lm_status upload(lm_tree_s *t, T **dst, const std::vector<T> &src, cudaStream_t st)
 {
@@ -264,45 +320,22 @@ lm_status lm_setup_adaptive(lm_tree_s *t, const double *x, const double *y, cuda
     LM_CUDA(cudaMemcpyAsync(hx.data(), x, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     LM_CUDA(cudaMemcpyAsync(hy.data(), y, n * sizeof(double), cudaMemcpyDeviceToHost, st));
     LM_CUDA(cudaStreamSynchronize(st));
-    double mn = hx[0], mx = hx[0];
-    for (int64_t i = 0; i < n; ++i) {
-        if (!isfinite(hx[i]) || !isfinite(hy[i]) || !(hy[i] < 0.0) || !(hy[i] > -d)) {
-            lm_set_error("build_tree: a point is non-finite or not strictly inside -d < y < 0");
-            return LM_EINVAL;
-        }
-        mn = fmin(mn, hx[i]);
-        mx = fmax(mx, hx[i]);
-    }
-    const double f0 = floor(mn / d), f1 = floor(mx / d);
-    if (f1 - f0 + 1.0 > (double)(1 << 22)) {
-        lm_set_error("build_tree: the points span more than 2^22 roots; not supported by the adaptive tree");
-        return LM_ENOTSUP;
-    }
-    t->x0 = f0 * d;
-    t->R = (int)(f1 - f0) + 1;
     Builder B;
-    B.n = n;
-    B.d = d;
-    B.x0 = t->x0;
-    B.R = t->R;
-    B.Lmax = t->med.opt.depth >= 0 ? t->med.opt.depth : 14;
-    B.s = t->med.opt.leaf_target;
-    B.build(hx, hy);
+    std::vector<int64_t> perm, pstart;
+    Rows V, U;
+    TRY_A(plan(hx.data(), hy.data(), n, d, t->med.opt.leaf_target, t->med.opt.depth >= 0 ? t->med.opt.depth : 14,
+               "build_tree", B, perm, pstart, V, U));
+    t->x0 = B.x0;
+    t->R = B.R;
     const int64_t nbox = (int64_t)B.box.size();
-    if (nbox >= INT32_MAX / 4) {
-        lm_set_error("build_tree: %lld boxes is beyond this build", (long long)nbox);
-        return LM_ENOTSUP;
-    }
     A.nbox = nbox;
     A.lev_start = B.lev_start;
     t->L = (int)A.lev_start.size() - 2;
     // boxes: geometry, links, point ranges; points in tree order
     std::vector<double> bcx(nbox), bcy(nbox), bw(nbox), xs(n), ys(n);
     std::vector<int32_t> par(nbox), pos(nbox), chl(4 * nbox), leaves, nonleaf;
-    std::vector<int64_t> perm(n), pstart(nbox + 1);
     A.hbox.resize(4 * nbox);
     A.nl_start.assign(1, 0);
-    int64_t at = 0;
     for (int64_t b = 0; b < nbox; ++b) {
         const HBox &h = B.box[b];
         const double w = ldexp(d, -h.level);
@@ -316,20 +349,12 @@ lm_status lm_setup_adaptive(lm_tree_s *t, const double *x, const double *y, cuda
         A.hbox[4 * b + 1] = h.col;
         A.hbox[4 * b + 2] = h.row;
         A.hbox[4 * b + 3] = h.leaf ? 1 : 0;
-        pstart[b] = at;
-        if (h.leaf) {
-            leaves.push_back((int32_t)b);
-            std::vector<int64_t> idx(B.order.begin() + h.lo, B.order.begin() + h.hi);
-            std::sort(idx.begin(), idx.end());
-            for (int64_t i : idx) {
-                perm[at] = i;
-                xs[at] = hx[i];
-                ys[at] = hy[i];
-                ++at;
-            }
-        }
+        if (h.leaf) leaves.push_back((int32_t)b);
     }
-    pstart[nbox] = at;
+    for (int64_t i = 0; i < n; ++i) {
+        xs[i] = hx[perm[i]];
+        ys[i] = hy[perm[i]];
+    }
     for (int l = 0; l <= t->L; ++l) {
         for (int64_t b = A.lev_start[l]; b < A.lev_start[l + 1]; ++b)
             if (!B.box[b].leaf) nonleaf.push_back((int32_t)b);
@@ -337,13 +362,6 @@ lm_status lm_setup_adaptive(lm_tree_s *t, const double *x, const double *y, cuda
     }
     A.nleaf = (int64_t)leaves.size();
     t->nleaf = A.nleaf;
-    // lists
-    std::vector<std::tuple<int64_t, int, int64_t>> V, U;
-    for (int64_t tb = 0; tb < t->R; ++tb)
-        for (int64_t sb = 0; sb < t->R; ++sb)
-            for (int m = 0; m < 5; ++m) B.visit(tb, sb, m, V, U);
-    std::sort(V.begin(), V.end());
-    std::sort(U.begin(), U.end());
     // V classes and CSR
     std::map<std::tuple<int, int, int, int64_t, int64_t>, int> cmap;
     std::vector<int64_t> vstart(nbox + 1, 0);
@@ -569,4 +587,47 @@ void lm_free_adaptive(lm_tree_s *t)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     A = AdaptTree();
+}
+
+extern "C" lm_status lm_adaptive_plan(const double *x, const double *y, int64_t n, double d, int leaf_target,
+                                      int depth, double *x_origin, int *R, int64_t *nbox, int64_t *boxes,
+                                      int64_t box_cap, int64_t *perm, int64_t *pstart, int64_t *nv,
+                                      int64_t *vrows, int64_t v_cap, int64_t *nu, int64_t *urows, int64_t u_cap)
+{
+    if (!x || !y || n < 1 || !isfinite(d) || !(d > 0.0) || leaf_target < 1 || depth < -1 || depth > 14 ||
+        box_cap < 0 || v_cap < 0 || u_cap < 0 || (box_cap > 0 && !boxes) || (v_cap > 0 && !vrows) ||
+        (u_cap > 0 && !urows)) {
+        lm_set_error("adaptive_plan: bad argument");
+        return LM_EINVAL;
+    }
+    Builder B;
+    std::vector<int64_t> hperm, hpstart;
+    Rows V, U;
+    lm_status s = plan(x, y, n, d, leaf_target, depth >= 0 ? depth : 14, "adaptive_plan", B, hperm, hpstart, V, U);
+    if (s != LM_OK) return s;
+    const int64_t nb = (int64_t)B.box.size();
+    if (x_origin) *x_origin = B.x0;
+    if (R) *R = B.R;
+    if (nbox) *nbox = nb;
+    if (nv) *nv = (int64_t)V.size();
+    if (nu) *nu = (int64_t)U.size();
+    for (int64_t b = 0; b < std::min(nb, box_cap); ++b) {
+        const HBox &h = B.box[b];
+        boxes[4 * b] = h.level;
+        boxes[4 * b + 1] = h.col;
+        boxes[4 * b + 2] = h.row;
+        boxes[4 * b + 3] = h.leaf ? 1 : 0;
+    }
+    if (perm) memcpy(perm, hperm.data(), n * sizeof(int64_t));
+    if (pstart && box_cap >= nb) memcpy(pstart, hpstart.data(), (nb + 1) * sizeof(int64_t));
+    auto put = [](const Rows &L, int64_t *out, int64_t cap) {
+        for (int64_t e = 0; e < std::min((int64_t)L.size(), cap); ++e) {
+            out[3 * e] = std::get<0>(L[e]);
+            out[3 * e + 1] = std::get<1>(L[e]);
+            out[3 * e + 2] = std::get<2>(L[e]);
+        }
+    };
+    put(V, vrows, v_cap);
+    put(U, urows, u_cap);
+    return LM_OK;
 }
