@@ -208,7 +208,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
 void lm_free_mixed(lm_tree_s *t);
 // tensor-core M2L (lmfmm_tc.cu)
 lm_status lm_setup_tc(lm_tree_s *t, cudaStream_t st);
-lm_status lm_launch_m2l_tc(lm_tree_s *t, int l, cudaStream_t st);
+lm_status lm_launch_m2l_tc(lm_tree_s *t, int l, cudaStream_t st, int nvs); // nvs: 4 or 16 vector slots
 template <typename T>
 lm_status lm_dalloc(lm_tree_s *t, T **p, size_t count)
 {

@@ -271,7 +271,7 @@ __global__ void k_inverse_perm(const int64_t *perm, int64_t n, int64_t *iperm)
 // S2M in FP32 (Eq. (multipole_coef), scaled): one block per leaf
 #define P2M32_CHUNK 32
 __global__ void k_p2m32(int P, float k, float w, const float *xl, const float *yl, const int64_t *ls,
-                        const zf *qs, zf *M)
+                        const zf *qs, int nvs, zf *M)
 {
     extern __shared__ unsigned char smem[];
     const int np = 2 * P + 1;
@@ -280,7 +280,7 @@ __global__ void k_p2m32(int P, float k, float w, const float *xl, const float *y
     const int64_t b = blockIdx.x;
     const int64_t lo = ls[b], hi = ls[b + 1];
     const float sc = k * w;
-    const int nent = np * LM_MAXV;
+    const int nent = np * nvs; // (order, vector) entries computed; M keeps 16 vector slots
     zf acc[8];
     for (int e = 0; e < 8; ++e) acc[e] = zf{0.f, 0.f};
     for (int64_t base = lo; base < hi; base += P2M32_CHUNK) {
@@ -316,7 +316,7 @@ __global__ void k_p2m32(int P, float k, float w, const float *xl, const float *y
         for (int e = 0; e < 8; ++e) {
             int idx = threadIdx.x + e * blockDim.x;
             if (idx >= nent) break;
-            int qi = idx / LM_MAXV, v = idx % LM_MAXV;
+            int qi = idx / nvs, v = idx % nvs;
             zf s = acc[e];
             for (int jj = 0; jj < cnt; ++jj) cfmaf(s, B[jj * np + qi], Q[jj * LM_MAXV + v]);
             acc[e] = s;
@@ -325,7 +325,7 @@ __global__ void k_p2m32(int P, float k, float w, const float *xl, const float *y
     for (int e = 0; e < 8; ++e) {
         int idx = threadIdx.x + e * blockDim.x;
         if (idx >= nent) break;
-        M[b * nent + idx] = acc[e];
+        M[(b * np + idx / nvs) * LM_MAXV + idx % nvs] = acc[e];
     }
 }
 
@@ -648,19 +648,22 @@ __device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
 // own before it is added (blocked FP32 accumulation).  Used by the rest-list
 // M2L, M2M (4 child entries) and L2L (1 parent entry).
 // ---------------------------------------------------------------------------
-template <int NP>
+// NVS: vector slots computed (16, or 4 for the batched form's 4-vector applies);
+// thread (v, g) of 128 owns vector v < NVS and rows g, g + NG, g + 2 NG, ...
+template <int NP, int NVS = LM_MAXV>
 struct Staged {
-    static constexpr int NR = (NP + 7) / 8;
+    static constexpr int NG = 128 / NVS; // row groups
+    static constexpr int NR = (NP + NG - 1) / NG;
     // two buffers while they fit the 48 KB of static shared memory (all orders but p = 24)
     static constexpr int NB = 2 * (NP * NP + NP * LM_MAXV) * 8 <= 48 * 1024 ? 2 : 1;
 };
-template <int NP, class EntryF>
+template <int NP, int NVS, class EntryF>
 __device__ __forceinline__ void staged_contract(int ne, EntryF entry, const zf *tab, const zf *M,
-                                                zf (&acc)[Staged<NP>::NR], zf (*Ts)[NP * NP],
+                                                zf (&acc)[Staged<NP, NVS>::NR], zf (*Ts)[NP * NP],
                                                 zf (*Ms)[NP * LM_MAXV])
 {
-    constexpr int NR = Staged<NP>::NR, NB = Staged<NP>::NB;
-    const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
+    constexpr int NR = Staged<NP, NVS>::NR, NB = Staged<NP, NVS>::NB, NG = Staged<NP, NVS>::NG;
+    const int v = threadIdx.x & (NVS - 1), g = threadIdx.x / NVS;
     auto stage = [&](int e, int buf) {
         int slot;
         int64_t src;
@@ -669,7 +672,10 @@ __device__ __forceinline__ void staged_contract(int ne, EntryF entry, const zf *
         const zf *T = tab + (int64_t)slot * NP * NP;
         for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) cp_async8(&Ts[buf][i], T + i);
         const zf *Mm = M + src * NP * LM_MAXV;
-        for (int i = threadIdx.x; i < NP * LM_MAXV / 2; i += blockDim.x) cp_async16(&Ms[buf][2 * i], Mm + 2 * i);
+        for (int i = threadIdx.x; i < NP * NVS / 2; i += blockDim.x) {
+            const int q = i / (NVS / 2), o = q * LM_MAXV + 2 * (i % (NVS / 2));
+            cp_async16(&Ms[buf][o], Mm + o);
+        }
     };
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = zf{0.f, 0.f};
@@ -701,7 +707,7 @@ __device__ __forceinline__ void staged_contract(int ne, EntryF entry, const zf *
             const zf m = Mb[q * LM_MAXV];
 #pragma unroll
             for (int r = 0; r < NR; ++r) {
-                const int p = g + 8 * r;
+                const int p = g + NG * r;
                 if (p < NP) cfmaf(tmp[r], Tb[p * NP + q], m);
             }
         }
@@ -713,12 +719,12 @@ __device__ __forceinline__ void staged_contract(int ne, EntryF entry, const zf *
 
 // Remaining V-list entries (level 0 and the image terms): one block per target
 // box with such entries; adds into L
-template <int NP>
+template <int NP, int NVS>
 __global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const int64_t *rstart,
                                                     const int32_t *rsrc, const int32_t *rslot, const zf *tab,
                                                     const zf *M, zf *Lc)
 {
-    constexpr int NR = Staged<NP>::NR, NB = Staged<NP>::NB;
+    constexpr int NR = Staged<NP, NVS>::NR, NB = Staged<NP, NVS>::NB, NG = Staged<NP, NVS>::NG;
     __shared__ __align__(16) zf Ts[NB][NP * NP];
     __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
     const int64_t b = rtgt[blockIdx.x];
@@ -728,11 +734,11 @@ __global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const i
         *src = rsrc[e0 + e];
     };
     zf acc[NR];
-    staged_contract<NP>((int)(rstart[b + 1] - e0), entry, tab, M, acc, Ts, Ms);
-    const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
+    staged_contract<NP, NVS>((int)(rstart[b + 1] - e0), entry, tab, M, acc, Ts, Ms);
+    const int v = threadIdx.x & (NVS - 1), g = threadIdx.x / NVS;
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
-        const int p = g + 8 * r;
+        const int p = g + NG * r;
         if (p < NP) {
             zf *o = Lc + (b * NP + p) * LM_MAXV + v;
             *o = *o + acc[r];
@@ -742,10 +748,10 @@ __global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const i
 
 // M2M (Lemma M2M): a parent (this level) from its four children (level l + 1),
 // table slot = child position (dy, dx); writes the parent's coefficients
-template <int NP>
+template <int NP, int NVS>
 __global__ void __launch_bounds__(128) k_m2m32(int64_t ncol, const zf *tabs, const zf *Mc, zf *Mp)
 {
-    constexpr int NR = Staged<NP>::NR, NB = Staged<NP>::NB;
+    constexpr int NR = Staged<NP, NVS>::NR, NB = Staged<NP, NVS>::NB, NG = Staged<NP, NVS>::NG;
     __shared__ __align__(16) zf Ts[NB][NP * NP];
     __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
     const int64_t b = blockIdx.x, r = b / ncol, c = b % ncol, ncc = 2 * ncol;
@@ -754,21 +760,21 @@ __global__ void __launch_bounds__(128) k_m2m32(int64_t ncol, const zf *tabs, con
         *src = (2 * r + (pos >> 1)) * ncc + 2 * c + (pos & 1);
     };
     zf acc[NR];
-    staged_contract<NP>(4, entry, tabs, Mc, acc, Ts, Ms);
-    const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
+    staged_contract<NP, NVS>(4, entry, tabs, Mc, acc, Ts, Ms);
+    const int v = threadIdx.x & (NVS - 1), g = threadIdx.x / NVS;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        const int p = g + 8 * k;
+        const int p = g + NG * k;
         if (p < NP) Mp[(b * NP + p) * LM_MAXV + v] = acc[k];
     }
 }
 
 // L2L (Lemma L2L): a child (this level) from its parent (level l - 1), table
 // slot = the child's position in the parent; writes the child's coefficients
-template <int NP>
+template <int NP, int NVS>
 __global__ void __launch_bounds__(128) k_l2l32(int64_t ncol, const zf *tabs, const zf *Lp, zf *Lc)
 {
-    constexpr int NR = Staged<NP>::NR, NB = Staged<NP>::NB;
+    constexpr int NR = Staged<NP, NVS>::NR, NB = Staged<NP, NVS>::NB, NG = Staged<NP, NVS>::NG;
     __shared__ __align__(16) zf Ts[NB][NP * NP];
     __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
     const int64_t b = blockIdx.x, r = b / ncol, c = b % ncol;
@@ -777,11 +783,11 @@ __global__ void __launch_bounds__(128) k_l2l32(int64_t ncol, const zf *tabs, con
         *src = (r / 2) * (ncol / 2) + c / 2;
     };
     zf acc[NR];
-    staged_contract<NP>(1, entry, tabs, Lp, acc, Ts, Ms);
-    const int v = threadIdx.x & (LM_MAXV - 1), g = threadIdx.x / LM_MAXV;
+    staged_contract<NP, NVS>(1, entry, tabs, Lp, acc, Ts, Ms);
+    const int v = threadIdx.x & (NVS - 1), g = threadIdx.x / NVS;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
-        const int p = g + 8 * k;
+        const int p = g + NG * k;
         if (p < NP) Lc[(b * NP + p) * LM_MAXV + v] = acc[k];
     }
 }
@@ -957,24 +963,35 @@ static void launch_stencil(const Level &lv, cudaStream_t st, int rg)
     if (rg == 8) return launch_stencil_rg<NP, 8>(lv, st);
     launch_stencil_rg<NP, 4>(lv, st);
 }
+// nvs: vector slots the apply computes (4 or 16)
 template <int P>
-static void launch_m2m(const Level &lv, const Level &child, cudaStream_t st)
+static void launch_m2m(const Level &lv, const Level &child, cudaStream_t st, int nvs)
 {
     constexpr int NP = 2 * P + 1;
-    k_m2m32<NP><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.m2m32, child.M32, lv.M32);
+    if (nvs == 4)
+        k_m2m32<NP, 4><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.m2m32, child.M32, lv.M32);
+    else
+        k_m2m32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.m2m32, child.M32, lv.M32);
 }
 template <int P>
-static void launch_l2l(const Level &lv, const Level &par, cudaStream_t st)
+static void launch_l2l(const Level &lv, const Level &par, cudaStream_t st, int nvs)
 {
     constexpr int NP = 2 * P + 1;
-    k_l2l32<NP><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
+    if (nvs == 4)
+        k_l2l32<NP, 4><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
+    else
+        k_l2l32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
 }
 template <int P>
-static void launch_rest(const Level &lv, cudaStream_t st)
+static void launch_rest(const Level &lv, cudaStream_t st, int nvs)
 {
     constexpr int NP = 2 * P + 1;
-    k_m2l_rest32<NP><<<(unsigned)lv.nrtgt, 128, 0, st>>>(lv.rtgt, lv.rstart, lv.rsrc, lv.rslot, lv.tab32,
-                                                       lv.M32, lv.L32);
+    if (nvs == 4)
+        k_m2l_rest32<NP, 4><<<(unsigned)lv.nrtgt, 128, 0, st>>>(lv.rtgt, lv.rstart, lv.rsrc, lv.rslot, lv.tab32,
+                                                              lv.M32, lv.L32);
+    else
+        k_m2l_rest32<NP, LM_MAXV><<<(unsigned)lv.nrtgt, 128, 0, st>>>(lv.rtgt, lv.rstart, lv.rsrc, lv.rslot,
+                                                                    lv.tab32, lv.M32, lv.L32);
 }
 template <int P>
 static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st, int nv)
@@ -1038,6 +1055,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
                  t->med.opt.top_bc != LM_BC_IMPEDANCE && t->med.opt.bottom_bc != LM_BC_IMPEDANCE};
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
+        const int nvs = nv <= 4 ? 4 : LM_MAXV; // vector slots the contractions compute
         lm_phase_begin(t, PH_PERMUTE, st);
         if (c64)
             k_permute_in32<zf><<<gridm(n, 256), 256, 0, st>>>((const zf *)q + (int64_t)v0 * n, t->iperm, n, nv,
@@ -1051,12 +1069,12 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
             Level &lv = t->lev[L];
             size_t shm = (P2M32_CHUNK * np + P2M32_CHUNK * LM_MAXV) * sizeof(zf);
             k_p2m32<<<(unsigned)lv.nbox, 128, shm, st>>>(P, k, (float)lv.w, t->xl32, t->yl32, t->leaf_start,
-                                                         t->qs32, lv.M32);
+                                                         t->qs32, nvs, lv.M32);
         }
         lm_phase_end(t, PH_S2M, st, 1);
         if (L > 0) lm_phase_begin(t, PH_M2M, st);
         for (int l = L - 1; l >= 0; --l) {
-            MX_DISPATCH(P, launch_m2m, t->lev[l], t->lev[l + 1], st);
+            MX_DISPATCH(P, launch_m2m, t->lev[l], t->lev[l + 1], st, nvs);
         }
         if (L > 0) lm_phase_end(t, PH_M2M, st, L);
         for (int l = 0; l <= L; ++l) {
@@ -1066,13 +1084,13 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
             if (l == 0)
                 LM_CUDA(cudaMemsetAsync(lv.L32, 0, lv.nbox * np * LM_MAXV * sizeof(zf), st));
             else
-                MX_DISPATCH(P, launch_l2l, lv, t->lev[l - 1], st);
+                MX_DISPATCH(P, launch_l2l, lv, t->lev[l - 1], st, nvs);
             lm_phase_end(t, PH_L2L, st, l > 0);
             lm_phase_begin(t, PH_M2L, st);
             int launches = 0;
             if (l > 0) {
                 if (lv.m2l_impl == 0 && t->tc_ready) {
-                    lm_status s = lm_launch_m2l_tc(t, l, st);
+                    lm_status s = lm_launch_m2l_tc(t, l, st, nvs);
                     if (s != LM_OK) return s;
                 } else {
                     MX_DISPATCH(P, launch_stencil, lv, st, lv.m2l_impl > 0 ? lv.m2l_impl : 4);
@@ -1080,7 +1098,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
                 ++launches;
             }
             if (lv.nrest > 0) {
-                MX_DISPATCH(P, launch_rest, lv, st);
+                MX_DISPATCH(P, launch_rest, lv, st, nvs);
                 ++launches;
             }
             lm_phase_end(t, PH_M2L, st, launches);
@@ -1144,7 +1162,7 @@ lm_status lm_autotune_mixed(lm_tree_s *t, cudaStream_t st, int *choice, float *m
         for (int ci = 0; ci < nc && status == LM_OK; ++ci) {
             lv.m2l_impl = cand[ci];
             auto run = [&]() -> lm_status {
-                if (cand[ci] == 0) return lm_launch_m2l_tc(t, l, st);
+                if (cand[ci] == 0) return lm_launch_m2l_tc(t, l, st, LM_MAXV);
                 MX_DISPATCH(P, launch_stencil, lv, st, cand[ci]);
                 return LM_OK;
             };

@@ -5,9 +5,10 @@
 //     [Re L; Im L] += [[Ar, -Ai], [Ai, Ar]] [Re M; Im M],
 // a real 2(2p+1)-square block matrix (2(2p+1) <= 64) applied to the source
 // multipoles of every (box, vector) column.  One CTA takes 8 target boxes of
-// one parity class x 16 vectors = 128 rows: D[128 x 64] (rows = columns of
-// the problem, 64 = padded real orders) accumulates K = 64 per offset in
-// tensor memory, over the (up to) 27 offsets of the class.
+// one parity class x 16 vectors = 128 rows (or, for applies of at most 4
+// vectors, 32 boxes x 4 vectors): D[128 x 64] (rows = columns of the problem,
+// 64 = padded real orders) accumulates K = 64 per offset in tensor memory,
+// over the (up to) 27 offsets of the class.
 //
 // Operands are staged in shared memory in the canonical K-major no-swizzle
 // layout (8-row x 16-byte core matrices; K-adjacent core matrices 128 B apart,
@@ -139,10 +140,12 @@ __device__ __forceinline__ void tc_commit(uint32_t mb)
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
 }
 
-template <int NP>
+// VB: log2 of the vector slots per box in a tile (4: 8 boxes x 16 vectors; 2: 32 boxes x 4 vectors)
+template <int NP, int VB>
 __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int64_t ncol, int64_t nrow, const int32_t *stencil,
                                                          const zf *tab, const zf *M, zf *Lc, int *err)
 {
+    constexpr int BOXES = TC_ROWS >> VB, VMASK = (1 << VB) - 1;
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char *stage = smem;
     uint64_t *mbar = (uint64_t *)(smem + TC_STAGE);
@@ -153,8 +156,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int64_t ncol, int64_t 
     const int cls = blockIdx.y, pc = cls & 1, pr = cls >> 1;
     const int64_t hc = ncol / 2, hr = nrow / 2;
     const int row = tid & (TC_ROWS - 1), h = tid >> 7;
-    const int lb = row >> 4, v = row & 15;
-    const int64_t cidx = (int64_t)blockIdx.x * 8 + lb;
+    const int lb = row >> VB, v = row & VMASK;
+    const int64_t cidx = (int64_t)blockIdx.x * BOXES + lb;
     const bool active = cidx < hc * hr;
     const int64_t c = 2 * (active ? cidx % hc : 0) + pc, r = 2 * (active ? cidx / hc : 0) + pr;
     const int quad = warp & 3, chalf = warp >> 2;
@@ -224,8 +227,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int64_t ncol, int64_t 
     if (ok && issued > 0) {
         fold();
         const int orow = 32 * quad + lane;
-        const int lb2 = orow >> 4, v2 = orow & 15;
-        const int64_t cidx2 = (int64_t)blockIdx.x * 8 + lb2;
+        const int lb2 = orow >> VB, v2 = orow & VMASK;
+        const int64_t cidx2 = (int64_t)blockIdx.x * BOXES + lb2;
         if (cidx2 < hc * hr) {
             const int64_t c2 = 2 * (cidx2 % hc) + pc, r2 = 2 * (cidx2 / hc) + pr;
             float *out = (float *)(Lc + (r2 * ncol + c2) * NP * LM_MAXV + v2);
@@ -248,17 +251,24 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_m2l_tc(int64_t ncol, int64_t 
 template <int NP>
 static lm_status attr_tc_np()
 {
-    LM_CUDA(cudaFuncSetAttribute(k_m2l_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    LM_CUDA(cudaFuncSetAttribute(k_m2l_tc<NP, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
+    LM_CUDA(cudaFuncSetAttribute(k_m2l_tc<NP, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM));
     return LM_OK;
 }
 
 template <int NP>
-static lm_status launch_tc_np(lm_tree_s *t, const Level &lv, cudaStream_t st)
+static lm_status launch_tc_np(lm_tree_s *t, const Level &lv, cudaStream_t st, int nvs)
 {
-    int64_t ncls = (lv.ncol / 2) * (lv.nrow / 2);
-    dim3 g((unsigned)((ncls + 7) / 8), 4);
-    k_m2l_tc<NP><<<g, TC_THREADS, TC_SMEM, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32, lv.M32, lv.L32,
-                                                  t->dflag + 1);
+    const int64_t ncls = (lv.ncol / 2) * (lv.nrow / 2);
+    if (nvs == 4) {
+        dim3 g((unsigned)((ncls + 31) / 32), 4);
+        k_m2l_tc<NP, 2><<<g, TC_THREADS, TC_SMEM, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32, lv.M32, lv.L32,
+                                                         t->dflag + 1);
+    } else {
+        dim3 g((unsigned)((ncls + 7) / 8), 4);
+        k_m2l_tc<NP, 4><<<g, TC_THREADS, TC_SMEM, st>>>(lv.ncol, lv.nrow, lv.stencil, lv.tab32, lv.M32, lv.L32,
+                                                         t->dflag + 1);
+    }
     return LM_OK;
 }
 
@@ -294,10 +304,10 @@ lm_status lm_setup_tc(lm_tree_s *t, cudaStream_t)
     return s;
 }
 
-lm_status lm_launch_m2l_tc(lm_tree_s *t, int l, cudaStream_t st)
+lm_status lm_launch_m2l_tc(lm_tree_s *t, int l, cudaStream_t st, int nvs)
 {
     const Level &lv = t->lev[l];
-    TC_SWITCH(t->p, launch_tc_np, t, lv, st);
+    TC_SWITCH(t->p, launch_tc_np, t, lv, st, nvs);
     lm_set_error("tensor-core M2L: order %d not instantiated", t->p);
     return LM_ENOTSUP;
 }

@@ -95,9 +95,10 @@ def test_batched_instances_match_oracle(lm, oracle):
 
 
 def test_few_vectors_match_full_width(lm):
-    """Applies of up to 4 vectors take the 4-vector leaf kernel; they agree with the
-    same vectors computed inside a 16-vector apply (same FP32 arithmetic per vector,
-    other kernels around it)."""
+    """Applies of up to 4 vectors take the 4-vector forms of every contraction (S2M,
+    M2M, L2L, rest-list and tensor-core M2L: 32 boxes x 4 vectors per tile; the leaf
+    kernel); they agree with the same vectors computed inside a 16-vector apply (the
+    same FP32 arithmetic per vector)."""
     import torch
 
     x, y, q = workloads.uniform_strip(60_000, 0.0, 8.0, -0.95, -0.05, nvec=16, seed=9)
@@ -105,5 +106,6 @@ def test_few_vectors_match_full_width(lm):
     t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     qd = torch.from_numpy(q).cuda()
     full = lm.apply(t, qd).cpu().numpy()
-    few = lm.apply(t, qd[:3].contiguous()).cpu().numpy()
-    assert np.linalg.norm(few - full[:3]) <= 1e-7 * np.linalg.norm(full[:3])
+    for nv in (3, 1):
+        few = lm.apply(t, qd[:nv].contiguous()).cpu().numpy()
+        assert np.linalg.norm(few - full[:nv]) <= 1e-7 * np.linalg.norm(full[:nv]), nv
