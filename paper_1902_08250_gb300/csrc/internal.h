@@ -94,6 +94,7 @@ struct Level {
     zd *M, *Lc;      // [nbox][np][LM_MAXV]
     // FP64 form, double-float M2L: tables and multipoles as (re hi, re lo, im hi, im lo)
     float4 *tabdf;   // [nclass][np][np]
+    float4 *tabdft;  // the same, each table transposed ([q][p])
     float4 *Mdf;     // [nbox][np][LM_MAXV], scaled by 2^-qexp
     float4 *m2mdf, *l2ldf; // [4][np][np] copies of m2m, l2l
     // mixed-precision copies (FP32, rounded from the FP64 tables)
@@ -134,7 +135,7 @@ struct AdaptTree {
     int32_t *vsrc = nullptr, *vslot = nullptr, *vterm = nullptr;
     zd *tab = nullptr;                                 // [nclass][np][np] scaled M2L tables
     zd *M = nullptr, *Lc = nullptr;                    // [nbox][np][LM_MAXV]
-    float4 *tabdf = nullptr, *Mdf = nullptr;           // double-float copies (as Level)
+    float4 *tabdf = nullptr, *tabdft = nullptr, *Mdf = nullptr; // double-float copies (as Level)
 };
 
 struct lm_tree_s {

@@ -583,7 +583,7 @@ void lm_free_adaptive(lm_tree_s *t)
     AdaptTree &A = t->at;
     void *ptrs[] = {A.cx,     A.cy,     A.w,      A.parent, A.pos,   A.child, A.leaves, A.nonleaf,
                     A.pwleaves, A.vstart, A.vsrc, A.vslot,  A.vterm, A.tab,   A.M,      A.Lc,
-                    A.tabdf,  A.Mdf};
+                    A.tabdf,  A.tabdft, A.Mdf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     A = AdaptTree();

@@ -280,6 +280,15 @@ __global__ void k_tab_df(const zd *tab, int64_t count, float4 *out)
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < count) out[i] = df_split(tab[i]);
 }
+// the same, each np x np table transposed ([q][p])
+__global__ void k_tab_df_t(const zd *tab, int64_t count, int np, float4 *out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t slot = i / ((int64_t)np * np);
+    const int r = (int)(i % ((int64_t)np * np)), p = r / np, q = r % np;
+    out[slot * np * np + (int64_t)q * np + p] = df_split(tab[i]);
+}
 
 // largest |re|, |im| of the densities [nvec][n] -> its binary exponent, max-reduced into *qexp
 __global__ void k_qexp(const zd *qs, int64_t n, int nvec, int *qexp)
@@ -315,7 +324,12 @@ __global__ void k_m_df(int64_t b0, int64_t nb, int P, int nvec, const zd *M, con
     Mdf[r] = df_split(zd{ldexp(a.re, e), ldexp(a.im, e)});
 }
 
-// M2L over the V list, double-float: one thread per (target box, order p, vector)
+// M2L over the V list, double-float: one thread per (target box, order p, vector).
+// TR: tables transposed ([q][p]).  With few vectors a warp spans 32 orders p of one
+// box, and the transposed rows make its table reads contiguous; with many vectors
+// a warp spans 2 orders, each thread reads its own row, and the row-major layout
+// keeps a thread's reads on few cache lines.
+template <bool TR>
 __global__ void __launch_bounds__(128) k_m2l_df(int64_t nbox, int P, int nvec, const int64_t *vstart,
                                                 const int32_t *vsrc, const int32_t *vslot, const float4 *tab,
                                                 const float4 *Mdf, const int *qexp, zd *Lc)
@@ -328,9 +342,10 @@ __global__ void __launch_bounds__(128) k_m2l_df(int64_t nbox, int P, int nvec, c
     const int64_t b = idx / (nvec * np);
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t e = vstart[b]; e < vstart[b + 1]; ++e) {
-        const float4 *T = tab + ((int64_t)vslot[e] * np + p) * np;
+        const float4 *T = tab + (int64_t)vslot[e] * np * np + (TR ? p : (int64_t)p * np);
+        const int ts = TR ? np : 1;
         const float4 *m = Mdf + (int64_t)vsrc[e] * np * LM_MAXV + v;
-        for (int q = 0; q < np; ++q) dfc_mac(acc, T[q], m[q * LM_MAXV]);
+        for (int q = 0; q < np; ++q) dfc_mac(acc, T[q * ts], m[q * LM_MAXV]);
     }
     const int ex = qexp_of(qexp);
     zd &o = Lc[(b * np + p) * LM_MAXV + v];
@@ -342,6 +357,7 @@ __global__ void __launch_bounds__(128) k_m2l_df(int64_t nbox, int P, int nvec, c
 // expansion (L2L) are converted once into shared memory, scaled by 2^-qexp;
 // each thread accumulates up to DF_MAXO outputs (order, vector).
 #define DF_THREADS 128
+#define DF_TR_NV 2 // applies of up to this many vectors read the transposed M2L tables
 #define DF_MAXO 13 // (2 * LM_MAXP + 1) * LM_MAXV / DF_THREADS, rounded up
 struct GridParents { // uniform tree: parent i of a level with ncol columns; children one level down
     int64_t ncol;
@@ -877,9 +893,12 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
                                                                    A.Lc);
             lm_phase_end(t, PH_L2L, st, l > 0);
             lm_phase_begin(t, PH_M2L, st);
-            if (A.lev_nv[l] > 0 && t->m2l_df)
-                k_m2l_df<<<gridn(nb * np * nv, 128), 128, 0, st>>>(nb, P, nv, A.vstart + b0, A.vsrc, A.vslot, A.tabdf,
-                                                                   A.Mdf, t->qexp, A.Lc + b0 * np * LM_MAXV);
+            if (A.lev_nv[l] > 0 && t->m2l_df && nv <= DF_TR_NV)
+                k_m2l_df<true><<<gridn(nb * np * nv, 128), 128, 0, st>>>(
+                    nb, P, nv, A.vstart + b0, A.vsrc, A.vslot, A.tabdft, A.Mdf, t->qexp, A.Lc + b0 * np * LM_MAXV);
+            else if (A.lev_nv[l] > 0 && t->m2l_df)
+                k_m2l_df<false><<<gridn(nb * np * nv, 128), 128, 0, st>>>(
+                    nb, P, nv, A.vstart + b0, A.vsrc, A.vslot, A.tabdf, A.Mdf, t->qexp, A.Lc + b0 * np * LM_MAXV);
             else if (A.lev_nv[l] > 0)
                 k_m2l64<<<gridn(nb * np * nv, 128), 128, 0, st>>>(nb, P, nv, A.vstart + b0, A.vsrc, A.vslot, A.tab,
                                                                   A.M, A.Lc + b0 * np * LM_MAXV);
@@ -978,9 +997,12 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
                                                          lv.Lc);
             lm_phase_end(t, PH_L2L, st, l > 0);
             lm_phase_begin(t, PH_M2L, st);
-            if (lv.nv > 0 && t->m2l_df)
-                k_m2l_df<<<gridn(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot, lv.tabdf,
-                                                          lv.Mdf, t->qexp, lv.Lc);
+            if (lv.nv > 0 && t->m2l_df && nv <= DF_TR_NV)
+                k_m2l_df<true><<<gridn(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot,
+                                                                lv.tabdft, lv.Mdf, t->qexp, lv.Lc);
+            else if (lv.nv > 0 && t->m2l_df)
+                k_m2l_df<false><<<gridn(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot,
+                                                                 lv.tabdf, lv.Mdf, t->qexp, lv.Lc);
             else if (lv.nv > 0)
                 k_m2l64<<<gridn(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot, lv.tab,
                                                          lv.M, lv.Lc);
@@ -1048,6 +1070,13 @@ lm_status lm_setup_df(lm_tree_s *t, cudaStream_t st)
         k_tab_df<<<gridn(cnt, 256), 256, 0, st>>>(tab, cnt, *out);
         return LM_OK;
     };
+    auto conv_t = [&](const zd *tab, int64_t ncls, float4 **out) -> lm_status {
+        const int64_t cnt = std::max<int64_t>(1, ncls) * np * np;
+        lm_status s = lm_dalloc(t, out, cnt);
+        if (s != LM_OK) return s;
+        k_tab_df_t<<<gridn(cnt, 256), 256, 0, st>>>(tab, cnt, np, *out);
+        return LM_OK;
+    };
     for (Level &lv : t->lev) {
         if (lv.m2m) {
             lm_status s = conv(lv.m2m, 4, &lv.m2mdf); // 4 child positions
@@ -1060,12 +1089,14 @@ lm_status lm_setup_df(lm_tree_s *t, cudaStream_t st)
     }
     if (t->adaptive) {
         lm_status s = conv(t->at.tab, (int64_t)t->at.cls_term.size(), &t->at.tabdf);
+        if (s == LM_OK) s = conv_t(t->at.tab, (int64_t)t->at.cls_term.size(), &t->at.tabdft);
         if (s != LM_OK) return s;
         s = lm_dalloc(t, &t->at.Mdf, (size_t)t->at.nbox * np * LM_MAXV);
         if (s != LM_OK) return s;
     } else {
         for (Level &lv : t->lev) {
             lm_status s = conv(lv.tab, (int64_t)lv.cls_term.size(), &lv.tabdf);
+            if (s == LM_OK) s = conv_t(lv.tab, (int64_t)lv.cls_term.size(), &lv.tabdft);
             if (s != LM_OK) return s;
             s = lm_dalloc(t, &lv.Mdf, (size_t)lv.nbox * np * LM_MAXV);
             if (s != LM_OK) return s;

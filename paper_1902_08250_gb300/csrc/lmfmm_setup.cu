@@ -856,7 +856,7 @@ void lm_free_tree_device(lm_tree_s *t)
         if (p) cudaFree(p);
     for (Level &lv : t->lev) {
         void *lp[] = {lv.vstart, lv.vsrc, lv.vslot, lv.vterm, lv.tab, lv.scale, lv.m2m, lv.l2l, lv.M, lv.Lc,
-                      lv.tabdf, lv.Mdf, lv.m2mdf, lv.l2ldf};
+                      lv.tabdf, lv.tabdft, lv.Mdf, lv.m2mdf, lv.l2ldf};
         for (void *p : lp)
             if (p) cudaFree(p);
     }

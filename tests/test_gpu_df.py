@@ -1,5 +1,6 @@
 """The FP64 form's double-float M2L, M2M and L2L (pairs of FP32 numbers on the
-FP32 pipes) against the IEEE FP64 contractions, on uniform and adaptive trees, and its
+FP32 pipes; M2L tables row-major, or transposed for applies of 1-2 vectors)
+against the IEEE FP64 contractions, on uniform and adaptive trees, and its
 exponent scaling over the whole FP64 range of density magnitudes."""
 import numpy as np
 import pytest
@@ -29,17 +30,18 @@ def _apply(lm, x, y, q, **opt):
     return lm.apply(t, torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy()
 
 
-@pytest.mark.parametrize("case", ["uniform", "adaptive", "dg_dd"])
+@pytest.mark.parametrize("case", ["uniform", "uniform1", "adaptive", "adaptive1", "dg_dd"])
 def test_df_m2l_matches_fp64_m2l(lm, case):
     """Same tree, same everything but the M2L arithmetic: the two results agree to
     the double-float rounding -- each of the ~1300 additions per output rounds the
     low word at 2^-48 of the partial sum, sqrt(1300) 2^-48 ~ 1.3e-13 -- far inside
     the 1e-10 bar against the oracle."""
-    if case == "adaptive":
-        x, y, q = workloads.clustered(6000, 3, seed=3)
+    nvec = 1 if case.endswith("1") else 5
+    if case.startswith("adaptive"):
+        x, y, q = workloads.clustered(6000, nvec, seed=3)
         opt = dict(p=20, adaptive=True, leaf_target=16)
     else:
-        x, y, q = workloads.uniform_strip(20000, 0.0, 4.0, -0.9, -0.1, nvec=3, seed=2)
+        x, y, q = workloads.uniform_strip(20000, 0.0, 4.0, -0.9, -0.1, nvec=nvec, seed=2)
         opt = dict(p=20, depth=3)
         if case == "dg_dd":
             opt["kernel"] = lm.KERNEL_DG_DD
@@ -54,7 +56,7 @@ def test_df_m2l_density_scale(lm):
     """u(s q) = s u(q) for s from 1e-200 to 1e200: the multipoles are rescaled by a
     power of two per apply, so FP32's exponent range never binds; zero densities
     give exactly zero."""
-    x, y, q = workloads.uniform_strip(5000, 0.0, 2.0, -0.9, -0.1, nvec=2, seed=4)
+    x, y, q = workloads.uniform_strip(5000, 0.0, 2.0, -0.9, -0.1, nvec=4, seed=4)
     opt = dict(p=16, depth=3)
     u1 = _apply(lm, x, y, q, **opt)
     for s in (1e-200, 1e-30, 1e30, 1e200):
