@@ -129,6 +129,7 @@ struct AdaptTree {
     int32_t *parent = nullptr, *pos = nullptr;         // [nbox] parent id (-1 for roots), child position
     int32_t *child = nullptr;                          // [nbox][4] (-1 for leaves)
     int32_t *leaves = nullptr, *nonleaf = nullptr, *pwleaves = nullptr; // box id lists
+    std::vector<int32_t> hpw;                          // host copy of pwleaves
     int64_t nv = 0;
     std::vector<int64_t> lev_nv;                       // [L + 1] V entries of the targets of level l
     int64_t *vstart = nullptr;                         // [nbox + 1] V list, target-major
@@ -164,6 +165,8 @@ struct lm_tree_s {
     zf *nq_seg_lam, *nq_seg_s2, *nq_seg_w, *nq_tail_lam, *nq_tail_s2, *nq_tail_w;
     bool tc_ready; // tensor-core M2L tables built
     bool near_pw64; // FP64 reflected near field: segment factorised per leaf (k_near_pw64)
+    int32_t *pwidx; // [boxes of the leaf level / of the tree] slot of an interface leaf, or -1
+    zd *pwC;        // [slots][2 terms][2 nseg][LM_MAXV] per-leaf segment coefficients (k_pw_src64)
     bool adaptive;  // boxes refined where the points are (AdaptTree), FP64 only
     AdaptTree at;
     int *dflag;  // device error flag
@@ -200,6 +203,7 @@ void lm_free_tree_device(lm_tree_s *t);
 lm_status lm_run_apply(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoint, cudaStream_t st);
 size_t lm_near_pw64_smem(int nseg);
 lm_status lm_near_pw64_attr(size_t bytes);
+lm_status lm_setup_pwsrc(lm_tree_s *t, cudaStream_t st); // interface-leaf slots and coefficient buffer
 lm_status lm_setup_df(lm_tree_s *t, cudaStream_t st); // double-float tables and multipole buffers
 lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, zd *uy, cudaStream_t st);
 // mixed precision (lmfmm_mixed.cu)

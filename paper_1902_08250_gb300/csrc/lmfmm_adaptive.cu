@@ -416,6 +416,18 @@ lm_status lm_setup_adaptive(lm_tree_s *t, const double *x, const double *y, cuda
     for (int64_t b = 0; b < nbox; ++b)
         if (haspw[b]) pwl.push_back((int32_t)b);
     A.npw = (int64_t)pwl.size();
+    A.hpw = pwl;
+    { // the factorised segment forms a source leaf's coefficients for the terms of its own entries, so
+      // every tt (bb) source leaf must have a tt (bb) entry itself (the lists are symmetric per term)
+        std::vector<char> hast(2 * (size_t)nbox, 0);
+        for (const auto &r : U)
+            if (std::get<1>(r) > 0) hast[2 * std::get<0>(r) + std::get<1>(r) - 1] = 1;
+        for (const auto &r : U)
+            if (std::get<1>(r) > 0 && !hast[2 * std::get<2>(r) + std::get<1>(r) - 1]) {
+                lm_set_error("build_tree: internal error, a reflected source leaf lacks an entry of that term");
+                return LM_ECUDA;
+            }
+    }
     // device copies
     TRY_A(upload(t, &A.cx, bcx, st));
     TRY_A(upload(t, &A.cy, bcy, st));

@@ -576,19 +576,77 @@ __global__ void __launch_bounds__(LEAF64_THREADS)
 // leaf's targets and adds to us.  One block per leaf of the top (and bottom) row.
 // ---------------------------------------------------------------------------
 #define PW64_SRC 64
-size_t lm_near_pw64_smem(int nseg) { return ((size_t)2 * nseg * LM_MAXV + PW64_SRC * LM_MAXV) * sizeof(zd) + 2 * PW64_SRC * sizeof(double); }
+size_t lm_near_pw64_smem(int nseg) { return (size_t)2 * nseg * LM_MAXV * sizeof(zd); }
+#define PW64_SRC_SMEM (PW64_SRC * LM_MAXV * sizeof(zd) + 2 * PW64_SRC * sizeof(double))
+// Phase A works per U entry through the source leaf's own coefficients: with
+// c_s the source leaf centre, x_j - x_T = (x_j - c_s) + (c_s - x_T), so
+//   C_{k,s}(S) = sum_{j in S} e^{-s i lambda_k (x_j - c_s)} E(y_j) q_j
+// is formed once per interface leaf and apply (k_pw_src64), and each U entry
+// adds e^{-s i lambda_k (c_s - x_T)} C_{k,s}(S): one exponential per node and
+// entry instead of one per node and source point.  An interface leaf's tt (bb)
+// sources are interface leaves themselves (the image adjacency is symmetric),
+// so every source has its coefficients; pwidx maps a box to its slot.
+template <class Geo>
+__global__ void __launch_bounds__(256) k_pw_src64(Geo geo, double d, const double *xs, const double *ys,
+                                                  const int64_t *ls, const int64_t *ustart, const int32_t *uterm,
+                                                  NearQuadD nq, const zd *qs, int64_t n, int nvec, zd *C)
+{
+    extern __shared__ unsigned char smem[];
+    const int nk = 2 * nq.nseg;
+    zd *SQ = (zd *)smem;                              // [PW64_SRC][LM_MAXV]
+    double *SX = (double *)(SQ + PW64_SRC * LM_MAXV); // [PW64_SRC]
+    double *SY = SX + PW64_SRC;                       // [PW64_SRC]
+    const int64_t slot = blockIdx.x, b = geo.id(slot);
+    double cs, ys_, ws;
+    geo.centre(b, &cs, &ys_, &ws);
+    for (int term = 1; term <= 2; ++term) {
+        bool any = false;
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) any |= (uterm[e] == term);
+        if (!any) continue; // block-uniform
+        const int m = term - 1;
+        zd *Cm = C + ((slot * 2 + m) * nk) * LM_MAXV;
+        for (int k = threadIdx.x; k < nk; k += blockDim.x)
+            for (int v = 0; v < nvec; ++v) Cm[k * LM_MAXV + v] = zd{0.0, 0.0};
+        for (int64_t j0 = ls[b]; j0 < ls[b + 1]; j0 += PW64_SRC) {
+            const int cnt = (int)min((int64_t)PW64_SRC, ls[b + 1] - j0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < cnt * nvec; t += blockDim.x) {
+                const int jj = t % cnt, v = t / cnt;
+                SQ[jj * LM_MAXV + v] = qs[(int64_t)v * n + j0 + jj];
+            }
+            for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+                SX[t] = xs[j0 + t] - cs;
+                SY[t] = ys[j0 + t];
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+                const zd lam = nq.seg_lam[k >> 1], s2 = nq.seg_s2[k >> 1];
+                const double sg = (k & 1) ? -1.0 : 1.0;
+                zd part[LM_MAXV];
+                for (int v = 0; v < nvec; ++v) part[v] = zd{0.0, 0.0};
+                for (int t = 0; t < cnt; ++t) {
+                    const double x = SX[t], y = SY[t];
+                    zd ex = {sg * lam.im * x, -sg * lam.re * x}; // -s i lambda (x_j - c_s)
+                    ex = ex + (m == 0 ? y * s2 : -(y + d) * s2);
+                    const zd f = cexpd(ex);
+                    for (int v = 0; v < nvec; ++v) cfma(part[v], f, SQ[t * LM_MAXV + v]);
+                }
+                for (int v = 0; v < nvec; ++v) Cm[k * LM_MAXV + v] = Cm[k * LM_MAXV + v] + part[v];
+            }
+        }
+    }
+}
+
 template <class Geo>
 __global__ void __launch_bounds__(256) k_near_pw64(Geo geo, double d, const double *xs,
                                                    const double *ys, const int64_t *ls, const int64_t *ustart,
                                                    const int32_t *usrc, const int32_t *uterm, NearQuadD nq,
-                                                   const zd *qs, int64_t n, int nvec, zd *us)
+                                                   const zd *qs, const zd *C, const int32_t *pwidx, int64_t n,
+                                                   int nvec, zd *us)
 {
     extern __shared__ unsigned char smem[];
     const int nk = 2 * nq.nseg;
     zd *B = (zd *)smem;                              // [nk][LM_MAXV]
-    zd *SQ = B + (size_t)nk * LM_MAXV;               // [PW64_SRC][LM_MAXV]
-    double *SX = (double *)(SQ + PW64_SRC * LM_MAXV); // [PW64_SRC]
-    double *SY = SX + PW64_SRC;                      // [PW64_SRC]
     const int64_t b = geo.id(blockIdx.x);
     double xT, yT, wT;
     geo.centre(b, &xT, &yT, &wT);
@@ -600,35 +658,19 @@ __global__ void __launch_bounds__(256) k_near_pw64(Geo geo, double d, const doub
         const zd *W = nq.seg_w + (int64_t)m * nq.nseg;
         __syncthreads();
         for (int k = threadIdx.x; k < nk * LM_MAXV; k += blockDim.x) B[k] = zd{0.0, 0.0};
+        __syncthreads();
         for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
             if (uterm[e] != term) continue;
             const int64_t s = usrc[e];
-            for (int64_t j0 = ls[s]; j0 < ls[s + 1]; j0 += PW64_SRC) {
-                const int cnt = (int)min((int64_t)PW64_SRC, ls[s + 1] - j0);
-                __syncthreads();
-                for (int t = threadIdx.x; t < cnt * nvec; t += blockDim.x) {
-                    const int jj = t % cnt, v = t / cnt;
-                    SQ[jj * LM_MAXV + v] = qs[(int64_t)v * n + j0 + jj];
-                }
-                for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-                    SX[t] = xs[j0 + t] - xT;
-                    SY[t] = ys[j0 + t];
-                }
-                __syncthreads();
-                for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-                    const zd lam = nq.seg_lam[k >> 1], s2 = nq.seg_s2[k >> 1];
-                    const double sg = (k & 1) ? -1.0 : 1.0;
-                    zd part[LM_MAXV];
-                    for (int v = 0; v < nvec; ++v) part[v] = zd{0.0, 0.0};
-                    for (int t = 0; t < cnt; ++t) {
-                        const double x = SX[t], y = SY[t];
-                        zd ex = {sg * lam.im * x, -sg * lam.re * x}; // -s i lambda x
-                        ex = ex + (m == 0 ? y * s2 : -(y + d) * s2);
-                        const zd f = cexpd(ex);
-                        for (int v = 0; v < nvec; ++v) cfma(part[v], f, SQ[t * LM_MAXV + v]);
-                    }
-                    for (int v = 0; v < nvec; ++v) B[k * LM_MAXV + v] = B[k * LM_MAXV + v] + part[v];
-                }
+            double cs, ysc, wsc;
+            geo.centre(s, &cs, &ysc, &wsc);
+            const double dx = cs - xT;
+            const zd *Cs = C + (((int64_t)pwidx[s] * 2 + m) * nk) * LM_MAXV;
+            for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+                const zd lam = nq.seg_lam[k >> 1];
+                const double sg = (k & 1) ? -1.0 : 1.0;
+                const zd f = cexpd(zd{sg * lam.im * dx, -sg * lam.re * dx}); // -s i lambda (c_s - x_T)
+                for (int v = 0; v < nvec; ++v) cfma(B[k * LM_MAXV + v], f, Cs[k * LM_MAXV + v]);
             }
         }
         __syncthreads();
@@ -921,10 +963,14 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
         const int pw = t->near_pw64 ? 1 : 0;
         k_leaf64<<<(unsigned)A.nleaf, LEAF64_THREADS, 0, st>>>(leaves, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart,
                                                    t->usrc, t->uterm, nq, A.Lc, t->qs, n, nv, free_on, pw, t->us);
-        if (pw && A.npw > 0)
+        if (pw && A.npw > 0) {
+            k_pw_src64<<<(unsigned)A.npw, 256, PW64_SRC_SMEM, st>>>(pwl, t->med.d, t->xs, t->ys, t->leaf_start,
+                                                                    t->ustart, t->uterm, nq, t->qs, n, nv, t->pwC);
             k_near_pw64<<<(unsigned)A.npw, 256, lm_near_pw64_smem(t->nq.nseg), st>>>(
-                pwl, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, t->qs, n, nv, t->us);
-        lm_phase_end(t, PH_LEAF, st, (pw && A.npw > 0) ? 2 : 1);
+                pwl, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, t->qs, t->pwC, t->pwidx,
+                n, nv, t->us);
+        }
+        lm_phase_end(t, PH_LEAF, st, (pw && A.npw > 0) ? 3 : 1);
         lm_phase_begin(t, PH_PERMUTE, st);
         k_permute_out<<<gridn(n, 256), 256, 0, st>>>(t->us, t->perm, n, nv, adjoint, u + (int64_t)v0 * n);
         lm_phase_end(t, PH_PERMUTE, st, 1);
@@ -1033,13 +1079,17 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             k_leaf64<<<(unsigned)lv.nbox, LEAF64_THREADS, 0, st>>>(GridLeaves{g}, P, k, t->med.d, t->xs, t->ys, t->leaf_start,
                                                        t->ustart, t->usrc, t->uterm, nq, lv.Lc, t->qs, n,
                                                        nv, free_on, pw, t->us);
-            if (pw)
-                k_near_pw64<<<(unsigned)(lv.nrow == 1 ? lv.ncol : 2 * lv.ncol), 256,
-                              lm_near_pw64_smem(t->nq.nseg), st>>>(EdgeRowLeaves{g, lv.nrow}, t->med.d, t->xs, t->ys,
-                                                                   t->leaf_start, t->ustart, t->usrc, t->uterm,
-                                                                   nq, t->qs, n, nv, t->us);
+            if (pw) {
+                const unsigned npw = (unsigned)(lv.nrow == 1 ? lv.ncol : 2 * lv.ncol);
+                const EdgeRowLeaves er{g, lv.nrow};
+                k_pw_src64<<<npw, 256, PW64_SRC_SMEM, st>>>(er, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart,
+                                                             t->uterm, nq, t->qs, n, nv, t->pwC);
+                k_near_pw64<<<npw, 256, lm_near_pw64_smem(t->nq.nseg), st>>>(
+                    er, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, t->qs, t->pwC,
+                    t->pwidx, n, nv, t->us);
+            }
         }
-        lm_phase_end(t, PH_LEAF, st, t->near_pw64 ? 2 : 1);
+        lm_phase_end(t, PH_LEAF, st, t->near_pw64 ? 3 : 1);
         lm_phase_begin(t, PH_PERMUTE, st);
         k_permute_out<<<gridn(n, 256), 256, 0, st>>>(t->us, t->perm, n, nv, adjoint, u + (int64_t)v0 * n);
         lm_phase_end(t, PH_PERMUTE, st, 1);
@@ -1104,4 +1154,31 @@ lm_status lm_setup_df(lm_tree_s *t, cudaStream_t st)
     }
     LM_CUDA(cudaGetLastError());
     return LM_OK;
+}
+
+// slots of the interface leaves (the blocks of k_pw_src64 / k_near_pw64) and their
+// per-apply plane-wave coefficients (FP64 form with the factorised segment)
+lm_status lm_setup_pwsrc(lm_tree_s *t, cudaStream_t st)
+{
+    if (!t->near_pw64) return LM_OK;
+    std::vector<int32_t> idx;
+    int64_t npw;
+    if (t->adaptive) {
+        idx.assign(t->at.nbox, -1);
+        npw = (int64_t)t->at.hpw.size();
+        for (int64_t i = 0; i < npw; ++i) idx[t->at.hpw[i]] = (int32_t)i;
+    } else {
+        const Level &lv = t->lev[t->L];
+        idx.assign(lv.nbox, -1);
+        npw = lv.nrow == 1 ? lv.ncol : 2 * lv.ncol;
+        for (int64_t i = 0; i < npw; ++i) { // the block order of EdgeRowLeaves
+            const int64_t row = (lv.nrow == 1 || i < lv.ncol) ? 0 : lv.nrow - 1;
+            idx[row * lv.ncol + i % lv.ncol] = (int32_t)i;
+        }
+    }
+    lm_status s = lm_dalloc(t, &t->pwidx, idx.size());
+    if (s != LM_OK) return s;
+    LM_CUDA(cudaMemcpyAsync(t->pwidx, idx.data(), idx.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    LM_CUDA(cudaStreamSynchronize(st)); // idx is a host temporary
+    return lm_dalloc(t, &t->pwC, (size_t)std::max<int64_t>(1, npw) * 2 * 2 * t->nq.nseg * LM_MAXV);
 }

@@ -675,6 +675,7 @@ lm_status lm_setup_near(lm_tree_s *t, cudaStream_t st)
     if (t->precision == LM_FP64 && pw <= 200 * 1024) {
         TRY(lm_near_pw64_attr(pw));
         t->near_pw64 = true;
+        TRY(lm_setup_pwsrc(t, st));
     }
     return LM_OK;
 }
@@ -850,7 +851,7 @@ void lm_free_tree_device(lm_tree_s *t)
     lm_free_mixed(t);
     lm_free_adaptive(t);
     void *ptrs[] = {t->xs, t->ys, t->perm, t->leaf_start, t->ustart, t->usrc, t->uterm, t->qs, t->us,
-                    t->dflag, t->qexp, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
+                    t->dflag, t->qexp, t->pwidx, t->pwC, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
                     t->nq.tail_w};
     for (void *p : ptrs)
         if (p) cudaFree(p);
