@@ -597,6 +597,7 @@ __global__ void __launch_bounds__(256) k_pw_src64(Geo geo, double d, const doubl
     double *SX = (double *)(SQ + PW64_SRC * LM_MAXV); // [PW64_SRC]
     double *SY = SX + PW64_SRC;                       // [PW64_SRC]
     const int64_t slot = blockIdx.x, b = geo.id(slot);
+    if (ls[b + 1] == ls[b]) return; // an empty leaf: its coefficients are never read
     double cs, ys_, ws;
     geo.centre(b, &cs, &ys_, &ws);
     for (int term = 1; term <= 2; ++term) {
@@ -648,6 +649,7 @@ __global__ void __launch_bounds__(256) k_near_pw64(Geo geo, double d, const doub
     const int nk = 2 * nq.nseg;
     zd *B = (zd *)smem;                              // [nk][LM_MAXV]
     const int64_t b = geo.id(blockIdx.x);
+    if (ls[b + 1] == ls[b]) return; // no targets (block-uniform)
     double xT, yT, wT;
     geo.centre(b, &xT, &yT, &wT);
     for (int term = 1; term <= 2; ++term) {
@@ -662,6 +664,7 @@ __global__ void __launch_bounds__(256) k_near_pw64(Geo geo, double d, const doub
         for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
             if (uterm[e] != term) continue;
             const int64_t s = usrc[e];
+            if (ls[s + 1] == ls[s]) continue; // no sources (uniform over the block)
             double cs, ysc, wsc;
             geo.centre(s, &cs, &ysc, &wsc);
             const double dx = cs - xT;
