@@ -73,6 +73,10 @@ struct NearQuad {
     // device arrays
     zd *seg_lam, *seg_s2, *seg_w;    // [nseg], [nseg], [2][nseg]: w * lambda' * sigma_m / s2 / 4pi
     zd *tail_lam, *tail_s2, *tail_w; // [nray][ntail], ..., [2 terms][P, M][nray][ntail] (see k_near_tail)
+    // FP64 target gradient: the differentiated tails decay more slowly and take their own,
+    // longer rule (ntail_g >= 64 points per ray), same layout
+    int ntail_g;
+    zd *tail_lam_g, *tail_s2_g, *tail_w_g;
 };
 
 struct Level {

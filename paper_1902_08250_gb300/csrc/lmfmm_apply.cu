@@ -887,6 +887,9 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
     const double k = t->med.k2;
     NearQuadD nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq.seg_lam, t->nq.seg_s2,
                  t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w};
+    // the target gradient integrates its differentiated tails with the longer rule
+    const NearQuadD nqg{t->nq.nseg, t->nq.nray, t->nq.ntail_g, t->nq.seg_lam, t->nq.seg_s2,
+                        t->nq.seg_w, t->nq.tail_lam_g, t->nq.tail_s2_g, t->nq.tail_w_g};
     const ListBoxes leaves{A.leaves, A.cx, A.cy, A.w}, pwl{A.pwleaves, A.cx, A.cy, A.w};
     const int free_on = t->med.opt.kernel == LM_KERNEL_G;
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
@@ -956,7 +959,7 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
             int ng = 0;
             for (int w0 = 0; w0 < nv; w0 += GV, ++ng)
                 k_leaf64_grad<<<(unsigned)A.nleaf, LEAF64_THREADS, 0, st>>>(
-                    leaves, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, A.Lc,
+                    leaves, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nqg, A.Lc,
                     t->qs, n, w0, std::min(GV, nv - w0), free_on, t->perm, u ? u + off + (int64_t)w0 * n : nullptr,
                     ux + off + (int64_t)w0 * n, uy + off + (int64_t)w0 * n);
             lm_phase_end(t, PH_LEAF, st, ng);
@@ -992,6 +995,9 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
     const double k = t->med.k2;
     NearQuadD nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq.seg_lam, t->nq.seg_s2,
                  t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w};
+    // the target gradient integrates its differentiated tails with the longer rule
+    const NearQuadD nqg{t->nq.nseg, t->nq.nray, t->nq.ntail_g, t->nq.seg_lam, t->nq.seg_s2,
+                        t->nq.seg_w, t->nq.tail_lam_g, t->nq.tail_s2_g, t->nq.tail_w_g};
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         lm_phase_begin(t, PH_PERMUTE, st);
@@ -1067,7 +1073,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             int nl = 0;
             for (int w0 = 0; w0 < nv; w0 += GV, ++nl)
                 k_leaf64_grad<<<(unsigned)lv.nbox, LEAF64_THREADS, 0, st>>>(
-                    GridLeaves{g}, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, lv.Lc,
+                    GridLeaves{g}, P, k, t->med.d, t->xs, t->ys, t->leaf_start, t->ustart, t->usrc, t->uterm, nqg, lv.Lc,
                     t->qs, n, w0, std::min(GV, nv - w0), free_on, t->perm,
                     u ? u + off + (int64_t)w0 * n : nullptr, ux + off + (int64_t)w0 * n,
                     uy + off + (int64_t)w0 * n);

@@ -668,6 +668,15 @@ lm_status lm_setup_near(lm_tree_s *t, cudaStream_t st)
     k_near_seg<<<grid_for(q.nseg, 64), 64, 0, st>>>(md, q.c, a, delta, nflat, order, q.seg_lam, q.seg_s2,
                                                      q.seg_w, q.nseg);
     k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2, q.tail_w);
+    if (t->precision == LM_FP64) {
+        q.ntail_g = std::max(64, q.ntail);
+        const int ng = q.nray * q.ntail_g;
+        TRY(dalloc(t, &q.tail_lam_g, ng));
+        TRY(dalloc(t, &q.tail_s2_g, ng));
+        TRY(dalloc(t, &q.tail_w_g, 4 * ng));
+        k_near_tail<<<grid_for(ng, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail_g, q.tail_lam_g, q.tail_s2_g,
+                                                      q.tail_w_g);
+    }
     LM_CUDA(cudaGetLastError());
     // FP64: factorise the segment per leaf when its coefficients fit in shared memory
     const size_t pw = lm_near_pw64_smem(q.nseg);
@@ -852,7 +861,7 @@ void lm_free_tree_device(lm_tree_s *t)
     lm_free_adaptive(t);
     void *ptrs[] = {t->xs, t->ys, t->perm, t->leaf_start, t->ustart, t->usrc, t->uterm, t->qs, t->us,
                     t->dflag, t->qexp, t->pwidx, t->pwC, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
-                    t->nq.tail_w};
+                    t->nq.tail_w, t->nq.tail_lam_g, t->nq.tail_s2_g, t->nq.tail_w_g};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (Level &lv : t->lev) {
