@@ -359,6 +359,11 @@ __global__ void __launch_bounds__(128) k_m2l_df(int64_t nbox, int P, int nvec, c
 #define DF_THREADS 128
 #define DF_TR_NV 2 // applies of up to this many vectors read the transposed M2L tables
 #define DF_MAXO 13 // (2 * LM_MAXP + 1) * LM_MAXV / DF_THREADS, rounded up
+// threads of a double-float M2M / L2L block: 64 while its outputs (M2M: one box, L2L: four children)
+// fit, else DF_THREADS
+static int df_threads(int nout) { return nout <= 64 ? 64 : DF_THREADS; }
+// threads of an S2M block: the (order, vector) entries rounded up to warps, 64 to 256
+static int p2m_threads(int nent) { return std::max(64, std::min(256, (nent + 31) / 32 * 32)); }
 struct GridParents { // uniform tree: parent i of a level with ncol columns; children one level down
     int64_t ncol;
     __device__ int64_t parent(int64_t i) const { return i; }
@@ -395,7 +400,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_m2m_df(Geo geo, int P, int nvec,
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < DF_MAXO; ++k) {
-            const int o = threadIdx.x + k * DF_THREADS;
+            const int o = threadIdx.x + k * blockDim.x;
             if (o < nout) {
                 const int p = o / nvec, v = o % nvec;
                 const float4 *T = tabs + ((int64_t)pos * np + p) * np;
@@ -405,7 +410,7 @@ __global__ void __launch_bounds__(DF_THREADS) k_m2m_df(Geo geo, int P, int nvec,
     }
 #pragma unroll
     for (int k = 0; k < DF_MAXO; ++k) {
-        const int o = threadIdx.x + k * DF_THREADS;
+        const int o = threadIdx.x + k * blockDim.x;
         if (o < nout)
             Mp[(b * np + o / nvec) * LM_MAXV + o % nvec] =
                 zd{ldexp((double)acc[k].x + (double)acc[k].y, e), ldexp((double)acc[k].z + (double)acc[k].w, e)};
@@ -904,7 +909,7 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
         // step 2: S2M at every leaf, M2M up the levels
         lm_phase_begin(t, PH_S2M, st);
         const size_t shm = (P2M_CHUNK * np + P2M_CHUNK * LM_MAXV) * sizeof(zd);
-        k_p2m64_list<<<(unsigned)A.nleaf, 256, shm, st>>>(leaves, P, k, t->xs, t->ys, t->leaf_start, t->qs, n, nv,
+        k_p2m64_list<<<(unsigned)A.nleaf, p2m_threads(np * nv), shm, st>>>(leaves, P, k, t->xs, t->ys, t->leaf_start, t->qs, n, nv,
                                                            A.M);
         lm_phase_end(t, PH_S2M, st, 1);
         int nl = 0;
@@ -913,7 +918,7 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
             const int64_t npar = A.nl_start[l + 1] - A.nl_start[l];
             if (npar == 0) continue;
             if (t->m2l_df)
-                k_m2m_df<<<(unsigned)npar, DF_THREADS, np * nv * sizeof(float4), st>>>(
+                k_m2m_df<<<(unsigned)npar, df_threads(np * nv), np * nv * sizeof(float4), st>>>(
                     ListParents{A.nonleaf + A.nl_start[l], A.child}, P, nv, t->lev[l].m2mdf, A.M, t->qexp, A.M);
             else
                 k_m2m64a<<<gridn(npar * np * nv, 128), 128, 0, st>>>(npar, A.nonleaf + A.nl_start[l], A.child, P,
@@ -934,7 +939,7 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
                 LM_CUDA(cudaMemsetAsync(A.Lc, 0, nb * np * LM_MAXV * sizeof(zd), st));
             else if (t->m2l_df) {
                 const int64_t npar = A.nl_start[l] - A.nl_start[l - 1]; // the parents of level l
-                k_l2l_df<<<(unsigned)npar, DF_THREADS, np * nv * sizeof(float4), st>>>(
+                k_l2l_df<<<(unsigned)npar, df_threads(4 * np * nv), np * nv * sizeof(float4), st>>>(
                     ListParents{A.nonleaf + A.nl_start[l - 1], A.child}, P, nv, t->lev[l].l2ldf, A.Lc, t->qexp, A.Lc);
             } else
                 k_l2l64a<<<gridn(nb * np * nv, 128), 128, 0, st>>>(b0, nb, A.parent, A.pos, P, nv, t->lev[l].l2l,
@@ -1013,7 +1018,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             Level &lv = t->lev[L];
             LeafGeom g{lv.ncol, t->x0, lv.w};
             size_t shm = (P2M_CHUNK * np + P2M_CHUNK * LM_MAXV) * sizeof(zd);
-            k_p2m64<<<(unsigned)lv.nbox, 256, shm, st>>>(g, P, k, t->xs, t->ys, t->leaf_start, t->qs, n,
+            k_p2m64<<<(unsigned)lv.nbox, p2m_threads(np * nv), shm, st>>>(g, P, k, t->xs, t->ys, t->leaf_start, t->qs, n,
                                                         nv, lv.M);
         }
         lm_phase_end(t, PH_S2M, st, 1);
@@ -1022,7 +1027,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             Level &lv = t->lev[l];
             int64_t tot = lv.nbox * np * nv;
             if (t->m2l_df)
-                k_m2m_df<<<(unsigned)lv.nbox, DF_THREADS, np * nv * sizeof(float4), st>>>(
+                k_m2m_df<<<(unsigned)lv.nbox, df_threads(np * nv), np * nv * sizeof(float4), st>>>(
                     GridParents{lv.ncol}, P, nv, lv.m2mdf, t->lev[l + 1].M, t->qexp, lv.M);
             else
                 k_m2m64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.m2m, t->lev[l + 1].M, lv.M);
@@ -1045,7 +1050,7 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
             if (l == 0)
                 LM_CUDA(cudaMemsetAsync(lv.Lc, 0, lv.nbox * np * LM_MAXV * sizeof(zd), st));
             else if (t->m2l_df)
-                k_l2l_df<<<(unsigned)t->lev[l - 1].nbox, DF_THREADS, np * nv * sizeof(float4), st>>>(
+                k_l2l_df<<<(unsigned)t->lev[l - 1].nbox, df_threads(4 * np * nv), np * nv * sizeof(float4), st>>>(
                     GridParents{t->lev[l - 1].ncol}, P, nv, lv.l2ldf, t->lev[l - 1].Lc, t->qexp, lv.Lc);
             else
                 k_l2l64<<<gridn(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.l2l, t->lev[l - 1].Lc,
