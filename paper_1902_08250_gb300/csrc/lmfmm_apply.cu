@@ -468,6 +468,52 @@ struct H0Series {
     }
 };
 __constant__ H0Series c_h0s = H0Series();
+// J1 and Y1 for the target gradient (A&S 9.1.10, 9.1.11 with n = 1):
+//   J1 = (x/2) sum_m (-z)^m / (m! (m+1)!),
+//   Y1 = -2/(pi x) + (2/pi) ln(x/2) J1 - (x/(2 pi)) sum_m (-z)^m (psi(m+1) + psi(m+2)) / (m! (m+1)!),
+// psi(m+1) = H_m - gamma; within 5e-16 of scipy's J1, Y1 on (0, 2]
+struct H1Series {
+    double c[H0S_TERMS], e[H0S_TERMS]; // (-1)^m / (m! (m+1)!), (-1)^m (psi(m+1) + psi(m+2)) / (m! (m+1)!)
+    constexpr H1Series() : c(), e()
+    {
+        double f = 1.0, h = 0.0; // 1/(m! (m+1)!), H_m
+        for (int m = 0; m < H0S_TERMS; ++m) {
+            if (m > 0) {
+                f /= (double)m * (double)(m + 1);
+                h += 1.0 / m;
+            }
+            const double psi = (h - 0.57721566490153286061) + (h + 1.0 / (m + 1) - 0.57721566490153286061);
+            c[m] = (m & 1) ? -f : f;
+            e[m] = (m & 1) ? -psi * f : psi * f;
+        }
+    }
+};
+__constant__ H1Series c_h1s = H1Series();
+// (i/4) H0^(1)(x) and (i/4) H1^(1)(x) together (series for x <= 2, else the library's)
+__device__ __forceinline__ void h01_free64(double x, zd *h0, zd *h1)
+{
+    if (x > 2.0) {
+        *h0 = zd{-0.25 * y0(x), 0.25 * j0(x)};
+        *h1 = zd{-0.25 * y1(x), 0.25 * j1(x)};
+        return;
+    }
+    const double z = 0.25 * x * x;
+    double j = c_h0s.cj[H0S_TERMS - 1], sy = c_h0s.cy[H0S_TERMS - 1];
+    double a = c_h1s.c[H0S_TERMS - 1], b = c_h1s.e[H0S_TERMS - 1];
+#pragma unroll
+    for (int m = H0S_TERMS - 2; m >= 0; --m) {
+        j = fma(j, z, c_h0s.cj[m]);
+        sy = fma(sy, z, c_h0s.cy[m]);
+        a = fma(a, z, c_h1s.c[m]);
+        b = fma(b, z, c_h1s.e[m]);
+    }
+    const double tpi = 0.63661977236758134308, lg = log(0.5 * x);
+    const double yv0 = tpi * ((lg + 0.57721566490153286061) * j + sy);
+    const double jv1 = 0.5 * x * a;
+    const double yv1 = -tpi / x + tpi * lg * jv1 - 0.5 * tpi * 0.5 * x * b;
+    *h0 = zd{-0.25 * yv0, 0.25 * j};
+    *h1 = zd{-0.25 * yv1, 0.25 * jv1};
+}
 __device__ __forceinline__ zd h0_free64(double x)
 {
     if (x > 2.0) return zd{-0.25 * y0(x), 0.25 * j0(x)};
@@ -876,8 +922,9 @@ __global__ void __launch_bounds__(LEAF64_THREADS) k_leaf64_grad(Geo geo, int P, 
                 if (term == 0) {
                     if (j == i) continue;
                     const double Dy = yi - ys[j], r = hypot(Dx, Dy);
-                    gv = zd{-0.25 * y0(k * r), 0.25 * j0(k * r)};                // (i/4) H0
-                    const zd dr = zd{0.25 * k * y1(k * r), -0.25 * k * j1(k * r)}; // (i/4)(-k) H1
+                    zd h1;
+                    h01_free64(k * r, &gv, &h1);    // (i/4) H0, (i/4) H1
+                    const zd dr = (-k) * h1;          // d/dr (i/4) H0(k r) = (i/4)(-k) H1
                     gx = (Dx / r) * dr;
                     gy = (Dy / r) * dr;
                 } else {
