@@ -67,7 +67,8 @@ typedef struct {
     int max_nvec;    /* largest nvec one apply processes at once (larger nvec is
                         processed in chunks); 0 -> 16 */
     int seg_order;   /* near-field contour: Gauss-Legendre points per segment panel; 0 -> 16 (FP64), 10 (mixed) */
-    int tail_order;  /* near-field tail: Gauss-Legendre points per ray; 0 -> 48 (FP64), 24 (mixed).
+    int tail_order;  /* near-field tail: Gauss-Legendre points per ray; 0 -> 48 (FP64; 192 with an
+                        impedance wall, whose reflection tends to 1 only like 1/lambda), 24 (mixed).
                         The FP64 target gradient (lm_apply_grad) integrates its differentiated
                         tails, which decay more slowly, with max(64, tail_order) points. */
     int tail_rays;   /* near-field tail: rays between the north and east directions; 0 -> 9 */

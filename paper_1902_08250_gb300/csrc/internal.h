@@ -77,6 +77,18 @@ struct NearQuad {
     // longer rule (ntail_g >= 64 points per ray), same layout
     int ntail_g;
     zd *tail_lam_g, *tail_s2_g, *tail_w_g;
+    // wall media: the tables integrate sigma - rinf; each pair adds rinf (i/4) H0(k2 rho_image)
+    double rinf[2];
+    // Between two walls the remainder sigma - rinf is carried by the multiple reflections,
+    // e^{-2 d s2}: images at height h + 2d.  Their integrand decays along the ray nearest
+    // atan2(X, h + 2d), not along the north ray that a pair close to a wall would pick
+    // from atan2(X, h), where e^{-2 d s2} only oscillates.  hray = 2d then, else 0.
+    double hray;
+    // FP64 with walls on both sides: tail_w holds the single reflection R - rinf (summed on
+    // the ray of atan2(X, h); identically zero for Dirichlet / Neumann walls, a_zero) and
+    // tail_w2 the multiple reflections sigma - R (ray of atan2(X, h + 2d)); same layout.
+    bool split, a_zero;
+    zd *tail_w2, *tail_w2_g;
 };
 
 struct Level {

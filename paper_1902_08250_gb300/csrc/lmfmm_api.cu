@@ -86,7 +86,11 @@ extern "C" lm_status lm_create_medium(double k1, double k2, double k3, double d,
     if (o.max_nvec <= 0) o.max_nvec = 16;
     if (o.seg_order <= 0) o.seg_order = o.precision == LM_MIXED ? 10 : 16;
     if (o.tail_rays <= 0) o.tail_rays = 9;
-    if (o.tail_order <= 0) o.tail_order = o.precision == LM_MIXED ? 24 : 48;
+    if (o.tail_order <= 0) {
+        // an impedance wall's reflection tends to 1 like 1/lambda: its tail converges more slowly
+        const bool imp = o.top_bc == LM_BC_IMPEDANCE || o.bottom_bc == LM_BC_IMPEDANCE;
+        o.tail_order = o.precision == LM_MIXED ? 24 : (imp ? 192 : 48);
+    }
     if (o.p < 1 || o.p > LM_MAXP) {
         lm_set_error("create_medium: p must be in 1..%d", LM_MAXP);
         return LM_EINVAL;

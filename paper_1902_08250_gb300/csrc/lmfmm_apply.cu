@@ -536,7 +536,31 @@ __device__ __forceinline__ zd h0_free64(double x)
 struct NearQuadD {
     int nseg, nray, ntail;
     const zd *seg_lam, *seg_s2, *seg_w, *tail_lam, *tail_s2, *tail_w;
+    double rinf[2]; // wall limit of sigma_tt, sigma_bb: the tables hold sigma - rinf (refl_inf)
+    double hray;    // added to h when the tail ray is chosen (see NearQuad)
+    const zd *tail_w2; // multiple-reflection tail weights (walls on both sides), else null
+    int a_zero;        // the single-reflection part tail_w is identically zero
+    double d2;         // 2d: the multiple reflections' extra image height
 };
+// tail ray nearest the steepest-descent direction of (X, h)
+__device__ __forceinline__ int tail_ray(const NearQuadD &q, double X, double h)
+{
+    return q.nray > 1 ? (int)rint(atan2(X, h) * (q.nray - 1) / (0.5 * M_PI)) : 0;
+}
+// sum P Re(E) + i M Im(E) over ray k of the weight table W (layout of NearQuad::tail_w)
+__device__ __forceinline__ zd tail_sum(const NearQuadD &q, const zd *W, int m, int k, double X, double h)
+{
+    const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
+    const int64_t tot = (int64_t)q.nray * q.ntail;
+    const zd *tP = W + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
+    zd acc = {0.0, 0.0};
+    for (int i = 0; i < q.ntail; ++i) {
+        const zd lam = tl[i], s2 = ts[i];
+        const zd e = cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
+        acc = acc + e.re * tP[i] + e.im * zd{-tM[i].im, tM[i].re};
+    }
+    return acc;
+}
 __device__ zd near_refl64(const NearQuadD &q, int m, double X, double h, bool seg = true)
 {
     zd acc = {0.0, 0.0};
@@ -549,16 +573,11 @@ __device__ zd near_refl64(const NearQuadD &q, int m, double X, double h, bool se
         zd e2 = cexpd(zd{er + lam.im * X, ei - lam.re * X});
         cfma(acc, W[i], e1 + e2);
     }
-    int k = q.nray > 1 ? (int)rint(atan2(X, h) * (q.nray - 1) / (0.5 * M_PI)) : 0;
-    const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
-    const int64_t tot = (int64_t)q.nray * q.ntail;
-    const zd *tP = q.tail_w + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
-    for (int i = 0; i < q.ntail; ++i) {
-        zd lam = tl[i], s2 = ts[i];
-        zd e = cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
-        acc = acc + e.re * tP[i] + e.im * zd{-tM[i].im, tM[i].re}; // P Re(E) + i M Im(E)
+    if (q.tail_w2) { // walls on both sides: single reflection on the ray of (X, h), multiples on (X, h + 2d)
+        if (!q.a_zero) acc = acc + tail_sum(q, q.tail_w, m, tail_ray(q, X, h), X, h);
+        return acc + tail_sum(q, q.tail_w2, m, tail_ray(q, X, h + q.d2), X, h);
     }
-    return acc;
+    return acc + tail_sum(q, q.tail_w, m, tail_ray(q, X, h + q.hray), X, h);
 }
 
 // ---------------------------------------------------------------------------
@@ -644,6 +663,8 @@ __global__ void __launch_bounds__(LEAF64_THREADS)
                     const double X = fabs(xi - xs[j]);
                     const double h = term == 1 ? -(yi + ys[j]) : yi + ys[j] + 2.0 * d;
                     gij = near_refl64(nq, term - 1, X, h, !pw); // segment added by k_near_pw64
+                    const double ri = nq.rinf[term - 1];
+                    if (ri != 0.0) gij = gij + ri * h0_free64(k * hypot(X, h)); // the wall's image, closed form
                 }
                 for (int v = 0; v < nvec; ++v) cfma(acc[v], gij, qs[(int64_t)v * n + j]);
             }
@@ -807,18 +828,27 @@ __device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, 
         cfma(a1, W[i] * zd{-lam.im, lam.re}, e1 - e2);
         cfma(a2, -1.0 * s2, we);
     }
-    int k = q.nray > 1 ? (int)rint(atan2(X, h) * (q.nray - 1) / (0.5 * M_PI)) : 0;
-    const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
-    const int64_t tot = (int64_t)q.nray * q.ntail;
-    const zd *tP = q.tail_w + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
-    for (int i = 0; i < q.ntail; ++i) {
-        zd lam = tl[i], s2 = ts[i];
-        const zd e = cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
-        const zd P = tP[i], iM = zd{-tM[i].im, tM[i].re};
-        const zd z1 = zd{-lam.im, lam.re} * e, z2 = -1.0 * (s2 * e); // i lam E, -s2 E
-        a0 = a0 + e.re * P + e.im * iM;
-        a1 = a1 + z1.re * P + z1.im * iM;
-        a2 = a2 + z2.re * P + z2.im * iM;
+    // the tail: one weight table on one ray, or (walls on both sides) single and multiple
+    // reflections on their own rays, as in near_refl64
+    auto tail = [&](const zd *Wt, int k) {
+        const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
+        const int64_t tot = (int64_t)q.nray * q.ntail;
+        const zd *tP = Wt + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
+        for (int i = 0; i < q.ntail; ++i) {
+            zd lam = tl[i], s2 = ts[i];
+            const zd e = cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
+            const zd P = tP[i], iM = zd{-tM[i].im, tM[i].re};
+            const zd z1 = zd{-lam.im, lam.re} * e, z2 = -1.0 * (s2 * e); // i lam E, -s2 E
+            a0 = a0 + e.re * P + e.im * iM;
+            a1 = a1 + z1.re * P + z1.im * iM;
+            a2 = a2 + z2.re * P + z2.im * iM;
+        }
+    };
+    if (q.tail_w2) {
+        if (!q.a_zero) tail(q.tail_w, tail_ray(q, X, h));
+        tail(q.tail_w2, tail_ray(q, X, h + q.d2));
+    } else {
+        tail(q.tail_w, tail_ray(q, X, h + q.hray));
     }
     *val = a0;
     *dX = a1;
@@ -932,6 +962,16 @@ __global__ void __launch_bounds__(LEAF64_THREADS) k_leaf64_grad(Geo geo, int P, 
                     const double h = term == 1 ? -(yi + ys[j]) : yi + ys[j] + 2.0 * d;
                     zd dX, dh;
                     near_refl64_grad(nq, term - 1, X, h, &gv, &dX, &dh);
+                    const double ri = nq.rinf[term - 1];
+                    if (ri != 0.0) { // the wall's image (i/4) H0(k rho), rho = |(X, h)|, and its derivatives
+                        const double rho = hypot(X, h);
+                        zd h0, h1;
+                        h01_free64(k * rho, &h0, &h1);
+                        const zd dr = (-k * ri / rho) * h1;
+                        gv = gv + ri * h0;
+                        dX = dX + X * dr;
+                        dh = dh + h * dr;
+                    }
                     gx = (Dx > 0.0 ? 1.0 : (Dx < 0.0 ? -1.0 : 0.0)) * dX;
                     gy = (term == 1 ? -1.0 : 1.0) * dh; // dh/dy: -1 (tt), +1 (bb)
                 }
@@ -980,10 +1020,13 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
     const int64_t n = t->n;
     const double k = t->med.k2;
     NearQuadD nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq.seg_lam, t->nq.seg_s2,
-                 t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w};
+                 t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w, {t->nq.rinf[0], t->nq.rinf[1]}, t->nq.hray,
+                 t->nq.tail_w2, t->nq.a_zero, 2.0 * t->med.d};
     // the target gradient integrates its differentiated tails with the longer rule
-    const NearQuadD nqg{t->nq.nseg, t->nq.nray, t->nq.ntail_g, t->nq.seg_lam, t->nq.seg_s2,
-                        t->nq.seg_w, t->nq.tail_lam_g, t->nq.tail_s2_g, t->nq.tail_w_g};
+    const NearQuadD nqg{t->nq.nseg,     t->nq.nray,       t->nq.ntail_g,   t->nq.seg_lam,
+                        t->nq.seg_s2,   t->nq.seg_w,      t->nq.tail_lam_g, t->nq.tail_s2_g,
+                        t->nq.tail_w_g, {t->nq.rinf[0], t->nq.rinf[1]}, t->nq.hray,
+                        t->nq.tail_w2_g, t->nq.a_zero, 2.0 * t->med.d};
     const ListBoxes leaves{A.leaves, A.cx, A.cy, A.w}, pwl{A.pwleaves, A.cx, A.cy, A.w};
     const int free_on = t->med.opt.kernel == LM_KERNEL_G;
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
@@ -1088,10 +1131,13 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
     const int64_t n = t->n;
     const double k = t->med.k2;
     NearQuadD nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq.seg_lam, t->nq.seg_s2,
-                 t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w};
+                 t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w, {t->nq.rinf[0], t->nq.rinf[1]}, t->nq.hray,
+                 t->nq.tail_w2, t->nq.a_zero, 2.0 * t->med.d};
     // the target gradient integrates its differentiated tails with the longer rule
-    const NearQuadD nqg{t->nq.nseg, t->nq.nray, t->nq.ntail_g, t->nq.seg_lam, t->nq.seg_s2,
-                        t->nq.seg_w, t->nq.tail_lam_g, t->nq.tail_s2_g, t->nq.tail_w_g};
+    const NearQuadD nqg{t->nq.nseg,     t->nq.nray,       t->nq.ntail_g,   t->nq.seg_lam,
+                        t->nq.seg_s2,   t->nq.seg_w,      t->nq.tail_lam_g, t->nq.tail_s2_g,
+                        t->nq.tail_w_g, {t->nq.rinf[0], t->nq.rinf[1]}, t->nq.hray,
+                        t->nq.tail_w2_g, t->nq.a_zero, 2.0 * t->med.d};
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         lm_phase_begin(t, PH_PERMUTE, st);

@@ -463,6 +463,9 @@ struct NearQuadF {
     int nseg, nray, ntail;
     const zf *seg_lam, *seg_s2, *seg_w, *tail_lam, *tail_s2, *tail_w;
     int sym; // sigma(conj lambda) = conj(sigma(lambda)) (no impedance wall): the tail is real
+    float rinf[2]; // wall limit of sigma_tt, sigma_bb: the tables hold sigma - rinf (refl_inf)
+    float hray;    // added to h when the tail ray is chosen (see NearQuad)
+    float k24;     // k2^2 / 4, for the wall image's closed form
 };
 // Tail of one reflected direct term (tt: m = 0, bb: m = 1) for a pair at
 // horizontal distance X and image height h: the rays lambda = c + t e^{i phi_k}
@@ -472,19 +475,24 @@ struct NearQuadF {
 // 128-register cap and slows the free-space loop by 9 % (measured).
 __device__ __noinline__ zf near_tail32(const NearQuadF &q, int m, float X, float h)
 {
-    int k = q.nray > 1 ? (int)rintf(atan2f(X, h) * (q.nray - 1) * 0.63661977236758134f) : 0;
+    int k = q.nray > 1 ? (int)rintf(atan2f(X, h + q.hray) * (q.nray - 1) * 0.63661977236758134f) : 0;
     const zf *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
     const int64_t tot = (int64_t)q.nray * q.ntail;
     const zf *tP = q.tail_w + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
     float re = 0.f, im = 0.f; // sum P Re(E) + i M Im(E)
-    if (q.sym) { // P real, M imaginary: only the real part survives
+    if (q.rinf[m] != 0.f) { // a wall's image (i/4) H0(k rho), rho = |(X, h)|, in closed form
+        const zf img = q.rinf[m] * green_free32_t(q.k24 * fmaf(X, X, h * h));
+        re = img.re;
+        im = img.im;
+    }
+    if (q.sym) { // P real, M imaginary: only the real part of the tail survives
         for (int i = 0; i < q.ntail; ++i) {
             zf lam = tl[i], s2 = ts[i];
             float a = expf(-lam.im * X - s2.re * h), sn, cs;
             sincosf(lam.re * X - s2.im * h, &sn, &cs);
             re += a * (tP[i].re * cs - tM[i].im * sn);
         }
-        return zf{re, 0.f};
+        return zf{re, im};
     }
     for (int i = 0; i < q.ntail; ++i) {
         zf lam = tl[i], s2 = ts[i];
@@ -1052,7 +1060,9 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
     const float k = (float)t->med.k2;
     NearQuadF nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w, t->nq_tail_lam,
                  t->nq_tail_s2, t->nq_tail_w,
-                 t->med.opt.top_bc != LM_BC_IMPEDANCE && t->med.opt.bottom_bc != LM_BC_IMPEDANCE};
+                 t->med.opt.top_bc != LM_BC_IMPEDANCE && t->med.opt.bottom_bc != LM_BC_IMPEDANCE,
+                 {(float)t->nq.rinf[0], (float)t->nq.rinf[1]}, (float)t->nq.hray,
+                 (float)(0.25 * t->med.k2 * t->med.k2)};
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         const int nvs = nv <= 4 ? 4 : LM_MAXV; // vector slots the contractions compute

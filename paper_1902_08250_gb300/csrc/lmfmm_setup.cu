@@ -308,11 +308,14 @@ __global__ void k_near_seg(MediumD m, double c, double a, double delta, int nfla
     zd base = cdiv((0.5 * w / (4.0 * M_PI)) * dz, s2);
     lam_o[i] = lam;
     s2_o[i] = s2;
-    w_o[i] = base * sig[0];
-    w_o[nseg + i] = base * sig[1];
+    w_o[i] = base * (sig[0] - zd{refl_inf(m, 0), 0.0});
+    w_o[nseg + i] = base * (sig[1] - zd{refl_inf(m, 1), 0.0});
 }
 
-__global__ void k_near_tail(MediumD m, double c, int nray, int order, zd *lam_o, zd *s2_o, zd *w_o)
+// With w2_o set (walls on both sides, FP64): w_o takes the single reflection R - R_inf
+// and w2_o the multiple reflections sigma - R, summed on different rays (see NearQuad).
+__global__ void k_near_tail(MediumD m, double c, int nray, int order, zd *lam_o, zd *s2_o, zd *w_o,
+                            zd *w2_o = nullptr)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int tot = nray * order;
@@ -333,7 +336,18 @@ __global__ void k_near_tail(MediumD m, double c, int nray, int order, zd *lam_o,
     lam_o[i] = lam;
     s2_o[i] = s2;
     for (int mm = 0; mm < 2; ++mm) {
-        const zd wu = bu * sig[mm], wl = bl * sigl[mm];
+        const zd ri = {refl_inf(m, mm), 0.0};
+        if (w2_o) {
+            const double kj = mm == 0 ? m.k1 : m.k3;
+            const zd r = refl_coef(m, mm, s2, sbranch(lam, kj), kj), rl = refl_coef(m, mm, s2l, sbranch(laml, kj), kj);
+            const zd au = bu * (r - ri), al = bl * (rl - ri), mu = bu * (sig[mm] - r), ml = bl * (sigl[mm] - rl);
+            w_o[((size_t)(2 * mm) * tot) + i] = au + al;
+            w_o[((size_t)(2 * mm + 1) * tot) + i] = au - al;
+            w2_o[((size_t)(2 * mm) * tot) + i] = mu + ml;
+            w2_o[((size_t)(2 * mm + 1) * tot) + i] = mu - ml;
+            continue;
+        }
+        const zd wu = bu * (sig[mm] - ri), wl = bl * (sigl[mm] - ri);
         w_o[((size_t)(2 * mm) * tot) + i] = wu + wl;     // P
         w_o[((size_t)(2 * mm + 1) * tot) + i] = wu - wl; // M
     }
@@ -650,6 +664,13 @@ lm_status lm_setup_near(lm_tree_s *t, cudaStream_t st)
                {t->med.opt.top_bc, t->med.opt.bottom_bc},
                {t->med.opt.top_alpha, t->med.opt.bottom_alpha}};
     NearQuad &q = t->nq;
+    q.rinf[0] = refl_inf(md, 0);
+    q.rinf[1] = refl_inf(md, 1);
+    const bool walls = !md.deriv && md.bc[0] != LM_BC_TRANSMISSION && md.bc[1] != LM_BC_TRANSMISSION;
+    const bool imp = md.bc[0] == LM_BC_IMPEDANCE || md.bc[1] == LM_BC_IMPEDANCE;
+    q.hray = (walls && !imp) ? 2.0 * md.d : 0.0; // single table (mixed form): shift only for constant R
+    q.split = walls && t->precision == LM_FP64;   // FP64: single and multiple reflections apart
+    q.a_zero = !imp;                              // Dirichlet / Neumann: R - R_inf = 0
     double km = fmax(md.k1, fmax(md.k2, md.k3)), kmin = fmin(md.k1, fmin(md.k2, md.k3));
     q.c = 1.5 * km + 1.0;
     double a = 0.5, delta = fmin(0.25, 0.5 * kmin);
@@ -667,15 +688,18 @@ lm_status lm_setup_near(lm_tree_s *t, cudaStream_t st)
     TRY(dalloc(t, &q.tail_w, 4 * nt));
     k_near_seg<<<grid_for(q.nseg, 64), 64, 0, st>>>(md, q.c, a, delta, nflat, order, q.seg_lam, q.seg_s2,
                                                      q.seg_w, q.nseg);
-    k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2, q.tail_w);
+    if (q.split) TRY(dalloc(t, &q.tail_w2, 4 * nt));
+    k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2, q.tail_w,
+                                                  q.split ? q.tail_w2 : nullptr);
     if (t->precision == LM_FP64) {
         q.ntail_g = std::max(64, q.ntail);
         const int ng = q.nray * q.ntail_g;
         TRY(dalloc(t, &q.tail_lam_g, ng));
         TRY(dalloc(t, &q.tail_s2_g, ng));
         TRY(dalloc(t, &q.tail_w_g, 4 * ng));
+        if (q.split) TRY(dalloc(t, &q.tail_w2_g, 4 * ng));
         k_near_tail<<<grid_for(ng, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail_g, q.tail_lam_g, q.tail_s2_g,
-                                                      q.tail_w_g);
+                                                      q.tail_w_g, q.split ? q.tail_w2_g : nullptr);
     }
     LM_CUDA(cudaGetLastError());
     // FP64: factorise the segment per leaf when its coefficients fit in shared memory
@@ -861,7 +885,8 @@ void lm_free_tree_device(lm_tree_s *t)
     lm_free_adaptive(t);
     void *ptrs[] = {t->xs, t->ys, t->perm, t->leaf_start, t->ustart, t->usrc, t->uterm, t->qs, t->us,
                     t->dflag, t->qexp, t->pwidx, t->pwC, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
-                    t->nq.tail_w, t->nq.tail_lam_g, t->nq.tail_s2_g, t->nq.tail_w_g};
+                    t->nq.tail_w, t->nq.tail_lam_g, t->nq.tail_s2_g, t->nq.tail_w_g, t->nq.tail_w2,
+                    t->nq.tail_w2_g};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (Level &lv : t->lev) {

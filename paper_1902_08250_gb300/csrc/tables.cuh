@@ -60,6 +60,23 @@ __device__ inline zd refl_coef(const MediumD &m, int b, zd s2, zd sj, double kj)
     }
     }
 }
+// Limit of the reflected density sigma_tt (b = 0) or sigma_bb (b = 1) as Re s2 -> inf
+// (Sigma -> 1): a wall's constant reflection coefficient (Dirichlet -1, Neumann and
+// impedance +1), 0 for a transmission (R ~ 1/lambda^2) and for the dG/dd kernel.  The
+// near-field quadratures integrate sigma - R_inf; the pair adds R_inf (i/4) H0(k2 rho)
+// of the image point in closed form (the Sommerfeld identity), since sigma -> R_inf
+// leaves an integrand decaying only like e^{-lambda h}/lambda: the image's log
+// singularity, which fixed rules cannot follow as the pair nears the wall.
+__host__ __device__ inline double refl_inf(const MediumD &m, int b)
+{
+    if (m.deriv) return 0.0;
+    switch (m.bc[b]) {
+    case LM_BC_DIRICHLET: return -1.0;
+    case LM_BC_NEUMANN:
+    case LM_BC_IMPEDANCE: return 1.0;
+    default: return 0.0;
+    }
+}
 __device__ inline void densities(const MediumD &m, zd lam, zd *s2o, zd sig[3])
 {
     zd s1 = sbranch(lam, m.k1), s2 = sbranch(lam, m.k2), s3 = sbranch(lam, m.k3);

@@ -164,3 +164,52 @@ def test_single_point_and_unrefined(lm, oracle):
 def test_adaptive_rejects_mixed(lm):
     with pytest.raises(lm.LMError):
         lm.create_medium(*MED_A, precision="mixed", adaptive=True)
+
+
+@pytest.mark.parametrize("media", [(("impedance", 0.7), ("impedance", -0.3)), (("neumann", 0.0), ("dirichlet", 0.0))])
+def test_adaptive_media_near_both_walls(lm, oracle, media):
+    """Walls in place of the interfaces (Sec. 3, Examples 2 and 3) on an adaptive tree
+    refined near both of them: points within 0.01 of y = 0 and of y = -d, the FMM
+    against the oracle's direct sum on 32 targets."""
+    import torch
+
+    (tb, ta), (bb, ba) = media
+    rng = np.random.default_rng(31)
+    n = 4000
+    x = rng.uniform(0.0, 3.0, n)
+    y = np.concatenate([-0.01 * (1.0 - rng.uniform(0.0, 1.0, n // 4)),
+                        -1.0 + 0.01 * (1.0 - rng.uniform(0.0, 1.0, n // 4)),
+                        rng.uniform(-0.9, -0.1, n - n // 2)])
+    q = rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n))
+    med = (1.0, 1.5, 2.0, 1.0)
+    m = lm.create_medium(*med, p=22, adaptive=True, leaf_target=16, top_bc=tb, top_alpha=ta, bottom_bc=bb,
+                         bottom_alpha=ba)
+    t = lm.build_tree(m, *_dev(x, y))
+    sub = np.sort(np.concatenate([rng.choice(n // 4, 12, replace=False), n // 4 + rng.choice(n // 4, 12, replace=False),
+                                  n // 2 + rng.choice(n - n // 2, 8, replace=False)]))
+    u = lm.apply(t, torch.from_numpy(q).cuda()).cpu().numpy()[:, sub]
+    try:
+        oracle.set_boundaries(tb, ta, bb, ba)
+        ref = oracle.direct_apply(med, x, y, q, targets=sub)
+    finally:
+        oracle.set_boundaries()
+    err = np.linalg.norm(u - ref) / np.linalg.norm(ref)
+    print(f"adaptive {tb}/{bb}: rel-l2 {err:.3e}")
+    assert err <= 1e-10
+
+
+def test_adaptive_vector_chunks(lm):
+    """18 vectors on an adaptive tree go as 16 + 2: each chunk equals the same
+    vectors applied alone (the 2-vector chunk bit for bit; the 16-vector chunk to
+    the double-float rounding, its M2L tables being read in the other layout)."""
+    import torch
+
+    x, y, q = workloads.clustered(5000, 18, seed=12)
+    t = _tree(lm, x, y, p=18, leaf_target=16)
+    qd = torch.from_numpy(q).cuda()
+    u = lm.apply(t, qd).cpu().numpy()
+    assert np.array_equal(u[16:], lm.apply(t, qd[16:].contiguous()).cpu().numpy())
+    u4 = lm.apply(t, qd[4:8].contiguous()).cpu().numpy()
+    assert np.array_equal(u[4:8], u4)
+    u1 = lm.apply(t, qd[5:6].contiguous()).cpu().numpy()
+    assert np.linalg.norm(u1[0] - u[5]) <= 1e-12 * np.linalg.norm(u[5])
