@@ -89,6 +89,11 @@ struct NearQuad {
     // tail_w2 the multiple reflections sigma - R (ray of atan2(X, h + 2d)); same layout.
     bool split, a_zero;
     zd *tail_w2, *tail_w2_g;
+    // FP64 with an impedance wall: weights of 2 i beta / s2 on the segment ([2][nseg]) and on
+    // the gradient's tail rays (layout of tail_w_g), which the gradient's h-derivative
+    // subtracts (imp_beta); beta = k2 alpha per wall, 0 without one
+    zd *seg_c, *tail_c_g;
+    double beta[2];
 };
 
 struct Level {

@@ -541,6 +541,10 @@ struct NearQuadD {
     const zd *tail_w2; // multiple-reflection tail weights (walls on both sides), else null
     int a_zero;        // the single-reflection part tail_w is identically zero
     double d2;         // 2d: the multiple reflections' extra image height
+    // the target gradient with an impedance wall: weights of 2 i beta / s2 on the segment and
+    // on the tail rays of tail_w, taken out of the h-derivative (null otherwise), and beta per wall
+    const zd *seg_c, *tail_c;
+    double beta[2];
 };
 // tail ray nearest the steepest-descent direction of (X, h)
 __device__ __forceinline__ int tail_ray(const NearQuadD &q, double X, double h)
@@ -818,6 +822,9 @@ __device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, 
 {
     zd a0 = {0.0, 0.0}, a1 = {0.0, 0.0}, a2 = {0.0, 0.0};
     const zd *W = q.seg_w + (int64_t)m * q.nseg;
+    // an impedance wall: the h-derivative sums (sigma - 1 - 2 i beta / s2) s2, whose
+    // integrand decays with e^{-lam h}; the caller adds the 2 i beta / s2 part in closed form
+    const zd *Cs = q.seg_c ? q.seg_c + (int64_t)m * q.nseg : nullptr;
     for (int i = 0; i < q.nseg; ++i) {
         zd lam = q.seg_lam[i], s2 = q.seg_s2[i];
         double er = -s2.re * h, ei = -s2.im * h;
@@ -826,14 +833,15 @@ __device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, 
         zd we = W[i] * (e1 + e2);
         a0 = a0 + we;
         cfma(a1, W[i] * zd{-lam.im, lam.re}, e1 - e2);
-        cfma(a2, -1.0 * s2, we);
+        cfma(a2, -1.0 * s2, Cs ? we - Cs[i] * (e1 + e2) : we);
     }
     // the tail: one weight table on one ray, or (walls on both sides) single and multiple
-    // reflections on their own rays, as in near_refl64
-    auto tail = [&](const zd *Wt, int k) {
+    // reflections on their own rays, as in near_refl64; Ct (or null) the correction on Wt's rays
+    auto tail = [&](const zd *Wt, const zd *Ct, int k) {
         const zd *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
         const int64_t tot = (int64_t)q.nray * q.ntail;
-        const zd *tP = Wt + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
+        const int64_t o = (2 * m) * tot + (int64_t)k * q.ntail;
+        const zd *tP = Wt + o, *tM = tP + tot;
         for (int i = 0; i < q.ntail; ++i) {
             zd lam = tl[i], s2 = ts[i];
             const zd e = cexpd(zd{-lam.im * X - s2.re * h, lam.re * X - s2.im * h});
@@ -841,14 +849,19 @@ __device__ void near_refl64_grad(const NearQuadD &q, int m, double X, double h, 
             const zd z1 = zd{-lam.im, lam.re} * e, z2 = -1.0 * (s2 * e); // i lam E, -s2 E
             a0 = a0 + e.re * P + e.im * iM;
             a1 = a1 + z1.re * P + z1.im * iM;
-            a2 = a2 + z2.re * P + z2.im * iM;
+            if (Ct) {
+                const zd cP = Ct[o + i], ciM = zd{-Ct[o + tot + i].im, Ct[o + tot + i].re};
+                a2 = a2 + z2.re * (P - cP) + z2.im * (iM - ciM);
+            } else {
+                a2 = a2 + z2.re * P + z2.im * iM;
+            }
         }
     };
     if (q.tail_w2) {
-        if (!q.a_zero) tail(q.tail_w, tail_ray(q, X, h));
-        tail(q.tail_w2, tail_ray(q, X, h + q.d2));
+        if (!q.a_zero) tail(q.tail_w, q.tail_c, tail_ray(q, X, h));
+        tail(q.tail_w2, nullptr, tail_ray(q, X, h + q.d2));
     } else {
-        tail(q.tail_w, tail_ray(q, X, h + q.hray));
+        tail(q.tail_w, q.tail_c, tail_ray(q, X, h + q.hray));
     }
     *val = a0;
     *dX = a1;
@@ -970,7 +983,7 @@ __global__ void __launch_bounds__(LEAF64_THREADS) k_leaf64_grad(Geo geo, int P, 
                         const zd dr = (-k * ri / rho) * h1;
                         gv = gv + ri * h0;
                         dX = dX + X * dr;
-                        dh = dh + h * dr;
+                        dh = dh + h * dr + zd{0.0, -2.0 * nq.beta[term - 1]} * h0; // -2 i beta (i/4) H0
                     }
                     gx = (Dx > 0.0 ? 1.0 : (Dx < 0.0 ? -1.0 : 0.0)) * dX;
                     gy = (term == 1 ? -1.0 : 1.0) * dh; // dh/dy: -1 (tt), +1 (bb)
@@ -1021,12 +1034,13 @@ static lm_status run_fp64_adaptive(lm_tree_s *t, const zd *q, int nvec, zd *u, b
     const double k = t->med.k2;
     NearQuadD nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq.seg_lam, t->nq.seg_s2,
                  t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w, {t->nq.rinf[0], t->nq.rinf[1]}, t->nq.hray,
-                 t->nq.tail_w2, t->nq.a_zero, 2.0 * t->med.d};
+                 t->nq.tail_w2, t->nq.a_zero, 2.0 * t->med.d, nullptr, nullptr, {0.0, 0.0}};
     // the target gradient integrates its differentiated tails with the longer rule
     const NearQuadD nqg{t->nq.nseg,     t->nq.nray,       t->nq.ntail_g,   t->nq.seg_lam,
                         t->nq.seg_s2,   t->nq.seg_w,      t->nq.tail_lam_g, t->nq.tail_s2_g,
                         t->nq.tail_w_g, {t->nq.rinf[0], t->nq.rinf[1]}, t->nq.hray,
-                        t->nq.tail_w2_g, t->nq.a_zero, 2.0 * t->med.d};
+                        t->nq.tail_w2_g, t->nq.a_zero, 2.0 * t->med.d,
+                        t->nq.seg_c, t->nq.tail_c_g, {t->nq.beta[0], t->nq.beta[1]}};
     const ListBoxes leaves{A.leaves, A.cx, A.cy, A.w}, pwl{A.pwleaves, A.cx, A.cy, A.w};
     const int free_on = t->med.opt.kernel == LM_KERNEL_G;
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
@@ -1132,12 +1146,13 @@ static lm_status run_fp64(lm_tree_s *t, const zd *q, int nvec, zd *u, bool adjoi
     const double k = t->med.k2;
     NearQuadD nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq.seg_lam, t->nq.seg_s2,
                  t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2, t->nq.tail_w, {t->nq.rinf[0], t->nq.rinf[1]}, t->nq.hray,
-                 t->nq.tail_w2, t->nq.a_zero, 2.0 * t->med.d};
+                 t->nq.tail_w2, t->nq.a_zero, 2.0 * t->med.d, nullptr, nullptr, {0.0, 0.0}};
     // the target gradient integrates its differentiated tails with the longer rule
     const NearQuadD nqg{t->nq.nseg,     t->nq.nray,       t->nq.ntail_g,   t->nq.seg_lam,
                         t->nq.seg_s2,   t->nq.seg_w,      t->nq.tail_lam_g, t->nq.tail_s2_g,
                         t->nq.tail_w_g, {t->nq.rinf[0], t->nq.rinf[1]}, t->nq.hray,
-                        t->nq.tail_w2_g, t->nq.a_zero, 2.0 * t->med.d};
+                        t->nq.tail_w2_g, t->nq.a_zero, 2.0 * t->med.d,
+                        t->nq.seg_c, t->nq.tail_c_g, {t->nq.beta[0], t->nq.beta[1]}};
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         lm_phase_begin(t, PH_PERMUTE, st);

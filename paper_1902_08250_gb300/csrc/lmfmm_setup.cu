@@ -281,8 +281,9 @@ __global__ void k_scan64(int64_t *c, int64_t m)
 //  transmission and Dirichlet/Neumann walls sigma(conj lambda) = conj(sigma)
 //  and the tail is real; an impedance wall makes it complex.
 // ---------------------------------------------------------------------------
+// c_o (optional, [2][nseg]): the weights of 2 i beta / s2 (imp_beta) for the gradient's h-derivative
 __global__ void k_near_seg(MediumD m, double c, double a, double delta, int nflat, int order,
-                           zd *lam_o, zd *s2_o, zd *w_o, int nseg)
+                           zd *lam_o, zd *s2_o, zd *w_o, int nseg, zd *c_o = nullptr)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nseg) return;
@@ -310,12 +311,15 @@ __global__ void k_near_seg(MediumD m, double c, double a, double delta, int nfla
     s2_o[i] = s2;
     w_o[i] = base * (sig[0] - zd{refl_inf(m, 0), 0.0});
     w_o[nseg + i] = base * (sig[1] - zd{refl_inf(m, 1), 0.0});
+    if (c_o)
+        for (int mm = 0; mm < 2; ++mm) c_o[mm * nseg + i] = base * cdiv(zd{0.0, 2.0 * imp_beta(m, mm)}, s2);
 }
 
 // With w2_o set (walls on both sides, FP64): w_o takes the single reflection R - R_inf
 // and w2_o the multiple reflections sigma - R, summed on different rays (see NearQuad).
+// c_o (optional, layout of w_o): P, M weights of 2 i beta / s2 for the gradient's h-derivative
 __global__ void k_near_tail(MediumD m, double c, int nray, int order, zd *lam_o, zd *s2_o, zd *w_o,
-                            zd *w2_o = nullptr)
+                            zd *w2_o = nullptr, zd *c_o = nullptr)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int tot = nray * order;
@@ -337,6 +341,12 @@ __global__ void k_near_tail(MediumD m, double c, int nray, int order, zd *lam_o,
     s2_o[i] = s2;
     for (int mm = 0; mm < 2; ++mm) {
         const zd ri = {refl_inf(m, mm), 0.0};
+        if (c_o) {
+            const zd tb = {0.0, 2.0 * imp_beta(m, mm)};
+            const zd cu = bu * cdiv(tb, s2), cl = bl * cdiv(tb, s2l);
+            c_o[((size_t)(2 * mm) * tot) + i] = cu + cl;
+            c_o[((size_t)(2 * mm + 1) * tot) + i] = cu - cl;
+        }
         if (w2_o) {
             const double kj = mm == 0 ? m.k1 : m.k3;
             const zd r = refl_coef(m, mm, s2, sbranch(lam, kj), kj), rl = refl_coef(m, mm, s2l, sbranch(laml, kj), kj);
@@ -686,8 +696,12 @@ lm_status lm_setup_near(lm_tree_s *t, cudaStream_t st)
     TRY(dalloc(t, &q.tail_lam, nt));
     TRY(dalloc(t, &q.tail_s2, nt));
     TRY(dalloc(t, &q.tail_w, 4 * nt));
+    const bool impc = t->precision == LM_FP64 && (imp_beta(md, 0) != 0.0 || imp_beta(md, 1) != 0.0);
+    q.beta[0] = imp_beta(md, 0);
+    q.beta[1] = imp_beta(md, 1);
+    if (impc) TRY(dalloc(t, &q.seg_c, 2 * q.nseg));
     k_near_seg<<<grid_for(q.nseg, 64), 64, 0, st>>>(md, q.c, a, delta, nflat, order, q.seg_lam, q.seg_s2,
-                                                     q.seg_w, q.nseg);
+                                                     q.seg_w, q.nseg, impc ? q.seg_c : nullptr);
     if (q.split) TRY(dalloc(t, &q.tail_w2, 4 * nt));
     k_near_tail<<<grid_for(nt, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail, q.tail_lam, q.tail_s2, q.tail_w,
                                                   q.split ? q.tail_w2 : nullptr);
@@ -698,8 +712,10 @@ lm_status lm_setup_near(lm_tree_s *t, cudaStream_t st)
         TRY(dalloc(t, &q.tail_s2_g, ng));
         TRY(dalloc(t, &q.tail_w_g, 4 * ng));
         if (q.split) TRY(dalloc(t, &q.tail_w2_g, 4 * ng));
+        if (impc) TRY(dalloc(t, &q.tail_c_g, 4 * ng));
         k_near_tail<<<grid_for(ng, 64), 64, 0, st>>>(md, q.c, q.nray, q.ntail_g, q.tail_lam_g, q.tail_s2_g,
-                                                      q.tail_w_g, q.split ? q.tail_w2_g : nullptr);
+                                                      q.tail_w_g, q.split ? q.tail_w2_g : nullptr,
+                                                      impc ? q.tail_c_g : nullptr);
     }
     LM_CUDA(cudaGetLastError());
     // FP64: factorise the segment per leaf when its coefficients fit in shared memory
@@ -886,7 +902,7 @@ void lm_free_tree_device(lm_tree_s *t)
     void *ptrs[] = {t->xs, t->ys, t->perm, t->leaf_start, t->ustart, t->usrc, t->uterm, t->qs, t->us,
                     t->dflag, t->qexp, t->pwidx, t->pwC, t->nq.seg_lam, t->nq.seg_s2, t->nq.seg_w, t->nq.tail_lam, t->nq.tail_s2,
                     t->nq.tail_w, t->nq.tail_lam_g, t->nq.tail_s2_g, t->nq.tail_w_g, t->nq.tail_w2,
-                    t->nq.tail_w2_g};
+                    t->nq.tail_w2_g, t->nq.seg_c, t->nq.tail_c_g};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (Level &lv : t->lev) {

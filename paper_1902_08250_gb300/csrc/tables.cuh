@@ -77,6 +77,14 @@ __host__ __device__ inline double refl_inf(const MediumD &m, int b)
     default: return 0.0;
     }
 }
+// k2 alpha of an impedance wall b (0 otherwise): R - 1 = 2 i beta / (s2 - i beta) ~ 2 i beta / s2.
+// The target gradient's h-derivative integrates (R - 1) s2 ~ 2 i beta, which does not decay
+// beyond e^{-lambda h}; it takes 2 i beta / s2 out of its integrand and adds the closed form
+// -2 i beta (i/4) H0(k2 rho) instead.
+__host__ __device__ inline double imp_beta(const MediumD &m, int b)
+{
+    return (!m.deriv && m.bc[b] == LM_BC_IMPEDANCE) ? m.k2 * m.alpha[b] : 0.0;
+}
 __device__ inline void densities(const MediumD &m, zd lam, zd *s2o, zd sig[3])
 {
     zd s1 = sbranch(lam, m.k1), s2 = sbranch(lam, m.k2), s3 = sbranch(lam, m.k3);

@@ -121,13 +121,12 @@ def test_media_near_the_walls(lm, oracle, name, prec, p, tol):
     assert err < tol
 
 
-@pytest.mark.parametrize("name", ["impedance_walls", "neumann_over_dirichlet"])
+@pytest.mark.parametrize("name", ["impedance_walls", "impedance_over_layer", "neumann_over_dirichlet"])
 def test_media_gradient_near_the_walls(lm, oracle, name):
     """The target gradient near the walls, with the closed-form image term's H1.
-    Known limit: beside an impedance wall the y-derivative of the single reflection
-    integrates (R - 1) s2 ~ 2 i beta, which does not decay beyond e^{-lambda h}; the
-    fixed tail rule leaves 1.6e-6 there at h ~ 0.01 (subtracting 2 i beta / s2 and
-    adding -2 i beta (i/4) H0 would close it).  Bound 1e-5 for that one component."""
+    Beside an impedance wall the y-derivative of the single reflection integrates
+    (R - 1) s2 ~ 2 i beta, which does not decay beyond e^{-lambda h}; the kernels take
+    2 i beta / s2 out of that integrand and add -2 i beta (i/4) H0(k2 rho) instead."""
     import torch
 
     x, y, q, sub = _near_walls(3000, 43)
@@ -141,6 +140,6 @@ def test_media_gradient_near_the_walls(lm, oracle, name):
             g = got.cpu().numpy()[:, sub]
             err = np.linalg.norm(g - ref) / np.linalg.norm(ref)
             print(f"near walls {name} gradient {der}: rel-l2 {err:.2e}")
-            assert err < (1e-5 if (name == "impedance_walls" and der == oracle.DY) else 1e-9)
+            assert err < 1e-9
     finally:
         oracle.set_boundaries()
