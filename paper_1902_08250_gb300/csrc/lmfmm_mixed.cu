@@ -417,33 +417,37 @@ __global__ void __launch_bounds__(64 * ((NP + RG - 1) / RG))
 // H_m the harmonic numbers, are evaluated by Horner's rule to degree 8
 // (truncation < 1e-11); no square root is needed.  Larger x use the
 // library's j0f / y0f.
+// the series branch alone (valid for t <= 1; finite for any t > 0)
+__device__ __forceinline__ zf green_free32_series(float t)
+{
+    // c_m and H_m c_m for m = 8 .. 1, from the series definitions
+    const float c8 = 6.15118733e-10f, c7 = -3.93675989e-08f, c6 = 1.92901235e-06f, c5 = -6.94444444e-05f,
+                c4 = 1.73611111e-03f, c3 = -2.77777778e-02f, c2 = 0.25f, c1 = -1.0f;
+    const float e8 = 1.67180484e-09f, e7 = -1.02074560e-07f, e6 = 4.72608025e-06f, e5 = -1.58564815e-04f,
+                e4 = 3.61689815e-03f, e3 = -5.09259259e-02f, e2 = 0.375f, e1 = -1.0f;
+    const float2 tt = make_float2(t, t);
+    float2 pp = __ffma2_rn(make_float2(c8, e8), tt, make_float2(c7, e7));
+    pp = __ffma2_rn(pp, tt, make_float2(c6, e6));
+    pp = __ffma2_rn(pp, tt, make_float2(c5, e5));
+    pp = __ffma2_rn(pp, tt, make_float2(c4, e4));
+    pp = __ffma2_rn(pp, tt, make_float2(c3, e3));
+    pp = __ffma2_rn(pp, tt, make_float2(c2, e2));
+    pp = __ffma2_rn(pp, tt, make_float2(c1, e1));
+    const float j = fmaf(pp.x, t, 1.0f);
+    const float sh = pp.y * t;
+    // MUFU logarithm: absolute error ~1e-7, well inside the 1e-6 budget
+    const float y = 0.63661977236758134f * (fmaf(0.5f, __logf(t), 0.57721566490153286f) * j - sh);
+    return zf{-0.25f * y, 0.25f * j};
+}
+// t > 1: the library's j0f / y0f
+__device__ __noinline__ zf green_free32_far(float t)
+{
+    const float x = 2.0f * sqrtf(t);
+    return zf{-0.25f * y0f(x), 0.25f * j0f(x)};
+}
 __device__ __forceinline__ zf green_free32_t(float t)
 {
-    float j, y;
-    if (t <= 1.0f) {
-        // c_m and H_m c_m for m = 8 .. 1, from the series definitions
-        const float c8 = 6.15118733e-10f, c7 = -3.93675989e-08f, c6 = 1.92901235e-06f, c5 = -6.94444444e-05f,
-                    c4 = 1.73611111e-03f, c3 = -2.77777778e-02f, c2 = 0.25f, c1 = -1.0f;
-        const float e8 = 1.67180484e-09f, e7 = -1.02074560e-07f, e6 = 4.72608025e-06f, e5 = -1.58564815e-04f,
-                    e4 = 3.61689815e-03f, e3 = -5.09259259e-02f, e2 = 0.375f, e1 = -1.0f;
-        const float2 tt = make_float2(t, t);
-        float2 pp = __ffma2_rn(make_float2(c8, e8), tt, make_float2(c7, e7));
-        pp = __ffma2_rn(pp, tt, make_float2(c6, e6));
-        pp = __ffma2_rn(pp, tt, make_float2(c5, e5));
-        pp = __ffma2_rn(pp, tt, make_float2(c4, e4));
-        pp = __ffma2_rn(pp, tt, make_float2(c3, e3));
-        pp = __ffma2_rn(pp, tt, make_float2(c2, e2));
-        pp = __ffma2_rn(pp, tt, make_float2(c1, e1));
-        j = fmaf(pp.x, t, 1.0f);
-        const float sh = pp.y * t;
-        // MUFU logarithm: absolute error ~1e-7, well inside the 1e-6 budget
-        y = 0.63661977236758134f * (fmaf(0.5f, __logf(t), 0.57721566490153286f) * j - sh);
-    } else {
-        const float x = 2.0f * sqrtf(t);
-        j = j0f(x);
-        y = y0f(x);
-    }
-    return zf{-0.25f * y, 0.25f * j};
+    return t <= 1.0f ? green_free32_series(t) : green_free32_far(t);
 }
 __device__ __forceinline__ zf green_free32(float x, int) { return green_free32_t(0.25f * x * x); }
 
@@ -805,8 +809,9 @@ struct LeafChunk {
 };
 
 // NV: vectors computed (4 or 16); buffers keep the 16-vector layout
+#define LEAF32_THREADS 64
 template <int P, int NV>
-__global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
+__global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
                                                   const float *yl, const float *y32, const int64_t *ls,
                                                   const int64_t *ustart, const int32_t *usrc, const int32_t *uterm,
                                                   NearQuadF nq, const zf *Lc, const zf *qs, zf *us, int nterms,
@@ -815,6 +820,7 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
     constexpr int NP = 2 * P + 1;
     __shared__ __align__(16) zf sq[2][LCAP * LM_MAXV];
     __shared__ float sx[2][LCAP], sy[2][LCAP], sya[2][LCAP];
+    __shared__ __align__(16) zf sacc[NV * LEAF32_THREADS]; // running sums per target and vector
     const int64_t b = blockIdx.x;
     const int rt = (int)(b / ncol), ct = (int)(b % ncol);
     const zf *Lb = Lc + b * NP * LM_MAXV;
@@ -860,93 +866,111 @@ __global__ void __launch_bounds__(64, 8) k_leaf32(int64_t ncol, float w, float k
         const int i = i0 + threadIdx.x;
         const bool act = i < hi;
         const float xi = act ? xl[i] : 0.f, yi = act ? yl[i] : 0.f, ya = act ? y32[i] : -0.5f;
-        zf acc[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = zf{0.f, 0.f};
+        zf *sa = sacc + threadIdx.x; // this target's running sums, vector v at sa[v * LEAF32_THREADS]
         if (nch > 0) {
             issue(0, 0);
             cp_commit();
         }
-        if (act) {
-            float r = sqrtf(xi * xi + yi * yi);
-            float J[P + 1];
-            bessel_j_scaled<float>(P, k * r, k * w, J);
-            zf z = r > 0.f ? zf{xi / r, yi / r} : zf{1.f, 0.f};
-            zf zp = {1.f, 0.f};
+        {
+            zf acc[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) cfmaf(acc[v], zf{J[0], 0.f}, Lb[P * LM_MAXV + v]);
-            for (int m = 1; m <= P; ++m) {
-                zp = zp * z;
-                zf bp = J[m] * zp;
-                zf bn = ((m & 1) ? -J[m] : J[m]) * conj(zp);
+            for (int v = 0; v < NV; ++v) acc[v] = zf{0.f, 0.f};
+            if (act) {
+                float r = sqrtf(xi * xi + yi * yi);
+                float J[P + 1];
+                bessel_j_scaled<float>(P, k * r, k * w, J);
+                zf z = r > 0.f ? zf{xi / r, yi / r} : zf{1.f, 0.f};
+                zf zp = {1.f, 0.f};
 #pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    cfmaf(acc[v], bp, Lb[(P + m) * LM_MAXV + v]);
-                    cfmaf(acc[v], bn, Lb[(P - m) * LM_MAXV + v]);
+                for (int v = 0; v < NV; ++v) cfmaf(acc[v], zf{J[0], 0.f}, Lb[P * LM_MAXV + v]);
+                for (int m = 1; m <= P; ++m) {
+                    zp = zp * z;
+                    zf bp = J[m] * zp;
+                    zf bn = ((m & 1) ? -J[m] : J[m]) * conj(zp);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        cfmaf(acc[v], bp, Lb[(P + m) * LM_MAXV + v]);
+                        cfmaf(acc[v], bn, Lb[(P - m) * LM_MAXV + v]);
+                    }
                 }
             }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) sa[v * LEAF32_THREADS] = acc[v];
         }
         for (int c = 0; c < nch; ++c) {
             const int buf = c & 1;
+            // chunk c has landed; past this barrier every thread is done with chunk c - 1,
+            // so its buffer takes chunk c + 1 (one barrier per chunk)
+            cp_wait<0>();
+            __syncthreads();
             if (c + 1 < nch) {
                 issue(c + 1, buf ^ 1);
                 cp_commit();
-                cp_wait<1>();
-            } else {
-                cp_wait<0>();
             }
-            __syncthreads();
             const LeafChunk ch = chunk_at(c);
             const int s = usrc[ch.e], term = uterm[ch.e];
             const int rs = s / (int)ncol, cs = s % (int)ncol;
             const float ox = (float)(ct - cs) * w, oy = -(float)(rt - rs) * w; // centre_t - centre_s
             if (act) {
-                zf part[NV];
+                // the chunk's sums on the paired FP32 pipe: A_v = sum g.re q_v and B_v = sum g.im q_v,
+                // each a (re, im) pair, so that g q_v = (A.x - B.y, A.y + B.x) at the end of the chunk
+                float2 A[NV], B[NV];
 #pragma unroll
-                for (int v = 0; v < NV; ++v) part[v] = zf{0.f, 0.f};
+                for (int v = 0; v < NV; ++v) A[v] = B[v] = make_float2(0.f, 0.f);
+                auto mac = [&](zf g, int jj) {
+                    const float2 gr = make_float2(g.re, g.re), gi = make_float2(g.im, g.im);
+                    const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
+#pragma unroll
+                    for (int v2 = 0; v2 < NV / 2; ++v2) {
+                        const float4 t = qj[v2];
+                        const float2 q0 = make_float2(t.x, t.y), q1 = make_float2(t.z, t.w);
+                        A[2 * v2] = __ffma2_rn(gr, q0, A[2 * v2]);
+                        B[2 * v2] = __ffma2_rn(gi, q0, B[2 * v2]);
+                        A[2 * v2 + 1] = __ffma2_rn(gr, q1, A[2 * v2 + 1]);
+                        B[2 * v2 + 1] = __ffma2_rn(gi, q1, B[2 * v2 + 1]);
+                    }
+                };
                 if (term == 0 && free_on) {
                     const int self = i - ch.j0; // this target's slot in the chunk, if it is a source here
-#pragma unroll 2
-                    for (int jj = 0; jj < ch.cnt; ++jj) {
+                    // the free-space self term is excluded: a dummy t = 1 keeps the
+                    // evaluation finite and the weight is zeroed
+                    auto targ = [&](int jj) {
                         const float dx = (xi - sx[buf][jj]) + ox, dy = (yi - sy[buf][jj]) + oy;
-                        // the free-space self term is excluded: a dummy t = 1 keeps the
-                        // evaluation finite and the weight is zeroed
-                        const float t2 = jj == self ? 1.0f : k24 * fmaf(dx, dx, dy * dy);
-                        zf g = green_free32_t(t2);
-                        if (jj == self) g = zf{0.f, 0.f};
-                        const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
-#pragma unroll
-                        for (int v2 = 0; v2 < NV / 2; ++v2) {
-                            const float4 t = qj[v2];
-                            cfmaf(part[2 * v2], g, zf{t.x, t.y});
-                            cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
-                        }
+                        return jj == self ? 1.0f : k24 * fmaf(dx, dx, dy * dy);
+                    };
+                    // software pipeline: the series of pair jj + 1 is evaluated in the same
+                    // basic block as the multiply-adds of pair jj, so its serial Horner chain
+                    // overlaps them; the rare far-argument branch comes after them
+                    float tn = targ(0);
+                    zf gn = tn <= 1.0f ? green_free32_series(tn) : green_free32_far(tn);
+                    for (int jj = 0; jj < ch.cnt; ++jj) {
+                        const zf g = jj == self ? zf{0.f, 0.f} : gn;
+                        tn = targ(min(jj + 1, ch.cnt - 1));
+                        gn = green_free32_series(tn);
+                        mac(g, jj);
+                        if (tn > 1.0f) gn = green_free32_far(tn);
                     }
                 } else if (term != 0) {
                     for (int jj = 0; jj < ch.cnt; ++jj) {
                         // tail of a reflected direct term; its segment part is added by k_near_pw32
                         const float dx = (xi - sx[buf][jj]) + ox;
                         const float h = term == 1 ? -(ya + sya[buf][jj]) : ya + sya[buf][jj] + 2.0f * d;
-                        const zf g = near_tail32(nq, term - 1, fabsf(dx), h);
-                        const float4 *qj = (const float4 *)&sq[buf][jj * LM_MAXV];
-#pragma unroll
-                        for (int v2 = 0; v2 < NV / 2; ++v2) {
-                            const float4 t = qj[v2];
-                            cfmaf(part[2 * v2], g, zf{t.x, t.y});
-                            cfmaf(part[2 * v2 + 1], g, zf{t.z, t.w});
-                        }
+                        mac(near_tail32(nq, term - 1, fabsf(dx), h), jj);
                     }
                 }
 #pragma unroll
-                for (int v = 0; v < NV; ++v) acc[v] = acc[v] + part[v];
+                for (int v = 0; v < NV; ++v)
+                    sa[v * LEAF32_THREADS] = sa[v * LEAF32_THREADS] + zf{A[v].x - B[v].y, A[v].y + B[v].x};
             }
-            __syncthreads(); // buffer `buf` is refilled by the issue of chunk c + 2
         }
+        __syncthreads(); // the next pass of targets refills buffer 0
         if (act) {
             float4 *o = (float4 *)(us + (int64_t)i * LM_MAXV);
 #pragma unroll
-            for (int v2 = 0; v2 < NV / 2; ++v2)
-                o[v2] = make_float4(acc[2 * v2].re, acc[2 * v2].im, acc[2 * v2 + 1].re, acc[2 * v2 + 1].im);
+            for (int v2 = 0; v2 < NV / 2; ++v2) {
+                const zf a0 = sa[2 * v2 * LEAF32_THREADS], a1 = sa[(2 * v2 + 1) * LEAF32_THREADS];
+                o[v2] = make_float4(a0.re, a0.im, a1.re, a1.im);
+            }
         }
     }
 }
@@ -1009,12 +1033,12 @@ static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st, int 
     const int nterms = lm_h0_terms(t->med.k2 * lv.w * 2.0 * 1.4142135623730951 * 1.0001);
     const int free_on = t->med.opt.kernel == LM_KERNEL_G;
     if (nv <= 4) // the batched form's 4-vector applies: a quarter of the contraction
-        k_leaf32<P, 4><<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
+        k_leaf32<P, 4><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
                                                          t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart,
                                                          t->usrc, t->uterm, nq, lv.L32, t->qs32, t->us32, nterms,
                                                          free_on);
     else
-        k_leaf32<P, LM_MAXV><<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2,
+        k_leaf32<P, LM_MAXV><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2,
                                                                (float)t->med.d, t->xl32, t->yl32, t->y32,
                                                                t->leaf_start, t->ustart, t->usrc, t->uterm, nq,
                                                                lv.L32, t->qs32, t->us32, nterms, free_on);
