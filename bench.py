@@ -23,6 +23,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -40,7 +41,7 @@ PHASES = ["permute", "s2m", "m2m", "m2l", "l2l", "l2t_s2t", "refine"]
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
@@ -76,9 +77,15 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.skip = 0
+        # raw samples: $LM_CLOCKS_DIR if set, else the temporary directory
+        d = os.environ.get("LM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(d, f"lmfmm_clocks_rank{index}_{os.getpid()}.csv")
 
     def start(self):
+        """Start sampling and wait (up to 3 s) for the sampler's first line, so that
+        the region that follows is covered; lines written before it is entered are
+        left out of the summary."""
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -87,6 +94,15 @@ class Clocks:
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 3.0 and self.proc.poll() is None:
+            with open(self.path) as f:
+                n = sum(1 for _ in f)
+            if n:
+                self.skip = n
+                break
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -96,7 +112,9 @@ class Clocks:
         self.f.close()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for ln, line in enumerate(open(self.path)):
+            if ln < self.skip:
+                continue
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -189,9 +207,11 @@ def run_reference(args):
     for _ in range(args.warmup):
         cpu_baseline(x, y, q, med, budget_s=1.0, ntgt=cores)
     vals = []
+    # each step is a bounded sample: at most 6 s, and about 3 minutes over all steps
+    budget = min(6.0, 180.0 / max(1, args.steps))
     t0 = time.time()
     for _ in range(args.steps):
-        vals.append(cpu_baseline(x, y, q, med, budget_s=6.0, ntgt=cores))
+        vals.append(cpu_baseline(x, y, q, med, budget_s=budget, ntgt=cores))
     wall = time.time() - t0
     v = float(np.mean([c["value"] for c in vals]))
     line = {
