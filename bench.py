@@ -110,6 +110,11 @@ class Clocks:
         self.proc.terminate()
         self.proc.wait()
         self.f.close()
+        return self.summary()
+
+    def summary(self):
+        """Median SM clock, the maximum, and the throttle reasons seen in the samples
+        taken inside the region."""
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln, line in enumerate(open(self.path)):
