@@ -5,6 +5,7 @@
 // FP32 accumulation.  Points are handled in leaf-local FP32 coordinates so
 // that close pairs keep their relative accuracy.
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -932,24 +933,34 @@ __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, floa
                 };
                 if (term == 0 && free_on) {
                     const int self = i - ch.j0; // this target's slot in the chunk, if it is a source here
-                    // the free-space self term is excluded: a dummy t = 1 keeps the
-                    // evaluation finite and the weight is zeroed
-                    auto targ = [&](int jj) {
-                        const float dx = (xi - sx[buf][jj]) + ox, dy = (yi - sy[buf][jj]) + oy;
-                        return jj == self ? 1.0f : k24 * fmaf(dx, dx, dy * dy);
-                    };
+                    // the target relative to the source leaf's centre, once per chunk
+                    const float xo = xi + ox, yo = yi + oy;
                     // software pipeline: the series of pair jj + 1 is evaluated in the same
                     // basic block as the multiply-adds of pair jj, so its serial Horner chain
-                    // overlaps them; the rare far-argument branch comes after them
-                    float tn = targ(0);
-                    zf gn = tn <= 1.0f ? green_free32_series(tn) : green_free32_far(tn);
-                    for (int jj = 0; jj < ch.cnt; ++jj) {
-                        const zf g = jj == self ? zf{0.f, 0.f} : gn;
-                        tn = targ(min(jj + 1, ch.cnt - 1));
-                        gn = green_free32_series(tn);
-                        mac(g, jj);
-                        if (tn > 1.0f) gn = green_free32_far(tn);
-                    }
+                    // overlaps them; the rare far-argument branch comes after them.  Only the
+                    // chunk that holds the target itself tests for the self term, which is
+                    // excluded: a dummy t = 1 keeps the evaluation finite, the weight is zeroed.
+                    auto pairs = [&](auto has_self) {
+                        constexpr bool HS = decltype(has_self)::value;
+                        auto targ = [&](int jj) {
+                            const float dx = xo - sx[buf][jj], dy = yo - sy[buf][jj];
+                            const float t2 = k24 * fmaf(dx, dx, dy * dy);
+                            return (HS && jj == self) ? 1.0f : t2;
+                        };
+                        float tn = targ(0);
+                        zf gn = tn <= 1.0f ? green_free32_series(tn) : green_free32_far(tn);
+                        for (int jj = 0; jj < ch.cnt; ++jj) {
+                            const zf g = (HS && jj == self) ? zf{0.f, 0.f} : gn;
+                            tn = targ(min(jj + 1, ch.cnt - 1));
+                            gn = green_free32_series(tn);
+                            mac(g, jj);
+                            if (tn > 1.0f) gn = green_free32_far(tn);
+                        }
+                    };
+                    if (self >= 0 && self < ch.cnt)
+                        pairs(std::true_type{});
+                    else
+                        pairs(std::false_type{});
                 } else if (term != 0) {
                     for (int jj = 0; jj < ch.cnt; ++jj) {
                         // tail of a reflected direct term; its segment part is added by k_near_pw32
