@@ -450,7 +450,6 @@ __device__ __forceinline__ zf green_free32_t(float t)
 {
     return t <= 1.0f ? green_free32_series(t) : green_free32_far(t);
 }
-__device__ __forceinline__ zf green_free32(float x, int) { return green_free32_t(0.25f * x * x); }
 
 // terms of the J0/Y0 series needed for arguments up to xmax (truncation < 1e-9)
 int lm_h0_terms(double xmax)
