@@ -38,7 +38,7 @@ def _rank(rank, world, port, out):
 def test_max_over_ranks_and_whole_job_value():
     world = 2
     port = _free_port()
-    with mp.Manager() as mgr:
+    with mp.get_context("spawn").Manager() as mgr:   # no fork of this multi-threaded process
         out = mgr.dict()
         mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
         res = dict(out)
