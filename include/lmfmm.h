@@ -373,7 +373,11 @@ lm_status lm_apply_adjoint_c64(lm_tree t, const void *v, int nvec, void *w, void
  * The far field differentiates the local expansion (Eq. (local)) with
  * (d/dx +- i d/dy) J_n(kr) e^{i n theta} = -+k J_{n+-1}(kr) e^{i (n+-1) theta};
  * the free near field uses (i/4)(-k) H1(k r); the reflected near field
- * multiplies the Sommerfeld integrand by i lambda (x) and -s2 dh_m/dy (y).
+ * multiplies the Sommerfeld integrand by i lambda (x) and -s2 dh_m/dy (y),
+ * on tail rays of max(64, tail_order) points.  Beside a wall the image term
+ * R_inf (i/4) H0(k2 rho) and its H1 derivatives are added in closed form; an
+ * impedance wall (beta = k2 alpha) also moves the part 2 i beta / s2 of the
+ * y-derivative's integrand into the closed form -2 i beta (i/4) H0(k2 rho).
  * With reciprocity this gives every coordinate gradient of a misfit: for
  * J(u), g = dJ/d(Re u) + i dJ/d(Im u), dJ/dx_j = Re[conj(g_j) ux(q)_j +
  * q_j ux(conj g)_j] (and the same in y).
