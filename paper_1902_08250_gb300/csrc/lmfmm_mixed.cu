@@ -810,6 +810,8 @@ struct LeafChunk {
 
 // NV: vectors computed (4 or 16); buffers keep the 16-vector layout
 #define LEAF32_THREADS 64
+#define LEAF32_MAXE 64   // U entries whose source ranges are staged for the chunk table
+#define LEAF32_MAXCH 64  // chunks in the shared-memory chunk table
 template <int P, int NV>
 __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
                                                   const float *yl, const float *y32, const int64_t *ls,
@@ -844,13 +846,43 @@ __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, floa
         }
         return ch;
     };
-    int nch = 0;
-    for (int e = e0; e < e1; ++e) {
-        const int s = usrc[e];
-        nch += ((int)(ls[s + 1] - ls[s]) + LCAP - 1) / LCAP;
+    // the chunk table, built once per leaf in shared memory: each thread reads one U entry's
+    // source range, thread 0 lays the chunks out in list order; a list of more than
+    // LEAF32_MAXCH chunks falls back to chunk_at
+    __shared__ int cfirst[LEAF32_MAXE], ccount[LEAF32_MAXE];
+    __shared__ LeafChunk ctab[LEAF32_MAXCH];
+    __shared__ int s_nch, s_tabled;
+    const int ne = e1 - e0;
+    if (ne <= LEAF32_MAXE) {
+        for (int t = threadIdx.x; t < ne; t += blockDim.x) {
+            const int s = usrc[e0 + t];
+            cfirst[t] = (int)ls[s];
+            ccount[t] = (int)(ls[s + 1] - ls[s]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int n = 0;
+            for (int t = 0; t < ne; ++t)
+                for (int j = 0; j < ccount[t]; j += LCAP, ++n)
+                    if (n < LEAF32_MAXCH) ctab[n] = LeafChunk{e0 + t, cfirst[t] + j, min(LCAP, ccount[t] - j)};
+            s_nch = n;
+            s_tabled = n <= LEAF32_MAXCH;
+        }
+    } else if (threadIdx.x == 0) {
+        int n = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int s = usrc[e];
+            n += ((int)(ls[s + 1] - ls[s]) + LCAP - 1) / LCAP;
+        }
+        s_nch = n;
+        s_tabled = 0;
     }
+    __syncthreads();
+    const bool tabled = s_tabled != 0;
+    const int nch = s_nch;
+    auto chunk = [&](int c) { return tabled ? ctab[c] : chunk_at(c); };
     auto issue = [&](int c, int buf) {
-        const LeafChunk ch = chunk_at(c);
+        const LeafChunk ch = chunk(c);
         for (int t = threadIdx.x; t < ch.cnt * (NV / 2); t += blockDim.x) {
             const int j = t / (NV / 2), part = t % (NV / 2);
             cp_async16(&sq[buf][j * LM_MAXV + 2 * part], qs + (int64_t)(ch.j0 + j) * LM_MAXV + 2 * part);
@@ -907,7 +939,7 @@ __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, floa
                 issue(c + 1, buf ^ 1);
                 cp_commit();
             }
-            const LeafChunk ch = chunk_at(c);
+            const LeafChunk ch = chunk(c);
             const int s = usrc[ch.e], term = uterm[ch.e];
             const int rs = s / (int)ncol, cs = s % (int)ncol;
             const float ox = (float)(ct - cs) * w, oy = -(float)(rt - rs) * w; // centre_t - centre_s
