@@ -808,6 +808,15 @@ struct LeafChunk {
     int e, j0, cnt;
 };
 
+// Step 4 in FP32: L2T (Eq. (local)) and S2T for every target of a leaf, one
+// block per leaf, one thread per target.  The leaf's U list is cut into chunks
+// of at most LCAP source points (tabled once in shared memory); each chunk's
+// coordinates and densities are staged with cp.async, double-buffered, one
+// barrier per chunk.  A chunk's sums are kept apart from the running totals
+// (in shared memory) so that FP32 rounding grows with the chunk length, not the
+// list length.  Free pairs take (i/4) H0 from its series, evaluated one pair
+// ahead of the multiply-adds; reflected pairs add their tails (the segment part
+// comes from k_near_pw32).
 // NV: vectors computed (4 or 16); buffers keep the 16-vector layout
 #define LEAF32_THREADS 64
 #define LEAF32_MAXE 64   // U entries whose source ranges are staged for the chunk table
