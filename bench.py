@@ -110,7 +110,13 @@ class Clocks:
         self.proc.terminate()
         self.proc.wait()
         self.f.close()
-        return self.summary()
+        out = self.summary()
+        if not os.environ.get("LM_CLOCKS_DIR"):  # kept only where asked for
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
+        return out
 
     def summary(self):
         """Median SM clock, the maximum, and the throttle reasons seen in the samples
