@@ -655,8 +655,9 @@ def main():
     npc = 2 * P + 1
     peaks = measured_peaks()
     dom = max(phase_ms, key=phase_ms.get)
-    roof = roofline(lm, tree, dom, phase_ms[dom], npc, precision, dev, peaks)
-    roof_m2l = roofline(lm, tree, "m2l", phase_ms["m2l"], npc, precision, dev, peaks) if dom != "m2l" else None
+    mhz = ck.get("sm_mhz") if isinstance(ck, dict) else None
+    roof = roofline(lm, tree, dom, phase_ms[dom], npc, precision, dev, peaks, mhz)
+    roof_m2l = roofline(lm, tree, "m2l", phase_ms["m2l"], npc, precision, dev, peaks, mhz) if dom != "m2l" else None
 
     if rank != 0:
         return
@@ -706,7 +707,23 @@ def _probe(lm, kind, dev):
     return rate.value / 1e12
 
 
-def roofline(lm, tree, phase, ms, npc, precision, dev, peaks):
+FP32_LANES_PER_SM = 128      # FP32 FMA lanes per SM: 4 partitions x 32
+FP64_DENSE_TFLOPS = 1.25     # GB300 dense FP64, nominal
+SM_MAX_MHZ = 2070.0          # GB300 maximum SM clock
+
+
+def alu_peak(precision, n_sm, mhz=None):
+    """The ALU roofline denominator in TFLOP/s, from unit counts and clocks: FP32 FMA
+    lanes x 2 flop x SMs x SM clock (the clock sampled during the timed region, else the
+    maximum); FP64 at the part's nominal dense rate."""
+    if precision == "fp64":
+        return FP64_DENSE_TFLOPS, "nominal GB300 dense FP64"
+    mhz = float(mhz) if mhz else SM_MAX_MHZ
+    peak = n_sm * FP32_LANES_PER_SM * 2.0 * mhz * 1e6 / 1e12
+    return peak, f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz"
+
+
+def roofline(lm, tree, phase, ms, npc, precision, dev, peaks, mhz=None):
     """Algorithmic work of the dominant phase per apply over its measured time
     (CUDA events the library records on the launching stream)."""
     info = tree.info
@@ -731,15 +748,20 @@ def roofline(lm, tree, phase, ms, npc, precision, dev, peaks):
         U = tree.list_export(1)
         pairs = int(np.sum(cnt[U[:, 0]] * cnt[U[:, 2]])) - tree.n
         flops = 8.0 * NVEC * pairs + 8.0 * NVEC * npc * tree.n
-        peak = _probe(lm, 0 if precision == "fp64" else 1, dev)
+        import torch
+
+        peak, src = alu_peak(precision, torch.cuda.get_device_properties(dev).multi_processor_count, mhz)
+        probe = _probe(lm, 0 if precision == "fp64" else 1, dev)
         ach = flops / (ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": "k_leaf64" if precision == "fp64" else "k_leaf32 + k_near_pw32",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": recorded_traffic("l2t_s2t"),
                 "work": f"8 flop per complex MAC x 16 vectors over {pairs} direct pairs and (2p+1) local terms "
                         "per target (kernel evaluation itself not counted)",
-                "peak_source": "lm_peak_probe %s FMA chains on all SMs (measured live)" %
-                               ("FP64" if precision == "fp64" else "FP32")}
+                "peak_source": src,
+                "peak_probe": probe,
+                "peak_probe_source": "lm_peak_probe %s FMA chains on all SMs (measured live)" %
+                                     ("FP64" if precision == "fp64" else "FP32")}
     return {"bound": "alu", "kernel": phase, "achieved": None, "peak": None, "unit": "TFLOP/s",
             "frac": None, "traffic": recorded_traffic(phase), "phase_ms": ms}
 
