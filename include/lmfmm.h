@@ -172,8 +172,9 @@ lm_status lm_create_medium(double k1, double k2, double k3, double d, const lm_o
  * tree and its lists are built on the host (the points are copied back once);
  * tables, lists and expansions are on the device.
  * Errors: LM_EINVAL if a point is non-finite or not strictly inside
- * -d < y < 0; LM_ENOMEM; LM_ENOTSUP if a leaf holds more than 8192 points;
- * LM_ECUDA.
+ * -d < y < 0, or if the x extent needs more than 2^30 roots (checked in double
+ * precision before the count becomes an integer); LM_ENOMEM; LM_ENOTSUP if a
+ * leaf holds more than 8192 points; LM_ECUDA.
  */
 lm_status lm_build_tree(lm_medium m, const double *x, const double *y, int64_t n, void *stream,
                         lm_tree *out);
@@ -310,13 +311,19 @@ lm_status lm_peak_probe(int kind, int64_t iters, void *stream, double *rate);
  * Scratch: one file-scope device array of about 6.3 MB, resident on every GPU
  * that loads the library until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with
- * the device current.  The array is shared by all calls and keeps the last
+ * the device current, and caches it for the life of the process: after
+ * cudaDeviceReset (or a reset of the primary context) the module is loaded
+ * again, the array may move, and this entry point must not be called again
+ * in that process.  The array is shared by all calls and keeps the last
  * call's contents (the counters are cleared at the start of each call), so
  * calls whose device work overlaps -- on different streams or threads --
  * race and must be serialised by the caller.  Calls no cudaMalloc or
  * cudaFree and no allocating library routine.  Synchronises `stream`.
- * Errors: LM_EINVAL for sizes beyond the limits above, NULL pointers or
- * invalid points; LM_ENOTSUP if a leaf holds more than 8192 points; LM_ECUDA.
+ * Errors: LM_EINVAL for sizes beyond the limits above (the leaf count is
+ * checked in double precision before any integer conversion, so a huge x
+ * extent or a tiny d is rejected, not wrapped), a non-finite d, NULL
+ * pointers or invalid points; LM_ENOTSUP if a leaf holds more than 8192
+ * points; LM_ECUDA.
  */
 lm_status lm_tree_order_noalloc(const double *x, const double *y, int64_t n, double d, int depth,
                                 int64_t *perm, int64_t *leaf_start, int64_t leaf_cap, double *x_origin,
@@ -417,6 +424,19 @@ void lm_destroy_cross(lm_cross c);
  * otherwise.  Clears the recorded failure.
  */
 lm_status lm_sync_status(lm_tree t, void *stream);
+
+/*
+ * set_poll_limit -- failure-path check of the bounded waits (no counterpart
+ * in the paper).  For the next 16-vector apply of an LM_MIXED tree that runs
+ * the tile-form tensor-core M2L, the MMA issuer's first wait for its operands
+ * polls at most `limit` times (0: gives up at once) before it reports a
+ * timeout; every other wait, including the waits that let copies and MMAs in
+ * flight finish before tensor memory is freed, keeps the library's limit.
+ * The setting applies to one apply and is then cleared; limit < 0 clears it.
+ * That apply's result is invalid and lm_sync_status returns LM_ETIMEOUT.
+ * Errors: LM_EINVAL (NULL tree).
+ */
+lm_status lm_set_poll_limit(lm_tree t, int limit);
 
 void lm_destroy_tree(lm_tree t);
 void lm_destroy_medium(lm_medium m);

@@ -20,6 +20,8 @@
 #include <tuple>
 #include <vector>
 
+#include <cmath>
+
 #include "internal.h"
 #include "tables.cuh"
 
@@ -364,8 +366,15 @@ static lm_status cross_setup(lm_cross_s *c, const double *xs, const double *ys, 
     CTRY(cross_extent(c, xs, ym, c->ns, &mn, &mx, st));
     CTRY(cross_extent(c, xt, yt, c->nt, &mn, &mx, st));
     const double f0 = floor(mn / d), f1 = floor(mx / d);
+    // root count checked in double before it becomes an int
+    const double roots = f1 - f0 + 1.0;
+    if (!std::isfinite(roots) || roots < 1.0 || roots > (double)(1 << 30)) {
+        lm_set_error("build_cross: the x extent spans %g layer thicknesses; at most 2^30 roots are supported",
+                     roots);
+        return LM_EINVAL;
+    }
     c->x0 = f0 * d;
-    c->R = (int)(f1 - f0) + 1;
+    c->R = (int)roots;
     const int64_t nmax = std::max(c->ns, c->nt);
     if (c->med.opt.depth >= 0) {
         c->L = c->med.opt.depth;

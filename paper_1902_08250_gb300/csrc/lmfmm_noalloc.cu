@@ -5,7 +5,9 @@
 // GPU that loads the library holds it until the process exits.  Host code
 // never dereferences or passes the array's name: on first use on a device
 // (with that device current) the entry point asks the runtime for the
-// array's device address and caches it per device.
+// array's device address and caches it per device.  A device reset reloads
+// the module and may move the array, so the cache is not valid across one.
+#include <cmath>
 #include <mutex>
 
 #include "internal.h"
@@ -77,8 +79,8 @@ extern "C" lm_status lm_tree_order_noalloc(const double *x, const double *y, int
                      NA_MAXN);
         return LM_EINVAL;
     }
-    if (!(d > 0.0) || depth < 0 || depth > 14) {
-        lm_set_error("tree_order_noalloc: need d > 0 and depth in 0..14");
+    if (!(d > 0.0) || !std::isfinite(d) || depth < 0 || depth > 14) {
+        lm_set_error("tree_order_noalloc: need a finite d > 0 and depth in 0..14");
         return LM_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -110,13 +112,15 @@ extern "C" lm_status lm_tree_order_noalloc(const double *x, const double *y, int
         mx = fmax(mx, hmax[i]);
     }
     const double f0 = floor(mn / d), f1 = floor(mx / d);
-    const int Rv = (int)(f1 - f0) + 1;
-    const int64_t ncol = (int64_t)Rv << depth, nrow = (int64_t)1 << depth, nleaf = ncol * nrow;
-    if (nleaf > NA_MAXLEAF) {
-        lm_set_error("tree_order_noalloc: %lld leaves exceed the fixed scratch limit of %d", (long long)nleaf,
-                     NA_MAXLEAF);
+    // leaves counted in double before any integer conversion, so that a huge x
+    // extent (or a tiny d) cannot wrap the root count
+    const double dleaf = (f1 - f0 + 1.0) * ldexp(1.0, 2 * depth);
+    if (!std::isfinite(dleaf) || dleaf > (double)NA_MAXLEAF) {
+        lm_set_error("tree_order_noalloc: %g leaves exceed the fixed scratch limit of %d", dleaf, NA_MAXLEAF);
         return LM_EINVAL;
     }
+    const int Rv = (int)(f1 - f0) + 1;
+    const int64_t ncol = (int64_t)Rv << depth, nrow = (int64_t)1 << depth, nleaf = ncol * nrow;
     if (leaf_cap < nleaf + 1) {
         lm_set_error("tree_order_noalloc: leaf_start holds %lld entries, %lld needed", (long long)leaf_cap,
                      (long long)(nleaf + 1));

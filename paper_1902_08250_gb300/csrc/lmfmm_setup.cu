@@ -1,6 +1,7 @@
 // lmfmm_setup.cu -- Algorithm 1, step 1 on the device: the strip-forest
 // quadtree, interaction lists, translation tables and near-field quadrature.
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 #include <algorithm>
 #include <map>
@@ -513,8 +514,16 @@ lm_status lm_setup_tree(lm_tree_s *t, const double *x, const double *y, cudaStre
         mx = fmax(mx, hmax[i]);
     }
     double f0 = floor(mn / d), f1 = floor(mx / d);
+    // the number of d x d roots, checked in double before it becomes an int: an
+    // x extent of more than 2^30 thicknesses (or one that overflows) is rejected
+    const double roots = f1 - f0 + 1.0;
+    if (!std::isfinite(roots) || roots < 1.0 || roots > (double)(1 << 30)) {
+        lm_set_error("build_tree: the x extent spans %g layer thicknesses; at most 2^30 roots are supported",
+                     roots);
+        return LM_EINVAL;
+    }
     t->x0 = f0 * d;
-    t->R = (int)(f1 - f0) + 1;
+    t->R = (int)roots;
     if (t->med.opt.depth >= 0) {
         t->L = t->med.opt.depth;
     } else {

@@ -37,9 +37,12 @@ def test_tree_order_noalloc_matches_build_tree():
         pytest.fail("a CUDA GPU is required for -m gpu tests")
     import paper_1902_08250_gb300 as lm
 
-    cases = [(workloads.small_uniform(1000)[:2], workloads.MEDIUM_A, 3),
-             (workloads.wide_uniform(200_000, 1)[:2], workloads.MEDIUM_B, 5)]
-    for (x, y), med, depth in cases:     # two calls in a row, different sizes
+    large = (workloads.wide_uniform(200_000, 1)[:2], workloads.MEDIUM_B, 5)
+    small = (workloads.small_uniform(1000)[:2], workloads.MEDIUM_A, 3)
+    # calls in a row: large, small, large.  The small call reuses counters that the
+    # large call left in the shared array, and the second large call reuses
+    # counters beyond the small call's range, so a missing clear fails a comparison.
+    for (x, y), med, depth in (large, small, large):
         xd = torch.from_numpy(x).cuda()
         yd = torch.from_numpy(y).cuda()
         t = lm.build_tree(lm.create_medium(*med, p=4, depth=depth), xd, yd)
@@ -57,3 +60,14 @@ def test_tree_order_noalloc_matches_build_tree():
     assert st == 1 and b"entries" in lm._lib.lm_last_error()
     st, *_ = _noalloc(lm, xd, yd, 1.0, 10, 1 << 22)  # too many leaves
     assert st == 1 and b"scratch limit" in lm._lib.lm_last_error()
+    st, *_ = _noalloc(lm, xd, yd, float("inf"), 3, 1 << 10)  # non-finite thickness
+    assert st == 1 and b"finite" in lm._lib.lm_last_error()
+    # an x spread of 3e9 thicknesses: the leaf count is rejected, not wrapped to a negative int
+    xw = x.copy()
+    xw[-1] = 3e9
+    st, *_ = _noalloc(lm, torch.from_numpy(xw).cuda(), yd, 1.0, 0, 1 << 10)
+    assert st == 1 and b"scratch limit" in lm._lib.lm_last_error()
+    # the same spread through lm_build_tree: more than 2^30 roots is an invalid argument
+    with pytest.raises(lm.LMError) as e:
+        lm.build_tree(lm.create_medium(*workloads.MEDIUM_A, p=4, depth=0), torch.from_numpy(xw).cuda(), yd)
+    assert e.value.status == 1 and "roots" in str(e.value)
