@@ -79,6 +79,7 @@ def _load():
         "lm_peak_probe": (I, [I, I64, P, P]),
         "lm_tree_order_noalloc": (I, [P, P, I64, D, I, P, P, I64, P, P, P]),
         "lm_sync_status": (I, [V, P]),
+        "lm_set_poll_limit": (I, [V, I]),
         "lm_batch_create": (I, [P, I, P, P, P, P, P]),
         "lm_batch_launch": (I, [V, P]),
         "lm_build_cross": (I, [V, P, P, I64, P, P, I64, P, P]),
@@ -317,6 +318,12 @@ def apply(tree: Tree, q, u=None, stream=None):
 def sync_status(tree: Tree, stream=None):
     """Synchronise and raise LMError(LM_ETIMEOUT) if a bounded device wait gave up."""
     _check(_lib.lm_sync_status(tree._h, _stream(stream)))
+
+
+def set_poll_limit(tree: Tree, limit):
+    """Limit the polls of the tensor-core M2L's first operand wait in the tree's next
+    16-vector apply (lm_set_poll_limit; 0 gives up at once, < 0 clears)."""
+    _check(_lib.lm_set_poll_limit(tree._h, int(limit)))
 
 
 def apply_adjoint(tree: Tree, v, w=None, stream=None):

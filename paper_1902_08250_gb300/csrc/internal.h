@@ -185,6 +185,16 @@ struct lm_tree_s {
     zf *qs32, *us32;           // [n][LM_MAXV]
     zf *nq_seg_lam, *nq_seg_s2, *nq_seg_w, *nq_tail_lam, *nq_tail_s2, *nq_tail_w;
     bool tc_ready; // tensor-core M2L tables built
+    // tile form of the tensor-core M2L (16-vector applies): every V-list entry of every
+    // level (free space and the four image terms) as (tile of 8 target boxes, entry) work
+    bool tt_ready;
+    int64_t tt_ntile, tt_nent;
+    void *tt_tiles, *tt_ents;   // device TtTile[tt_ntile], TtEnt[tt_nent]
+    float *tt_tab;              // [classes of all levels][128 rows][64 K] TF32 hi/lo tables, canonical layout
+    float *tt_msplit;           // [boxes of all levels + 1][2048] TF32 hi/lo multipoles, canonical layout
+    std::vector<int64_t> tt_tbase, tt_mbase; // per level: first table, first box
+    int tt_grid;                // persistent CTAs (one per SM)
+    int tt_poll_limit;          // polls of the first operand wait (0: the library default)
     bool near_pw64; // FP64 reflected near field: segment factorised per leaf (k_near_pw64)
     int32_t *pwidx; // [boxes of the leaf level / of the tree] slot of an interface leaf, or -1
     zd *pwC;        // [slots][2 terms][2 nseg][LM_MAXV] per-leaf segment coefficients (k_pw_src64)
@@ -235,6 +245,10 @@ void lm_free_mixed(lm_tree_s *t);
 // tensor-core M2L (lmfmm_tc.cu)
 lm_status lm_setup_tc(lm_tree_s *t, cudaStream_t st);
 lm_status lm_launch_m2l_tc(lm_tree_s *t, int l, cudaStream_t st, int nvs); // nvs: 4 or 16 vector slots
+// tile form (lmfmm_tc_tiles.cu): set-up, and the apply's multipole split + M2L of all levels
+lm_status lm_setup_tt(lm_tree_s *t, cudaStream_t st);
+lm_status lm_launch_m2l_tt(lm_tree_s *t, cudaStream_t st);
+void lm_free_tt(lm_tree_s *t);
 template <typename T>
 lm_status lm_dalloc(lm_tree_s *t, T **p, size_t count)
 {

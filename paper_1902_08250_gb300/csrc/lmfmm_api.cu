@@ -294,6 +294,16 @@ extern "C" lm_status lm_apply_grad(lm_tree t, const void *q, int nvec, void *u, 
     return s;
 }
 
+extern "C" lm_status lm_set_poll_limit(lm_tree t, int limit)
+{
+    if (!t) {
+        lm_set_error("set_poll_limit: NULL tree");
+        return LM_EINVAL;
+    }
+    t->tt_poll_limit = limit < 0 ? -1 : limit;
+    return LM_OK;
+}
+
 extern "C" lm_status lm_sync_status(lm_tree t, void *stream)
 {
     if (!t) {

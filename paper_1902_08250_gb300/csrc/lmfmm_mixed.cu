@@ -194,6 +194,7 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
     }
     LM_CUDA(lm_raise_smem((const void *)k_near_pw32, LM_SMEM_NEAR_PW, (int)shm));
     if (t->med.opt.tensor_m2l) TRYM(lm_setup_tc(t, st));
+    if (t->tc_ready) TRYM(lm_setup_tt(t, st));
     for (Level &lv : t->lev) lv.m2l_impl = t->tc_ready ? 0 : 4;
     LM_CUDA(cudaGetLastError());
     LM_CUDA(cudaStreamSynchronize(st));
@@ -202,6 +203,7 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
 
 void lm_free_mixed(lm_tree_s *t)
 {
+    lm_free_tt(t);
     void *ptrs[] = {t->xl32, t->yl32, t->y32, t->qs32, t->us32, t->iperm, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w,
                     t->nq_tail_lam, t->nq_tail_s2, t->nq_tail_w};
     for (void *p : ptrs)
@@ -782,8 +784,9 @@ __global__ void __launch_bounds__(128) k_m2m32(int64_t ncol, const zf *tabs, con
 }
 
 // L2L (Lemma L2L): a child (this level) from its parent (level l - 1), table
-// slot = the child's position in the parent; writes the child's coefficients
-template <int NP, int NVS>
+// slot = the child's position in the parent; writes the child's coefficients,
+// or adds them (ACC) where the level's M2L has already written them
+template <int NP, int NVS, bool ACC = false>
 __global__ void __launch_bounds__(128) k_l2l32(int64_t ncol, const zf *tabs, const zf *Lp, zf *Lc)
 {
     constexpr int NR = Staged<NP, NVS>::NR, NB = Staged<NP, NVS>::NB, NG = Staged<NP, NVS>::NG;
@@ -800,7 +803,10 @@ __global__ void __launch_bounds__(128) k_l2l32(int64_t ncol, const zf *tabs, con
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         const int p = g + NG * k;
-        if (p < NP) Lc[(b * NP + p) * LM_MAXV + v] = acc[k];
+        if (p < NP) {
+            zf *o = Lc + (b * NP + p) * LM_MAXV + v;
+            *o = ACC ? *o + acc[k] : acc[k];
+        }
     }
 }
 
@@ -1065,6 +1071,13 @@ static void launch_l2l(const Level &lv, const Level &par, cudaStream_t st, int n
     else
         k_l2l32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
 }
+// L2L of the tile-form apply (16 vector slots): adds to the M2L's local expansions
+template <int P>
+static void launch_l2l_acc(const Level &lv, const Level &par, cudaStream_t st)
+{
+    constexpr int NP = 2 * P + 1;
+    k_l2l32<NP, LM_MAXV, true><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
+}
 template <int P>
 static void launch_rest(const Level &lv, cudaStream_t st, int nvs)
 {
@@ -1162,7 +1175,19 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
             MX_DISPATCH(P, launch_m2m, t->lev[l], t->lev[l + 1], st, nvs);
         }
         if (L > 0) lm_phase_end(t, PH_M2M, st, L);
-        for (int l = 0; l <= L; ++l) {
+        // tile form: the M2L of every level in one launch (it writes L), then L2L adds
+        bool tiles = t->tt_ready && nvs == LM_MAXV;
+        for (int l = 1; l <= L; ++l) tiles = tiles && t->lev[l].m2l_impl == 0;
+        if (tiles) {
+            lm_phase_begin(t, PH_M2L, st);
+            lm_status s = lm_launch_m2l_tt(t, st);
+            if (s != LM_OK) return s;
+            lm_phase_end(t, PH_M2L, st, 2);
+            if (L > 0) lm_phase_begin(t, PH_L2L, st);
+            for (int l = 1; l <= L; ++l) MX_DISPATCH(P, launch_l2l_acc, t->lev[l], t->lev[l - 1], st);
+            if (L > 0) lm_phase_end(t, PH_L2L, st, L);
+        }
+        for (int l = 0; l <= L && !tiles; ++l) {
             Level &lv = t->lev[l];
             int64_t tot = lv.nbox * np * LM_MAXV;
             lm_phase_begin(t, PH_L2L, st);

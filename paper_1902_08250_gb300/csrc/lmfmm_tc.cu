@@ -135,10 +135,6 @@ __device__ __forceinline__ void tc_issue(uint32_t dt, const unsigned char *stage
     }
 }
 
-__device__ __forceinline__ void tc_commit(uint32_t mb)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb) : "memory");
-}
 
 // VB: log2 of the vector slots per box in a tile (4: 8 boxes x 16 vectors; 2: 32 boxes x 4 vectors)
 template <int NP, int VB>

@@ -97,8 +97,10 @@ def test_batched_instances_match_oracle(lm, oracle):
 def test_few_vectors_match_full_width(lm):
     """Applies of up to 4 vectors take the 4-vector forms of every contraction (S2M,
     M2M, L2L, rest-list and tensor-core M2L: 32 boxes x 4 vectors per tile; the leaf
-    kernel); they agree with the same vectors computed inside a 16-vector apply (the
-    same FP32 arithmetic per vector)."""
+    kernel); they agree with the same vectors computed inside a 16-vector apply.  The
+    16-vector apply runs the tile-form M2L of all levels, which orders its sums
+    differently (and splits the tables from FP64), so the two agree to the mixed
+    path's rounding, not bit for bit; both meet the mixed bar against the FP64 apply."""
     import torch
 
     x, y, q = workloads.uniform_strip(60_000, 0.0, 8.0, -0.95, -0.05, nvec=16, seed=9)
@@ -106,6 +108,10 @@ def test_few_vectors_match_full_width(lm):
     t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     qd = torch.from_numpy(q).cuda()
     full = lm.apply(t, qd).cpu().numpy()
+    ref = lm.apply(lm.build_tree(lm.create_medium(*workloads.MEDIUM_B, p=20), t._x, t._y), qd[:3].contiguous())
+    ref = ref.cpu().numpy()
+    assert np.linalg.norm(full[:3] - ref) <= 1e-6 * np.linalg.norm(ref)
     for nv in (3, 1):
         few = lm.apply(t, qd[:nv].contiguous()).cpu().numpy()
-        assert np.linalg.norm(few - full[:nv]) <= 1e-7 * np.linalg.norm(full[:nv]), nv
+        assert np.linalg.norm(few - full[:nv]) <= 1e-6 * np.linalg.norm(full[:nv]), nv
+        assert np.linalg.norm(few - ref[:nv]) <= 1e-6 * np.linalg.norm(ref[:nv]), nv
