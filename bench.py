@@ -74,6 +74,10 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
+    # 10 ms: about 75 samples per second on GB300 (nvidia-smi returns one line per query), so a
+    # 0.1 s region of 20 applies still holds several samples
+    PERIOD_MS = 10
+
     def __init__(self, index):
         self.index = index
         self.proc = None
@@ -90,7 +94,7 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -550,10 +554,9 @@ def main():
         lm.apply(tree, qd, ud)
     torch.cuda.synchronize(dev)
 
-    # --- timed region (device time, CUDA events on the launching stream) ---
+    # --- timed region (device time, CUDA events on the launching stream; no per-phase events) ---
     clocks = Clocks(dev.index if dev.index is not None else 0)
     lib = lm._lib
-    lib.lm_profile_begin(tree._h, args.steps)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -569,12 +572,20 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1) / args.steps
+
+    # --- phase times: a second pass of K applies with the library's per-phase CUDA events on
+    # the launching stream (kept out of the timed region above) ---
     ph_ms = (ctypes.c_double * len(PHASES))()
     ph_n = (ctypes.c_int64 * len(PHASES))()
     napp = ctypes.c_int()
+    lib.lm_profile_begin(tree._h, args.steps)
+    for _ in range(args.steps):
+        lm.apply(tree, qd, ud)
+    torch.cuda.synchronize(dev)
     lib.lm_profile_end(tree._h, ph_ms, ph_n, len(PHASES), ctypes.byref(napp))
     phase_ms = {PHASES[i]: ph_ms[i] / max(1, napp.value) for i in range(len(PHASES))}
-    launches = int(sum(ph_n[i] for i in range(len(PHASES)))) + args.steps  # + permute-out per apply
+    launches = int(sum(ph_n[i] for i in range(len(PHASES))))  # per profiled apply x steps
+    launches = launches // max(1, napp.value) * args.steps
 
     # --- end to end: host (pinned) buffers through the C ABI ---
     # Every step copies its densities in from pinned host memory and its potentials
@@ -723,6 +734,35 @@ def alu_peak(precision, n_sm, mhz=None):
     return peak, f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz"
 
 
+H0_FLOPS = 60        # flops per free-space (i/4) H0 evaluation (series or far form)
+TAIL_NODE_FLOPS = 35 # flops per tail quadrature node of a reflected pair (about 4 transcendentals)
+BESSEL_FLOPS = 20    # flops per order of the per-target Bessel recurrence of L2T
+
+
+def leaf_work(tree, npc, nvec):
+    """Algorithmic flops of the leaf phase (L2T + S2T) per apply, counted per unit of
+    work: a free direct pair is one H0 evaluation plus nvec complex multiply-adds; a
+    reflected direct pair is its tail quadrature (tail_order nodes) plus nvec complex
+    multiply-adds; L2T is (2p+1) Bessel recurrence steps plus nvec (2p+1) complex
+    multiply-adds per target.  The MAC-only count leaves out the kernel evaluations."""
+    perm, ls = tree.export()
+    cnt = np.diff(ls)
+    U = tree.list_export(1)
+    pp = cnt[U[:, 0]] * cnt[U[:, 2]]
+    free = int(np.sum(pp[U[:, 1] == 0])) - tree.n
+    refl = int(np.sum(pp[U[:, 1] != 0]))
+    o = tree.medium.options
+    q_tail = o.get("tail_order") or (24 if o.get("precision") == 1 else 48)  # the library's defaults
+    mac = 8.0 * nvec
+    flops = (free * (H0_FLOPS + mac) + refl * (q_tail * TAIL_NODE_FLOPS + mac)
+             + tree.n * npc * (BESSEL_FLOPS + mac))
+    mac_flops = mac * (free + refl) + mac * npc * tree.n
+    desc = (f"{free} free pairs x ({H0_FLOPS} flop H0 + 8x{nvec} MAC) + {refl} reflected pairs x "
+            f"({q_tail} tail nodes x {TAIL_NODE_FLOPS} + 8x{nvec}) + {tree.n} targets x {npc} orders x "
+            f"({BESSEL_FLOPS} + 8x{nvec})")
+    return {"flops": flops, "mac_flops": mac_flops, "free_pairs": free, "refl_pairs": refl, "desc": desc}
+
+
 def roofline(lm, tree, phase, ms, npc, precision, dev, peaks, mhz=None):
     """Algorithmic work of the dominant phase per apply over its measured time
     (CUDA events the library records on the launching stream)."""
@@ -743,22 +783,19 @@ def roofline(lm, tree, phase, ms, npc, precision, dev, peaks, mhz=None):
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": recorded_traffic("m2l"),
                 "work": f"8 (2p+1)^2 flop per V-list entry per vector; {entries} entries", "peak_source": src}
     if phase == "l2t_s2t":
-        perm, ls = tree.export()
-        cnt = np.diff(ls)
-        U = tree.list_export(1)
-        pairs = int(np.sum(cnt[U[:, 0]] * cnt[U[:, 2]])) - tree.n
-        flops = 8.0 * NVEC * pairs + 8.0 * NVEC * npc * tree.n
+        w = leaf_work(tree, npc, NVEC)
         import torch
 
         peak, src = alu_peak(precision, torch.cuda.get_device_properties(dev).multi_processor_count, mhz)
         probe = _probe(lm, 0 if precision == "fp64" else 1, dev)
-        ach = flops / (ms * 1e-3) / 1e12
+        ach = w["flops"] / (ms * 1e-3) / 1e12
+        ach_mac = w["mac_flops"] / (ms * 1e-3) / 1e12
         return {"bound": "alu", "kernel": "k_leaf64" if precision == "fp64" else "k_leaf32 + k_near_pw32",
                 "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": recorded_traffic("l2t_s2t"),
-                "work": f"8 flop per complex MAC x 16 vectors over {pairs} direct pairs and (2p+1) local terms "
-                        "per target (kernel evaluation itself not counted)",
-                "peak_source": src,
+                "work": w["desc"],
+                "achieved_mac_only": ach_mac, "frac_mac_only": ach_mac / peak,
+                "peak_source": src + ("" if mhz else " (no clock samples: maximum clock assumed)"),
                 "peak_probe": probe,
                 "peak_probe_source": "lm_peak_probe %s FMA chains on all SMs (measured live)" %
                                      ("FP64" if precision == "fp64" else "FP32")}
