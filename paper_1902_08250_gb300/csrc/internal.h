@@ -194,7 +194,7 @@ struct lm_tree_s {
     float *tt_msplit;           // [boxes of all levels + 1][2048] TF32 hi/lo multipoles, canonical layout
     std::vector<int64_t> tt_tbase, tt_mbase; // per level: first table, first box
     int tt_grid;                // persistent CTAs (one per SM)
-    int tt_poll_limit;          // polls of the first operand wait (0: the library default)
+    int tt_poll_limit;          // polls of the first operand wait (-1: the library default)
     bool near_pw64; // FP64 reflected near field: segment factorised per leaf (k_near_pw64)
     int32_t *pwidx; // [boxes of the leaf level / of the tree] slot of an interface leaf, or -1
     zd *pwC;        // [slots][2 terms][2 nseg][LM_MAXV] per-leaf segment coefficients (k_pw_src64)

@@ -9,17 +9,13 @@
 #include <vector>
 
 #include "internal.h"
+#include "mixed_near.cuh"
 
 #define MX_MAXP 24
 bool lm_mixed_order_supported(int P);
 static int gridm(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
 LM_HD zf f2(zd a) { return zf{(float)a.re, (float)a.im}; }
-__device__ __forceinline__ void cfmaf(zf &a, zf b, zf c)
-{
-    a.re = fmaf(b.re, c.re, fmaf(-b.im, c.im, a.re));
-    a.im = fmaf(b.re, c.im, fmaf(b.im, c.re, a.im));
-}
 
 // ---------------------------------------------------------------------------
 // setup
@@ -90,7 +86,6 @@ __global__ void k_scan64b(int64_t *c, int64_t m)
     }
 }
 
-struct NearQuadF;
 static size_t near_pw_smem(const lm_tree_s *t);
 __global__ void k_inverse_perm(const int64_t *perm, int64_t n, int64_t *iperm);
 __global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, float w, float d, const float *xl,
@@ -413,46 +408,6 @@ __global__ void __launch_bounds__(64 * ((NP + RG - 1) / RG))
     }
 }
 
-// (i/4) H0^(1)(x) in FP32 as a function of t = x^2/4.  For t <= 1 (x <= 2)
-// the ascending series of J0 and Y0 (Abramowitz & Stegun 9.1.12, 9.1.13),
-//   J0 = sum_m c_m t^m,  c_m = (-1)^m/(m!)^2,
-//   Y0 = (2/pi) [ (ln(x/2) + gamma) J0 - sum_{m>=1} H_m c_m t^m ],  ln(x/2) = ln(t)/2,
-// H_m the harmonic numbers, are evaluated by Horner's rule to degree 8
-// (truncation < 1e-11); no square root is needed.  Larger x use the
-// library's j0f / y0f.
-// the series branch alone (valid for t <= 1; finite for any t > 0)
-__device__ __forceinline__ zf green_free32_series(float t)
-{
-    // c_m and H_m c_m for m = 8 .. 1, from the series definitions
-    const float c8 = 6.15118733e-10f, c7 = -3.93675989e-08f, c6 = 1.92901235e-06f, c5 = -6.94444444e-05f,
-                c4 = 1.73611111e-03f, c3 = -2.77777778e-02f, c2 = 0.25f, c1 = -1.0f;
-    const float e8 = 1.67180484e-09f, e7 = -1.02074560e-07f, e6 = 4.72608025e-06f, e5 = -1.58564815e-04f,
-                e4 = 3.61689815e-03f, e3 = -5.09259259e-02f, e2 = 0.375f, e1 = -1.0f;
-    const float2 tt = make_float2(t, t);
-    float2 pp = __ffma2_rn(make_float2(c8, e8), tt, make_float2(c7, e7));
-    pp = __ffma2_rn(pp, tt, make_float2(c6, e6));
-    pp = __ffma2_rn(pp, tt, make_float2(c5, e5));
-    pp = __ffma2_rn(pp, tt, make_float2(c4, e4));
-    pp = __ffma2_rn(pp, tt, make_float2(c3, e3));
-    pp = __ffma2_rn(pp, tt, make_float2(c2, e2));
-    pp = __ffma2_rn(pp, tt, make_float2(c1, e1));
-    const float j = fmaf(pp.x, t, 1.0f);
-    const float sh = pp.y * t;
-    // MUFU logarithm: absolute error ~1e-7, well inside the 1e-6 budget
-    const float y = 0.63661977236758134f * (fmaf(0.5f, __logf(t), 0.57721566490153286f) * j - sh);
-    return zf{-0.25f * y, 0.25f * j};
-}
-// t > 1: the library's j0f / y0f
-__device__ __noinline__ zf green_free32_far(float t)
-{
-    const float x = 2.0f * sqrtf(t);
-    return zf{-0.25f * y0f(x), 0.25f * j0f(x)};
-}
-__device__ __forceinline__ zf green_free32_t(float t)
-{
-    return t <= 1.0f ? green_free32_series(t) : green_free32_far(t);
-}
-
 // terms of the J0/Y0 series needed for arguments up to xmax (truncation < 1e-9)
 int lm_h0_terms(double xmax)
 {
@@ -463,52 +418,6 @@ int lm_h0_terms(double xmax)
         if (a * 3.1 < 1e-9) return m;
     }
     return 11;
-}
-
-struct NearQuadF {
-    int nseg, nray, ntail;
-    const zf *seg_lam, *seg_s2, *seg_w, *tail_lam, *tail_s2, *tail_w;
-    int sym; // sigma(conj lambda) = conj(sigma(lambda)) (no impedance wall): the tail is real
-    float rinf[2]; // wall limit of sigma_tt, sigma_bb: the tables hold sigma - rinf (refl_inf)
-    float hray;    // added to h when the tail ray is chosen (see NearQuad)
-    float k24;     // k2^2 / 4, for the wall image's closed form
-};
-// Tail of one reflected direct term (tt: m = 0, bb: m = 1) for a pair at
-// horizontal distance X and image height h: the rays lambda = c + t e^{i phi_k}
-// nearest the steepest-descent direction atan2(X, h) (Sec. 4.2, alternative
-// directions); 2 Re is taken because sigma(conj lambda) = conj(sigma(lambda)).
-// Kept out of line: inlined into k_leaf32 it pushes the kernel to its
-// 128-register cap and slows the free-space loop by 9 % (measured).
-__device__ __noinline__ zf near_tail32(const NearQuadF &q, int m, float X, float h)
-{
-    int k = q.nray > 1 ? (int)rintf(atan2f(X, h + q.hray) * (q.nray - 1) * 0.63661977236758134f) : 0;
-    const zf *tl = q.tail_lam + (int64_t)k * q.ntail, *ts = q.tail_s2 + (int64_t)k * q.ntail;
-    const int64_t tot = (int64_t)q.nray * q.ntail;
-    const zf *tP = q.tail_w + (2 * m) * tot + (int64_t)k * q.ntail, *tM = tP + tot;
-    float re = 0.f, im = 0.f; // sum P Re(E) + i M Im(E)
-    if (q.rinf[m] != 0.f) { // a wall's image (i/4) H0(k rho), rho = |(X, h)|, in closed form
-        const zf img = q.rinf[m] * green_free32_t(q.k24 * fmaf(X, X, h * h));
-        re = img.re;
-        im = img.im;
-    }
-    if (q.sym) { // P real, M imaginary: only the real part of the tail survives
-        for (int i = 0; i < q.ntail; ++i) {
-            zf lam = tl[i], s2 = ts[i];
-            float a = expf(-lam.im * X - s2.re * h), sn, cs;
-            sincosf(lam.re * X - s2.im * h, &sn, &cs);
-            re += a * (tP[i].re * cs - tM[i].im * sn);
-        }
-        return zf{re, im};
-    }
-    for (int i = 0; i < q.ntail; ++i) {
-        zf lam = tl[i], s2 = ts[i];
-        float a = expf(-lam.im * X - s2.re * h), sn, cs;
-        sincosf(lam.re * X - s2.im * h, &sn, &cs);
-        const zf P = tP[i], M = tM[i];
-        re += a * (P.re * cs - M.im * sn);
-        im += a * (P.im * cs + M.re * sn);
-    }
-    return zf{re, im};
 }
 
 // Segment part of the reflected direct terms, factorised per target leaf.
@@ -631,28 +540,6 @@ __global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, f
 // the inner loop reads broadcast shared-memory rows while the next chunk
 // is in flight.
 #define LCAP 64
-__device__ __forceinline__ void cp_async4(void *sdst, const void *gsrc)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
-                 "l"(gsrc)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
-{
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
-                 "l"(gsrc)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
-                 "l"(gsrc)
-                 : "memory");
-}
-
 // ---------------------------------------------------------------------------
 // Staged contraction of one output box: acc = sum over its entries e of
 // T[slot(e)] M[src(e)], each (NP x NP) x (NP x 16 vectors).  Each entry's table
@@ -814,6 +701,70 @@ struct LeafChunk {
     int e, j0, cnt;
 };
 
+#define LEAF32_MAXE 64   // U entries whose source ranges are staged for the chunk table
+#define LEAF32_MAXCH 64  // chunks in the shared-memory chunk table
+// A leaf's U list cut into chunks of at most LCAP source points, each (entry,
+// first point, count).  Built once per leaf in shared memory: every thread
+// reads one U entry's source range, thread 0 lays the chunks out in list order;
+// a list of more than LEAF32_MAXCH chunks is enumerated on the fly instead.
+struct LeafChunkTable {
+    int cfirst[LEAF32_MAXE], ccount[LEAF32_MAXE];
+    LeafChunk ctab[LEAF32_MAXCH];
+    int nch, tabled;
+};
+__device__ __forceinline__ LeafChunk leaf_chunk_at(const int64_t *ls, const int32_t *usrc, int e0, int e1, int c)
+{
+    LeafChunk ch{-1, 0, 0};
+    for (int e = e0; e < e1; ++e) {
+        const int s = usrc[e], a0 = (int)ls[s], a1 = (int)ls[s + 1];
+        const int nc = (a1 - a0 + LCAP - 1) / LCAP;
+        if (c < nc) {
+            ch.e = e;
+            ch.j0 = a0 + c * LCAP;
+            ch.cnt = min(LCAP, a1 - ch.j0);
+            return ch;
+        }
+        c -= nc;
+    }
+    return ch;
+}
+// all threads of the block; ends with a barrier
+__device__ __forceinline__ void leaf_chunk_build(LeafChunkTable &T, const int64_t *ls, const int32_t *usrc, int e0,
+                                                 int e1)
+{
+    const int ne = e1 - e0;
+    if (ne <= LEAF32_MAXE) {
+        for (int t = threadIdx.x; t < ne; t += blockDim.x) {
+            const int s = usrc[e0 + t];
+            T.cfirst[t] = (int)ls[s];
+            T.ccount[t] = (int)(ls[s + 1] - ls[s]);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int n = 0;
+            for (int t = 0; t < ne; ++t)
+                for (int j = 0; j < T.ccount[t]; j += LCAP, ++n)
+                    if (n < LEAF32_MAXCH) T.ctab[n] = LeafChunk{e0 + t, T.cfirst[t] + j, min(LCAP, T.ccount[t] - j)};
+            T.nch = n;
+            T.tabled = n <= LEAF32_MAXCH;
+        }
+    } else if (threadIdx.x == 0) {
+        int n = 0;
+        for (int e = e0; e < e1; ++e) {
+            const int s = usrc[e];
+            n += ((int)(ls[s + 1] - ls[s]) + LCAP - 1) / LCAP;
+        }
+        T.nch = n;
+        T.tabled = 0;
+    }
+    __syncthreads();
+}
+__device__ __forceinline__ LeafChunk leaf_chunk(const LeafChunkTable &T, const int64_t *ls, const int32_t *usrc,
+                                                int e0, int e1, int c)
+{
+    return T.tabled ? T.ctab[c] : leaf_chunk_at(ls, usrc, e0, e1, c);
+}
+
 // Step 4 in FP32: L2T (Eq. (local)) and S2T for every target of a leaf, one
 // block per leaf, one thread per target.  The leaf's U list is cut into chunks
 // of at most LCAP source points (tabled once in shared memory); each chunk's
@@ -825,8 +776,6 @@ struct LeafChunk {
 // comes from k_near_pw32).
 // NV: vectors computed (4 or 16); buffers keep the 16-vector layout
 #define LEAF32_THREADS 64
-#define LEAF32_MAXE 64   // U entries whose source ranges are staged for the chunk table
-#define LEAF32_MAXCH 64  // chunks in the shared-memory chunk table
 template <int P, int NV>
 __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
                                                   const float *yl, const float *y32, const int64_t *ls,
@@ -845,57 +794,10 @@ __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, floa
     const int e0 = (int)ustart[b], e1 = (int)ustart[b + 1];
     const float k24 = 0.25f * k * k;
 
-    // chunk c of the U list -> (entry, first point, count); enumerated on the fly
-    auto chunk_at = [&](int c) {
-        LeafChunk ch{-1, 0, 0};
-        for (int e = e0; e < e1; ++e) {
-            const int s = usrc[e], a0 = (int)ls[s], a1 = (int)ls[s + 1];
-            const int nc = (a1 - a0 + LCAP - 1) / LCAP;
-            if (c < nc) {
-                ch.e = e;
-                ch.j0 = a0 + c * LCAP;
-                ch.cnt = min(LCAP, a1 - ch.j0);
-                return ch;
-            }
-            c -= nc;
-        }
-        return ch;
-    };
-    // the chunk table, built once per leaf in shared memory: each thread reads one U entry's
-    // source range, thread 0 lays the chunks out in list order; a list of more than
-    // LEAF32_MAXCH chunks falls back to chunk_at
-    __shared__ int cfirst[LEAF32_MAXE], ccount[LEAF32_MAXE];
-    __shared__ LeafChunk ctab[LEAF32_MAXCH];
-    __shared__ int s_nch, s_tabled;
-    const int ne = e1 - e0;
-    if (ne <= LEAF32_MAXE) {
-        for (int t = threadIdx.x; t < ne; t += blockDim.x) {
-            const int s = usrc[e0 + t];
-            cfirst[t] = (int)ls[s];
-            ccount[t] = (int)(ls[s + 1] - ls[s]);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int n = 0;
-            for (int t = 0; t < ne; ++t)
-                for (int j = 0; j < ccount[t]; j += LCAP, ++n)
-                    if (n < LEAF32_MAXCH) ctab[n] = LeafChunk{e0 + t, cfirst[t] + j, min(LCAP, ccount[t] - j)};
-            s_nch = n;
-            s_tabled = n <= LEAF32_MAXCH;
-        }
-    } else if (threadIdx.x == 0) {
-        int n = 0;
-        for (int e = e0; e < e1; ++e) {
-            const int s = usrc[e];
-            n += ((int)(ls[s + 1] - ls[s]) + LCAP - 1) / LCAP;
-        }
-        s_nch = n;
-        s_tabled = 0;
-    }
-    __syncthreads();
-    const bool tabled = s_tabled != 0;
-    const int nch = s_nch;
-    auto chunk = [&](int c) { return tabled ? ctab[c] : chunk_at(c); };
+    __shared__ LeafChunkTable ctable;
+    leaf_chunk_build(ctable, ls, usrc, e0, e1);
+    const int nch = ctable.nch;
+    auto chunk = [&](int c) { return leaf_chunk(ctable, ls, usrc, e0, e1, c); };
     auto issue = [&](int c, int buf) {
         const LeafChunk ch = chunk(c);
         for (int t = threadIdx.x; t < ch.cnt * (NV / 2); t += blockDim.x) {

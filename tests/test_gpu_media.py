@@ -36,6 +36,15 @@ def case(oracle):
     oracle.set_boundaries()
 
 
+def _widen(q, nvec, seed):
+    """q with further N(0,1) vectors up to nvec (16-vector applies take the tile-form
+    tensor-core M2L and the tensor-core leaf step; 1-4 vectors the 4-slot kernels)."""
+    rng = np.random.default_rng(seed)
+    extra = rng.standard_normal((nvec - q.shape[0], q.shape[1])) + 1j * rng.standard_normal((nvec - q.shape[0],
+                                                                                              q.shape[1]))
+    return np.concatenate([q, extra])
+
+
 def _ref(oracle, spec, x, y, q, sub, deriv=None):
     med, tb, ta, bb, ba = spec
     oracle.set_boundaries(tb, ta, bb, ba)
@@ -45,13 +54,15 @@ def _ref(oracle, spec, x, y, q, sub, deriv=None):
 
 
 @pytest.mark.parametrize("name", list(MEDIA))
-@pytest.mark.parametrize("prec,p,tol", [("fp64", 24, 1e-10), ("mixed", 14, 1e-6)])
+@pytest.mark.parametrize("prec,p,tol", [("fp64", 24, 1e-10), ("mixed", 14, 1e-6), ("mixed16", 14, 1e-6)])
 def test_media_fmm_matches_oracle(lm, oracle, case, name, prec, p, tol):
     import torch
 
     x, y, q, sub = case
+    if prec == "mixed16":
+        q = _widen(q, 16, 23)
     med, tb, ta, bb, ba = MEDIA[name]
-    m = lm.create_medium(*med, p=p, depth=2, precision=prec, top_bc=tb, top_alpha=ta, bottom_bc=bb,
+    m = lm.create_medium(*med, p=p, depth=2, precision=prec[:5], top_bc=tb, top_alpha=ta, bottom_bc=bb,
                          bottom_alpha=ba)
     t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     u = lm.apply(t, torch.from_numpy(q).cuda()).cpu().numpy()[:, sub]
@@ -100,16 +111,19 @@ def _near_walls(n, seed):
 
 
 @pytest.mark.parametrize("name", list(MEDIA))
-@pytest.mark.parametrize("prec,p,tol", [("fp64", 22, 1e-10), ("mixed", 14, 1e-6)])
+@pytest.mark.parametrize("prec,p,tol", [("fp64", 22, 1e-10), ("mixed", 14, 1e-6), ("mixed16", 14, 1e-6)])
 def test_media_near_the_walls(lm, oracle, name, prec, p, tol):
     """Pairs within 0.02 of a wall: the quadratures integrate sigma - R_inf and each
     pair adds R_inf (i/4) H0 of its image point in closed form (uniform tree of
-    automatic depth)."""
+    automatic depth).  The 16-vector case runs the reflected tails inside the
+    tensor-core leaf step."""
     import torch
 
     x, y, q, sub = _near_walls(3000, 41)
+    if prec == "mixed16":
+        q = _widen(q, 16, 42)
     med, tb, ta, bb, ba = MEDIA[name]
-    m = lm.create_medium(*med, p=p, precision=prec, top_bc=tb, top_alpha=ta, bottom_bc=bb, bottom_alpha=ba)
+    m = lm.create_medium(*med, p=p, precision=prec[:5], top_bc=tb, top_alpha=ta, bottom_bc=bb, bottom_alpha=ba)
     t = lm.build_tree(m, torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda())
     u = lm.apply(t, torch.from_numpy(q).cuda()).cpu().numpy()[:, sub]
     try:

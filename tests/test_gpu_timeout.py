@@ -33,8 +33,7 @@ def test_tensor_core_wait_timeout_is_reported_and_recovers():
     u = lm.apply(t, qd)
     lm.sync_status(t)
     assert torch.equal(u, ref)
-    # and the tree still matches the CUDA-core M2L of the same tree shape
-    mc = lm.create_medium(*workloads.MEDIUM_B, p=14, depth=3, precision="mixed", tensor_m2l=0)
-    uc = lm.apply(lm.build_tree(mc, xd, yd), qd)
-    err = float(torch.linalg.norm(u - uc) / torch.linalg.norm(uc))
-    assert err < 5e-7, err
+    # and the result meets the mixed bar against the FP64 apply of the same points
+    uf = lm.apply(lm.build_tree(lm.create_medium(*workloads.MEDIUM_B, p=20), xd, yd), qd)
+    err = float(torch.linalg.norm(u - uf) / torch.linalg.norm(uf))
+    assert err < 1e-6, err
