@@ -774,9 +774,11 @@ __device__ __forceinline__ LeafChunk leaf_chunk(const LeafChunkTable &T, const i
 // list length.  Free pairs take (i/4) H0 from its series, evaluated one pair
 // ahead of the multiply-adds; reflected pairs add their tails (the segment part
 // comes from k_near_pw32).
-// NV: vectors computed (4 or 16); buffers keep the 16-vector layout
+// NV: vectors computed (4 or 16); buffers keep the 16-vector layout.
+// DEG > 0: every free near pair has t = (k r / 2)^2 <= 1 and the series of degree
+// DEG meets the 1e-9 truncation bound (lm_h0_terms); DEG = 0: degree 8 and the far form.
 #define LEAF32_THREADS 64
-template <int P, int NV>
+template <int P, int NV, int DEG = 0>
 __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
                                                   const float *yl, const float *y32, const int64_t *ls,
                                                   const int64_t *ustart, const int32_t *usrc, const int32_t *uterm,
@@ -896,13 +898,14 @@ __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, floa
                             return (HS && jj == self) ? 1.0f : t2;
                         };
                         float tn = targ(0);
-                        zf gn = tn <= 1.0f ? green_free32_series(tn) : green_free32_far(tn);
+                        zf gn = DEG ? green_free32_series_d<DEG ? DEG : 8>(tn)
+                                    : (tn <= 1.0f ? green_free32_series(tn) : green_free32_far(tn));
                         for (int jj = 0; jj < ch.cnt; ++jj) {
                             const zf g = (HS && jj == self) ? zf{0.f, 0.f} : gn;
                             tn = targ(min(jj + 1, ch.cnt - 1));
-                            gn = green_free32_series(tn);
+                            gn = DEG ? green_free32_series_d<DEG ? DEG : 8>(tn) : green_free32_series(tn);
                             mac(g, jj);
-                            if (tn > 1.0f) gn = green_free32_far(tn);
+                            if (!DEG && tn > 1.0f) gn = green_free32_far(tn);
                         }
                     };
                     if (self >= 0 && self < ch.cnt)
@@ -996,9 +999,14 @@ static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st, int 
 {
     const Level &lv = t->lev[t->L];
     // largest k r of a direct pair: two leaves apart diagonally
-    const int nterms = lm_h0_terms(t->med.k2 * lv.w * 2.0 * 1.4142135623730951 * 1.0001);
+    const double xmax = t->med.k2 * lv.w * 2.0 * 1.4142135623730951 * 1.0001;
+    const int nterms = lm_h0_terms(xmax);
     const int free_on = t->med.opt.kernel == LM_KERNEL_G;
-    if (nv <= 4) // the batched form's 4-vector applies: a quarter of the contraction
+    if (nv > 4 && xmax <= 2.0 && nterms <= 6) // short series, no far form (k2 w <= 0.7)
+        k_leaf32<P, LM_MAXV, 6><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(
+            lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d, t->xl32, t->yl32, t->y32, t->leaf_start,
+            t->ustart, t->usrc, t->uterm, nq, lv.L32, t->qs32, t->us32, nterms, free_on);
+    else if (nv <= 4) // the batched form's 4-vector applies: a quarter of the contraction
         k_leaf32<P, 4><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
                                                          t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart,
                                                          t->usrc, t->uterm, nq, lv.L32, t->qs32, t->us32, nterms,

@@ -24,8 +24,9 @@
 // operand reads at 96 B per tensor-core clock.
 //
 // Roles (10 warps, one CTA per SM, persistent over tiles):
-//   warp 8  producer: waits for a free stage, issues the bulk copies, which
-//           complete on the stage's `full` barrier;
+//   warp 8  producer: loads 32 entries at a time across its lanes; lane 0
+//           waits for a free stage and issues the bulk copies, which complete
+//           on the stage's `full` barrier;
 //   warp 9  MMA issuer: waits for the stage and for a free accumulator, issues
 //           the 8 MMAs, commits them to the stage's `empty` and the
 //           accumulator's `tfull` barrier;
@@ -204,39 +205,49 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     const uint32_t tmem = *tslot;
 
     if (warp == TT_EPI_WARPS) {
-        // ---- producer ----
-        if (lane == 0) {
-            uint32_t it = 0;
-            int last[2] = {-1, -1}; // last item copied into each stage
-            for (int tile = blockIdx.x; tile < ntiles && !*abort_s; tile += gridDim.x) {
-                const TtTile T = tiles[tile];
-                const int64_t ncol = lv.ncol[T.level], mb = lv.mbase[T.level];
-                const float *tb = tabs + lv.tbase[T.level] * TT_TAB_FLOATS;
-                for (int e = T.e0; e < T.e1; ++e, ++it) {
-                    const int s = it & 1;
-                    if (!mbar_wait_lim(bempty + 8 * s, ((it >> 1) & 1) ^ 1, TC_WAIT_LIMIT, abort_s, err)) {
-                        tt_fail(abort_s, err);
-                        break;
-                    }
-                    const TtEnt E = ents[e];
-                    const uint32_t st = sbase + s * TT_STAGE, fb = bfull + 8 * s;
-                    mbar_expect_tx(fb, TT_STAGE);
-                    bulk_g2s(st, tb + (int64_t)E.slot * TT_TAB_FLOATS, TT_STAGE_TAB, fb);
+        // ---- producer: the warp loads 32 entries at a time (one per lane, in parallel) and
+        // lane 0 takes them by shuffle, waits for stages and issues the copies ----
+        uint32_t it = 0;
+        int last[2] = {-1, -1}; // last item copied into each stage (lane 0)
+        bool stop = false;
+        for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
+            const TtTile T = tiles[tile];
+            const int64_t ncol = lv.ncol[T.level], mb = lv.mbase[T.level];
+            const float *tb = tabs + lv.tbase[T.level] * TT_TAB_FLOATS;
+            for (int base = T.e0; base < T.e1 && !stop; base += 32) {
+                const int cnt = min(32, T.e1 - base);
+                TtEnt mine = lane < cnt ? ents[base + lane] : TtEnt{0, 0, 0, 0u};
+                for (int i = 0; i < cnt; ++i, ++it) {
+                    const TtEnt E = {__shfl_sync(0xffffffffu, mine.slot, i), __shfl_sync(0xffffffffu, mine.dc, i),
+                                     __shfl_sync(0xffffffffu, mine.rs, i), __shfl_sync(0xffffffffu, mine.mask, i)};
+                    if (lane == 0) {
+                        const int s = it & 1;
+                        if (!mbar_wait_lim(bempty + 8 * s, ((it >> 1) & 1) ^ 1, TC_WAIT_LIMIT, abort_s, err)) {
+                            tt_fail(abort_s, err);
+                        } else {
+                            const uint32_t st = sbase + s * TT_STAGE, fb = bfull + 8 * s;
+                            mbar_expect_tx(fb, TT_STAGE);
+                            bulk_g2s(st, tb + (int64_t)E.slot * TT_TAB_FLOATS, TT_STAGE_TAB, fb);
 #pragma unroll 1
-                    for (int j = 0; j < TT_BOXES; ++j) {
-                        int64_t src = zero_box;
-                        if (j < T.nbox && ((E.mask >> j) & 1u))
-                            src = mb + (int64_t)E.rs * ncol + T.c0 + (int64_t)j * T.cstride - E.dc;
-                        bulk_g2s(st + TT_STAGE_TAB + j * TT_BOX_FLOATS * 4, msplit + src * TT_BOX_FLOATS,
-                                 TT_BOX_FLOATS * 4, fb);
+                            for (int j = 0; j < TT_BOXES; ++j) {
+                                int64_t src = zero_box;
+                                if (j < T.nbox && ((E.mask >> j) & 1u))
+                                    src = mb + (int64_t)E.rs * ncol + T.c0 + (int64_t)j * T.cstride - E.dc;
+                                bulk_g2s(st + TT_STAGE_TAB + j * TT_BOX_FLOATS * 4, msplit + src * TT_BOX_FLOATS,
+                                         TT_BOX_FLOATS * 4, fb);
+                            }
+                            last[s] = (int)it;
+                        }
                     }
-                    last[s] = (int)it;
+                    stop = __shfl_sync(0xffffffffu, (int)(*abort_s != 0), 0) != 0;
+                    if (stop) break;
                 }
             }
-            // copies in flight land before the CTA's shared memory is released
+        }
+        // copies in flight land before the CTA's shared memory is released
+        if (lane == 0)
             for (int s = 0; s < 2; ++s)
                 if (last[s] >= 0) mbar_wait_lim(bfull + 8 * s, (last[s] >> 1) & 1, TC_WAIT_LIMIT, nullptr, nullptr);
-        }
         __syncwarp();
     } else if (warp == TT_EPI_WARPS + 1) {
         // ---- MMA issuer ----

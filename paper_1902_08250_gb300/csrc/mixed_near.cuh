@@ -63,6 +63,25 @@ __device__ __forceinline__ zf green_free32_series(float t)
     const float y = 0.63661977236758134f * (fmaf(0.5f, __logf(t), 0.57721566490153286f) * j - sh);
     return zf{-0.25f * y, 0.25f * j};
 }
+// The same series truncated at degree DEG (5..8), for leaves whose near pairs all
+// have t <= t_max with the first dropped term below 1e-9 (lm_h0_terms).
+template <int DEG>
+__device__ __forceinline__ zf green_free32_series_d(float t)
+{
+    static_assert(DEG >= 5 && DEG <= 8, "series degree");
+    constexpr float c[9] = {1.0f, -1.0f, 0.25f, -2.77777778e-02f, 1.73611111e-03f, -6.94444444e-05f,
+                            1.92901235e-06f, -3.93675989e-08f, 6.15118733e-10f};
+    constexpr float e[9] = {0.0f, -1.0f, 0.375f, -5.09259259e-02f, 3.61689815e-03f, -1.58564815e-04f,
+                            4.72608025e-06f, -1.02074560e-07f, 1.67180484e-09f};
+    const float2 tt = make_float2(t, t);
+    float2 pp = make_float2(c[DEG], e[DEG]);
+#pragma unroll
+    for (int m = DEG - 1; m >= 1; --m) pp = __ffma2_rn(pp, tt, make_float2(c[m], e[m]));
+    const float j = fmaf(pp.x, t, 1.0f);
+    const float sh = pp.y * t;
+    const float y = 0.63661977236758134f * (fmaf(0.5f, __logf(t), 0.57721566490153286f) * j - sh);
+    return zf{-0.25f * y, 0.25f * j};
+}
 // t > 1: the library's j0f / y0f
 static __device__ __noinline__ zf green_free32_far(float t)
 {
