@@ -395,6 +395,31 @@ lm_status lm_apply_adjoint_c64(lm_tree t, const void *v, int nvec, void *w, void
 lm_status lm_apply_grad(lm_tree t, const void *q, int nvec, void *u, void *ux, void *uy, void *stream);
 
 /*
+ * misfit_grad -- every gradient of a real misfit J(u), u = G(x, y, d) q, from
+ * g = dJ/d(Re u) + i dJ/d(Im u) (device [nvec][n] complex128, input order),
+ * assembled by the library's kernels on `stream`:
+ *   gq = G^H g = conj(G conj g)                        (lm_apply_adjoint);
+ *   gx_j = Re sum_v [conj(g_vj) dx(G q_v)_j + q_vj dx(G conj g_v)_j], gy_j
+ *        the same in y: the target gradient at x_j (lm_apply_grad) over the
+ *        stacked vectors [q; conj g], with G(a, b) = G(b, a) (Sec. 3)
+ *        turning the target derivative into the source-point derivative;
+ *   gd = Re sum_v sum_i conj(g_vi) (dG/dd q_v)_i, from dtree: a tree built over
+ *        the same points with kernel = LM_KERNEL_DG_DD; reduced in a fixed
+ *        order (reproducible).
+ *   q, g: device [nvec][n] complex128.  gq: device [nvec][n] complex128; gx,
+ *   gy: device double [n]; gd: device double [1]; any output may be NULL (not
+ *   computed).  dtree: needed only for gd.  workspace: device memory of at
+ *   least lm_misfit_grad_workspace bytes, owned by the caller and needed
+ *   only for gx, gy or gd; the library allocates nothing here.
+ * Errors: LM_EINVAL for NULL inputs, nvec < 1, a short workspace, overlapping
+ * outputs or a missing / mismatched dtree; LM_ENOTSUP for gx or gy on an
+ * LM_MIXED tree (the target gradient is FP64 only); LM_ECUDA.
+ */
+lm_status lm_misfit_grad_workspace(lm_tree t, int nvec, size_t *bytes);
+lm_status lm_misfit_grad(lm_tree t, lm_tree dtree, const void *q, const void *g, int nvec, void *gq, double *gx,
+                         double *gy, double *gd, void *workspace, size_t ws_bytes, void *stream);
+
+/*
  * Cross-layer operator (Sec. 3, Example 4 as printed): sources in layer 1,
  * targets in the middle layer,
  *     u_i = sum_j q_j [g_2^t + g_2^b](x_i, x_j),

@@ -80,6 +80,8 @@ def _load():
         "lm_tree_order_noalloc": (I, [P, P, I64, D, I, P, P, I64, P, P, P]),
         "lm_sync_status": (I, [V, P]),
         "lm_set_poll_limit": (I, [V, I]),
+        "lm_misfit_grad_workspace": (I, [V, I, P]),
+        "lm_misfit_grad": (I, [V, V, P, P, I, P, P, P, P, P, ctypes.c_size_t, P]),
         "lm_batch_create": (I, [P, I, P, P, P, P, P]),
         "lm_batch_launch": (I, [V, P]),
         "lm_build_cross": (I, [V, P, P, I64, P, P, I64, P, P]),
@@ -356,10 +358,12 @@ def _autograd_function():
     import torch
 
     class _LayeredGreen(torch.autograd.Function):
-        """u = G(x, y, d) q.  With g = dL/du (PyTorch's convention for a real L):
-        dL/dq = G^H g (adjoint apply); dL/dx_j = Re[conj(g_j) ux(q)_j + q_j ux(conj g)_j]
-        and the same in y (target gradient + reciprocity G(a, b) = G(b, a));
-        dL/dd = Re sum_i conj(g_i) (dG/dd q)_i (the dG/dd tree)."""
+        """u = G(x, y, d) q.  With g = dL/du (PyTorch's convention for a real L) the
+        backward is one lm_misfit_grad call: dL/dq = G^H g, dL/dx_j = Re[conj(g_j) ux(q)_j
+        + q_j ux(conj g)_j] and the same in y (target gradient + reciprocity
+        G(a, b) = G(b, a)), dL/dd = Re sum_i conj(g_i) (dG/dd q)_i (the dG/dd tree), all
+        formed by the library's kernels.  This class only allocates the outputs and the
+        workspace and passes pointers."""
 
         @staticmethod
         def forward(ctx, q, x, y, d, tree):
@@ -373,23 +377,27 @@ def _autograd_function():
             (q,) = ctx.saved_tensors
             t = ctx.tree
             g = grad_u.contiguous()
-            g2 = g.reshape(1, -1) if ctx.one else g
-            q2 = q.reshape(1, -1) if ctx.one else q
-            gq = gx = gy = gd = None
-            if ctx.needs_input_grad[0]:
-                gq = apply_adjoint(t, g)
-            if ctx.needs_input_grad[1] or ctx.needs_input_grad[2]:
-                nv = q2.shape[0]
-                V = torch.cat([q2, torch.conj(g2)], 0).contiguous()
-                _, ux, uy = apply_grad(t, V, want_u=False)
-                gc = torch.conj(g2)
-                if ctx.needs_input_grad[1]:
-                    gx = torch.real(gc * ux[:nv] + q2 * ux[nv:]).sum(0)
-                if ctx.needs_input_grad[2]:
-                    gy = torch.real(gc * uy[:nv] + q2 * uy[nv:]).sum(0)
-            if ctx.needs_input_grad[3]:
-                dd = apply(t.d_tree(), q2.contiguous())
-                gd = torch.real(torch.sum(torch.conj(g2) * dd)).reshape(())
+            qc = q.contiguous()
+            nvec = 1 if ctx.one else q.shape[0]
+            need = ctx.needs_input_grad
+            dev = q.device
+            gq = torch.empty_like(qc) if need[0] else None
+            gx = torch.empty(t.n, dtype=torch.float64, device=dev) if need[1] else None
+            gy = torch.empty(t.n, dtype=torch.float64, device=dev) if need[2] else None
+            gd = torch.empty((), dtype=torch.float64, device=dev) if need[3] else None
+            dt = t.d_tree() if need[3] else None
+            ws, nbytes = None, 0
+            if need[1] or need[2] or need[3]:
+                b = ctypes.c_size_t()
+                _check(_lib.lm_misfit_grad_workspace(t._h, nvec, ctypes.byref(b)))
+                nbytes = b.value
+                ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+
+            def ptr(a):
+                return None if a is None else ctypes.c_void_p(a.data_ptr())
+
+            _check(_lib.lm_misfit_grad(t._h, dt._h if dt is not None else None, ptr(qc), ptr(g), nvec, ptr(gq),
+                                       ptr(gx), ptr(gy), ptr(gd), ptr(ws), nbytes, _stream(None)))
             return gq, gx, gy, gd, None
 
     return _LayeredGreen

@@ -217,6 +217,9 @@ enum { PH_PERMUTE = 0, PH_S2M, PH_M2M, PH_M2L, PH_L2L, PH_LEAF, PH_REFINE };
 // record phase boundaries of the apply in progress (no-ops unless profiling)
 void lm_phase_begin(lm_tree_s *t, int ph, cudaStream_t st);
 void lm_phase_end(lm_tree_s *t, int ph, cudaStream_t st, int launches);
+// bracket one apply for the phase profile (lmfmm_api.cu)
+void lm_profile_apply_start(lm_tree_s *t);
+void lm_profile_apply_stop(lm_tree_s *t);
 
 // setup (lmfmm_setup.cu)
 lm_status lm_setup_tree(lm_tree_s *t, const double *x, const double *y, cudaStream_t st);

@@ -200,3 +200,52 @@ def test_gradients_at_200k_match_central_differences(lm):
             assert abs(fd - an) <= 1e-5 * (abs(an) + 1e-2 * np.max(np.abs(gx))), (j, arr, fd, an)
     fd = dJ(u_at(x, y, MED[3] + h), u_at(x, y, MED[3] - h), h)
     assert abs(fd - gd) <= 1e-5 * abs(gd), (fd, gd)
+
+
+def test_misfit_grad_entry_point(lm):
+    """lm_misfit_grad through the C ABI: the same gradients as the autograd path (which calls
+    it), a NULL output skips that gradient, and bad arguments are rejected before any work."""
+    import ctypes
+
+    import torch
+
+    x, y, q = workloads.uniform_strip(3000, 0.0, 3.0, -0.9, -0.1, nvec=2, seed=31)
+    _, _, gg = workloads.uniform_strip(3000, 0.0, 3.0, -0.9, -0.1, nvec=2, seed=32)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    t = lm.build_tree(lm.create_medium(*workloads.MEDIUM_A, p=20), xd, yd)
+    dt = t.d_tree()
+    qd, gd_in = torch.from_numpy(q).cuda(), torch.from_numpy(gg).cuda()
+    b = ctypes.c_size_t()
+    assert lm._lib.lm_misfit_grad_workspace(t._h, 2, ctypes.byref(b)) == 0
+    ws = torch.empty(b.value, dtype=torch.uint8, device="cuda")
+    gq = torch.empty_like(qd)
+    gx = torch.empty(t.n, dtype=torch.float64, device="cuda")
+    gy = torch.empty_like(gx)
+    gdd = torch.empty((), dtype=torch.float64, device="cuda")
+    P = lambda a: None if a is None else ctypes.c_void_p(a.data_ptr())  # noqa: E731
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lm._lib.lm_misfit_grad(t._h, dt._h, P(qd), P(gd_in), 2, P(gq), P(gx), P(gy), P(gdd), P(ws), b.value,
+                                  st) == 0, lm._lib.lm_last_error()
+    # the same quantities from the separate applies, combined here in float64 as the check
+    ref_q = lm.apply_adjoint(t, gd_in)
+    _, ux, uy = lm.apply_grad(t, torch.cat([qd, torch.conj(gd_in)]).contiguous(), want_u=False)
+    ref_x = torch.real(torch.conj(gd_in) * ux[:2] + qd * ux[2:]).sum(0)
+    ref_y = torch.real(torch.conj(gd_in) * uy[:2] + qd * uy[2:]).sum(0)
+    ref_d = torch.real(torch.sum(torch.conj(gd_in) * lm.apply(dt, qd)))
+    assert torch.equal(gq, ref_q)
+    for got, ref in ((gx, ref_x), (gy, ref_y)):
+        assert float(torch.linalg.norm(got - ref) / torch.linalg.norm(ref)) < 1e-13
+    assert abs(float(gdd) - float(ref_d)) <= 1e-12 * abs(float(ref_d))
+    # outputs left NULL are not computed; the d-gradient alone needs no coordinate work
+    gd2 = torch.empty((), dtype=torch.float64, device="cuda")
+    assert lm._lib.lm_misfit_grad(t._h, dt._h, P(qd), P(gd_in), 2, None, None, None, P(gd2), P(ws), b.value,
+                                  st) == 0
+    assert float(gd2) == float(gdd)
+    # a short workspace, a missing dG/dd tree and a mixed tree's coordinate gradient are rejected
+    assert lm._lib.lm_misfit_grad(t._h, dt._h, P(qd), P(gd_in), 2, None, P(gx), None, None, P(ws), b.value - 8,
+                                  st) == 1
+    assert lm._lib.lm_misfit_grad(t._h, None, P(qd), P(gd_in), 2, None, None, None, P(gdd), P(ws), b.value,
+                                  st) == 1
+    tm = lm.build_tree(lm.create_medium(*workloads.MEDIUM_A, p=12, precision="mixed"), xd, yd)
+    assert lm._lib.lm_misfit_grad(tm._h, None, P(qd), P(gd_in), 2, None, P(gx), None, None, P(ws), b.value,
+                                  st) == 5
