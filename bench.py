@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64"])
     ap.add_argument("--n", type=int, default=N_POINTS)
+    ap.add_argument("--xmax", type=float, default=20.0,
+                    help="strip workload: x in [0, xmax] (20 for the headline; e.g. 400k points on [0, 8] keep its "
+                         "49 points per leaf at depth 5 for a smaller profiling case)")
     ap.add_argument("--p", type=int, default=0)
     ap.add_argument("--depth", type=int, default=-2, help="tree depth (-1 automatic; default per precision)")
     ap.add_argument("--tree", default="adaptive", choices=["adaptive", "uniform"],
@@ -534,7 +537,10 @@ def main():
         precision = "mixed" if getattr(lm, "HAS_MIXED", False) else "fp64"
     p = args.p or (14 if precision == "mixed" else 20)
     depth = args.depth if args.depth != -2 else (5 if precision == "mixed" else 6)
-    x, y, q = workloads.wide_uniform(args.n, NVEC, seed=0)
+    if args.xmax == 20.0:
+        x, y, q = workloads.wide_uniform(args.n, NVEC, seed=0)
+    else:
+        x, y, q = workloads.uniform_strip(args.n, 0.0, args.xmax, -0.95, -0.05, NVEC, seed=0)
     med = workloads.MEDIUM_B
     xd = torch.from_numpy(x).to(dev)
     yd = torch.from_numpy(y).to(dev)
@@ -685,10 +691,12 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if precision == "fp64" else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "wide-strip N=1M uniform x in [0,20], y in [-0.95,-0.05]; "
-                               "medium k=(1,8,2), d=1; 16 complex N(0,1) density vectors",
+        "config": {"workload": (f"wide-strip N={args.n / 1e6:g}M uniform x in [0,{args.xmax:g}], y in [-0.95,-0.05]; "
+                                "medium k=(1,8,2), d=1; 16 complex N(0,1) density vectors"),
                    "n": args.n, "nvec": NVEC, "precision": precision, "p": P, "depth": info["depth"],
-                   "roots": info["R"], "leaves": info["nleaf"], "l2": "inputs (256 MB) larger than L2",
+                   "roots": info["R"], "leaves": info["nleaf"],
+                   "l2": f"inputs ({q.nbytes / 1e6:.0f} MB of densities) larger than L2 (129 MB)"
+                         if q.nbytes > 129e6 else "inputs smaller than L2",
                    "parallelism": f"replicas x{world}", "setup_s": setup_s,
                    "target_vector_evals_per_s": value * NVEC},
         "clocks": ck,
