@@ -59,7 +59,8 @@ def parse():
     ap.add_argument("--workload", default="strip", choices=["strip", "batched", "adjoint", "clustered"],
                     help="strip: the 1M-point headline apply; batched: 48 independent instances in one graph; "
                          "adjoint: J = sum |u - u_obs|^2 and its gradients in q, x, y, d at N = 200k (FP64); "
-                         "clustered: N = 100k, half within 0.01 of y = 0, FP64 on the adaptive tree")
+                         "clustered: N = 100k, half within 0.01 of y = 0, on the adaptive tree (FP64, or "
+                         "--precision mixed)")
     return ap.parse_args()
 
 
@@ -429,9 +430,10 @@ def run_adjoint(args):
 
 def run_clustered(args):
     """N = 100k: half the points uniform in the middle layer, half within 0.01 of y = 0 (x spread
-    10), one complex128 vector, FP64, on the adaptive tree (--tree adaptive, default: 16 points
-    per leaf, p = 22) or the uniform tree of automatic (occupancy-driven) depth (p = 24); the
-    error is measured against the oracle's direct sum on 16 targets x all sources."""
+    10), one complex128 vector, FP64 (or --precision mixed, p = 14), on the adaptive tree (--tree
+    adaptive, default: 16 points per leaf, p = 22) or the uniform tree of automatic
+    (occupancy-driven) depth (p = 24); the error is measured against the oracle's direct sum on 16
+    targets x all sources."""
     import torch
 
     import oracle
@@ -445,10 +447,11 @@ def run_clustered(args):
     med = workloads.MEDIUM_A
     x, y, q = workloads.clustered(n, 1, seed=0)
     # the least order that meets 1e-10 on this workload: adaptive p = 22 (1.7e-11; p = 20 gives
-    # 1.35e-10), uniform p = 24 (4.5e-12; p = 20 gives 1.4e-10)
-    p = args.p or (22 if args.tree == "adaptive" else 24)
+    # 1.35e-10), uniform p = 24 (4.5e-12; p = 20 gives 1.4e-10); the mixed form's bar is 1e-6 (p = 14)
+    mixed = args.precision == "mixed"
+    p = args.p or (14 if mixed else (22 if args.tree == "adaptive" else 24))
     t0 = time.time()
-    opt = dict(p=p, adaptive=args.tree == "adaptive")
+    opt = dict(p=p, adaptive=args.tree == "adaptive", precision="mixed" if mixed else "fp64")
     if args.leaf_target > 0:
         opt["leaf_target"] = args.leaf_target
     elif args.tree == "adaptive":
@@ -492,9 +495,11 @@ def run_clustered(args):
         ref = oracle.direct_apply(med, x, y, q, targets=sub)
         err = float(np.linalg.norm(ud.cpu().numpy()[:, sub] - ref) / np.linalg.norm(ref))
     line = {
-        "metric": "targets/s, layered FMM apply, clustered N=100k (half within 0.01 of y=0), FP64",
+        "metric": "targets/s, layered FMM apply, clustered N=100k (half within 0.01 of y=0), "
+                  + ("mixed precision" if mixed else "FP64"),
         "value": n / (ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if mixed else "f64",
         "data": "synthetic",
         "config": {"workload": "N=100k: 50k x in [0,10], y in [-0.9,-0.1]; 50k x in [0,10], y in [-0.01,0); "
                                "medium k=(1,1.5,2), d=1; 1 complex N(0,1) vector",

@@ -83,8 +83,9 @@ typedef struct {
     int adaptive;    /* 1: adaptive tree (Algorithm 1, step 1) -- a box holding more than
                         leaf_target points is split into its four children while its level is
                         below depth (-1 -> 14); boxes of different levels interact through
-                        lists built by a dual traversal (see lm_build_tree).  LM_FP64 only
-                        (LM_ENOTSUP otherwise).  0 (default): uniform depth. */
+                        lists built by a dual traversal (see lm_build_tree).  Both precisions:
+                        LM_MIXED trees run M2L between any two levels on the CUDA-core staged
+                        contraction, the other steps on the box lists.  0 (default): uniform depth. */
     int m2l_fp64;    /* LM_FP64 trees: 1 runs the M2L, M2M and L2L contractions in IEEE FP64;
                         0 (default) runs them in double-float on the FP32 pipes -- each value a pair of
                         FP32 numbers (48-bit significand), exact products by fma and

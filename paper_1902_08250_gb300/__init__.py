@@ -144,7 +144,7 @@ def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP
     top_bc / bottom_bc: "transmission" (to the outer layer, k1 / k3), or a wall --
     "dirichlet", "neumann", "impedance" (du/dn - i k2 alpha u = 0, alpha = top_alpha /
     bottom_alpha).
-    adaptive = True builds adaptive trees (FP64): a box with more than leaf_target points is
+    adaptive = True builds adaptive trees (either precision): a box with more than leaf_target points is
     split while its level is below depth (-1 -> 14).
     m2l_fp64 = True runs the FP64 form's M2L, M2M and L2L contractions in IEEE FP64 instead of
     double-float on the FP32 pipes."""

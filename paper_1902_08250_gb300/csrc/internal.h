@@ -18,7 +18,7 @@ void lm_set_error(const char *fmt, ...);
 // tree: raise one (never lower it) so that trees built earlier, with larger
 // needs, still launch.  slot names the kernel in a small per-device cache.
 enum { LM_SMEM_NEAR_PW = 0, LM_SMEM_IMAGE_M2L = 1, LM_SMEM_CROSS_M2L = 2, LM_SMEM_NEAR_PW64 = 3,
-       LM_SMEM_IMAGE_M2L_A = 4, LM_SMEM_NEAR_PW64_A = 5, LM_SMEM_SLOTS = 6 };
+       LM_SMEM_IMAGE_M2L_A = 4, LM_SMEM_NEAR_PW64_A = 5, LM_SMEM_NEAR_PW_A = 6, LM_SMEM_SLOTS = 7 };
 cudaError_t lm_raise_smem(const void *func, int slot, int bytes);
 
 #define LM_CUDA(call)                                                                       \
@@ -158,6 +158,10 @@ struct AdaptTree {
     zd *tab = nullptr;                                 // [nclass][np][np] scaled M2L tables
     zd *M = nullptr, *Lc = nullptr;                    // [nbox][np][LM_MAXV]
     float4 *tabdf = nullptr, *tabdft = nullptr, *Mdf = nullptr; // double-float copies (as Level)
+    // mixed form: FP32 copies of the tables and expansions, and per level the boxes with V entries
+    zf *tab32 = nullptr, *M32 = nullptr, *L32 = nullptr;
+    std::vector<int32_t *> m2l_tgt;
+    std::vector<int64_t> m2l_ntgt;
 };
 
 struct lm_tree_s {
@@ -242,6 +246,7 @@ lm_status lm_setup_df(lm_tree_s *t, cudaStream_t st); // double-float tables and
 lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, zd *uy, cudaStream_t st);
 // mixed precision (lmfmm_mixed.cu)
 lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st);
+lm_status lm_setup_mixed_adaptive(lm_tree_s *t, cudaStream_t st);
 lm_status lm_autotune_mixed(lm_tree_s *t, cudaStream_t st, int *choice, float *ms);
 lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st);
 void lm_free_mixed(lm_tree_s *t);

@@ -562,6 +562,7 @@ lm_status lm_setup_adaptive(lm_tree_s *t, const double *x, const double *y, cuda
         lm_set_error("build_tree: a layered M2L table overflowed; lower p");
         return LM_ENOTSUP;
     }
+    if (t->precision == LM_MIXED) return lm_setup_mixed_adaptive(t, st);
     return lm_setup_df(t, st);
 }
 

@@ -120,10 +120,6 @@ extern "C" lm_status lm_create_medium(double k1, double k2, double k3, double d,
         lm_set_error("create_medium: adaptive must be 0 or 1");
         return LM_EINVAL;
     }
-    if (o.adaptive && o.precision != LM_FP64) {
-        lm_set_error("create_medium: the adaptive tree is built for LM_FP64 only");
-        return LM_ENOTSUP;
-    }
     if (o.seg_order > 64 || o.tail_order > 256 || o.tail_rays > 64) {
         lm_set_error("create_medium: quadrature orders out of range");
         return LM_EINVAL;
@@ -188,7 +184,8 @@ extern "C" lm_status lm_build_tree(lm_medium m, const double *x, const double *y
         s = lm_setup_tree(t, x, y, st);
         if (s == LM_OK) s = lm_setup_tables(t, st);
     }
-    if (s == LM_OK && t->precision == LM_MIXED && m->opt.autotune) s = lm_autotune_mixed(t, st, nullptr, nullptr);
+    if (s == LM_OK && t->precision == LM_MIXED && !t->adaptive && m->opt.autotune)
+        s = lm_autotune_mixed(t, st, nullptr, nullptr);
     if (s != LM_OK) {
         cudaStreamSynchronize(st);
         lm_destroy_tree(t);
@@ -239,7 +236,7 @@ extern "C" lm_status lm_autotune(lm_tree t, void *stream, int *choice, float *ms
         lm_set_error("autotune: NULL tree");
         return LM_EINVAL;
     }
-    if (t->precision != LM_MIXED) {
+    if (t->precision != LM_MIXED || t->adaptive) { // no tile shapes to choose: FP64, or the adaptive tree's list M2L
         for (int l = 0; l <= t->L; ++l) {
             if (choice) choice[l] = -1;
             if (ms) ms[l] = 0.f;

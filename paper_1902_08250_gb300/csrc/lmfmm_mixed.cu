@@ -17,6 +17,66 @@ static int gridm(int64_t n, int b) { return (int)((n + b - 1) / b); }
 
 LM_HD zf f2(zd a) { return zf{(float)a.re, (float)a.im}; }
 
+// Box geometry of the FP32 kernels.  Grid32: leaf i of the uniform leaf lattice
+// (ncol columns of width w); List32: box ids[i] of the adaptive tree, with
+// centres and widths from its arrays.  offset(t, s) = centre_t - centre_s.
+struct Grid32 {
+    int64_t ncol;
+    float w;
+    __device__ int64_t id(int64_t i) const { return i; }
+    __device__ float width(int64_t) const { return w; }
+    __device__ void offset(int64_t bt, int64_t bs, float &ox, float &oy) const
+    {
+        const int rt = (int)(bt / ncol), ct = (int)(bt % ncol), rs = (int)(bs / ncol), cs = (int)(bs % ncol);
+        ox = (float)(ct - cs) * w;
+        oy = -(float)(rt - rs) * w;
+    }
+};
+struct EdgeGrid32 : Grid32 { // the leaves of the top row, then (nrow > 1) of the bottom row
+    int64_t nrow;
+    __device__ int64_t id(int64_t i) const { return ((nrow == 1 || i < ncol) ? 0 : nrow - 1) * ncol + i % ncol; }
+};
+struct List32 {
+    const int32_t *ids;
+    const double *bx, *by, *bw;
+    __device__ int64_t id(int64_t i) const { return ids[i]; }
+    __device__ float width(int64_t b) const { return (float)bw[b]; }
+    __device__ void offset(int64_t bt, int64_t bs, float &ox, float &oy) const
+    {
+        ox = (float)(bx[bt] - bx[bs]);
+        oy = (float)(by[bt] - by[bs]);
+    }
+};
+// parents and their four children: the lattice one level down, or the adaptive tree's links
+struct GridKids32 {
+    int64_t ncol;
+    __device__ int64_t parent(int64_t i) const { return i; }
+    __device__ int64_t child(int64_t b, int pos) const
+    {
+        const int64_t r = b / ncol, c = b % ncol;
+        return (2 * r + (pos >> 1)) * (2 * ncol) + 2 * c + (pos & 1);
+    }
+};
+struct ListKids32 {
+    const int32_t *ids, *kids;
+    __device__ int64_t parent(int64_t i) const { return ids[i]; }
+    __device__ int64_t child(int64_t b, int pos) const { return kids[4 * b + pos]; }
+};
+// boxes of a level and their parents: the lattice one level up, or the adaptive tree's links
+struct GridPar32 {
+    int64_t ncol;
+    __device__ int64_t box(int64_t i) const { return i; }
+    __device__ int64_t parent(int64_t b) const { return (b / ncol / 2) * (ncol / 2) + (b % ncol) / 2; }
+    __device__ int pos(int64_t b) const { return (int)(((b / ncol) & 1) * 2 + ((b % ncol) & 1)); }
+};
+struct ListPar32 {
+    int64_t b0;
+    const int32_t *par, *cpos;
+    __device__ int64_t box(int64_t i) const { return b0 + i; }
+    __device__ int64_t parent(int64_t b) const { return par[b]; }
+    __device__ int pos(int64_t b) const { return cpos[b]; }
+};
+
 // ---------------------------------------------------------------------------
 // setup
 // ---------------------------------------------------------------------------
@@ -88,10 +148,10 @@ __global__ void k_scan64b(int64_t *c, int64_t m)
 
 static size_t near_pw_smem(const lm_tree_s *t);
 __global__ void k_inverse_perm(const int64_t *perm, int64_t n, int64_t *iperm);
-__global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, float w, float d, const float *xl,
-                                                   const float *y32, const int64_t *ls, const int64_t *ustart,
-                                                   const int32_t *usrc, const int32_t *uterm, NearQuadF nq,
-                                                   const zf *qs, zf *us);
+template <class G>
+__global__ void __launch_bounds__(256) k_near_pw32(G geo, float d, const float *xl, const float *y32,
+                                                   const int64_t *ls, const int64_t *ustart, const int32_t *usrc,
+                                                   const int32_t *uterm, NearQuadF nq, const zf *qs, zf *us);
 
 #define TRYM(x)                      \
     do {                             \
@@ -107,6 +167,7 @@ static lm_status conv(lm_tree_s *t, const A *src, B **dst, int64_t n, cudaStream
     return LM_OK;
 }
 
+static lm_status setup_mixed_points(lm_tree_s *t, cudaStream_t st);
 lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
 {
     const int L = t->L, P = t->p, np = 2 * P + 1;
@@ -170,6 +231,21 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
         k_local_coords<<<(unsigned)lv.nbox, 64, 0, st>>>(lv.ncol, t->x0, lv.w, t->leaf_start, t->xs, t->ys,
                                                           t->xl32, t->yl32, t->y32);
     }
+    TRYM(setup_mixed_points(t, st));
+    if (t->med.opt.tensor_m2l) TRYM(lm_setup_tc(t, st));
+    if (t->tc_ready) TRYM(lm_setup_tt(t, st));
+    for (Level &lv : t->lev) lv.m2l_impl = t->tc_ready ? 0 : 4;
+    LM_CUDA(cudaGetLastError());
+    LM_CUDA(cudaStreamSynchronize(st));
+    return LM_OK;
+}
+
+// tree-order point data of the mixed form that does not depend on the tree kind:
+// the inverse permutation, FP32 density / potential scratch and the FP32 near-field
+// quadrature tables (the leaf-local coordinates are written by the caller)
+static lm_status setup_mixed_points(lm_tree_s *t, cudaStream_t st)
+{
+    const int64_t n = t->n;
     TRYM(lm_dalloc(t, &t->iperm, n));
     k_inverse_perm<<<gridm(n, 256), 256, 0, st>>>(t->perm, n, t->iperm);
     TRYM(lm_dalloc(t, &t->qs32, n * LM_MAXV));
@@ -187,10 +263,72 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
         lm_set_error("build_tree: near-field segment of %d nodes is too long for the factorised kernel", q.nseg);
         return LM_ENOTSUP;
     }
-    LM_CUDA(lm_raise_smem((const void *)k_near_pw32, LM_SMEM_NEAR_PW, (int)shm));
-    if (t->med.opt.tensor_m2l) TRYM(lm_setup_tc(t, st));
-    if (t->tc_ready) TRYM(lm_setup_tt(t, st));
-    for (Level &lv : t->lev) lv.m2l_impl = t->tc_ready ? 0 : 4;
+    LM_CUDA(lm_raise_smem((const void *)k_near_pw32<EdgeGrid32>, LM_SMEM_NEAR_PW, (int)shm));
+    LM_CUDA(lm_raise_smem((const void *)k_near_pw32<List32>, LM_SMEM_NEAR_PW_A, (int)shm));
+    return LM_OK;
+}
+
+// leaf-local coordinates of the adaptive tree's leaves (box centres from its arrays)
+__global__ void k_local_coords_list(const int32_t *leaves, const double *bx, const double *by, const int64_t *ls,
+                                    const double *xs, const double *ys, float *xl, float *yl, float *y32)
+{
+    const int64_t b = leaves[blockIdx.x];
+    const double cx = bx[b], cy = by[b];
+    for (int64_t i = ls[b] + threadIdx.x; i < ls[b + 1]; i += blockDim.x) {
+        xl[i] = (float)(xs[i] - cx);
+        yl[i] = (float)(ys[i] - cy);
+        y32[i] = (float)ys[i];
+    }
+}
+
+// Mixed form of the adaptive tree (Algorithm 1 step 1, reading G14): FP32 copies of
+// the cross-level M2L tables and of each level's M2M / L2L tables, FP32 expansions
+// of every box, per level the boxes that have V entries, and the leaf-local points.
+// The M2L runs on the staged CUDA-core contraction over the V list (any two levels);
+// the leaf, S2M, M2M, L2L and segment kernels take the box lists as their geometry.
+lm_status lm_setup_mixed_adaptive(lm_tree_s *t, cudaStream_t st)
+{
+    AdaptTree &A = t->at;
+    const int L = t->L, P = t->p, np = 2 * P + 1;
+    if (P > MX_MAXP || !lm_mixed_order_supported(P)) {
+        lm_set_error("build_tree: the mixed-precision path supports p in {4,6,8..14,16,18,20,24}");
+        return LM_ENOTSUP;
+    }
+    const int64_t ncls = (int64_t)A.cls_term.size();
+    TRYM(conv(t, A.tab, &A.tab32, std::max<int64_t>(1, ncls) * np * np, st));
+    for (int l = 0; l <= L; ++l) {
+        Level &lv = t->lev[l];
+        if (lv.m2m) TRYM(conv(t, lv.m2m, &lv.m2m32, 4 * np * np, st));
+        if (lv.l2l) TRYM(conv(t, lv.l2l, &lv.l2l32, 4 * np * np, st));
+    }
+    TRYM(lm_dalloc(t, &A.M32, (size_t)A.nbox * np * LM_MAXV));
+    TRYM(lm_dalloc(t, &A.L32, (size_t)A.nbox * np * LM_MAXV));
+    {
+        std::vector<int64_t> hs(A.nbox + 1);
+        LM_CUDA(cudaMemcpyAsync(hs.data(), A.vstart, (A.nbox + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        LM_CUDA(cudaStreamSynchronize(st));
+        A.m2l_tgt.assign(L + 1, nullptr);
+        A.m2l_ntgt.assign(L + 1, 0);
+        for (int l = 0; l <= L; ++l) {
+            std::vector<int32_t> tg;
+            for (int64_t b = A.lev_start[l]; b < A.lev_start[l + 1]; ++b)
+                if (hs[b + 1] > hs[b]) tg.push_back((int32_t)b);
+            A.m2l_ntgt[l] = (int64_t)tg.size();
+            TRYM(lm_dalloc(t, &A.m2l_tgt[l], tg.size()));
+            if (!tg.empty())
+                LM_CUDA(cudaMemcpyAsync(A.m2l_tgt[l], tg.data(), tg.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                                        st));
+            LM_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+    const int64_t n = t->n;
+    TRYM(lm_dalloc(t, &t->xl32, n));
+    TRYM(lm_dalloc(t, &t->yl32, n));
+    TRYM(lm_dalloc(t, &t->y32, n));
+    if (A.nleaf > 0)
+        k_local_coords_list<<<(unsigned)A.nleaf, 64, 0, st>>>(A.leaves, A.cx, A.cy, t->leaf_start, t->xs, t->ys,
+                                                              t->xl32, t->yl32, t->y32);
+    TRYM(setup_mixed_points(t, st));
     LM_CUDA(cudaGetLastError());
     LM_CUDA(cudaStreamSynchronize(st));
     return LM_OK;
@@ -199,6 +337,14 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
 void lm_free_mixed(lm_tree_s *t)
 {
     lm_free_tt(t);
+    {
+        AdaptTree &A = t->at;
+        void *ap[] = {A.tab32, A.M32, A.L32};
+        for (void *p : ap)
+            if (p) cudaFree(p);
+        for (int32_t *p : A.m2l_tgt)
+            if (p) cudaFree(p);
+    }
     void *ptrs[] = {t->xl32, t->yl32, t->y32, t->qs32, t->us32, t->iperm, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w,
                     t->nq_tail_lam, t->nq_tail_s2, t->nq_tail_w};
     for (void *p : ptrs)
@@ -268,16 +414,17 @@ __global__ void k_inverse_perm(const int64_t *perm, int64_t n, int64_t *iperm)
 
 // S2M in FP32 (Eq. (multipole_coef), scaled): one block per leaf
 #define P2M32_CHUNK 32
-__global__ void k_p2m32(int P, float k, float w, const float *xl, const float *yl, const int64_t *ls,
+template <class G>
+__global__ void k_p2m32(G geo, int P, float k, const float *xl, const float *yl, const int64_t *ls,
                         const zf *qs, int nvs, zf *M)
 {
     extern __shared__ unsigned char smem[];
     const int np = 2 * P + 1;
     zf *B = (zf *)smem;                        // [P2M32_CHUNK][np]
     zf *Q = B + P2M32_CHUNK * np;              // [P2M32_CHUNK][LM_MAXV]
-    const int64_t b = blockIdx.x;
+    const int64_t b = geo.id(blockIdx.x);
     const int64_t lo = ls[b], hi = ls[b + 1];
-    const float sc = k * w;
+    const float sc = k * geo.width(b);
     const int nent = np * nvs; // (order, vector) entries computed; M keeps 16 vector slots
     zf acc[8];
     for (int e = 0; e < 8; ++e) acc[e] = zf{0.f, 0.f};
@@ -428,7 +575,8 @@ int lm_h0_terms(double xmax)
 // B_{n,s} (phase A) and then evaluates them at its targets (phase B).
 // One block per leaf in the top or bottom row; adds into us.
 #define PW_SRC 128
-__global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, float w, float d, const float *xl,
+template <class G>
+__global__ void __launch_bounds__(256) k_near_pw32(G geo, float d, const float *xl,
                                                    const float *y32, const int64_t *ls, const int64_t *ustart,
                                                    const int32_t *usrc, const int32_t *uterm, NearQuadF nq,
                                                    const zf *qs, zf *us)
@@ -439,9 +587,7 @@ __global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, f
     zf *SQ = B + (size_t)nk * LM_MAXV;          // [PW_SRC][LM_MAXV]
     float *SX = (float *)(SQ + PW_SRC * LM_MAXV); // [PW_SRC]
     float *SY = SX + PW_SRC;                    // [PW_SRC]
-    const int64_t row = (nrow == 1 || blockIdx.x < ncol) ? 0 : nrow - 1;
-    const int64_t col = blockIdx.x % ncol;
-    const int64_t b = row * ncol + col;
+    const int64_t b = geo.id(blockIdx.x);
     for (int term = 1; term <= 2; ++term) {
         bool any = false;
         for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) any |= (uterm[e] == term);
@@ -453,7 +599,8 @@ __global__ void __launch_bounds__(256) k_near_pw32(int64_t ncol, int64_t nrow, f
         for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
             if (uterm[e] != term) continue;
             const int64_t s = usrc[e];
-            const float ox = (float)(s % ncol - col) * w; // centre_s - centre_T
+            float ox, oy;
+            geo.offset(s, b, ox, oy); // centre_s - centre_T
             for (int64_t j0 = ls[s]; j0 < ls[s + 1]; j0 += PW_SRC) {
                 const int cnt = (int)min((int64_t)PW_SRC, ls[s + 1] - j0);
                 __syncthreads();
@@ -649,16 +796,16 @@ __global__ void __launch_bounds__(128) k_m2l_rest32(const int32_t *rtgt, const i
 
 // M2M (Lemma M2M): a parent (this level) from its four children (level l + 1),
 // table slot = child position (dy, dx); writes the parent's coefficients
-template <int NP, int NVS>
-__global__ void __launch_bounds__(128) k_m2m32(int64_t ncol, const zf *tabs, const zf *Mc, zf *Mp)
+template <int NP, int NVS, class K = GridKids32>
+__global__ void __launch_bounds__(128) k_m2m32(K kids, const zf *tabs, const zf *Mc, zf *Mp)
 {
     constexpr int NR = Staged<NP, NVS>::NR, NB = Staged<NP, NVS>::NB, NG = Staged<NP, NVS>::NG;
     __shared__ __align__(16) zf Ts[NB][NP * NP];
     __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
-    const int64_t b = blockIdx.x, r = b / ncol, c = b % ncol, ncc = 2 * ncol;
+    const int64_t b = kids.parent(blockIdx.x);
     auto entry = [&](int pos, int *slot, int64_t *src) {
         *slot = pos;
-        *src = (2 * r + (pos >> 1)) * ncc + 2 * c + (pos & 1);
+        *src = kids.child(b, pos);
     };
     zf acc[NR];
     staged_contract<NP, NVS>(4, entry, tabs, Mc, acc, Ts, Ms);
@@ -673,16 +820,16 @@ __global__ void __launch_bounds__(128) k_m2m32(int64_t ncol, const zf *tabs, con
 // L2L (Lemma L2L): a child (this level) from its parent (level l - 1), table
 // slot = the child's position in the parent; writes the child's coefficients,
 // or adds them (ACC) where the level's M2L has already written them
-template <int NP, int NVS, bool ACC = false>
-__global__ void __launch_bounds__(128) k_l2l32(int64_t ncol, const zf *tabs, const zf *Lp, zf *Lc)
+template <int NP, int NVS, bool ACC = false, class K = GridPar32>
+__global__ void __launch_bounds__(128) k_l2l32(K par, const zf *tabs, const zf *Lp, zf *Lc)
 {
     constexpr int NR = Staged<NP, NVS>::NR, NB = Staged<NP, NVS>::NB, NG = Staged<NP, NVS>::NG;
     __shared__ __align__(16) zf Ts[NB][NP * NP];
     __shared__ __align__(16) zf Ms[NB][NP * LM_MAXV];
-    const int64_t b = blockIdx.x, r = b / ncol, c = b % ncol;
+    const int64_t b = par.box(blockIdx.x);
     auto entry = [&](int, int *slot, int64_t *src) {
-        *slot = (int)((r & 1) * 2 + (c & 1));
-        *src = (r / 2) * (ncol / 2) + c / 2;
+        *slot = par.pos(b);
+        *src = par.parent(b);
     };
     zf acc[NR];
     staged_contract<NP, NVS>(1, entry, tabs, Lp, acc, Ts, Ms);
@@ -778,8 +925,8 @@ __device__ __forceinline__ LeafChunk leaf_chunk(const LeafChunkTable &T, const i
 // DEG > 0: every free near pair has t = (k r / 2)^2 <= 1 and the series of degree
 // DEG meets the 1e-9 truncation bound (lm_h0_terms); DEG = 0: degree 8 and the far form.
 #define LEAF32_THREADS 64
-template <int P, int NV, int DEG = 0>
-__global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, float w, float k, float d, const float *xl,
+template <int P, int NV, int DEG = 0, class G = Grid32>
+__global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(G geo, float k, float d, const float *xl,
                                                   const float *yl, const float *y32, const int64_t *ls,
                                                   const int64_t *ustart, const int32_t *usrc, const int32_t *uterm,
                                                   NearQuadF nq, const zf *Lc, const zf *qs, zf *us, int nterms,
@@ -789,8 +936,8 @@ __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, floa
     __shared__ __align__(16) zf sq[2][LCAP * LM_MAXV];
     __shared__ float sx[2][LCAP], sy[2][LCAP], sya[2][LCAP];
     __shared__ __align__(16) zf sacc[NV * LEAF32_THREADS]; // running sums per target and vector
-    const int64_t b = blockIdx.x;
-    const int rt = (int)(b / ncol), ct = (int)(b % ncol);
+    const int64_t b = geo.id(blockIdx.x);
+    const float w = geo.width(b);
     const zf *Lb = Lc + b * NP * LM_MAXV;
     const int lo = (int)ls[b], hi = (int)ls[b + 1];
     const int e0 = (int)ustart[b], e1 = (int)ustart[b + 1];
@@ -860,8 +1007,8 @@ __global__ void __launch_bounds__(LEAF32_THREADS, 8) k_leaf32(int64_t ncol, floa
             }
             const LeafChunk ch = chunk(c);
             const int s = usrc[ch.e], term = uterm[ch.e];
-            const int rs = s / (int)ncol, cs = s % (int)ncol;
-            const float ox = (float)(ct - cs) * w, oy = -(float)(rt - rs) * w; // centre_t - centre_s
+            float ox, oy;
+            geo.offset(b, s, ox, oy); // centre_t - centre_s
             if (act) {
                 // the chunk's sums on the paired FP32 pipe: A_v = sum g.re q_v and B_v = sum g.im q_v,
                 // each a (re, im) pair, so that g q_v = (A.x - B.y, A.y + B.x) at the end of the chunk
@@ -963,25 +1110,25 @@ static void launch_m2m(const Level &lv, const Level &child, cudaStream_t st, int
 {
     constexpr int NP = 2 * P + 1;
     if (nvs == 4)
-        k_m2m32<NP, 4><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.m2m32, child.M32, lv.M32);
+        k_m2m32<NP, 4><<<(unsigned)lv.nbox, 128, 0, st>>>(GridKids32{lv.ncol}, lv.m2m32, child.M32, lv.M32);
     else
-        k_m2m32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.m2m32, child.M32, lv.M32);
+        k_m2m32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(GridKids32{lv.ncol}, lv.m2m32, child.M32, lv.M32);
 }
 template <int P>
 static void launch_l2l(const Level &lv, const Level &par, cudaStream_t st, int nvs)
 {
     constexpr int NP = 2 * P + 1;
     if (nvs == 4)
-        k_l2l32<NP, 4><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
+        k_l2l32<NP, 4><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
     else
-        k_l2l32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
+        k_l2l32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
 }
 // L2L of the tile-form apply (16 vector slots): adds to the M2L's local expansions
 template <int P>
 static void launch_l2l_acc(const Level &lv, const Level &par, cudaStream_t st)
 {
     constexpr int NP = 2 * P + 1;
-    k_l2l32<NP, LM_MAXV, true><<<(unsigned)lv.nbox, 128, 0, st>>>(lv.ncol, lv.l2l32, par.L32, lv.L32);
+    k_l2l32<NP, LM_MAXV, true><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
 }
 template <int P>
 static void launch_rest(const Level &lv, cudaStream_t st, int nvs)
@@ -1004,15 +1151,15 @@ static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st, int 
     const int free_on = t->med.opt.kernel == LM_KERNEL_G;
     if (nv > 4 && xmax <= 2.0 && nterms <= 6) // short series, no far form (k2 w <= 0.7)
         k_leaf32<P, LM_MAXV, 6><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(
-            lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d, t->xl32, t->yl32, t->y32, t->leaf_start,
+            Grid32{lv.ncol, (float)lv.w}, (float)t->med.k2, (float)t->med.d, t->xl32, t->yl32, t->y32, t->leaf_start,
             t->ustart, t->usrc, t->uterm, nq, lv.L32, t->qs32, t->us32, nterms, free_on);
     else if (nv <= 4) // the batched form's 4-vector applies: a quarter of the contraction
-        k_leaf32<P, 4><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2, (float)t->med.d,
+        k_leaf32<P, 4><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(Grid32{lv.ncol, (float)lv.w}, (float)t->med.k2, (float)t->med.d,
                                                          t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart,
                                                          t->usrc, t->uterm, nq, lv.L32, t->qs32, t->us32, nterms,
                                                          free_on);
     else
-        k_leaf32<P, LM_MAXV><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(lv.ncol, (float)lv.w, (float)t->med.k2,
+        k_leaf32<P, LM_MAXV><<<(unsigned)lv.nbox, LEAF32_THREADS, 0, st>>>(Grid32{lv.ncol, (float)lv.w}, (float)t->med.k2,
                                                                (float)t->med.d, t->xl32, t->yl32, t->y32,
                                                                t->leaf_start, t->ustart, t->usrc, t->uterm, nq,
                                                                lv.L32, t->qs32, t->us32, nterms, free_on);
@@ -1051,16 +1198,138 @@ bool lm_mixed_order_supported(int P)
     }
 }
 
-lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st)
+static NearQuadF nqf_of(const lm_tree_s *t)
 {
+    return NearQuadF{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w, t->nq_tail_lam,
+                     t->nq_tail_s2, t->nq_tail_w,
+                     t->med.opt.top_bc != LM_BC_IMPEDANCE && t->med.opt.bottom_bc != LM_BC_IMPEDANCE,
+                     {(float)t->nq.rinf[0], (float)t->nq.rinf[1]}, (float)t->nq.hray,
+                     (float)(0.25 * t->med.k2 * t->med.k2)};
+}
+
+// the mixed apply on the adaptive tree: the steps of the uniform apply over box lists
+template <int P>
+static void launch_m2m_list(const AdaptTree &A, const Level &lv, int l, cudaStream_t st, int nvs)
+{
+    constexpr int NP = 2 * P + 1;
+    const int64_t npar = A.nl_start[l + 1] - A.nl_start[l];
+    if (npar == 0) return;
+    const ListKids32 kids{A.nonleaf + A.nl_start[l], A.child};
+    if (nvs == 4)
+        k_m2m32<NP, 4, ListKids32><<<(unsigned)npar, 128, 0, st>>>(kids, lv.m2m32, A.M32, A.M32);
+    else
+        k_m2m32<NP, LM_MAXV, ListKids32><<<(unsigned)npar, 128, 0, st>>>(kids, lv.m2m32, A.M32, A.M32);
+}
+template <int P>
+static void launch_l2l_list(const AdaptTree &A, const Level &lv, int l, cudaStream_t st, int nvs)
+{
+    constexpr int NP = 2 * P + 1;
+    const int64_t b0 = A.lev_start[l], nb = A.lev_start[l + 1] - b0;
+    if (nb == 0) return;
+    const ListPar32 par{b0, A.parent, A.pos};
+    if (nvs == 4)
+        k_l2l32<NP, 4, false, ListPar32><<<(unsigned)nb, 128, 0, st>>>(par, lv.l2l32, A.L32, A.L32);
+    else
+        k_l2l32<NP, LM_MAXV, false, ListPar32><<<(unsigned)nb, 128, 0, st>>>(par, lv.l2l32, A.L32, A.L32);
+}
+template <int P>
+static void launch_rest_list(const AdaptTree &A, int l, cudaStream_t st, int nvs)
+{
+    constexpr int NP = 2 * P + 1;
+    if (A.m2l_ntgt[l] == 0) return;
+    if (nvs == 4)
+        k_m2l_rest32<NP, 4><<<(unsigned)A.m2l_ntgt[l], 128, 0, st>>>(A.m2l_tgt[l], A.vstart, A.vsrc, A.vslot,
+                                                                       A.tab32, A.M32, A.L32);
+    else
+        k_m2l_rest32<NP, LM_MAXV><<<(unsigned)A.m2l_ntgt[l], 128, 0, st>>>(A.m2l_tgt[l], A.vstart, A.vsrc,
+                                                                             A.vslot, A.tab32, A.M32, A.L32);
+}
+template <int P>
+static void launch_leaf_list(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st, int nv)
+{
+    const AdaptTree &A = t->at;
+    const List32 leaves{A.leaves, A.cx, A.cy, A.w};
+    const int free_on = t->med.opt.kernel == LM_KERNEL_G;
+    if (nv <= 4)
+        k_leaf32<P, 4, 0, List32><<<(unsigned)A.nleaf, LEAF32_THREADS, 0, st>>>(
+            leaves, (float)t->med.k2, (float)t->med.d, t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart, t->usrc,
+            t->uterm, nq, A.L32, t->qs32, t->us32, 11, free_on);
+    else
+        k_leaf32<P, LM_MAXV, 0, List32><<<(unsigned)A.nleaf, LEAF32_THREADS, 0, st>>>(
+            leaves, (float)t->med.k2, (float)t->med.d, t->xl32, t->yl32, t->y32, t->leaf_start, t->ustart, t->usrc,
+            t->uterm, nq, A.L32, t->qs32, t->us32, 11, free_on);
+}
+
+static lm_status run_mixed_adaptive(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64,
+                                    cudaStream_t st)
+{
+    const AdaptTree &A = t->at;
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const int64_t n = t->n;
     const float k = (float)t->med.k2;
-    NearQuadF nq{t->nq.nseg, t->nq.nray, t->nq.ntail, t->nq_seg_lam, t->nq_seg_s2, t->nq_seg_w, t->nq_tail_lam,
-                 t->nq_tail_s2, t->nq_tail_w,
-                 t->med.opt.top_bc != LM_BC_IMPEDANCE && t->med.opt.bottom_bc != LM_BC_IMPEDANCE,
-                 {(float)t->nq.rinf[0], (float)t->nq.rinf[1]}, (float)t->nq.hray,
-                 (float)(0.25 * t->med.k2 * t->med.k2)};
+    const NearQuadF nq = nqf_of(t);
+    const List32 leaves{A.leaves, A.cx, A.cy, A.w}, pwl{A.pwleaves, A.cx, A.cy, A.w};
+    for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
+        const int nv = std::min(LM_MAXV, nvec - v0);
+        const int nvs = nv <= 4 ? 4 : LM_MAXV;
+        lm_phase_begin(t, PH_PERMUTE, st);
+        if (c64)
+            k_permute_in32<zf><<<gridm(n, 256), 256, 0, st>>>((const zf *)q + (int64_t)v0 * n, t->iperm, n, nv,
+                                                             adjoint, t->qs32);
+        else
+            k_permute_in32<zd><<<gridm(n, 256), 256, 0, st>>>((const zd *)q + (int64_t)v0 * n, t->iperm, n, nv,
+                                                             adjoint, t->qs32);
+        lm_phase_end(t, PH_PERMUTE, st, 1);
+        lm_phase_begin(t, PH_S2M, st);
+        if (A.nleaf > 0) {
+            const size_t shm = (P2M32_CHUNK * np + P2M32_CHUNK * LM_MAXV) * sizeof(zf);
+            k_p2m32<List32><<<(unsigned)A.nleaf, 128, shm, st>>>(leaves, P, k, t->xl32, t->yl32, t->leaf_start,
+                                                                 t->qs32, nvs, A.M32);
+        }
+        lm_phase_end(t, PH_S2M, st, 1);
+        if (L > 0) lm_phase_begin(t, PH_M2M, st);
+        for (int l = L - 1; l >= 0; --l) MX_DISPATCH(P, launch_m2m_list, A, t->lev[l], l, st, nvs);
+        if (L > 0) lm_phase_end(t, PH_M2M, st, L);
+        for (int l = 0; l <= L; ++l) {
+            lm_phase_begin(t, PH_L2L, st);
+            if (l == 0) {
+                const int64_t nb = A.lev_start[1] - A.lev_start[0];
+                LM_CUDA(cudaMemsetAsync(A.L32 + A.lev_start[0] * np * LM_MAXV, 0, nb * np * LM_MAXV * sizeof(zf), st));
+            } else {
+                MX_DISPATCH(P, launch_l2l_list, A, t->lev[l], l, st, nvs);
+            }
+            lm_phase_end(t, PH_L2L, st, l > 0);
+            lm_phase_begin(t, PH_M2L, st);
+            MX_DISPATCH(P, launch_rest_list, A, l, st, nvs);
+            lm_phase_end(t, PH_M2L, st, A.m2l_ntgt[l] > 0);
+        }
+        lm_phase_begin(t, PH_LEAF, st);
+        if (A.nleaf > 0) MX_DISPATCH(P, launch_leaf_list, t, nq, st, nv);
+        if (A.npw > 0)
+            k_near_pw32<List32><<<(unsigned)A.npw, 256, near_pw_smem(t), st>>>(
+                pwl, (float)t->med.d, t->xl32, t->y32, t->leaf_start, t->ustart, t->usrc, t->uterm, nq, t->qs32,
+                t->us32);
+        lm_phase_end(t, PH_LEAF, st, 1 + (A.npw > 0));
+        lm_phase_begin(t, PH_PERMUTE, st);
+        if (c64)
+            k_permute_out32<zf><<<gridm(n, 256), 256, 0, st>>>(t->us32, t->iperm, n, nv, adjoint,
+                                                              (zf *)u + (int64_t)v0 * n);
+        else
+            k_permute_out32<zd><<<gridm(n, 256), 256, 0, st>>>(t->us32, t->iperm, n, nv, adjoint,
+                                                              (zd *)u + (int64_t)v0 * n);
+        lm_phase_end(t, PH_PERMUTE, st, 1);
+        LM_CUDA(cudaGetLastError());
+    }
+    return LM_OK;
+}
+
+lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st)
+{
+    if (t->adaptive) return run_mixed_adaptive(t, q, nvec, u, adjoint, c64, st);
+    const int L = t->L, P = t->p, np = 2 * P + 1;
+    const int64_t n = t->n;
+    const float k = (float)t->med.k2;
+    const NearQuadF nq = nqf_of(t);
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         const int nvs = nv <= 4 ? 4 : LM_MAXV; // vector slots the contractions compute
@@ -1076,7 +1345,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
         {
             Level &lv = t->lev[L];
             size_t shm = (P2M32_CHUNK * np + P2M32_CHUNK * LM_MAXV) * sizeof(zf);
-            k_p2m32<<<(unsigned)lv.nbox, 128, shm, st>>>(P, k, (float)lv.w, t->xl32, t->yl32, t->leaf_start,
+            k_p2m32<<<(unsigned)lv.nbox, 128, shm, st>>>(Grid32{lv.ncol, (float)lv.w}, P, k, t->xl32, t->yl32, t->leaf_start,
                                                          t->qs32, nvs, lv.M32);
         }
         lm_phase_end(t, PH_S2M, st, 1);
@@ -1128,7 +1397,11 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
         {
             const Level &lv = t->lev[L];
             const unsigned nb = (unsigned)(lv.nrow == 1 ? lv.ncol : 2 * lv.ncol);
-            k_near_pw32<<<nb, 256, near_pw_smem(t), st>>>(lv.ncol, lv.nrow, (float)lv.w, (float)t->med.d, t->xl32,
+            EdgeGrid32 eg;
+            eg.ncol = lv.ncol;
+            eg.w = (float)lv.w;
+            eg.nrow = lv.nrow;
+            k_near_pw32<<<nb, 256, near_pw_smem(t), st>>>(eg, (float)t->med.d, t->xl32,
                                                           t->y32, t->leaf_start, t->ustart, t->usrc, t->uterm, nq,
                                                           t->qs32, t->us32);
         }
