@@ -266,8 +266,9 @@ def whole_job_value(n_per_rank, world, ms):
 
 def run_batched(args):
     """48 independent instances (own medium, N log-uniform in [10k, 500k], 4
-    complex64 vectors), mixed precision with autotuned M2L tile shapes, captured
-    into one CUDA graph; one step = one launch of the whole batch."""
+    complex64 vectors), mixed precision, captured into one CUDA graph with one
+    tile-form M2L launch over every instance; one step = one launch of the whole
+    batch."""
     import torch
 
     import paper_1902_08250_gb300 as lm
@@ -278,29 +279,19 @@ def run_batched(args):
     stream = torch.cuda.current_stream(dev)
     inst = workloads.batched_instances(48, seed=0)
     t0 = time.time()
-    trees, qs, us, launches = [], [], [], 0
-    tunes = {}
+    trees, qs, us = [], [], []
     for med, x, y, q in inst:
-        m = lm.create_medium(*med, p=14, precision="mixed", autotune=1)
+        m = lm.create_medium(*med, p=14, precision="mixed")
         t = lm.build_tree(m, torch.from_numpy(x).to(dev), torch.from_numpy(y).to(dev))
         qd = torch.from_numpy(q).to(dev)
         ud = torch.empty_like(qd)
-        # launches of one apply of this tree (profiled outside the graph)
-        lm._lib.lm_profile_begin(t._h, 1)
-        lm.apply(t, qd, ud)
-        ph_ms = (ctypes.c_double * len(PHASES))()
-        ph_n = (ctypes.c_int64 * len(PHASES))()
-        napp = ctypes.c_int()
-        lm._lib.lm_profile_end(t._h, ph_ms, ph_n, len(PHASES), ctypes.byref(napp))
-        launches += int(sum(ph_n)) + 1
-        for c in (c for c, _ in t.autotune()[1:]):
-            tunes[c] = tunes.get(c, 0) + 1
         trees.append(t)
         qs.append(qd)
         us.append(ud)
     torch.cuda.synchronize(dev)
     setup_s = time.time() - t0
     batch = lm.Batch(trees, qs, us)
+    launches, joint_m2l = batch.info()   # kernel nodes of the captured graph
     for _ in range(args.warmup):
         batch.launch()
     torch.cuda.synchronize(dev)
@@ -350,7 +341,7 @@ def run_batched(args):
         "config": {"workload": "48 instances, N log-uniform in [10k, 500k], k1,k2,k3 ~ U[0.5,4], d ~ U[0.5,2], "
                                "x ~ U[0,10], y ~ U[-0.9d,-0.1d]; 4 complex64 N(0,1) vectors each",
                    "instances": 48, "points": ntot, "nvec": 4, "precision": "mixed", "p": 14,
-                   "io": "complex64", "autotune_choices": {str(k): v for k, v in sorted(tunes.items())},
+                   "io": "complex64", "joint_m2l": joint_m2l,
                    "setup_s": setup_s, "parallelism": "replicas x1",
                    "target_vector_evals_per_s": ntot * 4 / (ms * 1e-3)},
         "clocks": ck,

@@ -342,12 +342,18 @@ lm_status lm_tree_order_noalloc(const double *x, const double *y, int64_t n, dou
  *     The trees must be distinct and outlive the batch, and no other apply may
  *     use them while a launch is in flight.  Profiling must be off on them.
  *   batch_launch: enqueue the whole batch on `stream`.
+ *   batch_info: the number of kernel launches one batch_launch makes (kernel
+ *     nodes of the graph) and whether the batch runs one M2L launch over
+ *     every tree (joint_m2l = 1: at least two LM_MIXED trees that all use the
+ *     tile-form M2L at one expansion order and vector width); either output
+ *     may be NULL.
  * Errors: LM_EINVAL for bad arguments, LM_ECUDA if capture or instantiation fails.
  */
 typedef struct lm_batch_s *lm_batch;
 lm_status lm_batch_create(const lm_tree *trees, int count, const void *const *q, const int *nvec,
                           void *const *u, const int *c64, lm_batch *out);
 lm_status lm_batch_launch(lm_batch b, void *stream);
+lm_status lm_batch_info(lm_batch b, int64_t *kernels, int *joint_m2l);
 void lm_batch_destroy(lm_batch b);
 
 /*

@@ -84,6 +84,7 @@ def _load():
         "lm_misfit_grad": (I, [V, V, P, P, I, P, P, P, P, P, ctypes.c_size_t, P]),
         "lm_batch_create": (I, [P, I, P, P, P, P, P]),
         "lm_batch_launch": (I, [V, P]),
+        "lm_batch_info": (I, [V, P, P]),
         "lm_build_cross": (I, [V, P, P, I64, P, P, I64, P, P]),
         "lm_cross_apply": (I, [V, P, I, P, P]),
         "lm_cross_info": (I, [V, P, P, P, P, P]),
@@ -455,6 +456,12 @@ class Batch:
 
     def launch(self, stream=None):
         _check(_lib.lm_batch_launch(self._h, _stream(stream)))
+
+    def info(self):
+        """(kernel launches per launch(), whether one M2L launch serves every tree)."""
+        k, j = ctypes.c_int64(), ctypes.c_int()
+        _check(_lib.lm_batch_info(self._h, ctypes.byref(k), ctypes.byref(j)))
+        return k.value, bool(j.value)
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

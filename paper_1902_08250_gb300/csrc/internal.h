@@ -192,10 +192,13 @@ struct lm_tree_s {
     // tile form of the tensor-core M2L (16-vector applies): every V-list entry of every
     // level (free space and the four image terms) as (tile of 8 target boxes, entry) work
     bool tt_ready;
-    int64_t tt_ntile, tt_nent;
-    void *tt_tiles, *tt_ents;   // device TtTile[tt_ntile], TtEnt[tt_nent]
+    // [0]: 16-vector form (tiles of 8 boxes), [1]: 4-vector form (tiles of 32 boxes)
+    int64_t tt_ntile[2], tt_nent[2];
+    void *tt_tiles[2], *tt_ents[2]; // device TtTile[tt_ntile], TtEnt[tt_nent]
+    void *tt_lv[2];             // device level descriptors (TtLevel[L + 1]) of each form
     float *tt_tab;              // [classes of all levels][128 rows][64 K] TF32 hi/lo tables, canonical layout
-    float *tt_msplit;           // [boxes of all levels + 1][2048] TF32 hi/lo multipoles, canonical layout
+    float *tt_msplit;           // [boxes of all levels + 1][2048] TF32 hi/lo multipoles (the 4-vector form
+                                // packs 512 floats per box in the same buffer), canonical layout
     std::vector<int64_t> tt_tbase, tt_mbase; // per level: first table, first box
     int tt_grid;                // persistent CTAs (one per SM)
     int tt_poll_limit;          // polls of the first operand wait (-1: the library default)
@@ -248,14 +251,25 @@ lm_status lm_run_apply_grad(lm_tree_s *t, const zd *q, int nvec, zd *u, zd *ux, 
 lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st);
 lm_status lm_setup_mixed_adaptive(lm_tree_s *t, cudaStream_t st);
 lm_status lm_autotune_mixed(lm_tree_s *t, cudaStream_t st, int *choice, float *ms);
-lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st);
+lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st,
+                             int part = 0);
 void lm_free_mixed(lm_tree_s *t);
 // tensor-core M2L (lmfmm_tc.cu)
 lm_status lm_setup_tc(lm_tree_s *t, cudaStream_t st);
 lm_status lm_launch_m2l_tc(lm_tree_s *t, int l, cudaStream_t st, int nvs); // nvs: 4 or 16 vector slots
 // tile form (lmfmm_tc_tiles.cu): set-up, and the apply's multipole split + M2L of all levels
 lm_status lm_setup_tt(lm_tree_s *t, cudaStream_t st);
-lm_status lm_launch_m2l_tt(lm_tree_s *t, cudaStream_t st);
+lm_status lm_launch_m2l_tt(lm_tree_s *t, cudaStream_t st, int nvs); // nvs: 16 or 4 vector slots
+lm_status lm_launch_msplit_tt(lm_tree_s *t, cudaStream_t st, int nvs);
+// one tile-form M2L launch over the tiles of several trees (batched applies)
+struct lm_tt_batch_s;
+lm_status lm_tt_batch_build(lm_tree_s *const *trees, int count, int nvs, lm_tt_batch_s **out);
+lm_status lm_tt_batch_launch(const lm_tt_batch_s *b, cudaStream_t st);
+void lm_tt_batch_free(lm_tt_batch_s *b);
+// the mixed apply in parts: 0 all; 1 up to the split multipoles (the tile M2L left out);
+// 2 from L2L on (after a tile M2L of the tree has run).  Parts 1 and 2 need the tile
+// form and at most 16 vectors.
+bool lm_mixed_tiles(const lm_tree_s *t, int nvec);
 void lm_free_tt(lm_tree_s *t);
 template <typename T>
 lm_status lm_dalloc(lm_tree_s *t, T **p, size_t count)

@@ -618,6 +618,8 @@ extern "C" lm_status lm_peak_probe(int kind, int64_t iters, void *stream, double
 struct lm_batch_s {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    lm_tt_batch_s *tiles = nullptr; // one tile-form M2L over every tree (nullptr: per-tree applies)
+    int64_t kernels = 0;            // kernel nodes of the captured graph
 };
 
 extern "C" void lm_batch_destroy(lm_batch b)
@@ -625,6 +627,7 @@ extern "C" void lm_batch_destroy(lm_batch b)
     if (!b) return;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    lm_tt_batch_free(b->tiles);
     delete b;
 }
 
@@ -668,15 +671,33 @@ extern "C" lm_status lm_batch_create(const lm_tree *trees, int count, const void
         lm_set_error("batch_create: host allocation failed");
         return LM_ENOMEM;
     }
+    // One M2L launch for the whole batch when every tree runs the tile form with the
+    // same p and vector slots: the trees' upward passes (permute, S2M, M2M, multipole
+    // split) run on the side streams, then one persistent tile launch walks the
+    // concatenated work list of every tree's tiles, then the downward passes (L2L,
+    // leaf step, permute) run on the side streams again.
+    bool joint = count >= 2;
+    const int nvs0 = nvec[0] <= 4 ? 4 : LM_MAXV;
+    for (int i = 0; i < count && joint; ++i)
+        joint = lm_mixed_tiles(trees[i], nvec[i]) && trees[i]->p == trees[0]->p &&
+                (nvec[i] <= 4 ? 4 : LM_MAXV) == nvs0;
     lm_status st = LM_OK;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
+    if (joint) {
+        std::vector<lm_tree_s *> tv(trees, trees + count);
+        st = lm_tt_batch_build(tv.data(), count, nvs0, &b->tiles);
+        if (st != LM_OK) {
+            lm_batch_destroy(b);
+            return st;
+        }
+    }
+    auto capture_part = [&](int part) {
         cudaEventRecord(fork, cs);
         for (int k = 0; k < nstream; ++k) cudaStreamWaitEvent(side[k], fork, 0);
         for (int i = 0; i < count && st == LM_OK; ++i) {
-            st = (c64 && c64[i]) ? lm_run_apply_mixed(trees[i], q[i], nvec[i], u[i], false, true, side[i % nstream])
-                                 : lm_run_apply(trees[i], (const zd *)q[i], nvec[i], (zd *)u[i], false,
-                                                side[i % nstream]);
+            const bool f = c64 && c64[i];
+            st = (f || part != 0)
+                     ? lm_run_apply_mixed(trees[i], q[i], nvec[i], u[i], false, f, side[i % nstream], part)
+                     : lm_run_apply(trees[i], (const zd *)q[i], nvec[i], (zd *)u[i], false, side[i % nstream]);
             if (st != LM_OK) {
                 std::string why = lm_last_error();
                 lm_set_error("batch_create: capturing the apply of tree %d failed: %s", i, why.c_str());
@@ -686,13 +707,32 @@ extern "C" lm_status lm_batch_create(const lm_tree *trees, int count, const void
             cudaEventRecord(join[k], side[k]);
             cudaStreamWaitEvent(cs, join[k], 0);
         }
+    };
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        if (joint) {
+            capture_part(1);
+            if (st == LM_OK) st = lm_tt_batch_launch(b->tiles, cs);
+            if (st == LM_OK) capture_part(2);
+        } else {
+            capture_part(0);
+        }
         cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
         if (st == LM_OK && e2 != cudaSuccess) {
             lm_set_error("batch_create: capture failed: %s", cudaGetErrorString(e2));
             st = LM_ECUDA;
         }
         if (st == LM_OK) {
-            e2 = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            size_t nn = 0;
+            e2 = cudaGraphGetNodes(b->graph, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (e2 == cudaSuccess && nn) e2 = cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+            for (size_t i = 0; i < nn && e2 == cudaSuccess; ++i) {
+                cudaGraphNodeType ty;
+                e2 = cudaGraphNodeGetType(nodes[i], &ty);
+                b->kernels += ty == cudaGraphNodeTypeKernel;
+            }
+            if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&b->exec, b->graph, 0);
             if (e2 != cudaSuccess) {
                 lm_set_error("batch_create: graph instantiation failed: %s", cudaGetErrorString(e2));
                 st = LM_ECUDA;
@@ -724,6 +764,17 @@ extern "C" lm_status lm_batch_launch(lm_batch b, void *stream)
         return LM_EINVAL;
     }
     LM_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
+    return LM_OK;
+}
+
+extern "C" lm_status lm_batch_info(lm_batch b, int64_t *kernels, int *joint_m2l)
+{
+    if (!b) {
+        lm_set_error("batch_info: NULL batch");
+        return LM_EINVAL;
+    }
+    if (kernels) *kernels = b->kernels;
+    if (joint_m2l) *joint_m2l = b->tiles != nullptr;
     return LM_OK;
 }
 

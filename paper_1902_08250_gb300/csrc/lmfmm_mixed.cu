@@ -1123,12 +1123,16 @@ static void launch_l2l(const Level &lv, const Level &par, cudaStream_t st, int n
     else
         k_l2l32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
 }
-// L2L of the tile-form apply (16 vector slots): adds to the M2L's local expansions
+// L2L of the tile-form apply: adds to the M2L's local expansions
 template <int P>
-static void launch_l2l_acc(const Level &lv, const Level &par, cudaStream_t st)
+static void launch_l2l_acc(const Level &lv, const Level &par, cudaStream_t st, int nvs)
 {
     constexpr int NP = 2 * P + 1;
-    k_l2l32<NP, LM_MAXV, true><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
+    if (nvs == 4)
+        k_l2l32<NP, 4, true><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
+    else
+        k_l2l32<NP, LM_MAXV, true><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32,
+                                                                       lv.L32);
 }
 template <int P>
 static void launch_rest(const Level &lv, cudaStream_t st, int nvs)
@@ -1323,16 +1327,36 @@ static lm_status run_mixed_adaptive(lm_tree_s *t, const void *q, int nvec, void 
     return LM_OK;
 }
 
-lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st)
+// the tile-form M2L of all levels applies to this tree
+static bool tiles_ready(const lm_tree_s *t)
+{
+    bool ok = t->tt_ready && !t->adaptive;
+    for (int l = 1; l <= t->L && ok; ++l) ok = t->lev[l].m2l_impl == 0;
+    return ok;
+}
+bool lm_mixed_tiles(const lm_tree_s *t, int nvec)
+{
+    return t->precision == LM_MIXED && nvec >= 1 && nvec <= LM_MAXV && tiles_ready(t);
+}
+
+lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, bool adjoint, bool c64, cudaStream_t st,
+                             int part)
 {
     if (t->adaptive) return run_mixed_adaptive(t, q, nvec, u, adjoint, c64, st);
+    if (part != 0 && !lm_mixed_tiles(t, nvec)) {
+        lm_set_error("apply: a split apply needs the tile-form M2L and at most %d vectors", LM_MAXV);
+        return LM_ENOTSUP;
+    }
     const int L = t->L, P = t->p, np = 2 * P + 1;
     const int64_t n = t->n;
     const float k = (float)t->med.k2;
     const NearQuadF nq = nqf_of(t);
+    const bool up = part != 2, down = part != 1;
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         const int nvs = nv <= 4 ? 4 : LM_MAXV; // vector slots the contractions compute
+        const bool tiles = tiles_ready(t);
+        if (up) {
         lm_phase_begin(t, PH_PERMUTE, st);
         if (c64)
             k_permute_in32<zf><<<gridm(n, 256), 256, 0, st>>>((const zf *)q + (int64_t)v0 * n, t->iperm, n, nv,
@@ -1354,16 +1378,22 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
             MX_DISPATCH(P, launch_m2m, t->lev[l], t->lev[l + 1], st, nvs);
         }
         if (L > 0) lm_phase_end(t, PH_M2M, st, L);
+        }
         // tile form: the M2L of every level in one launch (it writes L), then L2L adds
-        bool tiles = t->tt_ready && nvs == LM_MAXV;
-        for (int l = 1; l <= L; ++l) tiles = tiles && t->lev[l].m2l_impl == 0;
         if (tiles) {
             lm_phase_begin(t, PH_M2L, st);
-            lm_status s = lm_launch_m2l_tt(t, st);
-            if (s != LM_OK) return s;
-            lm_phase_end(t, PH_M2L, st, 2);
+            if (up) {
+                lm_status s = lm_launch_msplit_tt(t, st, nvs);
+                if (s != LM_OK) return s;
+            }
+            if (part == 0) {
+                lm_status s = lm_launch_m2l_tt(t, st, nvs);
+                if (s != LM_OK) return s;
+            }
+            lm_phase_end(t, PH_M2L, st, up + (part == 0));
+            if (part == 1) continue;
             if (L > 0) lm_phase_begin(t, PH_L2L, st);
-            for (int l = 1; l <= L; ++l) MX_DISPATCH(P, launch_l2l_acc, t->lev[l], t->lev[l - 1], st);
+            for (int l = 1; l <= L; ++l) MX_DISPATCH(P, launch_l2l_acc, t->lev[l], t->lev[l - 1], st, nvs);
             if (L > 0) lm_phase_end(t, PH_L2L, st, L);
         }
         for (int l = 0; l <= L && !tiles; ++l) {

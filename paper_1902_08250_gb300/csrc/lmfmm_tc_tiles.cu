@@ -45,42 +45,52 @@
 #include <algorithm>
 #include <map>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
 #include "tc_common.cuh"
 
-#define TT_BOXES 8                                   // target boxes per tile
 #define TT_K 64                                      // real input orders per item (zero-padded)
 #define TT_TAB_FLOATS (128 * TT_K)                   // one split table: 64 hi + 64 lo rows
-#define TT_BOX_FLOATS (32 * TT_K)                    // one split box: 16 hi + 16 lo vector rows
 #define TT_STAGE_TAB (TT_TAB_FLOATS * 4)             // 32 KB
-#define TT_STAGE ((TT_TAB_FLOATS + TT_BOXES * TT_BOX_FLOATS) * 4) // 96 KB
+#define TT_STAGE (TT_STAGE_TAB + 256 * TT_K * 4)     // 96 KB: the table and 256 operand rows
 #define TT_NSTAGE 2
 #define TT_EPI_WARPS 8
 #define TT_THREADS ((TT_EPI_WARPS + 2) * 32)         // + producer + MMA warp
 #define TT_MAXLEV 16
-#define TT_CB_STRIDE 33                              // floats per (box, order) row of the combine buffer
+
+// NV vectors per box: a box is 2 NV operand rows ([hi v0..NV-1 | lo v0..NV-1]); a tile
+// holds TB = 128 / NV boxes (8 boxes of 16 vectors, or 32 of 4), N = 256 either way
+template <int NV>
+struct TtShape {
+    static constexpr int TB = 128 / NV;              // boxes per tile
+    static constexpr int BOX_FLOATS = 2 * NV * TT_K; // one split box
+    static constexpr int CB_STRIDE = 2 * NV + 1;     // floats per (box, order) row of the combine buffer
+    static constexpr int BPL = 32 / (2 * NV);        // boxes per 32-column tensor-memory load
+};
 
 struct TtTile {
-    int32_t level, row, c0, cstride, nbox, e0, e1, pad;
+    int32_t level, row, c0, cstride, nbox, e0, e1, pad; // level: index into the launch's level descriptors
 };
 struct TtEnt {
     int32_t slot, dc, rs;
     uint32_t mask; // bit j: target box j of the tile has this entry
 };
-struct TtLevels {
-    int64_t ncol[TT_MAXLEV];
-    int64_t mbase[TT_MAXLEV]; // first box of the level in the split multipoles
-    int64_t tbase[TT_MAXLEV]; // first table of the level in the split tables
-    const zf *M[TT_MAXLEV];   // multipoles [nbox][NP][16]
-    zf *L[TT_MAXLEV];         // local expansions [nbox][NP][16]
+// one level of one tree as the tile kernels see it
+struct TtLevel {
+    int64_t ncol;      // columns of the level
+    int64_t mstart;    // first box of the level in its tree's split-multipole buffer
+    const zf *M;       // multipoles [nbox][NP][16]
+    zf *L;             // local expansions [nbox][NP][16]
+    const float *tab;  // the level's first split table
+    float *ms;         // the level's first split box
 };
 
-template <int NP>
+template <int NP, int NV>
 struct TtSmem {
     static constexpr int CB_OFF = TT_NSTAGE * TT_STAGE;
-    static constexpr int CB_BYTES = (TT_BOXES * NP * TT_CB_STRIDE * 4 + 15) / 16 * 16;
+    static constexpr int CB_BYTES = (TtShape<NV>::TB * NP * TtShape<NV>::CB_STRIDE * 4 + 15) / 16 * 16;
     static constexpr int BAR_OFF = CB_OFF + CB_BYTES;
     static constexpr int BYTES = BAR_OFF + 8 * 8 + 16;
 };
@@ -124,20 +134,20 @@ __global__ void k_tsplit(const zd *tab, int ncls, int NP, float *out)
     *(float4 *)(o + tc_off(64 + r, 4 * c) / 4) = make_float4(lv[0], lv[1], lv[2], lv[3]);
 }
 
-// Multipoles of every level -> B operands, one 8 KB block per box: [hi v0-7 |
-// hi v8-15 | lo v0-7 | lo v8-15], each an 8-row x 64-K group of core matrices
-// (2 KB).  One thread per (box, K chunk of 4 = orders 2c, 2c + 1, vector);
-// a warp reads two orders' 16 vectors (256 B) and writes two 128-B rows.
-template <int NP>
-__global__ void k_msplit(TtLevels lv, int nlev, int64_t ntot, float *out)
+// Multipoles of every level of one tree -> B operands, one block of 2 NV rows per
+// box: [hi v0..NV-1 | lo v0..NV-1] x 64 K in the canonical layout (8-row groups of
+// 2 KB).  One thread per (box, K chunk of 4 = orders 2c, 2c + 1, vector).
+template <int NP, int NV>
+__global__ void k_msplit(const TtLevel *lv, int nlev, int64_t ntot)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= ntot * 256) return;
-    const int v = (int)(t & 15), c = (int)((t >> 4) & 15);
-    const int64_t gb = t >> 8;
+    if (t >= ntot * 16 * NV) return;
+    const int v = (int)(t % NV), c = (int)((t / NV) & 15);
+    const int64_t gb = t / (16 * NV);
     int l = 0;
-    while (l + 1 < nlev && gb >= lv.mbase[l + 1]) ++l;
-    const zf *m = lv.M[l] + (gb - lv.mbase[l]) * NP * LM_MAXV + v;
+    while (l + 1 < nlev && gb >= lv[l + 1].mstart) ++l;
+    const int64_t b = gb - lv[l].mstart;
+    const zf *m = lv[l].M + b * NP * LM_MAXV + v;
     float x[4];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -151,9 +161,10 @@ __global__ void k_msplit(TtLevels lv, int nlev, int64_t ntot, float *out)
     tt_split(x[1], hi.y, lo.y);
     tt_split(x[2], hi.z, lo.z);
     tt_split(x[3], hi.w, lo.w);
-    float *o = out + gb * TT_BOX_FLOATS + (v >> 3) * 512 + c * 32 + (v & 7) * 4;
-    *(float4 *)o = hi;
-    *(float4 *)(o + 1024) = lo;
+    float *o = lv[l].ms + b * TtShape<NV>::BOX_FLOATS;
+    const int rh = v, rl = NV + v; // operand rows of the hi and lo parts
+    *(float4 *)(o + (rh >> 3) * 512 + c * 32 + (rh & 7) * 4) = hi;
+    *(float4 *)(o + (rl >> 3) * 512 + c * 32 + (rl & 7) * 4) = lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -167,12 +178,13 @@ __device__ __forceinline__ void tt_fail(volatile int *abort_s, int *err)
 
 // first_limit >= 0: poll limit of the MMA issuer's first operand wait (the
 // timeout path's test); otherwise every wait polls up to TC_WAIT_LIMIT times
-template <int NP>
+template <int NP, int NV>
 __global__ void __launch_bounds__(TT_THREADS, 1)
-    k_m2l_tt(const TtTile *tiles, int ntiles, const TtEnt *ents, TtLevels lv, const float *msplit,
-             const float *tabs, int64_t zero_box, int *err, int first_limit)
+    k_m2l_tt(const TtTile *tiles, int ntiles, const TtEnt *ents, const TtLevel *lvs, const float *zero_box,
+             int *err, int first_limit)
 {
-    using S = TtSmem<NP>;
+    using S = TtSmem<NP, NV>;
+    using Sh = TtShape<NV>;
     extern __shared__ __align__(1024) unsigned char smem[];
     float *cb = (float *)(smem + S::CB_OFF);
     uint64_t *bars = (uint64_t *)(smem + S::BAR_OFF);
@@ -212,8 +224,9 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         bool stop = false;
         for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
             const TtTile T = tiles[tile];
-            const int64_t ncol = lv.ncol[T.level], mb = lv.mbase[T.level];
-            const float *tb = tabs + lv.tbase[T.level] * TT_TAB_FLOATS;
+            const TtLevel &lv = lvs[T.level];
+            const int64_t ncol = lv.ncol;
+            const float *tb = lv.tab, *ms = lv.ms;
             for (int base = T.e0; base < T.e1 && !stop; base += 32) {
                 const int cnt = min(32, T.e1 - base);
                 TtEnt mine = lane < cnt ? ents[base + lane] : TtEnt{0, 0, 0, 0u};
@@ -229,12 +242,12 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
                             mbar_expect_tx(fb, TT_STAGE);
                             bulk_g2s(st, tb + (int64_t)E.slot * TT_TAB_FLOATS, TT_STAGE_TAB, fb);
 #pragma unroll 1
-                            for (int j = 0; j < TT_BOXES; ++j) {
-                                int64_t src = zero_box;
+                            for (int j = 0; j < Sh::TB; ++j) {
+                                const float *src = zero_box;
                                 if (j < T.nbox && ((E.mask >> j) & 1u))
-                                    src = mb + (int64_t)E.rs * ncol + T.c0 + (int64_t)j * T.cstride - E.dc;
-                                bulk_g2s(st + TT_STAGE_TAB + j * TT_BOX_FLOATS * 4, msplit + src * TT_BOX_FLOATS,
-                                         TT_BOX_FLOATS * 4, fb);
+                                    src = ms + ((int64_t)E.rs * ncol + T.c0 + (int64_t)j * T.cstride - E.dc) *
+                                                   Sh::BOX_FLOATS;
+                                bulk_g2s(st + TT_STAGE_TAB + j * Sh::BOX_FLOATS * 4, src, Sh::BOX_FLOATS * 4, fb);
                             }
                             last[s] = (int)it;
                         }
@@ -282,7 +295,9 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         }
         __syncwarp();
     } else {
-        // ---- epilogue ----
+        // ---- epilogue: warp (quadrant Q, half H) holds accumulator rows 32 Q .. + 31 of
+        // boxes H TB/2 .. + TB/2 - 1 (128 columns) ----
+        constexpr int HB = Sh::TB / 2; // boxes per warp
         const int Q = warp & 3, H = warp >> 2;
         const int n = 32 * Q + lane, r = n & 63; // accumulator row; real-block row
         const bool rowok = r < 2 * NP;
@@ -291,11 +306,11 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         uint32_t it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const TtTile T = tiles[tile];
-            float acc[4][16];
+            float acc[HB][NV];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj)
+            for (int jj = 0; jj < HB; ++jj)
 #pragma unroll
-                for (int v = 0; v < 16; ++v) acc[jj][v] = 0.f;
+                for (int v = 0; v < NV; ++v) acc[jj][v] = 0.f;
             bool bad = *abort_s != 0;
             for (int e = T.e0; e < T.e1; ++e, ++it) {
                 if (bad) continue;
@@ -307,11 +322,14 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
+                for (int ld = 0; ld < 4; ++ld) {
                     float v[32];
-                    tc_ld32(lane_base + 256u * s + 32u * jj, v);
+                    tc_ld32(lane_base + 256u * s + 32u * ld, v);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) acc[jj][i] += v[i] + v[16 + i];
+                    for (int b4 = 0; b4 < Sh::BPL; ++b4)
+#pragma unroll
+                        for (int i = 0; i < NV; ++i)
+                            acc[ld * Sh::BPL + b4][i] += v[2 * NV * b4 + i] + v[2 * NV * b4 + NV + i];
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
@@ -323,22 +341,25 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
             if (*stop_s) break;
             if (n >= 64 && rowok)
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
+                for (int jj = 0; jj < HB; ++jj)
 #pragma unroll
-                    for (int v = 0; v < 16; ++v) cb[((4 * H + jj) * NP + p) * TT_CB_STRIDE + 2 * v + reim] = acc[jj][v];
+                    for (int v = 0; v < NV; ++v)
+                        cb[((HB * H + jj) * NP + p) * Sh::CB_STRIDE + 2 * v + reim] = acc[jj][v];
             asm volatile("bar.sync 1, 256;" ::: "memory");
             if (n < 64 && rowok)
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
+                for (int jj = 0; jj < HB; ++jj)
 #pragma unroll
-                    for (int v = 0; v < 16; ++v) cb[((4 * H + jj) * NP + p) * TT_CB_STRIDE + 2 * v + reim] += acc[jj][v];
+                    for (int v = 0; v < NV; ++v)
+                        cb[((HB * H + jj) * NP + p) * Sh::CB_STRIDE + 2 * v + reim] += acc[jj][v];
             asm volatile("bar.sync 1, 256;" ::: "memory");
-            float *Lg = (float *)lv.L[T.level];
-            const int64_t rowbase = (int64_t)T.row * lv.ncol[T.level] + T.c0;
-            for (int x = threadIdx.x; x < T.nbox * NP * 32; x += TT_EPI_WARPS * 32) {
-                const int jp = x >> 5, f = x & 31, j = jp / NP, pp = jp - j * NP;
+            const TtLevel &lv = lvs[T.level];
+            float *Lg = (float *)lv.L;
+            const int64_t rowbase = (int64_t)T.row * lv.ncol + T.c0;
+            for (int x = threadIdx.x; x < T.nbox * NP * 2 * NV; x += TT_EPI_WARPS * 32) {
+                const int jp = x / (2 * NV), f = x % (2 * NV), j = jp / NP, pp = jp - j * NP;
                 const int64_t box = rowbase + (int64_t)j * T.cstride;
-                Lg[(box * NP + pp) * 32 + f] = cb[jp * TT_CB_STRIDE + f];
+                Lg[(box * NP + pp) * 2 * LM_MAXV + f] = cb[jp * Sh::CB_STRIDE + f];
             }
         }
     }
@@ -357,37 +378,65 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         if (s_ != LM_OK) return s_;  \
     } while (0)
 
-static TtLevels tt_levels(const lm_tree_s *t)
+// the level descriptors of one tree for one vector form (NV = 16: 8 KB per split box,
+// NV = 4: 2 KB), in host memory
+static std::vector<TtLevel> tt_levels(const lm_tree_s *t, int nv)
 {
-    TtLevels lv{};
-    for (int l = 0; l <= t->L; ++l) {
-        lv.ncol[l] = t->lev[l].ncol;
-        lv.mbase[l] = t->tt_mbase[l];
-        lv.tbase[l] = t->tt_tbase[l];
-        lv.M[l] = t->lev[l].M32;
-        lv.L[l] = t->lev[l].L32;
-    }
+    const int64_t bf = 2 * nv * TT_K;
+    std::vector<TtLevel> lv(t->L + 1);
+    for (int l = 0; l <= t->L; ++l)
+        lv[l] = TtLevel{t->lev[l].ncol,  t->tt_mbase[l], t->lev[l].M32, t->lev[l].L32,
+                        t->tt_tab + t->tt_tbase[l] * TT_TAB_FLOATS, t->tt_msplit + t->tt_mbase[l] * bf};
     return lv;
 }
 
-template <int NP>
+template <int NP, int NV>
 static lm_status tt_attr()
 {
-    LM_CUDA(cudaFuncSetAttribute(k_m2l_tt<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, TtSmem<NP>::BYTES));
+    LM_CUDA(cudaFuncSetAttribute(k_m2l_tt<NP, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 TtSmem<NP, NV>::BYTES));
+    return LM_OK;
+}
+template <int NP>
+static lm_status tt_attr_np()
+{
+    lm_status s = tt_attr<NP, 16>();
+    return s == LM_OK ? tt_attr<NP, 4>() : s;
+}
+
+// split the multipoles of every level of one tree (one launch)
+template <int NP, int NV>
+static void tt_msplit_launch(const lm_tree_s *t, const void *lv, cudaStream_t st)
+{
+    const int64_t ntot = t->tt_mbase[t->L + 1];
+    k_msplit<NP, NV><<<(unsigned)((ntot * 16 * NV + 255) / 256), 256, 0, st>>>((const TtLevel *)lv, t->L + 1, ntot);
+}
+
+template <int NP>
+static lm_status tt_msplit(lm_tree_s *t, cudaStream_t st, int nvs)
+{
+    if (nvs == LM_MAXV)
+        tt_msplit_launch<NP, 16>(t, t->tt_lv[0], st);
+    else
+        tt_msplit_launch<NP, 4>(t, t->tt_lv[1], st);
     return LM_OK;
 }
 
 template <int NP>
-static lm_status tt_launch(lm_tree_s *t, cudaStream_t st)
+static lm_status tt_launch(lm_tree_s *t, cudaStream_t st, int nvs)
 {
-    const TtLevels lv = tt_levels(t);
-    const int64_t ntot = t->tt_mbase[t->L + 1];
-    k_msplit<NP><<<(unsigned)((ntot * 256 + 255) / 256), 256, 0, st>>>(lv, t->L + 1, ntot, t->tt_msplit);
+    const int f = nvs == LM_MAXV ? 0 : 1;
     const int first = t->tt_poll_limit;
     t->tt_poll_limit = -1; // a test limit applies to one launch
-    k_m2l_tt<NP><<<t->tt_grid, TT_THREADS, TtSmem<NP>::BYTES, st>>>(
-        (const TtTile *)t->tt_tiles, (int)t->tt_ntile, (const TtEnt *)t->tt_ents, lv, t->tt_msplit, t->tt_tab, ntot,
-        t->dflag + 1, first);
+    const float *zero = t->tt_msplit + t->tt_mbase[t->L + 1] * 2 * LM_MAXV * TT_K;
+    if (f == 0)
+        k_m2l_tt<NP, 16><<<t->tt_grid, TT_THREADS, TtSmem<NP, 16>::BYTES, st>>>(
+            (const TtTile *)t->tt_tiles[0], (int)t->tt_ntile[0], (const TtEnt *)t->tt_ents[0],
+            (const TtLevel *)t->tt_lv[0], zero, t->dflag + 1, first);
+    else
+        k_m2l_tt<NP, 4><<<t->tt_grid, TT_THREADS, TtSmem<NP, 4>::BYTES, st>>>(
+            (const TtTile *)t->tt_tiles[1], (int)t->tt_ntile[1], (const TtEnt *)t->tt_ents[1],
+            (const TtLevel *)t->tt_lv[1], zero, t->dflag + 1, first);
     return LM_OK;
 }
 
@@ -408,7 +457,7 @@ static lm_status tt_launch(lm_tree_s *t, cudaStream_t st)
 template <int NP>
 static int tt_bytes_np()
 {
-    return TtSmem<NP>::BYTES;
+    return std::max(TtSmem<NP, 16>::BYTES, TtSmem<NP, 4>::BYTES);
 }
 static int tt_bytes(int p)
 {
@@ -417,15 +466,60 @@ static int tt_bytes(int p)
 }
 static lm_status tt_set_attr(int p)
 {
-    TT_SWITCH(p, tt_attr);
+    TT_SWITCH(p, tt_attr_np);
     lm_set_error("tensor-core M2L tiles: order %d not instantiated", p);
     return LM_ENOTSUP;
 }
 
-// Set-up of the tile form: split tables, the split-multipole buffer (one zero
-// box at the end for masked sources) and the tile / entry lists built on the
-// host from the V lists of every level.  Leaves tt_ready false (the per-level
-// kernels then run) where the form does not apply.
+// Tiles of tb class-consecutive boxes over every level, from the host copies of the
+// V lists: per tile the union of its boxes' entries, each with the mask of boxes that have it
+static void tt_build_tiles(const std::vector<std::vector<int64_t>> &vs, const std::vector<std::vector<int32_t>> &vsrc,
+                           const std::vector<std::vector<int32_t>> &vslot, const lm_tree_s *t, int tb,
+                           std::vector<TtTile> &tiles, std::vector<TtEnt> &ents)
+{
+    for (int l = 0; l <= t->L; ++l) {
+        const Level &lv = t->lev[l];
+        const int64_t ncol = lv.ncol, nrow = lv.nrow;
+        const int cstride = l == 0 ? 1 : 2, npar = l == 0 ? 1 : 2;
+        const int64_t ncl = ncol / cstride; // boxes of one parity in a row (ncol is even at l >= 1)
+        for (int64_t r = 0; r < nrow; ++r)
+            for (int pc = 0; pc < npar; ++pc)
+                for (int64_t i0 = 0; i0 < ncl; i0 += tb) {
+                    TtTile T{l, (int32_t)r, (int32_t)(i0 * cstride + pc), cstride,
+                             (int32_t)std::min<int64_t>(tb, ncl - i0), (int32_t)ents.size(), 0, 0};
+                    std::map<std::tuple<int32_t, int32_t, int32_t>, uint32_t> m;
+                    for (int j = 0; j < T.nbox; ++j) {
+                        const int64_t c = T.c0 + (int64_t)j * cstride, b = r * ncol + c;
+                        for (int64_t e = vs[l][b]; e < vs[l][b + 1]; ++e) {
+                            const int64_t src = vsrc[l][e];
+                            const int32_t dc = (int32_t)(c - src % ncol), rs = (int32_t)(src / ncol);
+                            m[std::make_tuple(vslot[l][e], dc, rs)] |= 1u << j;
+                        }
+                    }
+                    for (const auto &kv : m)
+                        ents.push_back(TtEnt{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
+                                             kv.second});
+                    T.e1 = (int32_t)ents.size();
+                    tiles.push_back(T);
+                }
+    }
+}
+
+template <typename T>
+static lm_status tt_upload(lm_tree_s *t, const std::vector<T> &h, void **out, cudaStream_t st)
+{
+    T *d = nullptr;
+    TT_TRY(lm_dalloc(t, &d, std::max<size_t>(1, h.size())));
+    *out = d;
+    if (!h.empty()) LM_CUDA(cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return LM_OK;
+}
+
+// Set-up of the tile form: split tables, the split-multipole buffer (sized for the
+// 16-vector form, with one zero box at the end for masked sources), the level
+// descriptors of both vector forms and their tile / entry lists, built on the host
+// from the V lists of every level.  Leaves tt_ready false (the per-level kernels
+// then run) where the form does not apply.
 lm_status lm_setup_tt(lm_tree_s *t, cudaStream_t st)
 {
     const int L = t->L, np = 2 * t->p + 1;
@@ -446,9 +540,10 @@ lm_status lm_setup_tt(lm_tree_s *t, cudaStream_t st)
         t->tt_tbase[l + 1] = t->tt_tbase[l] + (int64_t)t->lev[l].cls_term.size();
         t->tt_mbase[l + 1] = t->tt_mbase[l] + t->lev[l].nbox;
     }
+    const int64_t bf16 = 2 * LM_MAXV * TT_K;
     TT_TRY(lm_dalloc(t, &t->tt_tab, (size_t)std::max<int64_t>(1, t->tt_tbase[L + 1]) * TT_TAB_FLOATS));
-    TT_TRY(lm_dalloc(t, &t->tt_msplit, (size_t)(t->tt_mbase[L + 1] + 1) * TT_BOX_FLOATS));
-    LM_CUDA(cudaMemsetAsync(t->tt_msplit + t->tt_mbase[L + 1] * TT_BOX_FLOATS, 0, TT_BOX_FLOATS * sizeof(float), st));
+    TT_TRY(lm_dalloc(t, &t->tt_msplit, (size_t)(t->tt_mbase[L + 1] + 1) * bf16));
+    LM_CUDA(cudaMemsetAsync(t->tt_msplit + t->tt_mbase[L + 1] * bf16, 0, bf16 * sizeof(float), st));
     for (int l = 0; l <= L; ++l) {
         const int ncls = (int)t->lev[l].cls_term.size();
         if (ncls == 0) continue;
@@ -456,74 +551,181 @@ lm_status lm_setup_tt(lm_tree_s *t, cudaStream_t st)
         k_tsplit<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(t->lev[l].tab, ncls, np,
                                                                t->tt_tab + t->tt_tbase[l] * TT_TAB_FLOATS);
     }
-    // tiles and entries
-    std::vector<TtTile> tiles;
-    std::vector<TtEnt> ents;
+    // host copies of the V lists
+    std::vector<std::vector<int64_t>> vs(L + 1);
+    std::vector<std::vector<int32_t>> vsrc(L + 1), vslot(L + 1);
     for (int l = 0; l <= L; ++l) {
         const Level &lv = t->lev[l];
-        std::vector<int64_t> hs(lv.nbox + 1);
-        std::vector<int32_t> hsrc(std::max<int64_t>(1, lv.nv)), hslot(std::max<int64_t>(1, lv.nv));
-        LM_CUDA(cudaMemcpyAsync(hs.data(), lv.vstart, (lv.nbox + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        vs[l].resize(lv.nbox + 1);
+        vsrc[l].resize(std::max<int64_t>(1, lv.nv));
+        vslot[l].resize(std::max<int64_t>(1, lv.nv));
+        LM_CUDA(cudaMemcpyAsync(vs[l].data(), lv.vstart, (lv.nbox + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         if (lv.nv > 0) {
-            LM_CUDA(cudaMemcpyAsync(hsrc.data(), lv.vsrc, lv.nv * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            LM_CUDA(cudaMemcpyAsync(hslot.data(), lv.vslot, lv.nv * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            LM_CUDA(cudaMemcpyAsync(vsrc[l].data(), lv.vsrc, lv.nv * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            LM_CUDA(cudaMemcpyAsync(vslot[l].data(), lv.vslot, lv.nv * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         }
-        LM_CUDA(cudaStreamSynchronize(st));
-        const int64_t ncol = lv.ncol, nrow = lv.nrow;
-        const int cstride = l == 0 ? 1 : 2, npar = l == 0 ? 1 : 2;
-        const int64_t ncl = ncol / cstride; // boxes of one parity in a row (ncol is even at l >= 1)
-        for (int64_t r = 0; r < nrow; ++r)
-            for (int pc = 0; pc < npar; ++pc)
-                for (int64_t i0 = 0; i0 < ncl; i0 += TT_BOXES) {
-                    TtTile T{l, (int32_t)r, (int32_t)(i0 * cstride + pc), cstride,
-                             (int32_t)std::min<int64_t>(TT_BOXES, ncl - i0), (int32_t)ents.size(), 0, 0};
-                    std::map<std::tuple<int32_t, int32_t, int32_t>, uint32_t> m;
-                    for (int j = 0; j < T.nbox; ++j) {
-                        const int64_t c = T.c0 + (int64_t)j * cstride, b = r * ncol + c;
-                        for (int64_t e = hs[b]; e < hs[b + 1]; ++e) {
-                            const int64_t s = hsrc[e];
-                            const int32_t dc = (int32_t)(c - s % ncol), rs = (int32_t)(s / ncol);
-                            m[std::make_tuple(hslot[e], dc, rs)] |= 1u << j;
-                        }
-                    }
-                    for (const auto &kv : m)
-                        ents.push_back(TtEnt{std::get<0>(kv.first), std::get<1>(kv.first), std::get<2>(kv.first),
-                                             kv.second});
-                    T.e1 = (int32_t)ents.size();
-                    tiles.push_back(T);
-                }
     }
-    if (ents.size() > (size_t)INT32_MAX || tiles.size() > (size_t)INT32_MAX) return LM_OK;
-    t->tt_ntile = (int64_t)tiles.size();
-    t->tt_nent = (int64_t)ents.size();
-    TtTile *dt = nullptr;
-    TtEnt *de = nullptr;
-    TT_TRY(lm_dalloc(t, &dt, tiles.size()));
-    TT_TRY(lm_dalloc(t, &de, std::max<size_t>(1, ents.size())));
-    t->tt_tiles = dt;
-    t->tt_ents = de;
-    LM_CUDA(cudaMemcpyAsync(dt, tiles.data(), tiles.size() * sizeof(TtTile), cudaMemcpyHostToDevice, st));
-    if (!ents.empty())
-        LM_CUDA(cudaMemcpyAsync(de, ents.data(), ents.size() * sizeof(TtEnt), cudaMemcpyHostToDevice, st));
     LM_CUDA(cudaStreamSynchronize(st));
-    t->tt_grid = std::max(1, std::min<int>(nsm, (int)tiles.size()));
+    int64_t maxtiles = 0;
+    for (int f = 0; f < 2; ++f) {
+        std::vector<TtTile> tiles;
+        std::vector<TtEnt> ents;
+        tt_build_tiles(vs, vsrc, vslot, t, f == 0 ? TtShape<16>::TB : TtShape<4>::TB, tiles, ents);
+        if (ents.size() > (size_t)INT32_MAX || tiles.size() > (size_t)INT32_MAX) return LM_OK;
+        t->tt_ntile[f] = (int64_t)tiles.size();
+        t->tt_nent[f] = (int64_t)ents.size();
+        TT_TRY(tt_upload(t, tiles, &t->tt_tiles[f], st));
+        TT_TRY(tt_upload(t, ents, &t->tt_ents[f], st));
+        TT_TRY(tt_upload(t, tt_levels(t, f == 0 ? 16 : 4), &t->tt_lv[f], st));
+        maxtiles = std::max(maxtiles, t->tt_ntile[f]);
+    }
+    LM_CUDA(cudaStreamSynchronize(st));
+    t->tt_grid = std::max(1, (int)std::min<int64_t>(nsm, maxtiles));
     TT_TRY(tt_set_attr(t->p));
     t->tt_ready = true;
     return LM_OK;
 }
 
-lm_status lm_launch_m2l_tt(lm_tree_s *t, cudaStream_t st)
+lm_status lm_launch_msplit_tt(lm_tree_s *t, cudaStream_t st, int nvs)
 {
-    TT_SWITCH(t->p, tt_launch, t, st);
+    TT_SWITCH(t->p, tt_msplit, t, st, nvs);
     lm_set_error("tensor-core M2L tiles: order %d not instantiated", t->p);
     return LM_ENOTSUP;
 }
 
-void lm_free_tt(lm_tree_s *t)
+lm_status lm_launch_m2l_tt(lm_tree_s *t, cudaStream_t st, int nvs)
 {
-    void *ptrs[] = {t->tt_tiles, t->tt_ents, t->tt_tab, t->tt_msplit};
+    TT_SWITCH(t->p, tt_launch, t, st, nvs);
+    lm_set_error("tensor-core M2L tiles: order %d not instantiated", t->p);
+    return LM_ENOTSUP;
+}
+
+// ---------------------------------------------------------------------------
+// one launch over the tiles of many trees (batched applies)
+// ---------------------------------------------------------------------------
+struct lm_tt_batch_s {
+    int p = 0, nvs = 0, grid = 0;
+    int64_t ntile = 0;
+    TtTile *tiles = nullptr;
+    TtEnt *ents = nullptr;
+    TtLevel *lv = nullptr;
+    const float *zero = nullptr;
+    int *err = nullptr;
+};
+
+template <typename T>
+static lm_status tt_fetch(const void *d, int64_t n, std::vector<T> &h)
+{
+    h.resize(n);
+    if (n > 0) LM_CUDA(cudaMemcpy(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost));
+    return LM_OK;
+}
+
+// Concatenates the trees' tile and entry lists of one vector form into one work
+// list: a tile's level index is offset into the concatenated level descriptors,
+// its entry range into the concatenated entries.  Every tree must have the tile
+// form ready with the same p.  A timeout of the launch is reported on trees[0].
+lm_status lm_tt_batch_build(lm_tree_s *const *trees, int count, int nvs, lm_tt_batch_s **out)
+{
+    *out = nullptr;
+    const int f = nvs == LM_MAXV ? 0 : 1;
+    std::vector<TtTile> tiles;
+    std::vector<TtEnt> ents;
+    std::vector<TtLevel> lv;
+    for (int i = 0; i < count; ++i) {
+        const lm_tree_s *t = trees[i];
+        std::vector<TtTile> ht;
+        std::vector<TtEnt> he;
+        std::vector<TtLevel> hl;
+        TT_TRY(tt_fetch(t->tt_tiles[f], t->tt_ntile[f], ht));
+        TT_TRY(tt_fetch(t->tt_ents[f], t->tt_nent[f], he));
+        TT_TRY(tt_fetch(t->tt_lv[f], t->L + 1, hl));
+        const int32_t eoff = (int32_t)ents.size(), loff = (int32_t)lv.size();
+        for (TtTile T : ht) {
+            T.level += loff;
+            T.e0 += eoff;
+            T.e1 += eoff;
+            tiles.push_back(T);
+        }
+        ents.insert(ents.end(), he.begin(), he.end());
+        lv.insert(lv.end(), hl.begin(), hl.end());
+        if (ents.size() > (size_t)INT32_MAX || tiles.size() > (size_t)INT32_MAX) {
+            lm_set_error("batch_create: too many M2L tiles for one launch");
+            return LM_ENOTSUP;
+        }
+    }
+    int dev = 0, nsm = 0;
+    LM_CUDA(cudaGetDevice(&dev));
+    LM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    lm_tt_batch_s *b = new (std::nothrow) lm_tt_batch_s();
+    if (!b) {
+        lm_set_error("batch_create: host allocation failed");
+        return LM_ENOMEM;
+    }
+    b->p = trees[0]->p;
+    b->nvs = nvs;
+    b->ntile = (int64_t)tiles.size();
+    b->grid = std::max(1, (int)std::min<int64_t>(nsm, b->ntile));
+    b->zero = trees[0]->tt_msplit + trees[0]->tt_mbase[trees[0]->L + 1] * 2 * LM_MAXV * TT_K;
+    b->err = trees[0]->dflag + 1;
+    auto up = [&](auto &v, auto **d) -> lm_status {
+        using T = typename std::remove_reference<decltype(v)>::type::value_type;
+        cudaError_t e = cudaMalloc((void **)d, std::max<size_t>(1, v.size()) * sizeof(T));
+        if (e != cudaSuccess) {
+            lm_set_error("batch_create: cudaMalloc failed: %s", cudaGetErrorString(e));
+            return LM_ENOMEM;
+        }
+        if (!v.empty()) LM_CUDA(cudaMemcpy(*d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return LM_OK;
+    };
+    lm_status s = up(tiles, &b->tiles);
+    if (s == LM_OK) s = up(ents, &b->ents);
+    if (s == LM_OK) s = up(lv, &b->lv);
+    if (s != LM_OK) {
+        lm_tt_batch_free(b);
+        return s;
+    }
+    *out = b;
+    return LM_OK;
+}
+
+template <int NP>
+static lm_status tt_batch_launch(const lm_tt_batch_s *b, cudaStream_t st)
+{
+    if (b->nvs == LM_MAXV)
+        k_m2l_tt<NP, 16><<<b->grid, TT_THREADS, TtSmem<NP, 16>::BYTES, st>>>(b->tiles, (int)b->ntile, b->ents, b->lv,
+                                                                          b->zero, b->err, -1);
+    else
+        k_m2l_tt<NP, 4><<<b->grid, TT_THREADS, TtSmem<NP, 4>::BYTES, st>>>(b->tiles, (int)b->ntile, b->ents, b->lv,
+                                                                        b->zero, b->err, -1);
+    return LM_OK;
+}
+
+lm_status lm_tt_batch_launch(const lm_tt_batch_s *b, cudaStream_t st)
+{
+    TT_SWITCH(b->p, tt_batch_launch, b, st);
+    lm_set_error("tensor-core M2L tiles: order %d not instantiated", b->p);
+    return LM_ENOTSUP;
+}
+
+void lm_tt_batch_free(lm_tt_batch_s *b)
+{
+    if (!b) return;
+    void *ptrs[] = {b->tiles, b->ents, b->lv};
     for (void *p : ptrs)
         if (p) cudaFree(p);
-    t->tt_tiles = t->tt_ents = nullptr;
+    delete b;
+}
+
+void lm_free_tt(lm_tree_s *t)
+{
+    for (int f = 0; f < 2; ++f) {
+        void *ptrs[] = {t->tt_tiles[f], t->tt_ents[f], t->tt_lv[f]};
+        for (void *p : ptrs)
+            if (p) cudaFree(p);
+        t->tt_tiles[f] = t->tt_ents[f] = t->tt_lv[f] = nullptr;
+    }
+    if (t->tt_tab) cudaFree(t->tt_tab);
+    if (t->tt_msplit) cudaFree(t->tt_msplit);
     t->tt_tab = t->tt_msplit = nullptr;
 }
