@@ -92,6 +92,10 @@ typedef struct {
                         error-free sums, densities scaled by a power of two per apply so
                         the expansions stay inside FP32's exponent range; about 1e-14
                         relative, and several times the FP64 pipe's rate on GB300. */
+    int tensor_leaf; /* LM_MIXED uniform trees, p <= 14, applies of 5-16 vectors: the leaf step's
+                        multiply-adds over the vectors (direct S2T pairs and L2T) on the tcgen05
+                        tensor cores, the kernel values on the CUDA cores (TF32 hi/lo split of both
+                        factors, FP32 accumulation); 1 on (lm_options_default), 0 off */
 } lm_options;
 
 /* Other media (Sec. 3, Examples 2 and 3): an interface of the middle layer

@@ -44,7 +44,8 @@ class _Options(ctypes.Structure):
                 ("tail_order", ctypes.c_int), ("tail_rays", ctypes.c_int), ("tensor_m2l", ctypes.c_int),
                 ("kernel", ctypes.c_int), ("autotune", ctypes.c_int), ("top_bc", ctypes.c_int),
                 ("bottom_bc", ctypes.c_int), ("top_alpha", ctypes.c_double), ("bottom_alpha", ctypes.c_double),
-                ("adaptive", ctypes.c_int), ("m2l_fp64", ctypes.c_int)]
+                ("adaptive", ctypes.c_int), ("m2l_fp64", ctypes.c_int),
+                ("tensor_leaf", ctypes.c_int)]
 
 
 class _TreeInfo(ctypes.Structure):
@@ -139,7 +140,7 @@ class Medium:
 def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP64, max_nvec=16,
                   seg_order=0, tail_order=0, tail_rays=9, tensor_m2l=1, kernel=KERNEL_G,
                   autotune=0, top_bc="transmission", top_alpha=0.0, bottom_bc="transmission",
-                  bottom_alpha=0.0, adaptive=False, m2l_fp64=False) -> Medium:
+                  bottom_alpha=0.0, adaptive=False, m2l_fp64=False, tensor_leaf=1) -> Medium:
     """kernel = KERNEL_G applies G; KERNEL_DG_DD applies dG/dd at fixed points.
     autotune = 1 tunes the M2L tile shapes of mixed-precision trees at build time.
     top_bc / bottom_bc: "transmission" (to the outer layer, k1 / k3), or a wall --
@@ -148,7 +149,8 @@ def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP
     adaptive = True builds adaptive trees (either precision): a box with more than leaf_target points is
     split while its level is below depth (-1 -> 14).
     m2l_fp64 = True runs the FP64 form's M2L, M2M and L2L contractions in IEEE FP64 instead of
-    double-float on the FP32 pipes."""
+    double-float on the FP32 pipes.
+    tensor_leaf = 0 keeps the mixed leaf step (S2T and L2T) of 16-vector applies on the CUDA cores."""
     if isinstance(precision, str):
         precision = {"fp64": FP64, "mixed": MIXED}[precision]
     for b in (top_bc, bottom_bc):
@@ -156,7 +158,7 @@ def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP
             raise ValueError(f"create_medium: unknown boundary kind {b!r} (one of {sorted(BC)})")
     o = _Options(p, depth, leaf_target, precision, max_nvec, seg_order, tail_order, tail_rays, tensor_m2l,
                  kernel, autotune, BC[top_bc], BC[bottom_bc], float(top_alpha), float(bottom_alpha),
-                 int(bool(adaptive)), int(bool(m2l_fp64)))
+                 int(bool(adaptive)), int(bool(m2l_fp64)), int(bool(tensor_leaf)))
     h = ctypes.c_void_p()
     _check(_lib.lm_create_medium(k1, k2, k3, d, ctypes.byref(o), ctypes.byref(h)))
     return Medium(h.value, k1, k2, k3, d, dict(p=p, depth=depth, leaf_target=leaf_target,
@@ -165,7 +167,7 @@ def create_medium(k1, k2, k3, d, *, p=20, depth=-1, leaf_target=48, precision=FP
                                               tensor_m2l=tensor_m2l, kernel=kernel, autotune=autotune,
                                               top_bc=top_bc, top_alpha=top_alpha, bottom_bc=bottom_bc,
                                               bottom_alpha=bottom_alpha, adaptive=bool(adaptive),
-                                              m2l_fp64=bool(m2l_fp64)))
+                                              m2l_fp64=bool(m2l_fp64), tensor_leaf=int(bool(tensor_leaf))))
 
 
 class Tree:

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "liblmfmm.so")
-SOURCES = ["lmfmm_setup.cu", "lmfmm_apply.cu", "lmfmm_mixed.cu", "lmfmm_api.cu", "lmfmm_noalloc.cu", "lmfmm_tc.cu", "lmfmm_tc_tiles.cu", "lmfmm_grad.cu",
+SOURCES = ["lmfmm_setup.cu", "lmfmm_apply.cu", "lmfmm_mixed.cu", "lmfmm_api.cu", "lmfmm_noalloc.cu", "lmfmm_tc.cu", "lmfmm_tc_tiles.cu", "lmfmm_leaf_tt.cu",
+           "lmfmm_grad.cu",
            "lmfmm_cross.cu", "lmfmm_adaptive.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", CSRC, "-I", INCLUDE]

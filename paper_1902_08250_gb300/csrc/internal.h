@@ -202,6 +202,15 @@ struct lm_tree_s {
     std::vector<int64_t> tt_tbase, tt_mbase; // per level: first table, first box
     int tt_grid;                // persistent CTAs (one per SM)
     int tt_poll_limit;          // polls of the first operand wait (-1: the library default)
+    // tensor-core leaf step (16-vector applies on uniform trees)
+    bool lf_ready;
+    void *lf_pts;               // [n] float4 (x, y relative to the leaf centre, absolute y, 0)
+    int32_t *lf_tot;            // [nleaf] U-list source points per leaf
+    void *lf_ent;               // [nleaf][32] int4 (first point, points, U term, source leaf) per U entry
+    uint32_t *lf_scl;           // [2] largest |component| of the apply's densities and leaf-level local
+                                // expansions (float bits), for the FP16 scales
+    int lf_grid;                // persistent CTAs (one per SM)
+    int lf_poll_limit;          // polls of the MMA issuer's first wait (-1: the library default)
     bool near_pw64; // FP64 reflected near field: segment factorised per leaf (k_near_pw64)
     int32_t *pwidx; // [boxes of the leaf level / of the tree] slot of an interface leaf, or -1
     zd *pwC;        // [slots][2 terms][2 nseg][LM_MAXV] per-leaf segment coefficients (k_pw_src64)
@@ -262,6 +271,11 @@ lm_status lm_setup_tt(lm_tree_s *t, cudaStream_t st);
 lm_status lm_launch_m2l_tt(lm_tree_s *t, cudaStream_t st, int nvs); // nvs: 16 or 4 vector slots
 lm_status lm_launch_msplit_tt(lm_tree_s *t, cudaStream_t st, int nvs);
 // one tile-form M2L launch over the tiles of several trees (batched applies)
+// tensor-core leaf step (lmfmm_leaf_tt.cu): L2T + S2T of 16-vector applies
+struct NearQuadF;
+lm_status lm_setup_leaf_tt(lm_tree_s *t, cudaStream_t st);
+lm_status lm_launch_leaf_tt(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st);
+void lm_free_leaf_tt(lm_tree_s *t);
 struct lm_tt_batch_s;
 lm_status lm_tt_batch_build(lm_tree_s *const *trees, int count, int nvs, lm_tt_batch_s **out);
 lm_status lm_tt_batch_launch(const lm_tt_batch_s *b, cudaStream_t st);

@@ -61,6 +61,7 @@ extern "C" lm_status lm_options_default(lm_options *o)
     o->bottom_alpha = 0.0;
     o->adaptive = 0;
     o->m2l_fp64 = 0;
+    o->tensor_leaf = 1;
     return LM_OK;
 }
 

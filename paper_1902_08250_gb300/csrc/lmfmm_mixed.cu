@@ -234,6 +234,7 @@ lm_status lm_setup_mixed(lm_tree_s *t, cudaStream_t st)
     TRYM(setup_mixed_points(t, st));
     if (t->med.opt.tensor_m2l) TRYM(lm_setup_tc(t, st));
     if (t->tc_ready) TRYM(lm_setup_tt(t, st));
+    TRYM(lm_setup_leaf_tt(t, st));
     for (Level &lv : t->lev) lv.m2l_impl = t->tc_ready ? 0 : 4;
     LM_CUDA(cudaGetLastError());
     LM_CUDA(cudaStreamSynchronize(st));
@@ -337,6 +338,7 @@ lm_status lm_setup_mixed_adaptive(lm_tree_s *t, cudaStream_t st)
 void lm_free_mixed(lm_tree_s *t)
 {
     lm_free_tt(t);
+    lm_free_leaf_tt(t);
     {
         AdaptTree &A = t->at;
         void *ap[] = {A.tab32, A.M32, A.L32};
@@ -363,7 +365,8 @@ void lm_free_mixed(lm_tree_s *t)
 // input order -> tree order: one thread per input point, coalesced reads of
 // q[v][j], one 128-byte row written at the point's tree position
 template <typename TIO>
-__global__ void k_permute_in32(const TIO *q, const int64_t *iperm, int64_t n, int nvec, int conjugate, zf *qs)
+__global__ void k_permute_in32(const TIO *q, const int64_t *iperm, int64_t n, int nvec, int conjugate, zf *qs,
+                               uint32_t *qmax)
 {
     int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -381,6 +384,15 @@ __global__ void k_permute_in32(const TIO *q, const int64_t *iperm, int64_t n, in
 #pragma unroll
     for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
         o[v2] = make_float4(a[2 * v2].re, a[2 * v2].im, a[2 * v2 + 1].re, a[2 * v2 + 1].im);
+    if (qmax) { // largest |component| of the densities (as bits of a non-negative float)
+        uint32_t m = 0;
+#pragma unroll
+        for (int v = 0; v < LM_MAXV; ++v)
+            m = max(m, max(__float_as_uint(a[v].re) & 0x7fffffffu, __float_as_uint(a[v].im) & 0x7fffffffu));
+        const uint32_t act = __activemask();
+        m = __reduce_max_sync(act, m);
+        if ((threadIdx.x & 31) == __ffs(act) - 1) atomicMax(qmax, m);
+    }
 }
 // tree order -> input order: one thread per input point, one 128-byte row
 // read at its tree position, coalesced writes of u[v][j]
@@ -821,7 +833,7 @@ __global__ void __launch_bounds__(128) k_m2m32(K kids, const zf *tabs, const zf 
 // slot = the child's position in the parent; writes the child's coefficients,
 // or adds them (ACC) where the level's M2L has already written them
 template <int NP, int NVS, bool ACC = false, class K = GridPar32>
-__global__ void __launch_bounds__(128) k_l2l32(K par, const zf *tabs, const zf *Lp, zf *Lc)
+__global__ void __launch_bounds__(128) k_l2l32(K par, const zf *tabs, const zf *Lp, zf *Lc, uint32_t *lmax)
 {
     constexpr int NR = Staged<NP, NVS>::NR, NB = Staged<NP, NVS>::NB, NG = Staged<NP, NVS>::NG;
     __shared__ __align__(16) zf Ts[NB][NP * NP];
@@ -834,13 +846,20 @@ __global__ void __launch_bounds__(128) k_l2l32(K par, const zf *tabs, const zf *
     zf acc[NR];
     staged_contract<NP, NVS>(1, entry, tabs, Lp, acc, Ts, Ms);
     const int v = threadIdx.x & (NVS - 1), g = threadIdx.x / NVS;
+    uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < NR; ++k) {
         const int p = g + NG * k;
         if (p < NP) {
             zf *o = Lc + (b * NP + p) * LM_MAXV + v;
-            *o = ACC ? *o + acc[k] : acc[k];
+            const zf r = ACC ? *o + acc[k] : acc[k];
+            *o = r;
+            m = max(m, max(__float_as_uint(r.re) & 0x7fffffffu, __float_as_uint(r.im) & 0x7fffffffu));
         }
+    }
+    if (lmax) { // largest |component| of the local expansions written (bits of a non-negative float)
+        m = __reduce_max_sync(0xffffffffu, m);
+        if ((threadIdx.x & 31) == 0) atomicMax(lmax, m);
     }
 }
 
@@ -1119,20 +1138,21 @@ static void launch_l2l(const Level &lv, const Level &par, cudaStream_t st, int n
 {
     constexpr int NP = 2 * P + 1;
     if (nvs == 4)
-        k_l2l32<NP, 4><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
+        k_l2l32<NP, 4><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32, nullptr);
     else
-        k_l2l32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
+        k_l2l32<NP, LM_MAXV><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32,
+                                                                 nullptr);
 }
 // L2L of the tile-form apply: adds to the M2L's local expansions
 template <int P>
-static void launch_l2l_acc(const Level &lv, const Level &par, cudaStream_t st, int nvs)
+static void launch_l2l_acc(const Level &lv, const Level &par, cudaStream_t st, int nvs, uint32_t *lmax)
 {
     constexpr int NP = 2 * P + 1;
     if (nvs == 4)
-        k_l2l32<NP, 4, true><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32);
+        k_l2l32<NP, 4, true><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32, lv.L32, lmax);
     else
         k_l2l32<NP, LM_MAXV, true><<<(unsigned)lv.nbox, 128, 0, st>>>(GridPar32{lv.ncol}, lv.l2l32, par.L32,
-                                                                       lv.L32);
+                                                                       lv.L32, lmax);
 }
 template <int P>
 static void launch_rest(const Level &lv, cudaStream_t st, int nvs)
@@ -1145,9 +1165,14 @@ static void launch_rest(const Level &lv, cudaStream_t st, int nvs)
         k_m2l_rest32<NP, LM_MAXV><<<(unsigned)lv.nrtgt, 128, 0, st>>>(lv.rtgt, lv.rstart, lv.rsrc, lv.rslot,
                                                                     lv.tab32, lv.M32, lv.L32);
 }
+static bool tiles_ready(const lm_tree_s *t);
 template <int P>
 static void launch_leaf(lm_tree_s *t, const NearQuadF &nq, cudaStream_t st, int nv)
 {
+    if (nv > 4 && t->lf_ready && tiles_ready(t)) { // 16 vector slots: the multiply-adds on the tensor cores
+        lm_launch_leaf_tt(t, nq, st);
+        return;
+    }
     const Level &lv = t->lev[t->L];
     // largest k r of a direct pair: two leaves apart diagonally
     const double xmax = t->med.k2 * lv.w * 2.0 * 1.4142135623730951 * 1.0001;
@@ -1232,9 +1257,10 @@ static void launch_l2l_list(const AdaptTree &A, const Level &lv, int l, cudaStre
     if (nb == 0) return;
     const ListPar32 par{b0, A.parent, A.pos};
     if (nvs == 4)
-        k_l2l32<NP, 4, false, ListPar32><<<(unsigned)nb, 128, 0, st>>>(par, lv.l2l32, A.L32, A.L32);
+        k_l2l32<NP, 4, false, ListPar32><<<(unsigned)nb, 128, 0, st>>>(par, lv.l2l32, A.L32, A.L32, nullptr);
     else
-        k_l2l32<NP, LM_MAXV, false, ListPar32><<<(unsigned)nb, 128, 0, st>>>(par, lv.l2l32, A.L32, A.L32);
+        k_l2l32<NP, LM_MAXV, false, ListPar32><<<(unsigned)nb, 128, 0, st>>>(par, lv.l2l32, A.L32, A.L32,
+                                                                             nullptr);
 }
 template <int P>
 static void launch_rest_list(const AdaptTree &A, int l, cudaStream_t st, int nvs)
@@ -1279,10 +1305,10 @@ static lm_status run_mixed_adaptive(lm_tree_s *t, const void *q, int nvec, void 
         lm_phase_begin(t, PH_PERMUTE, st);
         if (c64)
             k_permute_in32<zf><<<gridm(n, 256), 256, 0, st>>>((const zf *)q + (int64_t)v0 * n, t->iperm, n, nv,
-                                                             adjoint, t->qs32);
+                                                             adjoint, t->qs32, nullptr);
         else
             k_permute_in32<zd><<<gridm(n, 256), 256, 0, st>>>((const zd *)q + (int64_t)v0 * n, t->iperm, n, nv,
-                                                             adjoint, t->qs32);
+                                                             adjoint, t->qs32, nullptr);
         lm_phase_end(t, PH_PERMUTE, st, 1);
         lm_phase_begin(t, PH_S2M, st);
         if (A.nleaf > 0) {
@@ -1356,14 +1382,18 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
         const int nv = std::min(LM_MAXV, nvec - v0);
         const int nvs = nv <= 4 ? 4 : LM_MAXV; // vector slots the contractions compute
         const bool tiles = tiles_ready(t);
+        // the tensor-core leaf step takes the largest density and local-expansion components of
+        // this block of vectors (power-of-two scales into FP16's range), found by permute and L2L
+        const bool lft = nv > 4 && t->lf_ready && tiles;
         if (up) {
+        if (lft) LM_CUDA(cudaMemsetAsync(t->lf_scl, 0, 2 * sizeof(uint32_t), st));
         lm_phase_begin(t, PH_PERMUTE, st);
         if (c64)
             k_permute_in32<zf><<<gridm(n, 256), 256, 0, st>>>((const zf *)q + (int64_t)v0 * n, t->iperm, n, nv,
-                                                             adjoint, t->qs32);
+                                                             adjoint, t->qs32, lft ? t->lf_scl : nullptr);
         else
             k_permute_in32<zd><<<gridm(n, 256), 256, 0, st>>>((const zd *)q + (int64_t)v0 * n, t->iperm, n, nv,
-                                                             adjoint, t->qs32);
+                                                             adjoint, t->qs32, lft ? t->lf_scl : nullptr);
         lm_phase_end(t, PH_PERMUTE, st, 1);
         lm_phase_begin(t, PH_S2M, st);
         {
@@ -1393,7 +1423,8 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
             lm_phase_end(t, PH_M2L, st, up + (part == 0));
             if (part == 1) continue;
             if (L > 0) lm_phase_begin(t, PH_L2L, st);
-            for (int l = 1; l <= L; ++l) MX_DISPATCH(P, launch_l2l_acc, t->lev[l], t->lev[l - 1], st, nvs);
+            for (int l = 1; l <= L; ++l)
+                MX_DISPATCH(P, launch_l2l_acc, t->lev[l], t->lev[l - 1], st, nvs, (l == L && lft) ? t->lf_scl + 1 : nullptr);
             if (L > 0) lm_phase_end(t, PH_L2L, st, L);
         }
         for (int l = 0; l <= L && !tiles; ++l) {
