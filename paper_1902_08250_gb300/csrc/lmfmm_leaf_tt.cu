@@ -1,50 +1,52 @@
 // lmfmm_leaf_tt.cu -- step 4 of the mixed-precision apply for 16 density vectors
 // on uniform trees: the L2T evaluation of the local expansion (Eq. (local)) and
 // the direct S2T interactions of the U list, with the multiply-adds over the
-// vectors on the 5th-generation tensor cores (tcgen05, kind::tf32), as one
-// persistent launch.
+// vectors on the 5th-generation tensor cores (tcgen05, kind::f16 with FP32
+// accumulation), as one persistent launch.
 //
 // For the targets of one leaf (a pass of up to 64 of them) both parts are one
 // complex product
 //     U[t][v] = sum_j G[t][j] Q[j][v],
 // j over the leaf's U-list source points (free space: G = (i/4) H0(k2 r), the
 // self pair excluded; reflected terms: their tails, the segment part coming from
-// k_near_pw32), cut into chunks of 32, and in a last chunk over the orders
+// k_near_pw32), cut into chunks of 64, and in a last chunk over the orders
 // n = -p..p (G the scaled J_|n|(k2 r) e^{i n theta} basis, Q the leaf's local
-// expansion).  In real form, with K = (j, re / im) and N = (part h of Q's TF32
+// expansion).  In real form, with K = (j, re / im) and N = (part h of Q's FP16
 // split, output re / im, vector v):
 //     D[t][(h, o, v)] = sum_k A[t][k] B[(h, o, v)][k],
 //     A[t][(j, re)] = Re G,  A[t][(j, im)] = Im G,
 //     B[(h, re, v)] = (Re Q_h, -Im Q_h),  B[(h, im, v)] = (Im Q_h, Re Q_h)  at (j, re), (j, im).
-// A's rows 0..63 hold G's TF32 hi part for the 64 target slots and rows 64..127
-// its lo part, so one MMA chain per chunk (M = 128, N = 64, K = 64) forms every
-// product of the split; the four sums of an output are added in registers,
-// each chunk's D on its own (blocked accumulation).  The CUDA cores evaluate G
-// (the kernel values are the expensive part) and no thread multiplies over the
-// vectors.
+// A's rows 0..63 hold G's hi part for the 64 target slots and rows 64..127 its lo
+// part, so one MMA chain per chunk (M = 128, N = 64, K = 128) forms every product
+// of the split; the four sums of an output are added in registers, each chunk's D
+// on its own (blocked accumulation).  The CUDA cores evaluate G (the kernel values
+// are the expensive part) and no thread multiplies over the vectors.
 //
 // Roles (16 warps, one CTA per SM, persistent over the leaves):
-//   warp 0     producer: tables the leaf's U entries; per chunk its lanes write
-//              the sources' coordinates relative to the target leaf, their terms
-//              and point indices, and lane 0 bulk-copies the densities (rows of
-//              128 B, one copy per entry the chunk touches) or the leaf's local
-//              expansion into a stage;
-//   warp 1     converter: splits a stage's densities into the B operand
-//              (canonical K-major layout, hi/lo parts, real-block signs);
+//   warp 0     producer: tables the leaf's flattened U-list sources once per
+//              leaf; per chunk its lanes write each source's record (offset of
+//              the source leaf, point, U term), and the lane at the start of
+//              each run of consecutive points bulk-copies the run's densities
+//              (rows of 128 B) and coordinates (rows of 16 B), or lane 0 the
+//              leaf's local expansion;
+//   warps 1, 3 converters: split a stage's densities into the B operand
+//              (canonical K-major layout, hi/lo parts, real-block signs), 8
+//              vectors each; warp 1 also turns the records into coordinates;
 //   warp 2     MMA issuer, owner of the tensor memory;
 //   warps 4-11 kernel values: warp 4 + g evaluates G for target slots
-//              32 (g & 1) .. + 31 and the chunk's sources 8 (g >> 1) .. + 7 and
+//              32 (g & 1) .. + 31 and the chunk's sources 16 (g >> 1) .. + 15 and
 //              stores their hi and lo rows of A;
 //   warps 12-15 epilogue: warp 12 + Q reads tensor-memory lanes 32 Q .. + 31 of
 //              each chunk's accumulator; at the end of a pass the lo-part rows
 //              meet their hi-part rows in shared memory and the potentials are
 //              written.
-// Three source stages, two A buffers and two accumulators (2 x 64 columns) let
+// Four source stages, two A buffers and two accumulators (2 x 64 columns) let
 // copies, conversion, kernel values, MMAs and the epilogue of consecutive chunks
-// overlap.  Every wait is bounded: a role that gives up sets the CTA's abort word
-// and the launch's error flag, the others stop at their next wait (the warps that
-// share a named barrier decide together, once per pass), copies and MMAs in
-// flight are waited for (bounded) and the tensor memory is freed.
+// overlap; every role loads the next leaf's counts while it serves the current
+// one.  Every wait is bounded: a role that gives up sets the CTA's abort word and
+// the launch's error flag, the others stop at their next wait (the epilogue
+// warps, which share a named barrier, decide together once per pass), copies and
+// MMAs in flight are waited for (bounded) and the tensor memory is freed.
 #include <algorithm>
 
 #include "internal.h"
@@ -52,20 +54,21 @@
 #include "tc_common.cuh"
 #include <cuda_fp16.h>
 
-#define LF_CH 32                          // sources per chunk: K = 64 real columns
+#define LF_CH 64                          // sources per chunk: K = 128 real columns
+#define LF_K (2 * LF_CH)
 #define LF_TGT 64                         // target slots per pass
-#define LF_NS 8                           // source stages
-#define LF_NA 3                           // A buffers = accumulators (64 tensor-memory columns each)
+#define LF_NS 4                           // source stages
+#define LF_NA 2                           // A buffers = accumulators (64 tensor-memory columns each)
 #define LF_GW 8                           // kernel-value warps
-#define LF_JS 8                           // sources (order slots) per kernel-value thread and chunk
+#define LF_JS 16                          // sources (order slots) per kernel-value thread and chunk
 #define LF_EPI0 (4 + LF_GW)               // first epilogue warp (a multiple of 4)
 #define LF_THREADS ((LF_EPI0 + 4) * 32)
 #define LF_MAXE 32                        // U entries of a leaf (one per producer lane)
-#define LF_A_BYTES (128 * 64 * 2)         // 16 KB: FP16
-#define LF_B_BYTES (64 * 64 * 2)          // 8 KB
+#define LF_A_BYTES (128 * LF_K * 2)       // 32 KB: FP16
+#define LF_B_BYTES (64 * LF_K * 2)        // 16 KB
 #define LF_GSCALE 1024.0f                 // kernel values enter A multiplied by 2^10
-#define LF_Q_BYTES (LF_CH * LM_MAXV * 8)  // 4 KB: 32 rows of 16 complex densities
-#define LF_RAW_BYTES (LF_Q_BYTES + LF_CH * 16) // + 32 coordinate rows (x, y local; y absolute; 0)
+#define LF_Q_BYTES (LF_CH * LM_MAXV * 8)  // 8 KB: rows of 16 complex densities
+#define LF_RAW_BYTES (LF_Q_BYTES + LF_CH * 16) // + coordinate rows (x, y local; y absolute; 0)
 #define LF_XS 33                          // floats per target row of the exchange buffer
 
 // one stage's sources as the kernel-value warps read them, one 16-byte record each:
@@ -98,18 +101,18 @@ struct LfSmem {
 // component lies in [2^14, 2^15)), and the epilogue undoes the scales exactly.  Components
 // below 2^-24 of that largest one lose relative precision (FP16 subnormals): their absolute
 // error stays below 2^-39 of it.
-// Byte offset of element (row, k) of a K-major no-swizzle FP16 operand with K = 64:
-// 8-row x 16-byte core matrices, K-adjacent ones 128 B apart, 8-row groups 1 KB apart.
+// Byte offset of element (row, k) of a K-major no-swizzle FP16 operand with K = LF_K:
+// 8-row x 16-byte core matrices, K-adjacent ones 128 B apart, 8-row groups LF_K * 16 B apart.
 __host__ __device__ __forceinline__ uint32_t lf_off(int row, int k)
 {
-    return (uint32_t)((row >> 3) * 1024 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+    return (uint32_t)((row >> 3) * (LF_K * 16) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 __device__ __forceinline__ uint64_t lf_desc(uint32_t saddr)
 {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)(128 >> 4) << 16;   // LBO: K-direction core-matrix stride
-    d |= (uint64_t)(1024 >> 4) << 32;  // SBO: 8-row-group stride
+    d |= (uint64_t)((LF_K * 16) >> 4) << 32; // SBO: 8-row-group stride
     d |= (uint64_t)1 << 46;
     return d;
 }
@@ -198,7 +201,7 @@ __device__ __forceinline__ zf lf_h0s(float t)
     return zf{fmaf(wc, im, sh), im};
 }
 
-// L2T basis of the order slots LF_JS E .. LF_JS E + LF_JS - 1 (slot P + n <-> order n) for a target at
+// L2T basis of the order slots E .. E + 7 (slot P + n <-> order n) for a target at
 // (x, y) relative to its leaf centre, zeta = (x + i y) / w, t = (k r / 2)^2:
 //   n >= 0: s_n(t) zeta^n,   n < 0: (-1)^|n| s_|n|(t) conj(zeta)^|n|,
 // s_m(t) = sum_j (-t)^j m! / (j! (j + m)!) = J_m(k r) / ((k r / 2)^m / m!), the scaled
@@ -213,8 +216,8 @@ __device__ __forceinline__ void lf_basis(float xs, float ys, float t, zf *gv)
 #pragma unroll
     for (int m = 1; m <= P; ++m) pw[m] = pw[m - 1] * zf{xs, ys};
 #pragma unroll
-    for (int ii = 0; ii < LF_JS; ++ii) {
-        const int j = LF_JS * E + ii, n = j - P, a = n < 0 ? -n : n;
+    for (int ii = 0; ii < 8; ++ii) {
+        const int j = E + ii, n = j - P, a = n < 0 ? -n : n;
         if (j >= NP) {
             gv[ii] = zf{0.f, 0.f};
             continue;
@@ -425,36 +428,49 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                     const uint32_t raw = sbase + S::RAW_OFF + s * LF_RAW_BYTES;
                     if (c < nreg) {
                         const int g0 = c * LF_CH, n = min(LF_CH, T - g0);
-                        const bool valid = lane < n;
-                        int pi = -1, e = 0;
-                        if (valid) {
-                            const int g = g0 + lane;
-                            if (tabled) {
-                                pi = tpi[g];
-                                e = te[g];
-                            } else {
-                                while (epref[e + 1] <= g) ++e;
-                                pi = ebase[e] + (g - epref[e]);
+                        // slots lane and 32 + lane: point, meta record, start of a run of consecutive points
+                        int pi[2], last0 = -2;
+                        uint32_t starts[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int slot = 32 * h + lane;
+                            const bool valid = slot < n;
+                            int e = 0;
+                            pi[h] = -1;
+                            if (valid) {
+                                const int g = g0 + slot;
+                                if (tabled) {
+                                    pi[h] = tpi[g];
+                                    e = te[g];
+                                } else {
+                                    while (epref[e + 1] <= g) ++e;
+                                    pi[h] = ebase[e] + (g - epref[e]);
+                                }
                             }
+                            m.src[slot] = valid ? make_float4(eox[e], eoy[e], 0.f, __int_as_float((pi[h] << 2) | eterm[e]))
+                                                : make_float4(0.f, 0.f, 0.f, __int_as_float(-4));
+                            int prev = __shfl_up_sync(0xffffffffu, pi[h], 1);
+                            if (lane == 0) prev = last0; // slot 31 before slot 32; none before slot 0
+                            starts[h] = __ballot_sync(0xffffffffu, valid && pi[h] != prev + 1);
+                            last0 = __shfl_sync(0xffffffffu, pi[0], 31);
                         }
-                        m.src[lane] = valid ? make_float4(eox[e], eoy[e], 0.f, __int_as_float(eterm[e]))
-                                            : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
                         if (lane == 0) m.n = n;
-                        // runs of consecutive points: one pair of bulk copies (densities, coordinates) each
-                        const int prev = __shfl_up_sync(0xffffffffu, pi, 1);
-                        uint32_t starts = __ballot_sync(0xffffffffu, valid && (lane == 0 || pi != prev + 1));
                         __syncwarp();
                         if (lane == 0) mbar_expect_tx(rfull(s), (uint32_t)n * (LM_MAXV * 8 + 16));
-                        while (starts) {
-                            const int r = __ffs(starts) - 1;
-                            starts &= starts - 1;
-                            const int r1 = starts ? __ffs(starts) - 1 : n;
-                            const int pr = __shfl_sync(0xffffffffu, pi, r);
-                            if (lane == 0) {
+                        __syncwarp();
+                        // runs of consecutive points: the lane at a run's first slot copies its densities and
+                        // coordinates (the copies of a chunk are issued in parallel)
+                        const uint64_t st64 = (uint64_t)starts[0] | ((uint64_t)starts[1] << 32);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int r = 32 * h + lane;
+                            if ((st64 >> r) & 1) {
+                                const uint64_t after = r < 63 ? st64 >> (r + 1) : 0;
+                                const int r1 = after ? r + __ffsll((long long)after) : n;
                                 const uint32_t len = (uint32_t)(r1 - r);
-                                bulk_g2s(raw + (uint32_t)r * LM_MAXV * 8, qs + (int64_t)pr * LM_MAXV, len * LM_MAXV * 8,
+                                bulk_g2s(raw + (uint32_t)r * LM_MAXV * 8, qs + (int64_t)pi[h] * LM_MAXV, len * LM_MAXV * 8,
                                          rfull(s));
-                                bulk_g2s(raw + LF_Q_BYTES + (uint32_t)r * 16, pts + pr, len * 16, rfull(s));
+                                bulk_g2s(raw + LF_Q_BYTES + (uint32_t)r * 16, pts + pi[h], len * 16, rfull(s));
                             }
                         }
                     } else {
@@ -501,10 +517,14 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                     const int n = m.n;
                     const zf *raw = (const zf *)(smem + S::RAW_OFF + s * LF_RAW_BYTES);
                     if (cw == 0 && c < nreg) { // coordinates relative to the target leaf: X = x_s - (centre_t - centre_s)
-                        const float4 pt = lane < n ? ((const float4 *)(raw + LF_CH * LM_MAXV))[lane]
-                                                   : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float4 o = m.src[lane];
-                        m.src[lane] = make_float4(kh * (pt.x - o.x), kh * (pt.y - o.y), pt.z, o.w);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const int slot = 32 * h + lane;
+                            const float4 pt = slot < n ? ((const float4 *)(raw + LF_CH * LM_MAXV))[slot]
+                                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                            const float4 o = m.src[slot];
+                            m.src[slot] = make_float4(kh * (pt.x - o.x), kh * (pt.y - o.y), pt.z, o.w);
+                        }
                     }
                     unsigned char *B = smem + S::B_OFF + s * LF_B_BYTES;
                     const float sc = scq[c < nreg ? 0 : 1];
@@ -574,7 +594,7 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                         const uint64_t db = bdesc0 + (uint64_t)(s * (LF_B_BYTES >> 4));
                         const uint32_t dd = tmem + 64u * a;
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
+                        for (int kk = 0; kk < LF_K / 16; ++kk)
                             lf_mma(dd, da + 16u * kk, db + 16u * kk, idesc, kk > 0 ? 1u : 0u);
                         tc_commit(sempty(s));
                         tc_commit(aempty(a));
@@ -625,69 +645,74 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                     }
                     unsigned char *A = smem + S::A_OFF + a * LF_A_BYTES;
                     if (act) {
-                        zf gv[LF_JS];
-                        if (c < nreg) {
-                            // coordinates in units of 2/k, so that t = (k r / 2)^2 = dx^2 + dy^2; slots past the
-                            // chunk's sources hold zeros (finite values; B is zero there)
-                            const LfMeta &m = meta[s];
-                            float tv[LF_JS];
-                            bool special = false;
+                        // this thread's LF_JS sources (or order slots) in two rounds of 8
+#pragma unroll 1
+                        for (int hb = 0; hb < LF_JS / 8; ++hb) {
+                            const int jb = j0 + 8 * hb;
+                            zf gv[8];
+                            if (c < nreg) {
+                                // coordinates in units of 2/k, so that t = (k r / 2)^2 = dx^2 + dy^2; slots past
+                                // the chunk's sources hold zeros (finite values; B is zero there)
+                                const LfMeta &m = meta[s];
+                                float tv[8];
+                                bool special = false;
 #pragma unroll
-                            for (int ii = 0; ii < LF_JS; ++ii) {
-                                const float4 r4 = m.src[j0 + ii];
-                                const float dx = xk - r4.x, dy = yk - r4.y;
-                                tv[ii] = fmaf(dx, dx, dy * dy);
-                                special |= (__float_as_int(r4.w) != 0) | (!DEG && tv[ii] > 1.0f);
-                            }
+                                for (int ii = 0; ii < 8; ++ii) {
+                                    const float4 r4 = m.src[jb + ii];
+                                    const float dx = xk - r4.x, dy = yk - r4.y;
+                                    tv[ii] = fmaf(dx, dx, dy * dy);
+                                    special |= ((__float_as_int(r4.w) & 3) != 0) | (!DEG && tv[ii] > 1.0f);
+                                }
 #pragma unroll
-                            for (int ii = 0; ii < LF_JS; ++ii) gv[ii] = lf_h0s<DEG ? DEG : 8>(tv[ii]);
-                            if (!special) {
-                                // t = 0: the self pair (and points that coincide) is left out
+                                for (int ii = 0; ii < 8; ++ii) gv[ii] = lf_h0s<DEG ? DEG : 8>(tv[ii]);
+                                if (!special) {
+                                    // t = 0: the self pair (and points that coincide) is left out
 #pragma unroll
-                                for (int ii = 0; ii < LF_JS; ++ii)
-                                    if (tv[ii] == 0.f) gv[ii] = zf{0.f, 0.f};
-                            } else {
+                                    for (int ii = 0; ii < 8; ++ii)
+                                        if (tv[ii] == 0.f) gv[ii] = zf{0.f, 0.f};
+                                } else {
 #pragma unroll
-                                for (int ii = 0; ii < LF_JS; ++ii) {
-                                    const float4 r4 = m.src[j0 + ii]; // read again: the rare path
-                                    const int term = __float_as_int(r4.w);
-                                    if (term != 0) { // tail of a reflected direct term
-                                        const float X = fabsf(xk - r4.x) * (1.0f / kh);
-                                        const float h = term == 1 ? -(ya + r4.z) : ya + r4.z + 2.0f * d;
-                                        const zf tl = near_tail32(nq, term - 1, X, h);
-                                        gv[ii] = zf{tl.re * LF_GSCALE, tl.im * LF_GSCALE};
-                                    } else if (tv[ii] == 0.f) {
-                                        gv[ii] = zf{0.f, 0.f};
-                                    } else if (!DEG && tv[ii] > 1.0f) {
-                                        const zf fr = green_free32_far(tv[ii]);
-                                        gv[ii] = zf{fr.re * LF_GSCALE, fr.im * LF_GSCALE};
+                                    for (int ii = 0; ii < 8; ++ii) {
+                                        const float4 r4 = m.src[jb + ii]; // read again: the rare path
+                                        const int term = __float_as_int(r4.w) & 3;
+                                        if (term != 0) { // tail of a reflected direct term
+                                            const float X = fabsf(xk - r4.x) * (1.0f / kh);
+                                            const float h = term == 1 ? -(ya + r4.z) : ya + r4.z + 2.0f * d;
+                                            const zf tl = near_tail32(nq, term - 1, X, h);
+                                            gv[ii] = zf{tl.re * LF_GSCALE, tl.im * LF_GSCALE};
+                                        } else if (tv[ii] == 0.f) {
+                                            gv[ii] = zf{0.f, 0.f};
+                                        } else if (!DEG && tv[ii] > 1.0f) {
+                                            const zf fr = green_free32_far(tv[ii]);
+                                            gv[ii] = zf{fr.re * LF_GSCALE, fr.im * LF_GSCALE};
+                                        }
                                     }
                                 }
-                            }
-                        } else {
-                            // the L2T chunk: this warp's order slots (a compile-time set per part)
-                            const float xs = xi / w, ys = yi / w, tt = fmaf(xk, xk, yk * yk);
-                            switch (part) {
-                            case 0: lf_basis<P, 0>(xs, ys, tt, gv); break;
-                            case 1: lf_basis<P, 1>(xs, ys, tt, gv); break;
-                            case 2: lf_basis<P, 2>(xs, ys, tt, gv); break;
-                            case 3: lf_basis<P, 3>(xs, ys, tt, gv); break;
-                            case 4: lf_basis<P, 4>(xs, ys, tt, gv); break;
-                            case 5: lf_basis<P, 5>(xs, ys, tt, gv); break;
-                            case 6: lf_basis<P, 6>(xs, ys, tt, gv); break;
-                            default: lf_basis<P, 7>(xs, ys, tt, gv); break;
-                            }
-                        }
-                        // hi and lo rows of this target slot: one 16-byte store per 4 sources and part
+                            } else {
+                                // the L2T chunk: order slots jb .. jb + 7 (a compile-time set per case)
+                                const float xs = xi / w, ys = yi / w, tt = fmaf(xk, xk, yk * yk);
+                                switch (jb >> 3) {
+                                case 0: lf_basis<P, 0>(xs, ys, tt, gv); break;
+                                case 1: lf_basis<P, 8>(xs, ys, tt, gv); break;
+                                case 2: lf_basis<P, 16>(xs, ys, tt, gv); break;
+                                case 3: lf_basis<P, 24>(xs, ys, tt, gv); break;
+                                default: // slots past 2 P + 1 <= 29 hold zeros
 #pragma unroll
-                        for (int m4 = 0; m4 < LF_JS / 4; ++m4) {
-                            uint32_t h[4], l[4];
+                                    for (int ii = 0; ii < 8; ++ii) gv[ii] = zf{0.f, 0.f};
+                                    break;
+                                }
+                            }
+                            // hi and lo rows of this target slot: one 16-byte store per 4 sources and part
 #pragma unroll
-                            for (int jj = 0; jj < 4; ++jj)
-                                lf_split2(gv[4 * m4 + jj].re, gv[4 * m4 + jj].im, h[jj], l[jj]);
-                            const int kk = 2 * (j0 + 4 * m4);
-                            *(uint4 *)(A + lf_off(t, kk)) = make_uint4(h[0], h[1], h[2], h[3]);
-                            *(uint4 *)(A + lf_off(64 + t, kk)) = make_uint4(l[0], l[1], l[2], l[3]);
+                            for (int m4 = 0; m4 < 2; ++m4) {
+                                uint32_t h[4], l[4];
+#pragma unroll
+                                for (int jj = 0; jj < 4; ++jj)
+                                    lf_split2(gv[4 * m4 + jj].re, gv[4 * m4 + jj].im, h[jj], l[jj]);
+                                const int kk = 2 * (jb + 4 * m4);
+                                *(uint4 *)(A + lf_off(t, kk)) = make_uint4(h[0], h[1], h[2], h[3]);
+                                *(uint4 *)(A + lf_off(64 + t, kk)) = make_uint4(l[0], l[1], l[2], l[3]);
+                            }
                         }
                     }
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -810,7 +835,7 @@ lm_status lm_setup_leaf_tt(lm_tree_s *t, cudaStream_t st)
     default: break;
     }
     // the L2T basis series holds for k2 w <= 2 (t = (k2 r / 2)^2 <= 1/2 inside a leaf)
-    if (!inst || t->L < 1 || t->med.k2 * t->lev[t->L].w > 2.0) return LM_OK;
+    if (!inst || t->L < 1 || t->n >= ((int64_t)1 << 29) || t->med.k2 * t->lev[t->L].w > 2.0) return LM_OK;
     std::vector<int64_t> us(t->nleaf + 1);
     LM_CUDA(cudaMemcpyAsync(us.data(), t->ustart, us.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LM_CUDA(cudaStreamSynchronize(st));
