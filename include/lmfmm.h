@@ -136,6 +136,9 @@ typedef struct {
     int64_t nbox;     /* boxes of every level (uniform: sum over l of R 4^l) */
     int adaptive;     /* 1 for an adaptive tree: depth is then its deepest level and
                          nleaf its number of leaves */
+    int tensor_leaf;  /* 1 when applies of 5-16 vectors run the leaf step's multiply-adds on
+                         the tensor cores (LM_MIXED uniform tree, tile-form M2L, p <= 14,
+                         k2 w <= 2 at the leaves, lm_options.tensor_leaf set) */
 } lm_tree_info;
 
 /* Fill *opt with the defaults listed above. LM_EINVAL if opt is NULL. */

@@ -52,7 +52,7 @@ class _TreeInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("R", ctypes.c_int), ("depth", ctypes.c_int), ("p", ctypes.c_int),
                 ("x_origin", ctypes.c_double), ("nleaf", ctypes.c_int64), ("precision", ctypes.c_int),
                 ("max_nvec", ctypes.c_int), ("device_bytes", ctypes.c_int64), ("nbox", ctypes.c_int64),
-                ("adaptive", ctypes.c_int)]
+                ("adaptive", ctypes.c_int), ("tensor_leaf", ctypes.c_int)]
 
 
 def _load():

@@ -337,6 +337,7 @@ extern "C" lm_status lm_get_tree_info(lm_tree t, lm_tree_info *info)
     info->max_nvec = t->max_nvec;
     info->device_bytes = t->bytes;
     info->adaptive = t->adaptive ? 1 : 0;
+    info->tensor_leaf = (t->lf_ready && lm_mixed_tiles(t, LM_MAXV)) ? 1 : 0;
     if (t->adaptive) {
         info->nbox = t->at.nbox;
     } else {
