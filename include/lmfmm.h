@@ -440,14 +440,17 @@ lm_status lm_misfit_grad(lm_tree t, lm_tree dtree, const void *q, const void *g,
  * g_2^t, g_2^b with the printed densities sigma_2^t, sigma_2^b, through the
  * FMM with two wave numbers: multipoles in k1 about the source boxes, local
  * expansions in k2 about the target boxes (Sec. 2.1), on a source and a target
- * tree sharing one lattice of d x d roots.  FP64; the medium must have
- * precision LM_FP64, kernel LM_KERNEL_G and transmission interfaces.
+ * tree sharing one lattice of d x d roots.  The medium must have kernel
+ * LM_KERNEL_G and transmission interfaces.  Precision LM_FP64: every step in
+ * FP64.  LM_MIXED: tables and near-field quadrature built in FP64; expansions,
+ * translations and multiply-adds in FP32 (tables rounded once), near kernel
+ * values evaluated in FP64 and rounded.
  *   build_cross: xs, ys (device, [ns]) sources with 0 < ys < d; xt, yt
  *     (device, [nt]) targets with -d < yt < 0.  Copies what it needs.
  *   cross_apply: q device complex128 [nvec][ns]; u device complex128 [nvec][nt].
  *   cross_info: sizes and the shared lattice (any output may be NULL).
  * Errors: LM_EINVAL for bad points or arguments, LM_ENOTSUP for another
- * medium kind or precision, LM_ENOMEM, LM_ECUDA.
+ * medium kind, LM_ENOMEM, LM_ECUDA.
  */
 typedef struct lm_cross_s *lm_cross;
 lm_status lm_build_cross(lm_medium m, const double *xs, const double *ys, int64_t ns, const double *xt,

@@ -3,7 +3,7 @@
 //     u_i = sum_j q_j [g_2^t + g_2^b](x_i, x_j),
 // through the FMM with two wave numbers (Sec. 2.1: multipoles in k0 = k1 about
 // the source boxes, local expansions in k = k2 about the target boxes), on a
-// source tree and a target tree that share one lattice.  FP64.
+// source tree and a target tree that share one lattice.
 //
 // The sources are mirrored through y = 0 (y' = -y0), onto the lattice of the
 // middle layer.  Then g_2^t has the geometry of the middle layer's tt image
@@ -15,6 +15,10 @@
 // table depends on the target and source rows separately, so a class is
 // (term, dc, rt, rs).  g_2^b never reaches the near field (its image is d or
 // more below every target).
+// Precision: LM_FP64 runs every step in FP64.  LM_MIXED builds the tables and the
+// near-field quadrature in FP64 and keeps FP32 copies of the tables; the
+// expansions and every multiply-add are FP32, the near kernel values FP64 rounded
+// to FP32.
 #include <algorithm>
 #include <map>
 #include <tuple>
@@ -58,6 +62,8 @@ struct CrossLevel {
     int32_t *vsrc, *vslot;
     int ncls;
     zd *tab; // [ncls][np][np]
+    // mixed form: FP32 copies of the tables, FP32 expansions
+    zf *tab32, *m2m32, *l2l32, *M32, *L32;
 };
 
 struct lm_cross_s {
@@ -279,6 +285,192 @@ __global__ void k_cross_leaf(LeafGeom g, int P, double k2, const double *xt, con
             }
         }
         for (int v = 0; v < nvec; ++v) us[(int64_t)v * nt + i] = acc[v];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision form: the same steps with the expansions, the translation
+// tables (built in FP64, rounded once) and every multiply-add in FP32; the
+// near-field kernel values g_2^t come from the FP64 contour quadrature above
+// and are rounded per pair.
+// ---------------------------------------------------------------------------
+__global__ void k_cross_to32(const zd *a, int64_t n, zf *b)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = zf{(float)a[i].re, (float)a[i].im};
+}
+
+__device__ __forceinline__ void cfma32(zf &a, zf b, zf c)
+{
+    a.re = fmaf(b.re, c.re, fmaf(-b.im, c.im, a.re));
+    a.im = fmaf(b.re, c.im, fmaf(b.im, c.re, a.im));
+}
+
+#define CROSS32_CHUNK 32
+// S2M in k1 about the mirrored source leaves: one block per leaf, points staged
+// CROSS32_CHUNK at a time (basis row and densities), one thread per (order, vector)
+__global__ void __launch_bounds__(128) k_cross_p2m32(LeafGeom g, int P, double k, const double *xs,
+                                                     const double *ys, const int64_t *ls, const zd *qs, int64_t n,
+                                                     int nvec, zf *M)
+{
+    __shared__ zf B[CROSS32_CHUNK][2 * LM_MAXP + 1];
+    __shared__ zf Q[CROSS32_CHUNK][LM_MAXV];
+    const int np = 2 * P + 1;
+    const int64_t b = blockIdx.x, lo = ls[b], hi = ls[b + 1];
+    double cx, cy;
+    leaf_centre(g, b, &cx, &cy);
+    const float sc = (float)(k * g.w);
+    const int nent = np * nvec;
+    zf acc[8];
+    for (int e = 0; e < 8; ++e) acc[e] = zf{0.f, 0.f};
+    for (int64_t base = lo; base < hi; base += CROSS32_CHUNK) {
+        __syncthreads();
+        const int j = threadIdx.x;
+        if (j < CROSS32_CHUNK) {
+            const int64_t i = base + j;
+            zf *row = B[j] + P;
+            if (i < hi) {
+                const float rx = (float)(xs[i] - cx), ry = (float)(ys[i] - cy), r = sqrtf(rx * rx + ry * ry);
+                float J[LM_MAXP + 1];
+                bessel_j_scaled<float>(P, (float)k * r, sc, J);
+                const zf z = r > 0.f ? zf{rx / r, -ry / r} : zf{1.f, 0.f}; // e^{-i theta}
+                zf zp = {1.f, 0.f};
+                row[0] = zf{J[0], 0.f};
+                for (int m = 1; m <= P; ++m) {
+                    zp = zp * z;
+                    row[m] = J[m] * zp;
+                    row[-m] = ((m & 1) ? -J[m] : J[m]) * conj(zp);
+                }
+                for (int v = 0; v < nvec; ++v) {
+                    const zd qd = qs[(int64_t)v * n + i];
+                    Q[j][v] = zf{(float)qd.re, (float)qd.im};
+                }
+            } else {
+                for (int m = -P; m <= P; ++m) row[m] = zf{0.f, 0.f};
+                for (int v = 0; v < nvec; ++v) Q[j][v] = zf{0.f, 0.f};
+            }
+        }
+        __syncthreads();
+        for (int e = 0; e < 8; ++e) {
+            const int idx = threadIdx.x + e * blockDim.x;
+            if (idx >= nent) break;
+            const int qi = idx / nvec, v = idx % nvec;
+            zf s = zf{0.f, 0.f}; // each chunk summed on its own (blocked accumulation)
+            for (int jj = 0; jj < CROSS32_CHUNK; ++jj) cfma32(s, B[jj][qi], Q[jj][v]);
+            acc[e] = acc[e] + s;
+        }
+    }
+    for (int e = 0; e < 8; ++e) {
+        const int idx = threadIdx.x + e * blockDim.x;
+        if (idx >= nent) break;
+        const int qi = idx / nvec, v = idx % nvec;
+        M[(b * np + qi) * LM_MAXV + v] = acc[e];
+    }
+}
+
+// M2M in k1 (Lemma M2M): parent from its four children
+__global__ void k_cross_m2m32(int64_t ncol, int64_t nbox, int P, int nvec, const zf *tabs, const zf *Mc, zf *Mp)
+{
+    const int np = 2 * P + 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * nvec) return;
+    const int v = idx % nvec, p = (idx / nvec) % np;
+    const int64_t b = idx / (nvec * np), r = b / ncol, c = b % ncol, ncc = 2 * ncol;
+    zf acc = {0.f, 0.f};
+    for (int pos = 0; pos < 4; ++pos) {
+        const int64_t ch = (2 * r + (pos >> 1)) * ncc + 2 * c + (pos & 1);
+        const zf *T = tabs + ((int64_t)pos * np + p) * np;
+        const zf *m = Mc + ch * np * LM_MAXV + v;
+        for (int q = 0; q < np; ++q) cfma32(acc, T[q], m[q * LM_MAXV]);
+    }
+    Mp[(b * np + p) * LM_MAXV + v] = acc;
+}
+
+// L2L in k2 (Lemma L2L): child from its parent; sets L
+__global__ void k_cross_l2l32(int64_t ncol, int64_t nbox, int P, int nvec, const zf *tabs, const zf *Lp, zf *Lc)
+{
+    const int np = 2 * P + 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * nvec) return;
+    const int v = idx % nvec, p = (idx / nvec) % np;
+    const int64_t b = idx / (nvec * np), r = b / ncol, c = b % ncol;
+    const int pos = (int)((r & 1) * 2 + (c & 1));
+    const int64_t par = (r / 2) * (ncol / 2) + c / 2;
+    const zf *T = tabs + ((int64_t)pos * np + p) * np;
+    const zf *m = Lp + par * np * LM_MAXV + v;
+    zf acc = {0.f, 0.f};
+    for (int q = 0; q < np; ++q) cfma32(acc, T[q], m[q * LM_MAXV]);
+    Lc[(b * np + p) * LM_MAXV + v] = acc;
+}
+
+// M2L over the cross V list (classes (term, dc, rt, rs)); adds to L, each entry summed on its own
+__global__ void k_cross_m2l32(int64_t nbox, int P, int nvec, const int64_t *vstart, const int32_t *vsrc,
+                              const int32_t *vslot, const zf *tab, const zf *M, zf *Lc)
+{
+    const int np = 2 * P + 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nbox * np * nvec) return;
+    const int v = idx % nvec, p = (idx / nvec) % np;
+    const int64_t b = idx / (nvec * np);
+    zf acc = {0.f, 0.f};
+    for (int64_t e = vstart[b]; e < vstart[b + 1]; ++e) {
+        const zf *T = tab + ((int64_t)vslot[e] * np + p) * np;
+        const zf *m = M + (int64_t)vsrc[e] * np * LM_MAXV + v;
+        zf s = {0.f, 0.f};
+        for (int q = 0; q < np; ++q) cfma32(s, T[q], m[q * LM_MAXV]);
+        acc = acc + s;
+    }
+    Lc[(b * np + p) * LM_MAXV + v] = Lc[(b * np + p) * LM_MAXV + v] + acc;
+}
+
+// L2T in k2 (FP32) and the near g_2^t pairs (kernel values from the FP64 quadrature,
+// multiply-adds in FP32), one thread per target of a leaf
+__global__ void k_cross_leaf32(LeafGeom g, int P, double k2, const double *xt, const double *yt, const int64_t *lt,
+                               const int64_t *ustart, const int32_t *usrc, const double *xs, const double *ysm,
+                               const int64_t *lsrc, CrossNear nq, const zf *Lc, const zd *qs, int64_t ns,
+                               int64_t nt, int nvec, zd *us)
+{
+    const int np = 2 * P + 1;
+    const int64_t b = blockIdx.x;
+    double cx, cy;
+    leaf_centre(g, b, &cx, &cy);
+    const float sc = (float)(k2 * g.w);
+    const zf *Lb = Lc + b * np * LM_MAXV;
+    for (int64_t i = lt[b] + threadIdx.x; i < lt[b + 1]; i += blockDim.x) {
+        const double xi = xt[i], yi = yt[i];
+        zf acc[LM_MAXV];
+        for (int v = 0; v < nvec; ++v) acc[v] = zf{0.f, 0.f};
+        {
+            const float rx = (float)(xi - cx), ry = (float)(yi - cy), r = sqrtf(rx * rx + ry * ry);
+            float J[LM_MAXP + 1];
+            bessel_j_scaled<float>(P, (float)k2 * r, sc, J);
+            const zf z = r > 0.f ? zf{rx / r, ry / r} : zf{1.f, 0.f};
+            zf zp = {1.f, 0.f};
+            for (int v = 0; v < nvec; ++v) cfma32(acc[v], zf{J[0], 0.f}, Lb[P * LM_MAXV + v]);
+            for (int m = 1; m <= P; ++m) {
+                zp = zp * z;
+                const zf bp = J[m] * zp, bn = ((m & 1) ? -J[m] : J[m]) * conj(zp);
+                for (int v = 0; v < nvec; ++v) {
+                    cfma32(acc[v], bp, Lb[(P + m) * LM_MAXV + v]);
+                    cfma32(acc[v], bn, Lb[(P - m) * LM_MAXV + v]);
+                }
+            }
+        }
+        for (int64_t e = ustart[b]; e < ustart[b + 1]; ++e) {
+            const int32_t s = usrc[e];
+            zf part[LM_MAXV]; // one source leaf summed on its own
+            for (int v = 0; v < nvec; ++v) part[v] = zf{0.f, 0.f};
+            for (int64_t j = lsrc[s]; j < lsrc[s + 1]; ++j) {
+                const zd gd = cross_near(nq, k2, fabs(xi - xs[j]), yi, -ysm[j]);
+                const zf gij = {(float)gd.re, (float)gd.im};
+                for (int v = 0; v < nvec; ++v) {
+                    const zd qd = qs[(int64_t)v * ns + j];
+                    cfma32(part[v], gij, zf{(float)qd.re, (float)qd.im});
+                }
+            }
+            for (int v = 0; v < nvec; ++v) acc[v] = acc[v] + part[v];
+        }
+        for (int v = 0; v < nvec; ++v) us[(int64_t)v * nt + i] = zd{acc[v].re, acc[v].im};
     }
 }
 
@@ -549,6 +741,27 @@ static lm_status cross_setup(lm_cross_s *c, const double *xs, const double *ys, 
         lm_set_error("build_cross: an M2L table could not be built at this order");
         return LM_ENOTSUP;
     }
+    if (c->med.opt.precision == LM_MIXED) {
+        for (int l = 0; l <= L; ++l) {
+            CrossLevel &lv = c->lev[l];
+            const int64_t nt2 = (int64_t)std::max(1, lv.ncls) * np * np, ns2 = 4 * np * np;
+            CTRY(calloc_dev(c, &lv.tab32, nt2));
+            CTRY(calloc_dev(c, &lv.M32, (size_t)lv.nbox * np * LM_MAXV));
+            CTRY(calloc_dev(c, &lv.L32, (size_t)lv.nbox * np * LM_MAXV));
+            k_cross_to32<<<gridc(nt2, 256), 256, 0, st>>>(lv.tab, nt2, lv.tab32);
+            lv.m2m32 = lv.l2l32 = nullptr;
+            if (lv.m2m) {
+                CTRY(calloc_dev(c, &lv.m2m32, ns2));
+                k_cross_to32<<<gridc(ns2, 256), 256, 0, st>>>(lv.m2m, ns2, lv.m2m32);
+            }
+            if (lv.l2l) {
+                CTRY(calloc_dev(c, &lv.l2l32, ns2));
+                k_cross_to32<<<gridc(ns2, 256), 256, 0, st>>>(lv.l2l, ns2, lv.l2l32);
+            }
+        }
+        LM_CUDA(cudaGetLastError());
+        LM_CUDA(cudaStreamSynchronize(st));
+    }
     return LM_OK;
 }
 
@@ -567,9 +780,9 @@ extern "C" lm_status lm_build_cross(lm_medium m, const double *xs, const double 
         return LM_EINVAL;
     }
     *out = nullptr;
-    if (m->opt.precision != LM_FP64 || m->opt.kernel != LM_KERNEL_G || m->opt.top_bc != LM_BC_TRANSMISSION ||
+    if (m->opt.kernel != LM_KERNEL_G || m->opt.top_bc != LM_BC_TRANSMISSION ||
         m->opt.bottom_bc != LM_BC_TRANSMISSION) {
-        lm_set_error("build_cross: the cross-layer operator is FP64, kernel G, with transmission interfaces");
+        lm_set_error("build_cross: the cross-layer operator is kernel G, with transmission interfaces");
         return LM_ENOTSUP;
     }
     lm_cross_s *c = new (std::nothrow) lm_cross_s();
@@ -625,6 +838,37 @@ extern "C" lm_status lm_cross_apply(lm_cross c, const void *q, int nvec, void *u
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         k_permute_in<<<gridc(c->ns, 256), 256, 0, st>>>(qd + (int64_t)v0 * c->ns, c->perm_s, c->ns, nv, 0, c->qs);
+        if (c->med.opt.precision == LM_MIXED) {
+            {
+                const CrossLevel &lv = c->lev[L];
+                k_cross_p2m32<<<(unsigned)lv.nbox, 128, 0, st>>>(LeafGeom{lv.ncol, c->x0, lv.w}, P, c->med.k1,
+                                                                  c->xs_s, c->ys_s, c->ls_s, c->qs, c->ns, nv, lv.M32);
+            }
+            for (int l = L - 1; l >= 0; --l) {
+                const CrossLevel &lv = c->lev[l];
+                k_cross_m2m32<<<gridc(lv.nbox * np * nv, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.m2m32,
+                                                                            c->lev[l + 1].M32, lv.M32);
+            }
+            for (int l = 0; l <= L; ++l) {
+                const CrossLevel &lv = c->lev[l];
+                const int64_t tot = lv.nbox * np * nv;
+                if (l == 0)
+                    LM_CUDA(cudaMemsetAsync(lv.L32, 0, lv.nbox * np * LM_MAXV * sizeof(zf), st));
+                else
+                    k_cross_l2l32<<<gridc(tot, 128), 128, 0, st>>>(lv.ncol, lv.nbox, P, nv, lv.l2l32,
+                                                                   c->lev[l - 1].L32, lv.L32);
+                if (lv.nv > 0)
+                    k_cross_m2l32<<<gridc(tot, 128), 128, 0, st>>>(lv.nbox, P, nv, lv.vstart, lv.vsrc, lv.vslot,
+                                                                   lv.tab32, lv.M32, lv.L32);
+            }
+            const CrossLevel &lv = c->lev[L];
+            k_cross_leaf32<<<(unsigned)lv.nbox, 64, 0, st>>>(LeafGeom{lv.ncol, c->x0, lv.w}, P, c->med.k2, c->xs_t,
+                                                             c->ys_t, c->ls_t, c->ustart, c->usrc, c->xs_s, c->ys_s,
+                                                             c->ls_s, nq, lv.L32, c->qs, c->ns, c->nt, nv, c->us);
+            k_permute_out<<<gridc(c->nt, 256), 256, 0, st>>>(c->us, c->perm_t, c->nt, nv, 0, ud + (int64_t)v0 * c->nt);
+            LM_CUDA(cudaGetLastError());
+            continue;
+        }
         {
             const CrossLevel &lv = c->lev[L];
             const size_t shm = (CROSS_P2M_CHUNK * np + CROSS_P2M_CHUNK * LM_MAXV) * sizeof(zd);

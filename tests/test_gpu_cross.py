@@ -64,6 +64,36 @@ def test_cross_rejects_points_on_the_wrong_side(lm):
     m = lm.create_medium(*workloads.MEDIUM_A, p=10)
     with pytest.raises(lm.LMError):
         lm.build_cross(m, xs, ys, xt, yt)
-    mm = lm.create_medium(*workloads.MEDIUM_A, p=10, precision="mixed")
+    mw = lm.create_medium(*workloads.MEDIUM_A, p=10, top_bc="dirichlet")
     with pytest.raises(lm.LMError):
-        lm.build_cross(mm, xs, torch.abs(ys), xt, yt)
+        lm.build_cross(mw, xs, torch.abs(ys), xt, yt)   # the cross operator needs transmission interfaces
+
+
+MIXED = {
+    # name: (medium, p, depth, (ns, nt, x_hi, source band, target band))
+    "uniform": (workloads.MEDIUM_A, 14, 2, (1000, 1200, 3.0, (0.05, 0.95), (0.05, 0.95))),
+    "thin_interface": (workloads.MEDIUM_A, 14, 3, (1000, 1200, 3.0, (0.001, 0.02), (0.001, 0.02))),
+    "k2_8": (workloads.MEDIUM_B, 18, 3, (1000, 1200, 3.0, (0.05, 0.95), (0.05, 0.95))),
+}
+
+
+@pytest.mark.parametrize("name", list(MIXED))
+def test_cross_mixed_matches_oracle(lm, oracle, name):
+    """The mixed form of the cross operator (FP32 expansions, translations and
+    multiply-adds): 1e-6 against the oracle's direct sum, and close to the FP64 form."""
+    import torch
+
+    med, p, depth, shape = MIXED[name]
+    xs, ys, xt, yt, q = _case(*shape, d=med[3], seed=41)
+    pts = [torch.from_numpy(a).cuda() for a in (xs, ys, xt, yt)]
+    c = lm.build_cross(lm.create_medium(*med, p=p, depth=depth, precision="mixed"), *pts)
+    c64 = lm.build_cross(lm.create_medium(*med, p=p, depth=depth), *pts)
+    qd = torch.from_numpy(q).cuda()
+    u = c.apply(qd).cpu().numpy()
+    u64 = c64.apply(qd).cpu().numpy()
+    sub = np.sort(np.random.default_rng(42).choice(xt.size, 48, replace=False))
+    ref = oracle.cross_direct(med, xs, ys, xt, yt, q, targets=sub)
+    err = np.linalg.norm(u[:, sub] - ref) / np.linalg.norm(ref)
+    e64 = np.linalg.norm(u - u64) / np.linalg.norm(u64)
+    print(f"cross mixed {name} p={p}: rel-l2 {err:.2e} against the oracle, {e64:.2e} against the FP64 form")
+    assert err < 1e-6 and e64 < 1e-6
