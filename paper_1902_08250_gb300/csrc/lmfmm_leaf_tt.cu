@@ -40,7 +40,7 @@
 //              each chunk's accumulator; at the end of a pass the lo-part rows
 //              meet their hi-part rows in shared memory and the potentials are
 //              written.
-// Four source stages, two A buffers and two accumulators (2 x 64 columns) let
+// Four source stages, two A buffers and four accumulators (4 x 64 columns) let
 // copies, conversion, kernel values, MMAs and the epilogue of consecutive chunks
 // overlap; every role loads the next leaf's counts while it serves the current
 // one.  Every wait is bounded: a role that gives up sets the CTA's abort word and
@@ -58,7 +58,8 @@
 #define LF_K (2 * LF_CH)
 #define LF_TGT 64                         // target slots per pass
 #define LF_NS 4                           // source stages
-#define LF_NA 2                           // A buffers = accumulators (64 tensor-memory columns each)
+#define LF_NA 2                           // A buffers
+#define LF_ND 4                           // accumulators (64 tensor-memory columns each)
 #define LF_GW 8                           // kernel-value warps
 #define LF_JS 16                          // sources (order slots) per kernel-value thread and chunk
 #define LF_EPI0 (4 + LF_GW)               // first epilogue warp (a multiple of 4)
@@ -91,7 +92,7 @@ struct LfSmem {
     static constexpr int ETAB_OFF = XCH_OFF + 2 * LF_TGT * LF_XS * 4;
     static constexpr int TAB_OFF = ETAB_OFF + 6 * (LF_MAXE + 1) * 4;
     static constexpr int BAR_OFF = (TAB_OFF + LF_MAXT * 5 + 7) / 8 * 8;
-    static constexpr int NBAR = 3 * LF_NS + 4 * LF_NA;
+    static constexpr int NBAR = 3 * LF_NS + 2 * LF_NA + 2 * LF_ND;
     static constexpr int BYTES = BAR_OFF + NBAR * 8 + 16;
 };
 
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
     auto afull = [&](int a) { return b0 + 8u * (3 * LF_NS + a); };
     auto aempty = [&](int a) { return b0 + 8u * (3 * LF_NS + LF_NA + a); };
     auto dfull = [&](int a) { return b0 + 8u * (3 * LF_NS + 2 * LF_NA + a); };
-    auto dempty = [&](int a) { return b0 + 8u * (3 * LF_NS + 3 * LF_NA + a); };
+    auto dempty = [&](int a) { return b0 + 8u * (3 * LF_NS + 2 * LF_NA + LF_ND + a); };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // A buffers start as zeros: rows of empty target slots are read by the MMA
@@ -334,6 +335,8 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
         for (int a = 0; a < LF_NA; ++a) {
             mbar_init(afull(a), LF_GW);
             mbar_init(aempty(a), 1);
+        }
+        for (int a = 0; a < LF_ND; ++a) {
             mbar_init(dfull(a), 1);
             mbar_init(dempty(a), 4);
         }
@@ -577,12 +580,12 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                 const int nch = (cu.T + LF_CH - 1) / LF_CH + 1;
                 for (int i0 = lo; i0 < hi && !stop; i0 += LF_TGT) {
                     for (int c = 0; c < nch; ++c, ++cc) {
-                        const int s = (int)(cc % LF_NS), a = (int)(cc % LF_NA);
-                        const uint32_t pa = (cc / LF_NA) & 1;
+                        const int s = (int)(cc % LF_NS), a = (int)(cc % LF_NA), dn = (int)(cc % LF_ND);
+                        const uint32_t pa = (cc / LF_NA) & 1, pd = (cc / LF_ND) & 1;
                         const int lim = (cc == 0 && first_limit >= 0) ? first_limit : LF_WAIT_LIMIT;
                         if (!lf_wait(bfull(s), (cc / LF_NS) & 1, lim, abort_s, err) ||
                             !lf_wait(afull(a), pa, LF_WAIT_LIMIT, abort_s, err) ||
-                            !lf_wait(dempty(a), pa ^ 1, LF_WAIT_LIMIT, abort_s, err)) {
+                            !lf_wait(dempty(dn), pd ^ 1, LF_WAIT_LIMIT, abort_s, err)) {
                             lf_fail(abort_s, err);
                             stop = true;
                             break;
@@ -592,20 +595,20 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                         // address field (addresses < 256 KB, so the field does not carry)
                         const uint64_t da = adesc0 + (uint64_t)(a * (LF_A_BYTES >> 4));
                         const uint64_t db = bdesc0 + (uint64_t)(s * (LF_B_BYTES >> 4));
-                        const uint32_t dd = tmem + 64u * a;
+                        const uint32_t dd = tmem + 64u * dn;
 #pragma unroll
                         for (int kk = 0; kk < LF_K / 16; ++kk)
                             lf_mma(dd, da + 16u * kk, db + 16u * kk, idesc, kk > 0 ? 1u : 0u);
                         tc_commit(sempty(s));
                         tc_commit(aempty(a));
-                        tc_commit(dfull(a));
+                        tc_commit(dfull(dn));
                         last = (int)cc;
                     }
                 }
             }
             // MMAs in flight complete before the tensor memory is freed
             if (last >= 0)
-                lf_wait(dfull(last % LF_NA), (last / LF_NA) & 1, LF_WAIT_LIMIT, nullptr, nullptr);
+                lf_wait(dfull(last % LF_ND), (last / LF_ND) & 1, LF_WAIT_LIMIT, nullptr, nullptr);
         }
         __syncwarp();
     } else if (warp >= 4 && warp < LF_EPI0) {
@@ -743,8 +746,8 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                 for (int m = 0; m < 32; ++m) acc[m] = 0.f;
                 for (int c = 0; c < nch; ++c, ++cc) {
                     if (bad) continue;
-                    const int a = (int)(cc % LF_NA);
-                    if (!lf_wait(dfull(a), (cc / LF_NA) & 1, LF_WAIT_LIMIT, abort_s, err)) {
+                    const int a = (int)(cc % LF_ND);
+                    if (!lf_wait(dfull(a), (cc / LF_ND) & 1, LF_WAIT_LIMIT, abort_s, err)) {
                         lf_fail(abort_s, err);
                         bad = true;
                         continue;
