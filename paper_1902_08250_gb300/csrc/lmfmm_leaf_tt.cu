@@ -62,6 +62,7 @@
 #define LF_ND 4                           // accumulators (64 tensor-memory columns each)
 #define LF_GW 8                           // kernel-value warps
 #define LF_JS 16                          // sources (order slots) per kernel-value thread and chunk
+#define LF_RB 4                           // of which one round of evaluations takes LF_RB
 #define LF_EPI0 (4 + LF_GW)               // first epilogue warp (a multiple of 4)
 #define LF_THREADS ((LF_EPI0 + 4) * 32)
 #define LF_MAXE 32                        // U entries of a leaf (one per producer lane)
@@ -202,13 +203,13 @@ __device__ __forceinline__ zf lf_h0s(float t)
     return zf{fmaf(wc, im, sh), im};
 }
 
-// L2T basis of the order slots E .. E + 7 (slot P + n <-> order n) for a target at
+// L2T basis of the order slots E .. E + NS - 1 (slot P + n <-> order n) for a target at
 // (x, y) relative to its leaf centre, zeta = (x + i y) / w, t = (k r / 2)^2:
 //   n >= 0: s_n(t) zeta^n,   n < 0: (-1)^|n| s_|n|(t) conj(zeta)^|n|,
 // s_m(t) = sum_j (-t)^j m! / (j! (j + m)!) = J_m(k r) / ((k r / 2)^m / m!), the scaled
 // Bessel function of the local expansion (Eq. (local)), from its ascending series
 // (A&S 9.1.10) by Horner's rule to j = 8 (first dropped term < 2e-14 for t <= 1/2).
-template <int P, int E>
+template <int P, int E, int NS>
 __device__ __forceinline__ void lf_basis(float xs, float ys, float t, zf *gv)
 {
     constexpr int NP = 2 * P + 1;
@@ -217,7 +218,7 @@ __device__ __forceinline__ void lf_basis(float xs, float ys, float t, zf *gv)
 #pragma unroll
     for (int m = 1; m <= P; ++m) pw[m] = pw[m - 1] * zf{xs, ys};
 #pragma unroll
-    for (int ii = 0; ii < 8; ++ii) {
+    for (int ii = 0; ii < NS; ++ii) {
         const int j = E + ii, n = j - P, a = n < 0 ? -n : n;
         if (j >= NP) {
             gv[ii] = zf{0.f, 0.f};
@@ -648,34 +649,34 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                     }
                     unsigned char *A = smem + S::A_OFF + a * LF_A_BYTES;
                     if (act) {
-                        // this thread's LF_JS sources (or order slots) in two rounds of 8
+                        // this thread's LF_JS sources (or order slots) in rounds of LF_RB
 #pragma unroll 1
-                        for (int hb = 0; hb < LF_JS / 8; ++hb) {
-                            const int jb = j0 + 8 * hb;
-                            zf gv[8];
+                        for (int hb = 0; hb < LF_JS / LF_RB; ++hb) {
+                            const int jb = j0 + LF_RB * hb;
+                            zf gv[LF_RB];
                             if (c < nreg) {
                                 // coordinates in units of 2/k, so that t = (k r / 2)^2 = dx^2 + dy^2; slots past
                                 // the chunk's sources hold zeros (finite values; B is zero there)
                                 const LfMeta &m = meta[s];
-                                float tv[8];
+                                float tv[LF_RB];
                                 bool special = false;
 #pragma unroll
-                                for (int ii = 0; ii < 8; ++ii) {
+                                for (int ii = 0; ii < LF_RB; ++ii) {
                                     const float4 r4 = m.src[jb + ii];
                                     const float dx = xk - r4.x, dy = yk - r4.y;
                                     tv[ii] = fmaf(dx, dx, dy * dy);
                                     special |= ((__float_as_int(r4.w) & 3) != 0) | (!DEG && tv[ii] > 1.0f);
                                 }
 #pragma unroll
-                                for (int ii = 0; ii < 8; ++ii) gv[ii] = lf_h0s<DEG ? DEG : 8>(tv[ii]);
+                                for (int ii = 0; ii < LF_RB; ++ii) gv[ii] = lf_h0s<DEG ? DEG : 8>(tv[ii]);
                                 if (!special) {
                                     // t = 0: the self pair (and points that coincide) is left out
 #pragma unroll
-                                    for (int ii = 0; ii < 8; ++ii)
+                                    for (int ii = 0; ii < LF_RB; ++ii)
                                         if (tv[ii] == 0.f) gv[ii] = zf{0.f, 0.f};
                                 } else {
 #pragma unroll
-                                    for (int ii = 0; ii < 8; ++ii) {
+                                    for (int ii = 0; ii < LF_RB; ++ii) {
                                         const float4 r4 = m.src[jb + ii]; // read again: the rare path
                                         const int term = __float_as_int(r4.w) & 3;
                                         if (term != 0) { // tail of a reflected direct term
@@ -692,22 +693,28 @@ __global__ void __launch_bounds__(LF_THREADS, 1)
                                     }
                                 }
                             } else {
-                                // the L2T chunk: order slots jb .. jb + 7 (a compile-time set per case)
+                                // the L2T chunk: order slots jb .. jb + LF_RB - 1 (a compile-time set per case)
                                 const float xs = xi / w, ys = yi / w, tt = fmaf(xk, xk, yk * yk);
-                                switch (jb >> 3) {
-                                case 0: lf_basis<P, 0>(xs, ys, tt, gv); break;
-                                case 1: lf_basis<P, 8>(xs, ys, tt, gv); break;
-                                case 2: lf_basis<P, 16>(xs, ys, tt, gv); break;
-                                case 3: lf_basis<P, 24>(xs, ys, tt, gv); break;
+                                switch (jb / LF_RB) {
+                                case 0: lf_basis<P, 0, LF_RB>(xs, ys, tt, gv); break;
+                                case 1: lf_basis<P, LF_RB, LF_RB>(xs, ys, tt, gv); break;
+                                case 2: lf_basis<P, 2 * LF_RB, LF_RB>(xs, ys, tt, gv); break;
+                                case 3: lf_basis<P, 3 * LF_RB, LF_RB>(xs, ys, tt, gv); break;
+#if LF_RB == 4
+                                case 4: lf_basis<P, 16, 4>(xs, ys, tt, gv); break;
+                                case 5: lf_basis<P, 20, 4>(xs, ys, tt, gv); break;
+                                case 6: lf_basis<P, 24, 4>(xs, ys, tt, gv); break;
+                                case 7: lf_basis<P, 28, 4>(xs, ys, tt, gv); break;
+#endif
                                 default: // slots past 2 P + 1 <= 29 hold zeros
 #pragma unroll
-                                    for (int ii = 0; ii < 8; ++ii) gv[ii] = zf{0.f, 0.f};
+                                    for (int ii = 0; ii < LF_RB; ++ii) gv[ii] = zf{0.f, 0.f};
                                     break;
                                 }
                             }
                             // hi and lo rows of this target slot: one 16-byte store per 4 sources and part
 #pragma unroll
-                            for (int m4 = 0; m4 < 2; ++m4) {
+                            for (int m4 = 0; m4 < LF_RB / 4; ++m4) {
                                 uint32_t h[4], l[4];
 #pragma unroll
                                 for (int jj = 0; jj < 4; ++jj)
