@@ -486,6 +486,127 @@ __global__ void k_p2m32(G geo, int P, float k, const float *xl, const float *yl,
     }
 }
 
+// S2M of the 16 vector slots (Eq. (multipole_coef), scaled) on the leaves of a
+// uniform tree with k w <= 2: one warp per leaf, no recurrence.  Lane j forms
+// the basis row of point j of a chunk of 32 from the ascending series of the
+// scaled Bessel function (A&S 9.1.10 by Horner's rule to 8 terms; points lie
+// within w/sqrt(2) of the centre, so t = (k r / 2)^2 <= 1/2 and the first
+// dropped term is below 2e-14).  The lanes then own 2 orders x 4 vectors each.
+// Orders m and -m share their products: with b = a + i c the basis value of
+// order m >= 0 and q = x + i y a density, b q and conj(b) q follow from the
+// four sums of a x, c y, a y and c x, and the basis of order -m is
+// (-1)^m conj(b).
+#define S2M16_NB 16 // orders 0 .. 15 per basis row (P <= 15)
+#define S2M16_RS 18 // basis row stride in complex entries (144 bytes: 16-byte aligned rows)
+template <int P>
+__global__ void __launch_bounds__(128) k_s2m16(int64_t nbox, float w, float k, const float *xl, const float *yl,
+                                               const int64_t *ls, const zf *qs, zf *M)
+{
+    static_assert(P < S2M16_NB, "basis rows hold orders 0 .. 15");
+    constexpr int NP = 2 * P + 1;
+    __shared__ __align__(16) zf Bs[4][32 * S2M16_RS];
+    __shared__ __align__(16) float4 Qs[4][32 * LM_MAXV / 2];
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = blockIdx.x * 4LL + wp;
+    if (b >= nbox) return; // the warps of a block share no barrier
+    const int64_t lo = ls[b], hi = ls[b + 1];
+    const int og = lane >> 2, vg = lane & 3; // orders 2 og, 2 og + 1; vectors 4 vg .. 4 vg + 3
+    zf *B = Bs[wp];
+    float4 *Q = Qs[wp];
+    const float iw = 1.0f / w, hk2 = 0.25f * k * k;
+    float acc[2][4][4];
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+#pragma unroll
+            for (int s = 0; s < 4; ++s) acc[o][v][s] = 0.f;
+    for (int64_t base = lo; base < hi; base += 32) {
+        const int cnt = (int)min((int64_t)32, hi - base);
+        __syncwarp();
+        {
+            zf *row = B + lane * S2M16_RS;
+            float rx = 0.f, ry = 0.f;
+            if (lane < cnt) {
+                rx = xl[base + lane];
+                ry = yl[base + lane];
+            }
+            const float t = hk2 * fmaf(rx, rx, ry * ry);
+            const zf z = {rx * iw, -ry * iw};
+            zf pw = {lane < cnt ? 1.0f : 0.0f, 0.f};
+#pragma unroll
+            for (int m = 0; m < S2M16_NB; ++m) {
+                if (m <= P) {
+                    float sv = 1.0f;
+#pragma unroll
+                    for (int q = 8; q >= 1; --q) sv = fmaf(-t * (1.0f / (float)(q * (q + m))), sv, 1.0f);
+                    row[m] = sv * pw;
+                    pw = pw * z;
+                } else {
+                    row[m] = zf{0.f, 0.f};
+                }
+            }
+        }
+        const float4 *src = (const float4 *)(qs + base * LM_MAXV);
+#pragma unroll
+        for (int r = 0; r < LM_MAXV / 2; ++r) {
+            const int e = lane + 32 * r;
+            Q[e] = (e / (LM_MAXV / 2)) < cnt ? src[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        for (int p = 0; p < cnt; ++p) {
+            const float4 bb = *(const float4 *)(B + p * S2M16_RS + 2 * og);
+            const float4 q0 = Q[p * (LM_MAXV / 2) + 2 * vg], q1 = Q[p * (LM_MAXV / 2) + 2 * vg + 1];
+            const float br[2] = {bb.x, bb.z}, bi[2] = {bb.y, bb.w};
+            const float qr[4] = {q0.x, q0.z, q1.x, q1.z}, qi[4] = {q0.y, q0.w, q1.y, q1.w};
+#pragma unroll
+            for (int o = 0; o < 2; ++o)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    acc[o][v][0] = fmaf(br[o], qr[v], acc[o][v][0]);
+                    acc[o][v][1] = fmaf(bi[o], qi[v], acc[o][v][1]);
+                    acc[o][v][2] = fmaf(br[o], qi[v], acc[o][v][2]);
+                    acc[o][v][3] = fmaf(bi[o], qr[v], acc[o][v][3]);
+                }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+        const int m = 2 * og + o;
+        if (m > P) continue;
+        float4 pos[2], neg[2];
+        const float sg = (m & 1) ? -1.0f : 1.0f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float *a0 = acc[o][2 * h], *a1 = acc[o][2 * h + 1];
+            pos[h] = make_float4(a0[0] - a0[1], a0[2] + a0[3], a1[0] - a1[1], a1[2] + a1[3]);
+            neg[h] = make_float4(sg * (a0[0] + a0[1]), sg * (a0[2] - a0[3]), sg * (a1[0] + a1[1]),
+                                 sg * (a1[2] - a1[3]));
+        }
+        float4 *dp = (float4 *)(M + (b * NP + P + m) * LM_MAXV + 4 * vg);
+        dp[0] = pos[0];
+        dp[1] = pos[1];
+        if (m > 0) {
+            float4 *dn = (float4 *)(M + (b * NP + P - m) * LM_MAXV + 4 * vg);
+            dn[0] = neg[0];
+            dn[1] = neg[1];
+        }
+    }
+}
+
+// the series S2M on the leaf level (16 vector slots, P <= 15, k w <= 2)
+template <int P>
+static void launch_s2m16(const Level &lv, float k, const lm_tree_s *t, cudaStream_t st)
+{
+    if constexpr (P < S2M16_NB)
+        k_s2m16<P><<<(unsigned)((lv.nbox + 3) / 4), 128, 0, st>>>(lv.nbox, (float)lv.w, k, t->xl32, t->yl32,
+                                                                  t->leaf_start, t->qs32, lv.M32);
+}
+static bool s2m16_ok(const lm_tree_s *t, int nvs)
+{
+    return nvs == LM_MAXV && t->p < S2M16_NB && (double)(float)t->med.k2 * t->lev[t->L].w <= 2.0;
+}
+
 // Free-space M2L over the fixed 27-offset stencil of the V list (levels >= 1).
 // Boxes of one parity class share their offsets.  A block takes 16 boxes of
 // one class; its threads form (row group of 4 orders) x (box, 4 vectors)
@@ -1398,9 +1519,13 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
         lm_phase_begin(t, PH_S2M, st);
         {
             Level &lv = t->lev[L];
-            size_t shm = (P2M32_CHUNK * np + P2M32_CHUNK * LM_MAXV) * sizeof(zf);
-            k_p2m32<<<(unsigned)lv.nbox, 128, shm, st>>>(Grid32{lv.ncol, (float)lv.w}, P, k, t->xl32, t->yl32, t->leaf_start,
-                                                         t->qs32, nvs, lv.M32);
+            if (s2m16_ok(t, nvs)) {
+                MX_DISPATCH(P, launch_s2m16, lv, k, t, st);
+            } else {
+                size_t shm = (P2M32_CHUNK * np + P2M32_CHUNK * LM_MAXV) * sizeof(zf);
+                k_p2m32<<<(unsigned)lv.nbox, 128, shm, st>>>(Grid32{lv.ncol, (float)lv.w}, P, k, t->xl32, t->yl32,
+                                                             t->leaf_start, t->qs32, nvs, lv.M32);
+            }
         }
         lm_phase_end(t, PH_S2M, st, 1);
         if (L > 0) lm_phase_begin(t, PH_M2M, st);
