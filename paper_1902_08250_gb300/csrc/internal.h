@@ -196,9 +196,12 @@ struct lm_tree_s {
     int64_t tt_ntile[2], tt_nent[2];
     void *tt_tiles[2], *tt_ents[2]; // device TtTile[tt_ntile], TtEnt[tt_nent]
     void *tt_lv[2];             // device level descriptors (TtLevel[L + 1]) of each form
-    float *tt_tab;              // [classes of all levels][128 rows][64 K] TF32 hi/lo tables, canonical layout
-    float *tt_msplit;           // [boxes of all levels + 1][2048] TF32 hi/lo multipoles (the 4-vector form
-                                // packs 512 floats per box in the same buffer), canonical layout
+    float *tt_tab;              // [classes of all levels][128 rows][64 K] FP16 hi/lo tables, canonical layout
+                                // (4096 words per class)
+    float *tt_msplit;           // [boxes of all levels + 1][1024 words] FP16 hi/lo multipoles (the 4-vector
+                                // form packs 256 words per box in the same buffer), canonical layout
+    uint32_t *tt_tmax;          // per level: largest component of its tables (float bits)
+    uint32_t *tt_mmax;          // per level: largest multipole component of the apply (float bits)
     std::vector<int64_t> tt_tbase, tt_mbase; // per level: first table, first box
     int tt_grid;                // persistent CTAs (one per SM)
     int tt_poll_limit;          // polls of the first operand wait (-1: the library default)

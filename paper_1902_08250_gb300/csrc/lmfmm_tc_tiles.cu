@@ -1,6 +1,7 @@
 // lmfmm_tc_tiles.cu -- the M2L of every level, free space and the four image
 // terms of Lemma M2L (Sec. 2.1), on the 5th-generation tensor cores (tcgen05,
-// kind::tf32) as one persistent launch, for applies of 16 density vectors.
+// kind::f16 with FP32 accumulation) as one persistent launch, for applies of
+// 16 density vectors (and, in the batched form, of 4).
 //
 // Work is cut into tiles of 8 target boxes that lie in one row of one level,
 // in steps of 2 columns (one parity class; level 0: consecutive roots).  For
@@ -8,36 +9,45 @@
 // dc, source row) item, with a mask of the boxes that have it.  The 8 boxes'
 // sources of an item lie in one row, dc columns to the left of their targets.
 //
-// One item is one MMA chain in real-block form:
-//     D[128 x 256] = A[128 x 64] . B[256 x 64]^T,
-//   A rows 0..63   the table's TF32 hi part, rows 64..127 its lo part (real-block
+// One item adds one product in real-block form:
+//     D[128 x 256] += A[128 x 64] . B[256 x 64]^T,
+//   A rows 0..63   the table's FP16 hi part, rows 64..127 its lo part (real-block
 //                  rows [Re L_p; Im L_p], 2(2p+1) <= 64, zero-padded),
 //   B rows         8 boxes x (16 vectors of the multipoles' hi part, 16 of the
 //                  lo part), K = 64 real input orders (zero-padded).
 // So D holds hi*hi + hi*lo in rows 0..63 and lo*hi + lo*lo in rows 64..127,
-// every product of the TF32 split; the four sums per output are added in
-// registers.  Tables are split once at set-up, multipoles once per apply by
-// k_msplit, both into the canonical K-major layout the MMA reads (8-row x
-// 16-byte core matrices, K-adjacent ones 128 B apart, 8-row groups 2 KB apart),
-// so staging an item is 9 plain bulk copies (32 KB table + 8 x 8 KB boxes) and
-// no thread touches operand data.  M = 128 and N = 256 keep the shared-memory
-// operand reads at 96 B per tensor-core clock.
+// every product of the split; the four sums per output are added in registers.
+// FP16 hi/lo keeps 22 significant bits, as TF32 hi/lo did, in half the bytes.
+// Its range is met by powers of two: the tables of each level are scaled so
+// that their largest component lies in [2^14, 2^15) (found at set-up by
+// k_tmax), the multipoles of each level the same way (found per apply by
+// k_mmax); the epilogue multiplies the sums by the inverse of the two scales,
+// which is exact.  Components below 2^-24 of the largest one of their level
+// fall into FP16's subnormal range: their absolute error stays below 2^-39 of
+// that largest component.
+// Tables are split once at set-up, multipoles once per apply by k_msplit, both
+// into the canonical K-major layout the MMA reads (8-row x 16-byte core
+// matrices, K-adjacent ones 128 B apart, 8-row groups 1 KB apart), so staging
+// an item is 9 plain bulk copies (16 KB table + 8 x 4 KB boxes) and no thread
+// touches operand data.
 //
 // Roles (10 warps, one CTA per SM, persistent over tiles):
 //   warp 8  producer: loads 32 entries at a time across its lanes; lane 0
 //           waits for a free stage and issues the bulk copies, which complete
 //           on the stage's `full` barrier;
-//   warp 9  MMA issuer: waits for the stage and for a free accumulator, issues
-//           the 8 MMAs, commits them to the stage's `empty` and the
-//           accumulator's `tfull` barrier;
+//   warp 9  MMA issuer: takes a tile's items in groups of up to TT_G = 8, all
+//           of one group into one accumulator: waits for a free accumulator,
+//           then per item for its stage, issues the 4 MMAs and commits them to
+//           the stage's `empty` barrier; at the end of a group it commits to
+//           the accumulator's `tfull` barrier;
 //   warps 0-7 epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 of
-//           boxes 4 (w / 4) .. + 3, adds each item's D into registers (each
-//           entry summed on its own, blocked accumulation), and frees the
-//           accumulator.  At the end of a tile the lo-part rows go through
+//           boxes 4 (w / 4) .. + 3 once per group, adds it into registers
+//           (blocked accumulation: groups of 8 entries summed on their own),
+//           and frees the accumulator.  At the end of a tile the lo-part rows go through
 //           shared memory to their hi-part rows, and the tile's local
 //           expansions are written, coalesced, over L (this launch sets L;
 //           L2L adds to it afterwards).
-// Two shared-memory stages and two tensor-memory accumulators (2 x 256
+// Four shared-memory stages and two tensor-memory accumulators (2 x 256
 // columns) let copies, MMAs and the epilogue of consecutive items overlap.
 // Every wait is bounded; a role that gives up sets the CTA's abort word and
 // the launch's error flag, the others stop at their next wait, copies and
@@ -51,11 +61,17 @@
 #include "internal.h"
 #include "tc_common.cuh"
 
+#include <cuda_fp16.h>
+
 #define TT_K 64                                      // real input orders per item (zero-padded)
-#define TT_TAB_FLOATS (128 * TT_K)                   // one split table: 64 hi + 64 lo rows
-#define TT_STAGE_TAB (TT_TAB_FLOATS * 4)             // 32 KB
-#define TT_STAGE (TT_STAGE_TAB + 256 * TT_K * 4)     // 96 KB: the table and 256 operand rows
-#define TT_NSTAGE 2
+#define TT_ROW (TT_K * 2)                            // bytes of one FP16 operand row
+#define TT_TAB_FLOATS (128 * TT_ROW / 4)             // one split table (64 hi + 64 lo rows), in 4-byte words
+#define TT_STAGE_TAB (TT_TAB_FLOATS * 4)             // 16 KB
+#define TT_STAGE (TT_STAGE_TAB + 256 * TT_ROW)       // 48 KB: the table and 256 operand rows
+#define TT_NSTAGE 4
+#define TT_NBAR (2 * TT_NSTAGE + 4)                  // full / empty per stage, tfull / tempty per accumulator
+#define TT_SMAX 14                                   // largest component scaled into [2^14, 2^15)
+#define TT_G 4                                       // items of one tile summed in one accumulator
 #define TT_EPI_WARPS 8
 #define TT_THREADS ((TT_EPI_WARPS + 2) * 32)         // + producer + MMA warp
 #define TT_MAXLEV 16
@@ -65,7 +81,7 @@
 template <int NV>
 struct TtShape {
     static constexpr int TB = 128 / NV;              // boxes per tile
-    static constexpr int BOX_FLOATS = 2 * NV * TT_K; // one split box
+    static constexpr int BOX_FLOATS = 2 * NV * TT_ROW / 4; // one split box, in 4-byte words
     static constexpr int CB_STRIDE = 2 * NV + 1;     // floats per (box, order) row of the combine buffer
     static constexpr int BPL = 32 / (2 * NV);        // boxes per 32-column tensor-memory load
 };
@@ -85,6 +101,8 @@ struct TtLevel {
     zf *L;             // local expansions [nbox][NP][16]
     const float *tab;  // the level's first split table
     float *ms;         // the level's first split box
+    const uint32_t *tmax; // the largest component of the level's tables (float bits)
+    uint32_t *mmax;       // the level's largest multipole component (float bits), per apply
 };
 
 template <int NP, int NV>
@@ -92,79 +110,180 @@ struct TtSmem {
     static constexpr int CB_OFF = TT_NSTAGE * TT_STAGE;
     static constexpr int CB_BYTES = (TtShape<NV>::TB * NP * TtShape<NV>::CB_STRIDE * 4 + 15) / 16 * 16;
     static constexpr int BAR_OFF = CB_OFF + CB_BYTES;
-    static constexpr int BYTES = BAR_OFF + 8 * 8 + 16;
+    static constexpr int BYTES = BAR_OFF + TT_NBAR * 8 + 16;
 };
 
-// TF32 split: hi rounded to nearest (11 significant bits), lo = x - hi (exact in
-// FP32) rounded the same way, so the tensor core reads both exactly
-__device__ __forceinline__ void tt_split(float x, float &hi, float &lo)
+// byte offset of element (row, k) of a K-major no-swizzle FP16 operand with K = 64:
+// 8-row x 16-byte core matrices, K-adjacent ones 128 B apart, 8-row groups 1 KB apart
+__host__ __device__ __forceinline__ uint32_t tt_off(int row, int k)
 {
-    hi = tf32_rna(x);
-    lo = tf32_rna(__fsub_rn(x, hi));
+    return (uint32_t)((row >> 3) * (8 * TT_ROW) + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+__device__ __forceinline__ uint64_t tt_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)(128 >> 4) << 16;           // LBO: K-direction core-matrix stride
+    d |= (uint64_t)((8 * TT_ROW) >> 4) << 32;  // SBO: 8-row-group stride
+    d |= (uint64_t)1 << 46;
+    return d;
+}
+// instruction descriptor of kind::f16: D = F32, A = B = F16, both K-major, M x N
+__host__ __device__ constexpr uint32_t tt_idesc(int m, int n)
+{
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void tt_mma(uint32_t dtmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+// power-of-two scale exponent that puts the largest component (float bits) in
+// [2^14, 2^15); kept within [-126, 126] so that the scale and its inverse are normal
+__host__ __device__ __forceinline__ int tt_scale_exp(uint32_t mxbits)
+{
+    const int e = mxbits ? (int)((mxbits >> 23) & 0xff) - 127 : 0;
+    const int es = TT_SMAX - e;
+    return es < -126 ? -126 : (es > 126 ? 126 : es);
+}
+__device__ __forceinline__ float tt_pow2(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+// position of box (r, c) in a level's split-multipole buffer: within each row the
+// even columns, then the odd ones (levels >= 1, cstride 2), so that the sources of a
+// tile's boxes at one entry are consecutive; level 0 (cstride 1) keeps the box order
+__host__ __device__ __forceinline__ int64_t tt_pos(int64_t r, int64_t c, int64_t ncol, int cstride)
+{
+    return cstride == 2 ? r * ncol + (c & 1) * (ncol >> 1) + (c >> 1) : r * ncol + c;
+}
+// x -> FP16 hi (nearest) and lo = x - hi (nearest), packed two by two
+__device__ __forceinline__ void tt_split2(float a, float b, uint32_t &hi, uint32_t &lo)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi = *(const uint32_t *)&h;
+    lo = *(const uint32_t *)&l;
 }
 
 // ---------------------------------------------------------------------------
 // operand preparation
 // ---------------------------------------------------------------------------
+// The largest real or imaginary part over all table classes of one level, as
+// float bits by atomicMax into the level's word (zeroed before).  One block per class.
+__global__ void k_tmax(const zd *tab, int ncls, int NP, uint32_t *tmax)
+{
+    __shared__ uint32_t red[8];
+    const int64_t cls = blockIdx.x;
+    uint32_t m = 0;
+    for (int i = threadIdx.x; i < NP * NP; i += blockDim.x) {
+        const zd a = tab[cls * NP * NP + i];
+        m = max(m, __float_as_uint(fmaxf(fabsf((float)a.re), fabsf((float)a.im))));
+    }
+    m = __reduce_max_sync(0xffffffffu, m); // non-negative floats: bits order as values
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t mm = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = max(mm, red[w]);
+        if (mm) atomicMax(tmax, mm);
+    }
+}
 // Tables of one level -> real-block A operands: row r < NP is Re L_r with
 // (Re T, -Im T) at K = 2q, 2q + 1; row NP + r is Im L_r with (Im T, Re T).
-// hi part in rows 0..63, lo part (T - hi, split again) in rows 64..127.
-// One thread per (class, row 0..63, K chunk of 4).
-__global__ void k_tsplit(const zd *tab, int ncls, int NP, float *out)
+// Scaled by the level's power of two, hi part in rows 0..63, lo part (the
+// remainder, in FP64, rounded) in rows 64..127.  One thread per (class,
+// row 0..63, K chunk of 8).
+__global__ void k_tsplit(const zd *tab, int ncls, int NP, const uint32_t *tmax, float *out)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)ncls * 64 * 16) return;
-    const int c = (int)(t & 15), r = (int)((t >> 4) & 63);
-    const int64_t cls = t >> 10;
-    float hv[4], lv[4];
+    if (t >= (int64_t)ncls * 64 * 8) return;
+    const int c = (int)(t & 7), r = (int)((t >> 3) & 63);
+    const int64_t cls = t >> 9;
+    const double sc = (double)tt_pow2(tt_scale_exp(*tmax));
+    uint32_t hv[4], lv[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const int k = 4 * c + i, q = k >> 1, im = k & 1;
-        double v = 0.0;
-        if (r < 2 * NP && q < NP) {
-            const int p = r < NP ? r : r - NP;
-            const zd a = tab[(cls * NP + p) * NP + q];
-            v = r < NP ? (im ? -a.im : a.re) : (im ? a.re : a.im);
+        double v2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int k = 8 * c + 2 * i + h, q = k >> 1, im = k & 1;
+            double v = 0.0;
+            if (r < 2 * NP && q < NP) {
+                const int p = r < NP ? r : r - NP;
+                const zd a = tab[(cls * NP + p) * NP + q];
+                v = r < NP ? (im ? -a.im : a.re) : (im ? a.re : a.im);
+            }
+            v2[h] = v * sc;
         }
-        hv[i] = tf32_rna((float)v);
-        lv[i] = tf32_rna((float)(v - (double)hv[i]));
+        const __half2 hh = __floats2half2_rn((float)v2[0], (float)v2[1]);
+        const float2 hf = __half22float2(hh);
+        const __half2 ll = __floats2half2_rn((float)(v2[0] - (double)hf.x), (float)(v2[1] - (double)hf.y));
+        hv[i] = *(const uint32_t *)&hh;
+        lv[i] = *(const uint32_t *)&ll;
     }
-    float *o = out + cls * TT_TAB_FLOATS;
-    *(float4 *)(o + tc_off(r, 4 * c) / 4) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-    *(float4 *)(o + tc_off(64 + r, 4 * c) / 4) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+    unsigned char *o = (unsigned char *)(out + cls * TT_TAB_FLOATS);
+    *(uint4 *)(o + tt_off(r, 8 * c)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    *(uint4 *)(o + tt_off(64 + r, 8 * c)) = make_uint4(lv[0], lv[1], lv[2], lv[3]);
+}
+
+// The largest multipole component of each level (the first NV vector slots), as
+// float bits by atomicMax into the level's word (zeroed before).  Grid (chunks,
+// levels): block (x, l) reads part of level l's multipoles, 16 bytes per thread
+// and step, and adds one atomic.
+template <int NP, int NV>
+__global__ void __launch_bounds__(256) k_mmax(const TtLevel *lv, int nlev, int64_t ntot)
+{
+    __shared__ uint32_t red[8];
+    const int l = blockIdx.y;
+    const int64_t nb = (l + 1 < nlev ? lv[l + 1].mstart : ntot) - lv[l].mstart;
+    const int64_t n = nb * NP * (NV / 2);
+    const zf *M = lv[l].M;
+    uint32_t m = 0;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t bq = t / (NV / 2); // box * NP + order
+        const int v2 = (int)(t % (NV / 2));
+        const float4 x = *(const float4 *)(M + bq * LM_MAXV + 2 * v2);
+        m = max(m, max(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(x.y) & 0x7fffffffu),
+                       max(__float_as_uint(x.z) & 0x7fffffffu, __float_as_uint(x.w) & 0x7fffffffu)));
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t mm = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = max(mm, red[w]);
+        if (mm) atomicMax(lv[l].mmax, mm);
+    }
 }
 
 // Multipoles of every level of one tree -> B operands, one block of 2 NV rows per
 // box: [hi v0..NV-1 | lo v0..NV-1] x 64 K in the canonical layout (8-row groups of
-// 2 KB).  One thread per (box, K chunk of 4 = orders 2c, 2c + 1, vector).
+// 1 KB), scaled by the level's power of two.  One thread per (box, K chunk of 8 =
+// orders 4c .. 4c + 3, vector).
 template <int NP, int NV>
 __global__ void k_msplit(const TtLevel *lv, int nlev, int64_t ntot)
 {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= ntot * 16 * NV) return;
-    const int v = (int)(t % NV), c = (int)((t / NV) & 15);
-    const int64_t gb = t / (16 * NV);
+    if (t >= ntot * 8 * NV) return;
+    const int v = (int)(t % NV), c = (int)((t / NV) & 7);
+    const int64_t gb = t / (8 * NV);
     int l = 0;
     while (l + 1 < nlev && gb >= lv[l + 1].mstart) ++l;
     const int64_t b = gb - lv[l].mstart;
+    const float sc = tt_pow2(tt_scale_exp(*lv[l].mmax));
     const zf *m = lv[l].M + b * NP * LM_MAXV + v;
-    float x[4];
+    uint32_t hv[4], lo[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int q = 2 * c + h;
+    for (int h = 0; h < 4; ++h) {
+        const int q = 4 * c + h;
         const zf z = q < NP ? m[q * LM_MAXV] : zf{0.f, 0.f};
-        x[2 * h] = z.re;
-        x[2 * h + 1] = z.im;
+        tt_split2(z.re * sc, z.im * sc, hv[h], lo[h]);
     }
-    float4 hi, lo;
-    tt_split(x[0], hi.x, lo.x);
-    tt_split(x[1], hi.y, lo.y);
-    tt_split(x[2], hi.z, lo.z);
-    tt_split(x[3], hi.w, lo.w);
-    float *o = lv[l].ms + b * TtShape<NV>::BOX_FLOATS;
-    const int rh = v, rl = NV + v; // operand rows of the hi and lo parts
-    *(float4 *)(o + (rh >> 3) * 512 + c * 32 + (rh & 7) * 4) = hi;
-    *(float4 *)(o + (rl >> 3) * 512 + c * 32 + (rl & 7) * 4) = lo;
+    const int64_t ncol = lv[l].ncol;
+    unsigned char *o =
+        (unsigned char *)(lv[l].ms + tt_pos(b / ncol, b % ncol, ncol, l == 0 ? 1 : 2) * TtShape<NV>::BOX_FLOATS);
+    *(uint4 *)(o + tt_off(v, 8 * c)) = make_uint4(hv[0], hv[1], hv[2], hv[3]);
+    *(uint4 *)(o + tt_off(NV + v, 8 * c)) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -188,17 +307,20 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
     extern __shared__ __align__(1024) unsigned char smem[];
     float *cb = (float *)(smem + S::CB_OFF);
     uint64_t *bars = (uint64_t *)(smem + S::BAR_OFF);
-    uint32_t *tslot = (uint32_t *)(bars + 8);
+    uint32_t *tslot = (uint32_t *)(bars + TT_NBAR);
     volatile int *abort_s = (volatile int *)(tslot + 1);
     volatile int *stop_s = abort_s + 1;
     const uint32_t sbase = smem_u32(smem);
-    const uint32_t bfull = smem_u32(bars), bempty = bfull + 16, btfull = bfull + 32, btempty = bfull + 48;
+    const uint32_t bfull = smem_u32(bars), bempty = bfull + 8 * TT_NSTAGE, btfull = bfull + 16 * TT_NSTAGE,
+                   btempty = btfull + 16;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < TT_NSTAGE; ++i) {
             mbar_init(bfull + 8 * i, 1);
             mbar_init(bempty + 8 * i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(btfull + 8 * i, 1);
             mbar_init(btempty + 8 * i, TT_EPI_WARPS);
         }
@@ -220,7 +342,9 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         // ---- producer: the warp loads 32 entries at a time (one per lane, in parallel) and
         // lane 0 takes them by shuffle, waits for stages and issues the copies ----
         uint32_t it = 0;
-        int last[2] = {-1, -1}; // last item copied into each stage (lane 0)
+        int last[TT_NSTAGE]; // last item copied into each stage (lane 0)
+#pragma unroll
+        for (int s = 0; s < TT_NSTAGE; ++s) last[s] = -1;
         bool stop = false;
         for (int tile = blockIdx.x; tile < ntiles && !stop; tile += gridDim.x) {
             const TtTile T = tiles[tile];
@@ -234,18 +358,28 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
                     const TtEnt E = {__shfl_sync(0xffffffffu, mine.slot, i), __shfl_sync(0xffffffffu, mine.dc, i),
                                      __shfl_sync(0xffffffffu, mine.rs, i), __shfl_sync(0xffffffffu, mine.mask, i)};
                     if (lane == 0) {
-                        const int s = it & 1;
-                        if (!mbar_wait_lim(bempty + 8 * s, ((it >> 1) & 1) ^ 1, TC_WAIT_LIMIT, abort_s, err)) {
+                        const int s = (int)(it % TT_NSTAGE);
+                        if (!mbar_wait_lim(bempty + 8 * s, ((it / TT_NSTAGE) & 1) ^ 1, TC_WAIT_LIMIT, abort_s, err)) {
                             tt_fail(abort_s, err);
                         } else {
                             const uint32_t st = sbase + s * TT_STAGE, fb = bfull + 8 * s;
                             mbar_expect_tx(fb, TT_STAGE);
                             bulk_g2s(st, tb + (int64_t)E.slot * TT_TAB_FLOATS, TT_STAGE_TAB, fb);
+                            const uint32_t full = T.nbox >= 32 ? 0xffffffffu : (1u << T.nbox) - 1u;
+                            int j0 = 0;
+                            if (E.mask == full) {
+                                // every box of the tile has the entry: its sources are consecutive
+                                // in the buffer, one copy
+                                const float *src =
+                                    ms + tt_pos(E.rs, T.c0 - E.dc, ncol, T.cstride) * Sh::BOX_FLOATS;
+                                bulk_g2s(st + TT_STAGE_TAB, src, T.nbox * Sh::BOX_FLOATS * 4, fb);
+                                j0 = T.nbox;
+                            }
 #pragma unroll 1
-                            for (int j = 0; j < Sh::TB; ++j) {
+                            for (int j = j0; j < Sh::TB; ++j) {
                                 const float *src = zero_box;
                                 if (j < T.nbox && ((E.mask >> j) & 1u))
-                                    src = ms + ((int64_t)E.rs * ncol + T.c0 + (int64_t)j * T.cstride - E.dc) *
+                                    src = ms + tt_pos(E.rs, T.c0 + (int64_t)j * T.cstride - E.dc, ncol, T.cstride) *
                                                    Sh::BOX_FLOATS;
                                 bulk_g2s(st + TT_STAGE_TAB + j * Sh::BOX_FLOATS * 4, src, Sh::BOX_FLOATS * 4, fb);
                             }
@@ -259,39 +393,57 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         }
         // copies in flight land before the CTA's shared memory is released
         if (lane == 0)
-            for (int s = 0; s < 2; ++s)
-                if (last[s] >= 0) mbar_wait_lim(bfull + 8 * s, (last[s] >> 1) & 1, TC_WAIT_LIMIT, nullptr, nullptr);
+            for (int s = 0; s < TT_NSTAGE; ++s)
+                if (last[s] >= 0)
+                    mbar_wait_lim(bfull + 8 * s, (last[s] / TT_NSTAGE) & 1, TC_WAIT_LIMIT, nullptr, nullptr);
         __syncwarp();
     } else if (warp == TT_EPI_WARPS + 1) {
         // ---- MMA issuer ----
         if (lane == 0) {
-            const uint32_t idesc = tc_idesc_mn(128, 256);
-            uint32_t it = 0;
-            int last = -1;
-            for (int tile = blockIdx.x; tile < ntiles && !*abort_s; tile += gridDim.x) {
+            const uint32_t idesc = tt_idesc(128, 256);
+            uint32_t it = 0, gc = 0; // items, groups of up to TT_G items of one tile
+            int lastg = -1;
+            bool stop = false;
+            for (int tile = blockIdx.x; tile < ntiles && !stop && !*abort_s; tile += gridDim.x) {
                 const TtTile T = tiles[tile];
-                for (int e = T.e0; e < T.e1; ++e, ++it) {
-                    const int s = it & 1; // stage and accumulator
-                    const uint32_t ph = (it >> 1) & 1;
-                    const int lim = (it == 0 && first_limit >= 0) ? first_limit : TC_WAIT_LIMIT;
-                    if (!mbar_wait_lim(bfull + 8 * s, ph, lim, abort_s, err) ||
-                        !mbar_wait_lim(btempty + 8 * s, ph ^ 1, TC_WAIT_LIMIT, abort_s, err)) {
+                for (int g0 = T.e0; g0 < T.e1 && !stop; g0 += TT_G, ++gc) {
+                    const int g1 = min(T.e1, g0 + TT_G), ac = (int)(gc & 1);
+                    if (!mbar_wait_lim(btempty + 8 * ac, ((gc >> 1) & 1) ^ 1, TC_WAIT_LIMIT, abort_s, err)) {
                         tt_fail(abort_s, err);
+                        stop = true;
                         break;
                     }
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t a = sbase + s * TT_STAGE, b = a + TT_STAGE_TAB, d = tmem + 256u * s;
+                    const uint32_t d = tmem + 256u * ac;
+                    int issued = 0;
+                    for (int e = g0; e < g1; ++e, ++it, ++issued) {
+                        const int s = (int)(it % TT_NSTAGE);
+                        const int lim = (it == 0 && first_limit >= 0) ? first_limit : TC_WAIT_LIMIT;
+                        if (!mbar_wait_lim(bfull + 8 * s, (it / TT_NSTAGE) & 1, lim, abort_s, err)) {
+                            tt_fail(abort_s, err);
+                            stop = true;
+                            break;
+                        }
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const uint32_t a = sbase + s * TT_STAGE, b = a + TT_STAGE_TAB;
+                        // K = 16 per MMA (two 128-byte core matrices along K); the group's items
+                        // add into one accumulator
 #pragma unroll
-                    for (int kk = 0; kk < TT_K / 8; ++kk)
-                        tc_mma(d, tc_desc(a + kk * 256), tc_desc(b + kk * 256), idesc, kk > 0 ? 1u : 0u);
-                    tc_commit(bempty + 8 * s);
-                    tc_commit(btfull + 8 * s);
-                    last = (int)it;
+                        for (int kk = 0; kk < TT_K / 16; ++kk)
+                            tt_mma(d, tt_desc(a + kk * 256), tt_desc(b + kk * 256), idesc,
+                                   (e > g0 || kk > 0) ? 1u : 0u);
+                        tc_commit(bempty + 8 * s);
+                    }
+                    // (after a failed wait too: the drain below then covers every MMA issued)
+                    if (issued > 0) {
+                        tc_commit(btfull + 8 * ac);
+                        lastg = (int)gc;
+                    }
+                    if (stop) break;
                 }
             }
             // MMAs in flight complete before tensor memory is freed
-            if (last >= 0)
-                mbar_wait_lim(btfull + 8 * (last & 1), (last >> 1) & 1, TC_WAIT_LIMIT, nullptr, nullptr);
+            if (lastg >= 0)
+                mbar_wait_lim(btfull + 8 * (lastg & 1), (lastg >> 1) & 1, TC_WAIT_LIMIT, nullptr, nullptr);
         }
         __syncwarp();
     } else {
@@ -303,33 +455,41 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
         const bool rowok = r < 2 * NP;
         const int p = r < NP ? r : r - NP, reim = r < NP ? 0 : 1;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * Q) << 16) + 128u * H;
-        uint32_t it = 0;
+        uint32_t gc = 0; // groups of up to TT_G items, as the MMA issuer counts them
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const TtTile T = tiles[tile];
+            const TtLevel &lv = lvs[T.level];
+            // undoes the level's table and multipole scales (the bits k_tsplit and k_msplit read)
+            const float f = tt_pow2(-tt_scale_exp(*lv.tmax)) * tt_pow2(-tt_scale_exp(*lv.mmax));
             float acc[HB][NV];
 #pragma unroll
             for (int jj = 0; jj < HB; ++jj)
 #pragma unroll
                 for (int v = 0; v < NV; ++v) acc[jj][v] = 0.f;
             bool bad = *abort_s != 0;
-            for (int e = T.e0; e < T.e1; ++e, ++it) {
+            for (int g0 = T.e0; g0 < T.e1; g0 += TT_G, ++gc) {
                 if (bad) continue;
-                const int s = it & 1;
-                if (!mbar_wait_lim(btfull + 8 * s, (it >> 1) & 1, TC_WAIT_LIMIT, abort_s, err)) {
+                const int s = (int)(gc & 1);
+                if (!mbar_wait_lim(btfull + 8 * s, (gc >> 1) & 1, TC_WAIT_LIMIT, abort_s, err)) {
                     tt_fail(abort_s, err);
                     bad = true;
                     continue;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // two 32-column loads in flight per wait
 #pragma unroll
-                for (int ld = 0; ld < 4; ++ld) {
-                    float v[32];
-                    tc_ld32(lane_base + 256u * s + 32u * ld, v);
+                for (int ld = 0; ld < 4; ld += 2) {
+                    float v[2][32];
+                    tc_ld32x2(lane_base + 256u * s + 32u * ld, v[0], v[1]);
 #pragma unroll
-                    for (int b4 = 0; b4 < Sh::BPL; ++b4)
+                    for (int h = 0; h < 2; ++h)
 #pragma unroll
-                        for (int i = 0; i < NV; ++i)
-                            acc[ld * Sh::BPL + b4][i] += v[2 * NV * b4 + i] + v[2 * NV * b4 + NV + i];
+                        for (int b4 = 0; b4 < Sh::BPL; ++b4)
+#pragma unroll
+                            for (int k = 0; k < NV; ++k)
+                                acc[(ld + h) * Sh::BPL + b4][k] =
+                                    fmaf(v[h][2 * NV * b4 + k] + v[h][2 * NV * b4 + NV + k], f,
+                                         acc[(ld + h) * Sh::BPL + b4][k]);
                 }
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 __syncwarp();
@@ -353,7 +513,6 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
                     for (int v = 0; v < NV; ++v)
                         cb[((HB * H + jj) * NP + p) * Sh::CB_STRIDE + 2 * v + reim] += acc[jj][v];
             asm volatile("bar.sync 1, 256;" ::: "memory");
-            const TtLevel &lv = lvs[T.level];
             float *Lg = (float *)lv.L;
             const int64_t rowbase = (int64_t)T.row * lv.ncol + T.c0;
             for (int x = threadIdx.x; x < T.nbox * NP * 2 * NV; x += TT_EPI_WARPS * 32) {
@@ -382,11 +541,17 @@ __global__ void __launch_bounds__(TT_THREADS, 1)
 // NV = 4: 2 KB), in host memory
 static std::vector<TtLevel> tt_levels(const lm_tree_s *t, int nv)
 {
-    const int64_t bf = 2 * nv * TT_K;
+    const int64_t bf = nv == 16 ? TtShape<16>::BOX_FLOATS : TtShape<4>::BOX_FLOATS;
     std::vector<TtLevel> lv(t->L + 1);
     for (int l = 0; l <= t->L; ++l)
-        lv[l] = TtLevel{t->lev[l].ncol,  t->tt_mbase[l], t->lev[l].M32, t->lev[l].L32,
-                        t->tt_tab + t->tt_tbase[l] * TT_TAB_FLOATS, t->tt_msplit + t->tt_mbase[l] * bf};
+        lv[l] = TtLevel{t->lev[l].ncol,
+                        t->tt_mbase[l],
+                        t->lev[l].M32,
+                        t->lev[l].L32,
+                        t->tt_tab + t->tt_tbase[l] * TT_TAB_FLOATS,
+                        t->tt_msplit + t->tt_mbase[l] * bf,
+                        t->tt_tmax + l,
+                        t->tt_mmax + l};
     return lv;
 }
 
@@ -409,12 +574,17 @@ template <int NP, int NV>
 static void tt_msplit_launch(const lm_tree_s *t, const void *lv, cudaStream_t st)
 {
     const int64_t ntot = t->tt_mbase[t->L + 1];
-    k_msplit<NP, NV><<<(unsigned)((ntot * 16 * NV + 255) / 256), 256, 0, st>>>((const TtLevel *)lv, t->L + 1, ntot);
+    int64_t nbmax = 1;
+    for (int l = 0; l <= t->L; ++l) nbmax = std::max(nbmax, t->tt_mbase[l + 1] - t->tt_mbase[l]);
+    const int64_t nx = std::max<int64_t>(1, std::min<int64_t>((nbmax * NP * (NV / 2) + 1023) / 1024, 4096));
+    k_mmax<NP, NV><<<dim3((unsigned)nx, (unsigned)(t->L + 1)), 256, 0, st>>>((const TtLevel *)lv, t->L + 1, ntot);
+    k_msplit<NP, NV><<<(unsigned)((ntot * 8 * NV + 255) / 256), 256, 0, st>>>((const TtLevel *)lv, t->L + 1, ntot);
 }
 
 template <int NP>
 static lm_status tt_msplit(lm_tree_s *t, cudaStream_t st, int nvs)
 {
+    LM_CUDA(cudaMemsetAsync(t->tt_mmax, 0, (t->L + 1) * sizeof(uint32_t), st));
     if (nvs == LM_MAXV)
         tt_msplit_launch<NP, 16>(t, t->tt_lv[0], st);
     else
@@ -428,7 +598,7 @@ static lm_status tt_launch(lm_tree_s *t, cudaStream_t st, int nvs)
     const int f = nvs == LM_MAXV ? 0 : 1;
     const int first = t->tt_poll_limit;
     t->tt_poll_limit = -1; // a test limit applies to one launch
-    const float *zero = t->tt_msplit + t->tt_mbase[t->L + 1] * 2 * LM_MAXV * TT_K;
+    const float *zero = t->tt_msplit + t->tt_mbase[t->L + 1] * TtShape<16>::BOX_FLOATS;
     if (f == 0)
         k_m2l_tt<NP, 16><<<t->tt_grid, TT_THREADS, TtSmem<NP, 16>::BYTES, st>>>(
             (const TtTile *)t->tt_tiles[0], (int)t->tt_ntile[0], (const TtEnt *)t->tt_ents[0],
@@ -540,15 +710,20 @@ lm_status lm_setup_tt(lm_tree_s *t, cudaStream_t st)
         t->tt_tbase[l + 1] = t->tt_tbase[l] + (int64_t)t->lev[l].cls_term.size();
         t->tt_mbase[l + 1] = t->tt_mbase[l] + t->lev[l].nbox;
     }
-    const int64_t bf16 = 2 * LM_MAXV * TT_K;
+    const int64_t bf16 = TtShape<16>::BOX_FLOATS;
     TT_TRY(lm_dalloc(t, &t->tt_tab, (size_t)std::max<int64_t>(1, t->tt_tbase[L + 1]) * TT_TAB_FLOATS));
     TT_TRY(lm_dalloc(t, &t->tt_msplit, (size_t)(t->tt_mbase[L + 1] + 1) * bf16));
+    TT_TRY(lm_dalloc(t, &t->tt_tmax, (size_t)(L + 1)));
+    TT_TRY(lm_dalloc(t, &t->tt_mmax, (size_t)(L + 1)));
     LM_CUDA(cudaMemsetAsync(t->tt_msplit + t->tt_mbase[L + 1] * bf16, 0, bf16 * sizeof(float), st));
+    LM_CUDA(cudaMemsetAsync(t->tt_tmax, 0, (L + 1) * sizeof(uint32_t), st));
+    LM_CUDA(cudaMemsetAsync(t->tt_mmax, 0, (L + 1) * sizeof(uint32_t), st));
     for (int l = 0; l <= L; ++l) {
         const int ncls = (int)t->lev[l].cls_term.size();
         if (ncls == 0) continue;
-        const int64_t nt = (int64_t)ncls * 1024;
-        k_tsplit<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(t->lev[l].tab, ncls, np,
+        k_tmax<<<(unsigned)ncls, 256, 0, st>>>(t->lev[l].tab, ncls, np, t->tt_tmax + l);
+        const int64_t nt = (int64_t)ncls * 512;
+        k_tsplit<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(t->lev[l].tab, ncls, np, t->tt_tmax + l,
                                                                t->tt_tab + t->tt_tbase[l] * TT_TAB_FLOATS);
     }
     // host copies of the V lists
@@ -666,7 +841,7 @@ lm_status lm_tt_batch_build(lm_tree_s *const *trees, int count, int nvs, lm_tt_b
     b->nvs = nvs;
     b->ntile = (int64_t)tiles.size();
     b->grid = std::max(1, (int)std::min<int64_t>(nsm, b->ntile));
-    b->zero = trees[0]->tt_msplit + trees[0]->tt_mbase[trees[0]->L + 1] * 2 * LM_MAXV * TT_K;
+    b->zero = trees[0]->tt_msplit + trees[0]->tt_mbase[trees[0]->L + 1] * TtShape<16>::BOX_FLOATS;
     b->err = trees[0]->dflag + 1;
     auto up = [&](auto &v, auto **d) -> lm_status {
         using T = typename std::remove_reference<decltype(v)>::type::value_type;
@@ -727,5 +902,8 @@ void lm_free_tt(lm_tree_s *t)
     }
     if (t->tt_tab) cudaFree(t->tt_tab);
     if (t->tt_msplit) cudaFree(t->tt_msplit);
+    if (t->tt_tmax) cudaFree(t->tt_tmax);
+    if (t->tt_mmax) cudaFree(t->tt_mmax);
     t->tt_tab = t->tt_msplit = nullptr;
+    t->tt_tmax = t->tt_mmax = nullptr;
 }
