@@ -811,10 +811,11 @@ def roofline(lm, tree, phase, ms, npc, precision, dev, peaks, mhz=None):
         if precision == "fp64":
             peak, src = _probe(lm, 0, dev), "lm_peak_probe FP64 FMA chains on all SMs (measured live)"
         else:
-            # tcgen05 kind::tf32: the measured bf16 dense peak x the nominal tf32/bf16 ratio (1.1/2.25)
+            # the 16-vector tile form runs tcgen05 kind::f16 (FP16 hi/lo operands): the measured bf16
+            # dense peak (fp16 has the same dense rate)
             bf = (peaks or {}).get("bf16_tflops")
-            peak = bf * 1.1 / 2.25 if bf else 1900 * 1.1 / 2.25
-            src = "MEASURED_PEAKS bf16_tflops x 1.1/2.25 (tf32 nominal ratio)" if bf else "fallback 1.9 PF bf16 x 1.1/2.25"
+            peak = bf if bf else 1900.0
+            src = "MEASURED_PEAKS bf16_tflops (fp16 has the same dense rate)" if bf else "fallback 1.9 PF bf16"
         ach = flops / (ms * 1e-3) / 1e12
         return {"bound": "tensor" if precision != "fp64" else "alu", "kernel": "m2l", "achieved": ach,
                 "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "traffic": recorded_traffic("m2l"),
