@@ -72,8 +72,11 @@ typedef struct {
                         The FP64 target gradient (lm_apply_grad) integrates its differentiated
                         tails, which decay more slowly, with max(64, tail_order) points. */
     int tail_rays;   /* near-field tail: rays between the north and east directions; 0 -> 9 */
-    int tensor_m2l;  /* mixed path, p <= 14: free-space M2L on the tcgen05 tensor cores
-                        (TF32 hi/lo split, FP32 accumulation in tensor memory); 1 on, 0 off */
+    int tensor_m2l;  /* mixed path, p <= 14: M2L on the tcgen05 tensor cores, FP32 accumulation
+                        in tensor memory -- 16-vector applies on uniform trees: every level and
+                        image term in one launch, FP16 hi/lo operands with a power-of-two scale
+                        per level; 1-4 vectors: the free-space stencil per level, TF32 hi/lo;
+                        1 on, 0 off */
     int kernel;      /* lm_kernel: the operator the tree applies; 0 -> LM_KERNEL_G */
     int autotune;    /* LM_MIXED: run lm_autotune at the end of lm_build_tree; 0 off (default) */
     int top_bc;      /* lm_boundary of the interface y = 0; 0 -> LM_BC_TRANSMISSION (layer 1, k1) */
@@ -94,8 +97,9 @@ typedef struct {
                         relative, and several times the FP64 pipe's rate on GB300. */
     int tensor_leaf; /* LM_MIXED uniform trees, p <= 14, applies of 5-16 vectors: the leaf step's
                         multiply-adds over the vectors (direct S2T pairs and L2T) on the tcgen05
-                        tensor cores, the kernel values on the CUDA cores (TF32 hi/lo split of both
-                        factors, FP32 accumulation); 1 on (lm_options_default), 0 off */
+                        tensor cores, the kernel values on the CUDA cores (FP16 hi/lo split of both
+                        factors with power-of-two scales, FP32 accumulation); 1 on
+                        (lm_options_default), 0 off */
 } lm_options;
 
 /* Other media (Sec. 3, Examples 2 and 3): an interface of the middle layer

@@ -63,8 +63,8 @@ def test_wide_strip_mixed_sampled(case, p, depth):
 
 def test_tensor_core_m2l_matches_cuda_cores():
     """16-vector applies on the tensor cores (the tile-form tcgen05 M2L of all levels and
-    the tensor-core leaf step, TF32 hi/lo splits) against the FP32 CUDA-core kernels.
-    Both meet the mixed bar against FP64 (about 4e-7); their difference stays below
+    the tensor-core leaf step, FP16 hi/lo splits) against the FP32 CUDA-core kernels.
+    Both meet the mixed bar against FP64 (4e-7 to 5e-7); their difference stays below
     that bar too."""
     import torch
 
