@@ -368,30 +368,37 @@ template <typename TIO>
 __global__ void k_permute_in32(const TIO *q, const int64_t *iperm, int64_t n, int nvec, int conjugate, zf *qs,
                                uint32_t *qmax)
 {
-    int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n) return;
-    const int64_t i = iperm[j];
-    zf a[LM_MAXV];
+    __shared__ uint32_t red[32];
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    uint32_t m = 0;
+    if (j < n) {
+        const int64_t i = iperm[j];
+        zf a[LM_MAXV];
 #pragma unroll
-    for (int v = 0; v < LM_MAXV; ++v) {
-        a[v] = zf{0.f, 0.f};
-        if (v < nvec) {
-            const TIO b = q[(int64_t)v * n + j];
-            a[v] = zf{(float)b.re, (float)(conjugate ? -b.im : b.im)};
+        for (int v = 0; v < LM_MAXV; ++v) {
+            a[v] = zf{0.f, 0.f};
+            if (v < nvec) {
+                const TIO b = q[(int64_t)v * n + j];
+                a[v] = zf{(float)b.re, (float)(conjugate ? -b.im : b.im)};
+            }
         }
-    }
-    float4 *o = (float4 *)(qs + i * LM_MAXV);
+        float4 *o = (float4 *)(qs + i * LM_MAXV);
 #pragma unroll
-    for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
-        o[v2] = make_float4(a[2 * v2].re, a[2 * v2].im, a[2 * v2 + 1].re, a[2 * v2 + 1].im);
-    if (qmax) { // largest |component| of the densities (as bits of a non-negative float)
-        uint32_t m = 0;
+        for (int v2 = 0; v2 < LM_MAXV / 2; ++v2)
+            o[v2] = make_float4(a[2 * v2].re, a[2 * v2].im, a[2 * v2 + 1].re, a[2 * v2 + 1].im);
 #pragma unroll
         for (int v = 0; v < LM_MAXV; ++v)
             m = max(m, max(__float_as_uint(a[v].re) & 0x7fffffffu, __float_as_uint(a[v].im) & 0x7fffffffu));
-        const uint32_t act = __activemask();
-        m = __reduce_max_sync(act, m);
-        if ((threadIdx.x & 31) == __ffs(act) - 1) atomicMax(qmax, m);
+    }
+    if (qmax) { // largest |component| of the densities (as bits of a non-negative float): one atomic per block
+        m = __reduce_max_sync(0xffffffffu, m);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t mm = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = max(mm, red[w]);
+            if (mm) atomicMax(qmax, mm);
+        }
     }
 }
 // tree order -> input order: one thread per input point, one 128-byte row
@@ -979,8 +986,14 @@ __global__ void __launch_bounds__(128) k_l2l32(K par, const zf *tabs, const zf *
         }
     }
     if (lmax) { // largest |component| of the local expansions written (bits of a non-negative float)
+        __shared__ uint32_t red[4];
         m = __reduce_max_sync(0xffffffffu, m);
-        if ((threadIdx.x & 31) == 0) atomicMax(lmax, m);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t mm = max(max(red[0], red[1]), max(red[2], red[3]));
+            if (mm) atomicMax(lmax, mm);
+        }
     }
 }
 
@@ -1498,7 +1511,7 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
     const int64_t n = t->n;
     const float k = (float)t->med.k2;
     const NearQuadF nq = nqf_of(t);
-    const bool up = part != 2, down = part != 1;
+    const bool up = part != 2;
     for (int v0 = 0; v0 < nvec; v0 += LM_MAXV) {
         const int nv = std::min(LM_MAXV, nvec - v0);
         const int nvs = nv <= 4 ? 4 : LM_MAXV; // vector slots the contractions compute
@@ -1554,7 +1567,6 @@ lm_status lm_run_apply_mixed(lm_tree_s *t, const void *q, int nvec, void *u, boo
         }
         for (int l = 0; l <= L && !tiles; ++l) {
             Level &lv = t->lev[l];
-            int64_t tot = lv.nbox * np * LM_MAXV;
             lm_phase_begin(t, PH_L2L, st);
             if (l == 0)
                 LM_CUDA(cudaMemsetAsync(lv.L32, 0, lv.nbox * np * LM_MAXV * sizeof(zf), st));

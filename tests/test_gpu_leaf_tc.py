@@ -73,3 +73,24 @@ def test_tensor_leaf_few_vectors_and_off(lm):
     cc = lm.build_tree(lm.create_medium(*med, p=p, depth=depth, precision="mixed", tensor_leaf=0), xd, yd)
     q3 = torch.from_numpy(q[:3]).cuda()
     assert torch.equal(lm.apply(tc, q3), lm.apply(cc, q3))
+
+
+@pytest.mark.parametrize("e", [24, -24])
+def test_power_of_two_scaling_is_exact(lm, e):
+    """The FP16 operands of the tensor-core leaf step and of the tile-form M2L take
+    power-of-two scales from the apply's largest density, multipole and local-expansion
+    components; every other step is linear FP32 arithmetic, which a power of two passes
+    through exactly.  So the apply of 2^e q is 2^e times the apply of q, bit for bit, with
+    densities far outside FP16's range (2^24 above its largest value, or 2^-24 below 1)."""
+    import torch
+
+    x, y, q, med, p, depth = _case("strip_series")
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    t = lm.build_tree(lm.create_medium(*med, p=p, depth=depth, precision="mixed"), xd, yd)
+    assert t.info["tensor_leaf"]
+    qd = torch.from_numpy(q).cuda()
+    u1 = lm.apply(t, qd)
+    u2 = lm.apply(t, qd * 2.0**e)
+    lm.sync_status(t)
+    assert torch.isfinite(u1.real).all() and torch.isfinite(u1.imag).all()
+    assert torch.equal(u2, u1 * 2.0**e)
