@@ -239,12 +239,20 @@ __global__ void __launch_bounds__(256) k_mmax(const TtLevel *lv, int nlev, int64
     const int64_t n = nb * NP * (NV / 2);
     const zf *M = lv[l].M;
     uint32_t m = 0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t bq = t / (NV / 2); // box * NP + order
-        const int v2 = (int)(t % (NV / 2));
-        const float4 x = *(const float4 *)(M + bq * LM_MAXV + 2 * v2);
-        m = max(m, max(max(__float_as_uint(x.x) & 0x7fffffffu, __float_as_uint(x.y) & 0x7fffffffu),
-                       max(__float_as_uint(x.z) & 0x7fffffffu, __float_as_uint(x.w) & 0x7fffffffu)));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // four independent 16-byte loads in flight per thread and step
+    for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t0 < n; t0 += 4 * stride) {
+        float4 x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int64_t t = t0 + u * stride;
+            x[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (t < n) x[u] = *(const float4 *)(M + (t / (NV / 2)) * LM_MAXV + 2 * (int)(t % (NV / 2)));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            m = max(m, max(max(__float_as_uint(x[u].x) & 0x7fffffffu, __float_as_uint(x[u].y) & 0x7fffffffu),
+                           max(__float_as_uint(x[u].z) & 0x7fffffffu, __float_as_uint(x[u].w) & 0x7fffffffu)));
     }
     m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
@@ -576,7 +584,7 @@ static void tt_msplit_launch(const lm_tree_s *t, const void *lv, cudaStream_t st
     const int64_t ntot = t->tt_mbase[t->L + 1];
     int64_t nbmax = 1;
     for (int l = 0; l <= t->L; ++l) nbmax = std::max(nbmax, t->tt_mbase[l + 1] - t->tt_mbase[l]);
-    const int64_t nx = std::max<int64_t>(1, std::min<int64_t>((nbmax * NP * (NV / 2) + 1023) / 1024, 4096));
+    const int64_t nx = std::max<int64_t>(1, std::min<int64_t>((nbmax * NP * (NV / 2) + 2047) / 2048, 2048));
     k_mmax<NP, NV><<<dim3((unsigned)nx, (unsigned)(t->L + 1)), 256, 0, st>>>((const TtLevel *)lv, t->L + 1, ntot);
     k_msplit<NP, NV><<<(unsigned)((ntot * 8 * NV + 255) / 256), 256, 0, st>>>((const TtLevel *)lv, t->L + 1, ntot);
 }
